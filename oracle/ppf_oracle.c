@@ -1,0 +1,667 @@
+/*
+ * ppf_oracle.c -- plain, slow FP64 CPU reference of the SIR time step of
+ * "PPF - A Parallel Particle Filtering Library" (Demirel et al.).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load this file.  It shares no code,
+ * header, table or constant generator with the CUDA library; both sides
+ * implement the same published definitions independently.
+ *
+ * What it follows, step by step (Alg. 1, Sec. 2):
+ *   init        Alg. 1 initialisation: w = 1/N, x_0 drawn "uniformly at
+ *               random" (Sec. 7.3).
+ *   propagate   Alg. 1 SIS draw with the bootstrap proposal pi = p(x_k|x_{k-1}),
+ *               the near-constant-velocity model of Sec. 7.1.
+ *   weight      Alg. 1 weight update, likelihood eq. 4 with the appearance
+ *               model eq. 3 over the (2r+1)^2 patch S_x.
+ *   summary     Alg. 1 normalisation and effective sample size, the MMSE
+ *               estimate of Sec. 2, and the per-frame log-evidence.
+ *   quantise /  Alg. 1 resampling step (Pr[s(i)=l] = w_l), realised as
+ *   systematic  systematic resampling on 64-bit fixed-point weights.
+ *   schedule    Sec. 4: Greedy (Alg. 2), Sorted Greedy (Alg. 3) and Largest
+ *               Gradient (Alg. 4) schedulers for RPA particle routing.
+ *   resample    Sec. 3: RPA (proportional allocation) and RNA (local
+ *               resampling + ring migration).
+ *
+ * Readings of points the paper leaves open (kept identical on the CUDA side):
+ *   - dynamics (Sec. 7.1 names the model, gives no equations):
+ *       x' = x + vx + sm*e1, y' = y + vy + sm*e2, vx' = vx + sv*e3,
+ *       vy' = vy + sv*e4, I0' = I0 + sI*e5, one frame per step.
+ *   - patch S_x: a fixed (2r+1)x(2r+1) box centred on c = floor(x + 1/2);
+ *     pixels outside the image are left out of the sum.  Pixels outside S_x
+ *     are modelled as background, so the factor that eq. 4's "proportional
+ *     to" leaves out is the particle-independent whole-frame background term:
+ *       l = -sum_{S_x} [(Z - I)^2 - (Z - I_bg)^2] / (2 sigma_xi^2).
+ *     (For particles sharing an anchor this equals the literal form up to a
+ *     constant; across anchors it keeps particles that leave the image from
+ *     winning with an empty sum.)
+ *   - random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+ *     key = (seed_lo, seed_hi), counter = (index, frame, filter, purpose<<8|block);
+ *     uniform u = (2*(r>>9)+1) * 2^-24 (exact in float32); Box-Muller normals.
+ *   - resampling weights: q_i = floor(2^(s + t_i)) with t_i = (lw_i - M) log2 e,
+ *     evaluated in float32 by a fixed operation sequence (a float decides an
+ *     integer here, so the oracle takes that decision in the kernel's float32
+ *     precision), s = 63 - ceil(log2 n); ticket offset u = floor(r64 * Q / 2^64).
+ *
+ * parity pins: every function here is checked by the CPU test-suite against a
+ * closed form, a library routine, an invariant or brute force; nothing here is
+ * "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "ppf_oracle.h"
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al., SC'11: "Parallel random numbers: as easy as  */
+/* 1, 2, 3").  Round: two 32x32->64 products of counter words 0 and 2 with    */
+/* the multipliers, xor of the high halves with the other counter words and  */
+/* the key; the key is bumped by the Weyl constants between rounds.           */
+/* ------------------------------------------------------------------------ */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void orc_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void draw(uint64_t seed, uint32_t index, uint32_t frame, uint32_t filter,
+                 uint32_t purpose, uint32_t block, uint32_t out[4])
+{
+    uint32_t ctr[4] = {index, frame, filter, (purpose << 8) | block};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox(ctr, key, out);
+}
+
+double orc_u01(uint32_t r)
+{
+    /* odd multiple of 2^-24 in (0, 1): exactly representable in float32 */
+    return (double)(2u * (r >> 9) + 1u) * (1.0 / 16777216.0);
+}
+
+static void box_muller(uint32_t r1, uint32_t r2, double *z0, double *z1)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double u1 = orc_u01(r1), u2 = orc_u01(r2);
+    double rho = sqrt(-2.0 * log(u1));
+    *z0 = rho * cos(two_pi * u2);
+    *z1 = rho * sin(two_pi * u2);
+}
+
+void orc_normals5(uint64_t seed, uint32_t slot, uint32_t frame, uint32_t filter, double e[5])
+{
+    uint32_t a[4], b[4];
+    draw(seed, slot, frame, filter, ORC_PURPOSE_PROP, 0, a);
+    draw(seed, slot, frame, filter, ORC_PURPOSE_PROP, 1, b);
+    double spare;
+    box_muller(a[0], a[1], &e[0], &e[1]);
+    box_muller(a[2], a[3], &e[2], &e[3]);
+    box_muller(b[0], b[1], &e[4], &spare);
+}
+
+/* ------------------------------------------------------------------------ */
+/* S0: initialisation (Alg. 1, k = 0; particles drawn uniformly, Sec. 7.3)   */
+/* ------------------------------------------------------------------------ */
+void orc_init(const orc_model *m, int64_t N, double *st)
+{
+    double *x = st, *y = st + N, *vx = st + 2 * N, *vy = st + 3 * N, *I0 = st + 4 * N, *lw = st + 5 * N;
+    for (int64_t i = 0; i < N; ++i) {
+        uint32_t a[4], b[4];
+        draw(m->seed, (uint32_t)i, 0u, m->filter_id, ORC_PURPOSE_INIT, 0, a);
+        draw(m->seed, (uint32_t)i, 0u, m->filter_id, ORC_PURPOSE_INIT, 1, b);
+        x[i] = -0.5 + (double)m->width * orc_u01(a[0]);
+        y[i] = -0.5 + (double)m->height * orc_u01(a[1]);
+        vx[i] = m->v0_max * (2.0 * orc_u01(a[2]) - 1.0);
+        vy[i] = m->v0_max * (2.0 * orc_u01(a[3]) - 1.0);
+        I0[i] = m->amplitude * (0.5 + orc_u01(b[0]));
+        lw[i] = 0.0; /* w_0 = 1/N: equal unnormalised log-weights */
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* S1: bootstrap SIS draw (Alg. 1) with the NCV dynamics (Sec. 7.1).        */
+/* Slot i takes parent anc[i]; its noise is keyed by (slot, frame).          */
+/* The new log-weight starts at lw_prev[i] (the post-resampling weight).     */
+/* ------------------------------------------------------------------------ */
+void orc_propagate(const orc_model *m, int64_t N, int32_t frame, const double *par,
+                   const int32_t *anc, const double *lw_prev, double *st)
+{
+    const double *px = par, *py = par + N, *pvx = par + 2 * N, *pvy = par + 3 * N, *pI = par + 4 * N;
+    double *x = st, *y = st + N, *vx = st + 2 * N, *vy = st + 3 * N, *I0 = st + 4 * N, *lw = st + 5 * N;
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t a = anc[i];
+        double e[5];
+        orc_normals5(m->seed, (uint32_t)i, (uint32_t)frame, m->filter_id, e);
+        x[i] = px[a] + pvx[a] + m->sigma_m * e[0];
+        y[i] = py[a] + pvy[a] + m->sigma_m * e[1];
+        vx[i] = pvx[a] + m->sigma_v * e[2];
+        vy[i] = pvy[a] + m->sigma_v * e[3];
+        I0[i] = pI[a] + m->sigma_I * e[4];
+        lw[i] = lw_prev[i];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* S3: log-likelihood of one particle, eq. 4 with the appearance model eq. 3 */
+/* I(p) = I0 exp(-|p - (x,y)|^2 / (2 sigma^2)) + I_bg over the (2r+1)^2      */
+/* pixels around c = floor((x,y) + 1/2) that lie inside the image.  Outside  */
+/* S_x the frame is modelled as background, so eq. 4's proportionality holds */
+/* for a window that moves with the particle: the particle-independent sum   */
+/* of (Z - I_bg)^2 over the whole frame is dropped, leaving                  */
+/*   l = -sum_{S_x} [(Z - I)^2 - (Z - I_bg)^2] / (2 sigma_xi^2).             */
+/* frame: row-major H x W, values given as doubles (any storage precision   */
+/* is converted by the caller).                                              */
+/* ------------------------------------------------------------------------ */
+double orc_loglik(const orc_model *m, const double *frame, double x, double y, double I0)
+{
+    if (!isfinite(x) || !isfinite(y) || !isfinite(I0))
+        return -INFINITY;
+    const int r = m->patch_radius;
+    const double cxd = floor(x + 0.5), cyd = floor(y + 0.5);
+    /* anchors far outside the image see no pixel: empty sum */
+    if (cxd < -r - 1.0 || cxd > m->width + r || cyd < -r - 1.0 || cyd > m->height + r)
+        return 0.0;
+    const int64_t cx = (int64_t)cxd, cy = (int64_t)cyd;
+    const double two_s2 = 2.0 * m->psf_sigma * m->psf_sigma;
+    double sum = 0.0;
+    for (int64_t py = cy - r; py <= cy + r; ++py) {
+        if (py < 0 || py >= m->height)
+            continue;
+        for (int64_t px = cx - r; px <= cx + r; ++px) {
+            if (px < 0 || px >= m->width)
+                continue;
+            double d2 = ((double)px - x) * ((double)px - x) + ((double)py - y) * ((double)py - y);
+            double model = I0 * exp(-d2 / two_s2) + m->background;
+            double z = frame[py * (int64_t)m->width + px];
+            double res = z - model;          /* spot hypothesis, eq. 3 */
+            double res0 = z - m->background; /* background-only hypothesis */
+            sum += res * res - res0 * res0;
+        }
+    }
+    return -sum / (2.0 * m->sigma_xi * m->sigma_xi);
+}
+
+void orc_weight(const orc_model *m, int64_t N, const double *frame, double *st)
+{
+    const double *x = st, *y = st + N, *I0 = st + 4 * N;
+    double *lw = st + 5 * N;
+    for (int64_t i = 0; i < N; ++i)
+        lw[i] += orc_loglik(m, frame, x[i], y[i], I0[i]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* S4/S5: normalisation, N_eff, MMSE estimate, log-evidence (Alg. 1, Sec. 2) */
+/* out: mean[5], log_evidence, ess, max_lw                                    */
+/* log-evidence = log sum_i e^{lw_i} - log sum_i e^{lw_prev_i}               */
+/* ------------------------------------------------------------------------ */
+void orc_summary(int64_t N, const double *st, const double *lw_prev, double out[8])
+{
+    const double *lw = st + 5 * N;
+    double M = -INFINITY, Mp = -INFINITY;
+    for (int64_t i = 0; i < N; ++i) {
+        if (lw[i] > M) M = lw[i];
+        if (lw_prev[i] > Mp) Mp = lw_prev[i];
+    }
+    double total = 0.0, totalp = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        total += exp(lw[i] - M);
+        totalp += exp(lw_prev[i] - Mp);
+    }
+    double mean[5] = {0, 0, 0, 0, 0}, sumsq = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        double w = exp(lw[i] - M) / total;
+        for (int c = 0; c < 5; ++c)
+            mean[c] += w * st[c * N + i];
+        sumsq += w * w;
+    }
+    for (int c = 0; c < 5; ++c)
+        out[c] = mean[c];
+    out[5] = (M + log(total)) - (Mp + log(totalp));
+    out[6] = 1.0 / sumsq;
+    out[7] = M;
+}
+
+/* ------------------------------------------------------------------------ */
+/* S6: fixed-point resampling weight of one particle.                        */
+/* q = floor(p * 2^(s+k)), t = (lw - M) * log2(e) in float32, k = floor(t),   */
+/* f = t - k, p ~ 2^f by the degree-9 Taylor polynomial of e^(f ln 2)         */
+/* (coefficients (ln 2)^n / n! rounded to float32), Horner with fused         */
+/* multiply-add, all in float32.                                              */
+/* ------------------------------------------------------------------------ */
+int orc_scale_bits(int64_t n)
+{
+    int c = 0;
+    while (((int64_t)1 << c) < n)
+        ++c;
+    return 63 - c;
+}
+
+float orc_exp2_frac(float f)
+{
+    /* (ln 2)^n / n!, n = 0..9, each rounded to the nearest float32 */
+    static const float c[10] = {
+        0x1p+0f,            0x1.62e43p-1f,     0x1.ebfbep-3f,     0x1.c6b08ep-5f,
+        0x1.3b2ab6p-7f,     0x1.5d87fep-10f,   0x1.430912p-13f,   0x1.ffcbfcp-17f,
+        0x1.62c022p-20f,    0x1.b5253ep-24f,
+    };
+    float p = c[9];
+    for (int n = 8; n >= 0; --n)
+        p = fmaf(p, f, c[n]);
+    return p;
+}
+
+uint64_t orc_quantise(float lw, float M, int s)
+{
+    const float log2e = 0x1.715476p+0f; /* log2(e) rounded to float32 */
+    float d = lw - M;
+    float t = d * log2e;
+    if (!(t > -64.0f))      /* also catches NaN */
+        return 0;
+    float kf = floorf(t);
+    float f = t - kf;
+    float p = orc_exp2_frac(f);
+    int e = s + (int)kf;
+    /* p in [1, 2]: P = p * 2^23 is an exact integer */
+    uint64_t P = (uint64_t)ldexp((double)p, 23);
+    if (e < -25)
+        return 0;
+    if (e >= 23)
+        return P << (e - 23);
+    return P >> (23 - e);
+}
+
+/* ------------------------------------------------------------------------ */
+/* S7: systematic resampling on integers.                                    */
+/* With inclusive sums C_i of q and total Q, ticket j (0 <= j < n) sits at    */
+/* (u + j Q) / n and belongs to the first i with n * C_i > u + j Q.           */
+/* T(c) = #{j : u + jQ < n c} = clamp(ceil((n c - u) / Q), 0, n).             */
+/* ------------------------------------------------------------------------ */
+typedef unsigned __int128 u128;
+
+int64_t orc_tickets_below(uint64_t c, int64_t n, uint64_t u, uint64_t Q)
+{
+    u128 nc = (u128)c * (u128)(uint64_t)n;
+    if (nc <= (u128)u)
+        return 0;
+    u128 num = nc - (u128)u;
+    u128 t = (num + (u128)Q - 1) / (u128)Q;
+    if (t > (u128)(uint64_t)n)
+        t = (u128)(uint64_t)n;
+    return (int64_t)t;
+}
+
+uint64_t orc_ticket_offset(uint64_t seed, uint32_t filter, uint32_t frame, uint32_t purpose,
+                           uint32_t index, uint64_t Q)
+{
+    uint32_t r[4];
+    draw(seed, index, frame, filter, purpose, 0, r);
+    uint64_t r64 = ((uint64_t)r[1] << 32) | (uint64_t)r[0];
+    return (uint64_t)(((u128)r64 * (u128)Q) >> 64);
+}
+
+/* anc_out[j] = base + parent of ticket j, for n tickets over the n_in weights q */
+int orc_systematic(int64_t n_in, const uint64_t *q, int64_t n_tickets, uint64_t u,
+                   int64_t base, int32_t *anc_out, int64_t *offspring)
+{
+    uint64_t C = 0, Q = 0;
+    for (int64_t i = 0; i < n_in; ++i)
+        Q += q[i];
+    if (Q == 0)
+        return ORC_EDEGENERATE;
+    int64_t prev = 0;
+    for (int64_t i = 0; i < n_in; ++i) {
+        C += q[i];
+        int64_t T = orc_tickets_below(C, n_tickets, u, Q);
+        if (offspring)
+            offspring[i] = T - prev;
+        for (int64_t j = prev; j < T; ++j)
+            anc_out[j] = (int32_t)(base + i);
+        prev = T;
+    }
+    return prev == n_tickets ? ORC_OK : ORC_EINTERNAL;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4 schedulers.  count[g] = offspring of group g, target[g] = balanced */
+/* size.  Senders: count > target (surplus), receivers: count < target.      */
+/* GS (Alg. 2): senders and receivers in group order; each sender fills the  */
+/* current receiver, moving on when the receiver is full, until the sender    */
+/* is empty.  SGS (Alg. 3): both lists sorted by amount, descending (ties by  */
+/* group index), then GS.  LGS (Alg. 4): sorted as SGS, the i-th sender is    */
+/* paired with the i-th receiver for i < min(|S|,|R|), moving                 */
+/* min(surplus, deficit).                                                     */
+/* Returns the number of links written to (src, dst, cnt) in schedule order. */
+/* ------------------------------------------------------------------------ */
+typedef struct { int64_t amount; int32_t group; } orc_entry;
+
+static int entry_desc(const void *a, const void *b)
+{
+    const orc_entry *x = (const orc_entry *)a, *y = (const orc_entry *)b;
+    if (x->amount != y->amount)
+        return x->amount > y->amount ? -1 : 1;
+    return x->group < y->group ? -1 : (x->group > y->group);
+}
+
+int64_t orc_schedule(int scheme, int32_t G, const int64_t *count, const int64_t *target,
+                     int32_t *src, int32_t *dst, int64_t *cnt)
+{
+    orc_entry *S = (orc_entry *)malloc(sizeof(orc_entry) * (size_t)(G > 0 ? G : 1));
+    orc_entry *R = (orc_entry *)malloc(sizeof(orc_entry) * (size_t)(G > 0 ? G : 1));
+    int32_t nS = 0, nR = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        if (count[g] > target[g]) { S[nS].amount = count[g] - target[g]; S[nS].group = g; ++nS; }
+        if (count[g] < target[g]) { R[nR].amount = target[g] - count[g]; R[nR].group = g; ++nR; }
+    }
+    if (scheme != ORC_RPA_GS) {
+        qsort(S, (size_t)nS, sizeof(orc_entry), entry_desc);
+        qsort(R, (size_t)nR, sizeof(orc_entry), entry_desc);
+    }
+    int64_t L = 0;
+    if (scheme == ORC_RPA_LGS) {
+        int32_t C = nS < nR ? nS : nR;
+        for (int32_t i = 0; i < C; ++i) {
+            int64_t a = S[i].amount < R[i].amount ? S[i].amount : R[i].amount;
+            src[L] = S[i].group; dst[L] = R[i].group; cnt[L] = a; ++L;
+        }
+    } else {
+        int32_t j = 0;
+        for (int32_t i = 0; i < nS; ++i) {
+            int64_t left = S[i].amount;
+            while (left > 0 && j < nR) {
+                int64_t take = left < R[j].amount ? left : R[j].amount;
+                src[L] = S[i].group; dst[L] = R[j].group; cnt[L] = take; ++L;
+                left -= take;
+                R[j].amount -= take;
+                if (R[j].amount == 0)
+                    ++j;
+            }
+        }
+    }
+    free(S);
+    free(R);
+    return L;
+}
+
+/* balanced partition of N into G groups: the first N mod G get one more */
+void orc_balanced_offsets(int64_t N, int32_t G, int64_t *off)
+{
+    int64_t base = N / G, extra = N % G;
+    off[0] = 0;
+    for (int32_t g = 0; g < G; ++g)
+        off[g + 1] = off[g] + base + (g < extra ? 1 : 0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Resampling of all N particles held in the current group layout           */
+/* goff_in[0..G].  Writes the ancestor of every new slot, the new layout     */
+/* goff_out and each new slot's post-resampling log-weight lw_reset.         */
+/*   ORC_SYSTEMATIC      global systematic (Alg. 1), weights reset (lw = 0). */
+/*   ORC_RPA_GS/SGS/LGS  the same global tickets (proportional allocation,   */
+/*                       one global offset, so the ancestors do not depend on */
+/*                       G); group g keeps its first offspring, its surplus   */
+/*                       (the last ones) is routed to receivers per schedule. */
+/*   ORC_RNA             each group resamples its own slots from its own      */
+/*                       weights with its own offset; the offspring carry the */
+/*                       group weight log(W_g / n_g); then the last           */
+/*                       floor(alpha * min_g n_g) slots of group g move to     */
+/*                       group g+1 (ring).                                    */
+/* lw: float32 log-weights (the value the quantiser sees).                   */
+/* lw_sum: per-particle log-weights used for the RNA group weights (FP64).   */
+/* stats: links, moved, max group size, min group size.                      */
+/* ------------------------------------------------------------------------ */
+int orc_resample(const orc_model *m, int scheme, double alpha, int64_t N, int32_t frame,
+                 int32_t G, const int64_t *goff_in, const float *lw, const double *lw_sum,
+                 int32_t *anc, double *lw_reset, int64_t *goff_out, int64_t stats[4])
+{
+    int rc = ORC_OK;
+    stats[0] = stats[1] = 0;
+    if (scheme == ORC_RNA) {
+        int64_t minsz = INT64_MAX, maxsz = 0;
+        for (int32_t g = 0; g < G; ++g) {
+            int64_t sz = goff_in[g + 1] - goff_in[g];
+            if (sz < minsz) minsz = sz;
+            if (sz > maxsz) maxsz = sz;
+        }
+        int64_t mig = (int64_t)floor(alpha * (double)minsz);
+        /* group log-weights log W_g = log sum_g e^lw - log sum e^lw, in FP64 */
+        double Mall = -INFINITY;
+        for (int64_t i = 0; i < N; ++i)
+            if (lw_sum[i] > Mall) Mall = lw_sum[i];
+        double tot = 0.0;
+        for (int64_t i = 0; i < N; ++i)
+            tot += exp(lw_sum[i] - Mall);
+        const double log_tot = Mall + log(tot);
+        int32_t *local = (int32_t *)malloc(sizeof(int32_t) * (size_t)(maxsz > 0 ? maxsz : 1));
+        uint64_t *q = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(maxsz > 0 ? maxsz : 1));
+        for (int32_t g = 0; g < G; ++g) {
+            int64_t lo = goff_in[g], sz = goff_in[g + 1] - lo;
+            if (sz == 0)
+                continue;
+            float Mg = -INFINITY;
+            double Mgd = -INFINITY;
+            for (int64_t i = 0; i < sz; ++i) {
+                if (lw[lo + i] > Mg) Mg = lw[lo + i];
+                if (lw_sum[lo + i] > Mgd) Mgd = lw_sum[lo + i];
+            }
+            int s = orc_scale_bits(sz);
+            uint64_t Q = 0;
+            for (int64_t i = 0; i < sz; ++i) {
+                q[i] = orc_quantise(lw[lo + i], Mg, s);
+                Q += q[i];
+            }
+            double lwg;
+            if (Q == 0) {
+                /* every weight of the group is zero: it keeps its slots */
+                for (int64_t i = 0; i < sz; ++i)
+                    local[i] = (int32_t)(lo + i);
+                lwg = -INFINITY;
+            } else {
+                uint64_t u = orc_ticket_offset(m->seed, m->filter_id, (uint32_t)frame,
+                                               ORC_PURPOSE_GROUP_RESAMPLE, (uint32_t)g, Q);
+                int r2 = orc_systematic(sz, q, sz, u, lo, local, NULL);
+                if (r2 != ORC_OK) { rc = r2; break; }
+                double sg = 0.0;
+                for (int64_t i = 0; i < sz; ++i)
+                    sg += exp(lw_sum[lo + i] - Mgd);
+                lwg = (Mgd + log(sg)) - log_tot - log((double)sz);
+            }
+            int32_t gn = (g + 1) % G;
+            int64_t gn_lo = goff_in[gn], gn_sz = goff_in[gn + 1] - gn_lo;
+            for (int64_t s2 = 0; s2 < sz; ++s2) {
+                int64_t slot;
+                if (s2 < sz - mig)
+                    slot = lo + s2;
+                else
+                    slot = gn_lo + gn_sz - mig + (s2 - (sz - mig));
+                anc[slot] = local[s2];
+                lw_reset[slot] = lwg;
+            }
+        }
+        free(local);
+        free(q);
+        for (int32_t g = 0; g <= G; ++g)
+            goff_out[g] = goff_in[g];
+        stats[0] = G > 1 ? G : 0;
+        stats[1] = G > 1 ? mig * G : 0;
+        stats[2] = maxsz;
+        stats[3] = minsz;
+        return rc;
+    }
+
+    /* global systematic tickets */
+    float M = -INFINITY;
+    for (int64_t i = 0; i < N; ++i)
+        if (lw[i] > M) M = lw[i];
+    int s = orc_scale_bits(N);
+    uint64_t *q = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)N);
+    uint64_t Q = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        q[i] = orc_quantise(lw[i], M, s);
+        Q += q[i];
+    }
+    if (Q == 0) {
+        /* no usable weight at all: keep every particle and its weight */
+        for (int64_t i = 0; i < N; ++i) {
+            anc[i] = (int32_t)i;
+            lw_reset[i] = lw_sum[i];
+        }
+        for (int32_t g = 0; g <= G; ++g)
+            goff_out[g] = goff_in[g];
+        free(q);
+        return ORC_EDEGENERATE;
+    }
+    uint64_t u = orc_ticket_offset(m->seed, m->filter_id, (uint32_t)frame, ORC_PURPOSE_RESAMPLE, 0u, Q);
+    int32_t *sys = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    rc = orc_systematic(N, q, N, u, 0, sys, NULL);
+    if (rc != ORC_OK || scheme == ORC_SYSTEMATIC) {
+        if (rc == ORC_OK) {
+            memcpy(anc, sys, sizeof(int32_t) * (size_t)N);
+            for (int64_t i = 0; i < N; ++i)
+                lw_reset[i] = 0.0;
+            for (int32_t g = 0; g <= G; ++g)
+                goff_out[g] = goff_in[g];
+            int64_t mx = 0, mn = INT64_MAX;
+            for (int32_t g = 0; g < G; ++g) {
+                int64_t sz = goff_in[g + 1] - goff_in[g];
+                if (sz > mx) mx = sz;
+                if (sz < mn) mn = sz;
+            }
+            stats[2] = mx;
+            stats[3] = mn;
+        }
+        free(q);
+        free(sys);
+        return rc;
+    }
+
+    /* RPA: offspring per group = tickets inside the group's cumulative range */
+    int64_t *T = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G + 1));
+    int64_t *cnt_g = (int64_t *)malloc(sizeof(int64_t) * (size_t)G);
+    int64_t *tgt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G + 1));
+    uint64_t C = 0;
+    T[0] = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        for (int64_t i = goff_in[g]; i < goff_in[g + 1]; ++i)
+            C += q[i];
+        T[g + 1] = orc_tickets_below(C, N, u, Q);
+        cnt_g[g] = T[g + 1] - T[g];
+    }
+    orc_balanced_offsets(N, G, tgt);
+    int64_t *target = (int64_t *)malloc(sizeof(int64_t) * (size_t)G);
+    for (int32_t g = 0; g < G; ++g)
+        target[g] = tgt[g + 1] - tgt[g];
+    int32_t *lsrc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * G + 1));
+    int32_t *ldst = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * G + 1));
+    int64_t *lcnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * G + 1));
+    int64_t L = orc_schedule(scheme, G, cnt_g, target, lsrc, ldst, lcnt);
+    int64_t *sent = (int64_t *)calloc((size_t)G, sizeof(int64_t));
+    int64_t *recv = (int64_t *)calloc((size_t)G, sizeof(int64_t));
+    int64_t moved = 0;
+    for (int64_t l = 0; l < L; ++l) {
+        sent[lsrc[l]] += lcnt[l];
+        recv[ldst[l]] += lcnt[l];
+        moved += lcnt[l];
+    }
+    /* new layout */
+    goff_out[0] = 0;
+    for (int32_t g = 0; g < G; ++g)
+        goff_out[g + 1] = goff_out[g] + cnt_g[g] - sent[g] + recv[g];
+    /* kept offspring: the first cnt_g - sent tickets of the group */
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)G);
+    int64_t *sendpos = (int64_t *)malloc(sizeof(int64_t) * (size_t)G);
+    for (int32_t g = 0; g < G; ++g) {
+        int64_t keep = cnt_g[g] - sent[g];
+        for (int64_t t = 0; t < keep; ++t)
+            anc[goff_out[g] + t] = sys[T[g] + t];
+        fill[g] = keep;
+        sendpos[g] = T[g] + keep; /* the surplus tickets follow the kept ones */
+    }
+    /* routed offspring, in schedule order */
+    for (int64_t l = 0; l < L; ++l) {
+        int32_t a = lsrc[l], b = ldst[l];
+        for (int64_t t = 0; t < lcnt[l]; ++t)
+            anc[goff_out[b] + fill[b] + t] = sys[sendpos[a] + t];
+        fill[b] += lcnt[l];
+        sendpos[a] += lcnt[l];
+    }
+    for (int64_t i = 0; i < N; ++i)
+        lw_reset[i] = 0.0;
+    int64_t mx = 0, mn = INT64_MAX;
+    for (int32_t g = 0; g < G; ++g) {
+        int64_t sz = goff_out[g + 1] - goff_out[g];
+        if (sz > mx) mx = sz;
+        if (sz < mn) mn = sz;
+    }
+    stats[0] = L;
+    stats[1] = moved;
+    stats[2] = mx;
+    stats[3] = mn;
+    free(T); free(cnt_g); free(tgt); free(target); free(lsrc); free(ldst); free(lcnt);
+    free(sent); free(recv); free(fill); free(sendpos); free(q); free(sys);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* A whole SIR run (Alg. 1): init, then for each frame propagate, weight,    */
+/* summarise, resample.  frames: K x H x W doubles.  est: K x 8 (mean[5],    */
+/* log-evidence, ess, max lw).  st (6N) holds the last weighted particles.   */
+/* ------------------------------------------------------------------------ */
+int orc_run(const orc_model *m, int64_t N, int32_t group_size, int scheme, double alpha,
+            int32_t K, const double *frames, double *est, double *st_out)
+{
+    int32_t G = (int32_t)((N + group_size - 1) / group_size);
+    double *cur = (double *)malloc(sizeof(double) * (size_t)(6 * N));
+    double *nxt = (double *)malloc(sizeof(double) * (size_t)(6 * N));
+    double *lw_prev = (double *)malloc(sizeof(double) * (size_t)N);
+    float *lwf = (float *)malloc(sizeof(float) * (size_t)N);
+    int32_t *anc = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int64_t *goff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G + 1));
+    int64_t *goff2 = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G + 1));
+    int rc = ORC_OK;
+    orc_init(m, N, cur);
+    orc_balanced_offsets(N, G, goff);
+    for (int64_t i = 0; i < N; ++i) {
+        anc[i] = (int32_t)i;
+        lw_prev[i] = cur[5 * N + i];
+    }
+    const int64_t npix = (int64_t)m->width * m->height;
+    for (int32_t k = 0; k < K; ++k) {
+        orc_propagate(m, N, k + 1, cur, anc, lw_prev, nxt);
+        orc_weight(m, N, frames + (int64_t)k * npix, nxt);
+        orc_summary(N, nxt, lw_prev, est + 8 * (int64_t)k);
+        for (int64_t i = 0; i < N; ++i)
+            lwf[i] = (float)nxt[5 * N + i];
+        int64_t stats[4];
+        rc = orc_resample(m, scheme, alpha, N, k + 1, G, goff, lwf, nxt + 5 * N, anc, lw_prev, goff2, stats);
+        if (rc != ORC_OK)
+            break;
+        memcpy(goff, goff2, sizeof(int64_t) * (size_t)(G + 1));
+        double *t = cur; cur = nxt; nxt = t;
+    }
+    if (st_out)
+        memcpy(st_out, cur, sizeof(double) * (size_t)(6 * N));
+    free(cur); free(nxt); free(lw_prev); free(lwf); free(anc); free(goff); free(goff2);
+    return rc;
+}

@@ -1,0 +1,85 @@
+"""Whole-filter pin: the oracle's SIR recursion (Alg. 1: propagate, weight,
+normalise/estimate, systematic resampling) on a linear-Gaussian variant of the
+tracking model -- NCV dynamics of Sec. 7.1, position observed with Gaussian
+noise, Gaussian prior -- against the Kalman filter, whose posterior mean and
+predictive density are the exact answer (Kalman 1960).  The PSF likelihood is
+pinned separately; here the weight is the linear-Gaussian one.
+
+Monte Carlo error: 20 runs with independent random streams (the paper repeats
+each test 20 times, Sec. 7.3); the seed-mean of every posterior-mean component
+and of the log-evidence must lie within 4 standard errors of the closed form,
+the standard error taken from the spread across the 20 runs."""
+import math
+
+import numpy as np
+import pytest
+
+
+def kalman_axis(z, m0, P0, sm, sv, sz):
+    F = np.array([[1.0, 1.0], [0.0, 1.0]])
+    Qn = np.diag([sm * sm, sv * sv])
+    m, P = np.array(m0, float), np.array(P0, float)
+    means, logp = [], []
+    for zk in z:
+        m = F @ m
+        P = F @ P @ F.T + Qn
+        S = P[0, 0] + sz * sz
+        logp.append(-0.5 * (math.log(2 * math.pi * S) + (zk - m[0]) ** 2 / S))
+        K = P[:, 0] / S
+        m = m + K * (zk - m[0])
+        P = P - np.outer(K, K) * S
+        means.append(m.copy())
+    return np.array(means), np.array(logp)
+
+
+def run_sir(orc, seed, zs, prior_m, prior_s, sm, sv, sI, sz, N):
+    m = orc.Model(seed=seed, sigma_m=sm, sigma_v=sv, sigma_I=sI)
+    rng = np.random.default_rng(seed)
+    st = np.zeros((6, N))
+    st[:5] = prior_m[:, None] + prior_s[:, None] * rng.normal(size=(5, N))
+    anc = np.arange(N, dtype=np.int32)
+    lw_prev = np.zeros(N)
+    goff = orc.balanced_offsets(N, 4)
+    means, ev = [], []
+    for k in range(zs.shape[0]):
+        st = orc.propagate(m, k + 1, st, anc, lw_prev)
+        st[5] += -((st[0] - zs[k, 0]) ** 2 + (st[1] - zs[k, 1]) ** 2) / (2 * sz * sz)
+        s = orc.summary(st, lw_prev)
+        means.append(s["mean"])
+        # the weight leaves out the Gaussian normalising constant -log(2 pi sz^2)
+        ev.append(s["log_evidence"] - math.log(2 * math.pi * sz * sz))
+        rc, anc, lw_prev, goff, _ = orc.resample(m, orc.SYSTEMATIC, N, k + 1, goff,
+                                                 st[5].astype(np.float32), st[5])
+        assert rc == 0
+    return np.array(means), np.array(ev)
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_sir_matches_kalman(orc, case):
+    rng = np.random.default_rng(100 + case)
+    N, K, R = 1 << 14, 12, 20
+    sm, sv, sI, sz = 0.5, 0.15, 0.8, 0.7
+    prior_m = np.array([40.0, 30.0, 0.5, -0.3, 25.0])
+    prior_s = np.array([2.0, 1.5, 0.4, 0.3, 2.0])
+    t = rng.normal(prior_m, prior_s)
+    zs = []
+    for _ in range(K):
+        e = rng.normal(size=4)
+        t = np.array([t[0] + t[2] + sm * e[0], t[1] + t[3] + sm * e[1],
+                      t[2] + sv * e[2], t[3] + sv * e[3], t[4]])
+        zs.append(t[:2] + sz * rng.normal(size=2))
+    zs = np.array(zs)
+    kx = kalman_axis(zs[:, 0], [prior_m[0], prior_m[2]], np.diag([prior_s[0] ** 2, prior_s[2] ** 2]), sm, sv, sz)
+    ky = kalman_axis(zs[:, 1], [prior_m[1], prior_m[3]], np.diag([prior_s[1] ** 2, prior_s[3] ** 2]), sm, sv, sz)
+    want = np.stack([kx[0][:, 0], ky[0][:, 0], kx[0][:, 1], ky[0][:, 1], np.full(K, prior_m[4])], axis=1)
+    want_ev = kx[1] + ky[1]
+    runs = [run_sir(orc, 1000 * case + s, zs, prior_m, prior_s, sm, sv, sI, sz, N) for s in range(R)]
+    M = np.array([r[0] for r in runs])       # (R, K, 5)
+    E = np.array([r[1] for r in runs])       # (R, K)
+    se = M.std(axis=0, ddof=1) / math.sqrt(R)
+    z = np.abs(M.mean(axis=0) - want) / se
+    assert z.max() < 4.0, np.round(z, 2)
+    se_ev = E.std(axis=0, ddof=1) / math.sqrt(R)
+    zev = np.abs(E.mean(axis=0) - want_ev) / se_ev
+    assert zev.max() < 4.0, np.round(zev, 2)
+    assert np.max(np.abs(E.mean(axis=0) - want_ev)) < 0.02
