@@ -1,0 +1,313 @@
+#!/usr/bin/env python3
+"""Throughput of the SIR time step (Alg. 1) for single-spot tracking on GB300.
+
+Workload (the paper-scale plain SIR): N = 38,000,000 particles, state 6 x
+float32 SoA, 512 x 512 float32 Poisson frames with one Gaussian-PSF spot
+(sigma_PSF ~ U[1.2, 2.0], SNR ~ U[2, 8], seeded), 11 x 11 patch, groups of
+4096 particles, resampling every frame.  One step = one frame: propagate,
+likelihood, normalise + estimate, resample.  value = particle-steps / s over
+all ranks; frames are resident in HBM before the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SIR particle-steps/sec at N=38M vs plain FP32; % of roofline; grad steps/sec"
+UNIT = "particle-steps/s"
+N_FULL = 38_000_000
+GROUP = 4096
+W = H = 512
+R = 5
+# algorithmic HBM bytes per particle of the fused step kernel after a global
+# resample: ancestor 4 + gathered parent x, y, vx, vy, I0 20 + written state 24
+STEP_BYTES = 48
+
+
+def workload_desc(n, scheme):
+    return {
+        "workload": f"spot512: {W}x{H} float32 Poisson frames, one Gaussian-PSF spot, N={n:,} particles, "
+                    f"{2 * R + 1}x{2 * R + 1} patch, groups of {GROUP}, {scheme} resampling every frame",
+        "N": n, "frame": f"{W}x{H}", "patch": 2 * R + 1, "group_size": GROUP, "scheme": scheme,
+        "state": "6 x float32 SoA (x, y, vx, vy, I0, lw), double-buffered",
+        "l2": "inputs larger than L2: 1.8 GB of particle state per frame (no flush needed)",
+    }
+
+
+def make_workload(k_total, seed=0):
+    import synth
+    mv, p = synth.preset("spot512_k50", seed=seed, K=k_total)
+    params = dict(width=W, height=H, patch_radius=R, psf_sigma=float(p["sigma"]),
+                  amplitude=float(p["amplitude"]), background=10.0, sigma_xi=math.sqrt(10.0),
+                  sigma_m=0.5, sigma_v=0.1, sigma_I=1.0, v0_max=1.0)
+    return mv, params
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0, period_ms=100):
+        self.rows = []
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-i", str(device_index), "-lms", str(period_ms)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.t.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle legs
+def oracle_rate(params, frames, n, k, seed=0):
+    """The FP64 oracle as it stands (single thread) on n particles x k frames."""
+    import oracle as orc
+    m = orc.Model(**{**params, "seed": seed})
+    t0 = time.perf_counter()
+    rc, est, _ = orc.run(m, n, frames[:k], group_size=GROUP, scheme=orc.SYSTEMATIC)
+    dt = time.perf_counter() - t0
+    return n * k / dt, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as orc
+    n = args.ref_n
+    mv, params = make_workload(args.warmup + args.steps + 1)
+    m = orc.Model(**{**params, "seed": 0})
+    st = orc.init(m, n)
+    anc = np.arange(n, dtype=np.int32)
+    lw_prev = np.zeros(n)
+    goff = orc.balanced_offsets(n, (n + GROUP - 1) // GROUP)
+    times = []
+    for k in range(1, args.warmup + args.steps + 1):
+        t0 = time.perf_counter()
+        nxt = orc.propagate(m, k, st, anc, lw_prev)
+        nxt = orc.weight(m, mv.frames[k - 1], nxt)
+        orc.summary(nxt, lw_prev)
+        rc, anc, lw_prev, goff, _ = orc.resample(m, orc.SYSTEMATIC, n, k, goff, nxt[5].astype(np.float32), nxt[5])
+        st = nxt
+        if k > args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n * args.steps / total
+    sample = f"{n} particles of the same workload per step (one frame each), FP64, single thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_desc(N_FULL, "systematic"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- ours
+def timed_frames(pf, frames, k0, K, scheme, alpha, stream):
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(k0, k0 + K):
+        pf.step(frames[k - 1], k)
+        pf.resample(scheme, alpha)
+    ev1.record(stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def run_ours(args):
+    import torch
+    import paper_1310_5045_gb300 as ppf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = args.n
+    K, Wm = args.steps, args.warmup
+    extra = 0 if args.no_schemes else 5 * (args.scheme_steps + 2)
+    k_total = Wm + K + extra + (args.e2e_steps if not args.no_e2e else 0) + 2
+    mv, params = make_workload(k_total, seed=0)
+    model = ppf.Model(**params, seed=rank, filter_id=rank)
+    frames = torch.from_numpy(mv.frames).to(dev)
+    stream = torch.cuda.current_stream()
+    pf = ppf.ParticleFilter(model, n, group_size=GROUP, stream=stream)
+    scheme = ppf.SCHEMES[args.scheme]
+    for k in range(1, Wm + 1):
+        pf.step(frames[k - 1], k)
+        pf.resample(scheme, args.alpha)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    pf.profile_enable(True, capacity=K + 8)
+    clocks = ClockSampler(torch.cuda.current_device())
+    t_ms = timed_frames(pf, frames, Wm + 1, K, scheme, args.alpha, stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+        t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    prof = pf.profile_read()
+    est = pf.estimate()
+    kdone = Wm + K
+    value = n * K * world / (t_ms / 1e3)
+
+    step_ms = prof["step_ms"] / max(1, prof["timed_steps"])
+    achieved = STEP_BYTES * n / (step_ms / 1e3) / 1e9
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "hbm", "kernel": "step_kernel<5> (propagate + likelihood + weight partials)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "bytes_per_particle": STEP_BYTES, "step_kernel_ms": step_ms,
+                "traffic": None,
+                "phase_ms_per_step": {kk: prof[kk] / max(1, prof["timed_steps"]) for kk in
+                                      ("prepare_ms", "step_ms", "finalize_ms", "resample_ms")}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+            "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded Poisson spot movie, random-init particles)",
+            "config": workload_desc(n, args.scheme), "roofline": roofline, "clocks": clk,
+            "gpu_launches": int(prof["launches"]),
+            "last_estimate": {"mean": est.mean, "ess": est.ess, "log_evidence": est.log_evidence,
+                              "truth": mv.truth[kdone - 1].tolist()}}
+
+    # every allocation / routing scheme of Sec. 3-4 on the same workload
+    if not args.no_schemes:
+        sch = {}
+        k = kdone + 1
+        for name, alpha in [("rpa_gs", 0.0), ("rpa_sgs", 0.0), ("rpa_lgs", 0.0), ("rna", 0.1), ("rna", 0.5),
+                            ("systematic", 0.0)]:
+            sid = ppf.SCHEMES[name]
+            for _ in range(2):
+                pf.step(frames[k - 1], k)
+                pf.resample(sid, alpha)
+                k += 1
+            tm = timed_frames(pf, frames, k, args.scheme_steps, sid, alpha, stream)
+            k += args.scheme_steps
+            e = pf.estimate()
+            key = name if name != "rna" else f"rna_{alpha}"
+            sch[key] = {"value": n * args.scheme_steps / (tm / 1e3), "ms_per_step": tm / args.scheme_steps,
+                        "links": e.links, "moved": e.moved, "max_group": e.max_group, "min_group": e.min_group}
+        line["schemes"] = sch
+        kdone = k - 1
+
+    # end to end through the C ABI with host frames (pinned), estimate read back
+    if not args.no_e2e:
+        ke = args.e2e_steps
+        host = torch.from_numpy(mv.frames[kdone:kdone + ke]).pin_memory()
+        torch.cuda.synchronize()
+        pf.profile_enable(True, capacity=ke + 8)
+        t0 = time.perf_counter()
+        for i in range(ke):
+            pf.step_host(host[i], kdone + 1 + i)
+            pf.resample(scheme, args.alpha)
+            pf.estimate()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        pr = pf.profile_read()
+        line["e2e"] = {"value": n * ke * world / dt, "unit": UNIT, "steps": ke,
+                       "h2d_bytes_per_step": pr["h2d_bytes"] // ke, "d2h_bytes_per_step": pr["d2h_bytes"] // ke,
+                       "timing": "host wall clock around step_host + resample + estimate (sync) per frame"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cn, ck = args.cpu_n, args.cpu_frames
+        rate, dt = oracle_rate(params, mv.frames, cn, ck)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 C oracle, single thread, {cn} particles x {ck} frames of the "
+                                          f"same workload ({dt:.1f} s)"}
+    pf.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_FULL)
+    ap.add_argument("--scheme", default="systematic", choices=sorted(["systematic", "rpa_gs", "rpa_sgs",
+                                                                      "rpa_lgs", "rna"]))
+    ap.add_argument("--alpha", type=float, default=0.1)
+    ap.add_argument("--scheme-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--cpu-n", type=int, default=1 << 20)
+    ap.add_argument("--cpu-frames", type=int, default=3)
+    ap.add_argument("--ref-n", type=int, default=1 << 17)
+    ap.add_argument("--no-schemes", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

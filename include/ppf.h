@@ -1,0 +1,196 @@
+/*
+ * ppf.h -- C ABI of the GB300 SIR particle filter for single-spot tracking
+ * ("PPF - A Parallel Particle Filtering Library", Demirel et al.).
+ *
+ * One context = one particle filter of N particles on the current CUDA
+ * device.  The library owns every particle buffer (allocated in ppf_create);
+ * frames are caller-owned.  Every call returns a ppf_status; nothing throws
+ * across the ABI.  Unless stated otherwise a call only enqueues work on the
+ * context's stream and returns at once; device-side failures found by the
+ * kernels are reported by the next synchronising call (ppf_estimate).
+ *
+ * Layouts:
+ *   frame      row-major H x W (pixel (i, j) = column i <-> x, row j <-> y,
+ *              centres at integer coordinates), element type model.frame_dtype.
+ *   state      structure of arrays, 6 x N float32: x, y, vx, vy, I0, lw
+ *              (lw = unnormalised log-weight).
+ *   ancestors  N int32: slot i of the next propagation takes particle anc[i].
+ */
+#ifndef PPF_H
+#define PPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PPF_OK = 0,
+    PPF_EINVAL = 1,      /* bad argument (size, radius, pointer, scheme)        */
+    PPF_ENOMEM = 2,      /* device or host allocation failed                    */
+    PPF_ECUDA = 3,       /* a CUDA runtime call failed (see ppf_last_error)      */
+    PPF_ETIMEOUT = 4,    /* a bounded device-side wait gave up                  */
+    PPF_EDEGENERATE = 5, /* every weight was zero or NaN: nothing was resampled */
+    PPF_ESTATE = 6       /* call out of order (e.g. resample before a step)     */
+} ppf_status;
+
+/* Resampling schemes (Alg. 1 resampling step; Sec. 3; Sec. 4). */
+typedef enum {
+    PPF_SYSTEMATIC = 0, /* global systematic resampling                        */
+    PPF_RPA_GS = 1,     /* proportional allocation + Greedy Scheduler (Alg. 2)  */
+    PPF_RPA_SGS = 2,    /* proportional allocation + Sorted Greedy (Alg. 3)     */
+    PPF_RPA_LGS = 3,    /* proportional allocation + Largest Gradient (Alg. 4)  */
+    PPF_RNA = 4         /* non-proportional allocation + ring migration (Sec. 3)*/
+} ppf_scheme;
+
+typedef enum { PPF_F32 = 0, PPF_BF16 = 1, PPF_F16 = 2 } ppf_dtype;
+
+/* Model of Sec. 7: NCV dynamics (7.1), Gaussian-PSF appearance eq. 3 and
+ * patch likelihood eq. 4 (7.2).  All lengths in pixels, per frame. */
+typedef struct {
+    int32_t width, height;    /* frame size W, H                                 */
+    int32_t patch_radius;     /* r: S_x is the (2r+1)^2 box around the particle, 0..8 */
+    int32_t frame_dtype;      /* ppf_dtype of the frames given to ppf_step       */
+    float psf_sigma;          /* sigma_PSF of eq. 3                              */
+    float amplitude;          /* prior scale of I0: I0 ~ U[A/2, 3A/2]            */
+    float background;         /* I_bg of eq. 3                                   */
+    float sigma_xi;           /* sigma_xi of eq. 4                               */
+    float sigma_m;            /* position noise std                              */
+    float sigma_v;            /* velocity noise std                              */
+    float sigma_I;            /* intensity noise std                             */
+    float v0_max;             /* prior velocity range: v ~ U[-v0, v0]            */
+    uint64_t seed;            /* Philox key                                      */
+    uint32_t filter_id;       /* Philox counter word 2 (independent filters)     */
+    uint32_t reserved;
+} ppf_model;
+
+/* Per-frame results (Alg. 1 normalisation / N_eff; MMSE estimate of Sec. 2). */
+typedef struct {
+    double mean[5];           /* posterior mean of x, y, vx, vy, I0 (before resampling) */
+    double log_evidence;      /* log sum e^lw - log sum e^lw_prev (eq. 4 scale)  */
+    double ess;               /* 1 / sum w_i^2                                   */
+    double max_log_weight;    /* max_i lw_i                                      */
+    int32_t frame;            /* frame index of the last ppf_step                */
+    int32_t status_flags;     /* bit 0 degenerate weights, 1 wait timeout,
+                                 2 inconsistent routing (copy skipped),
+                                 3 caller ancestor out of range (identity used) */
+    int64_t links;            /* routing links of the last resample (Sec. 4-5)   */
+    int64_t moved;            /* particles moved between groups by that resample */
+    int64_t max_group;        /* largest / smallest group after it               */
+    int64_t min_group;
+} ppf_estimate_t;
+
+typedef struct ppf_ctx ppf_ctx;
+
+/* Alg. 1 initialisation (k = 0): allocates the context and draws N particles
+ * uniformly (Sec. 7.3): x, y ~ U[-1/2, W-1/2) x U[-1/2, H-1/2),
+ * v ~ U[-v0, v0]^2, I0 ~ U[A/2, 3A/2], equal weights.
+ *   model       host pointer, copied.
+ *   n           1 <= n <= 2^31 - 1 particles.
+ *   group_size  particles per group (the paper's process, Sec. 3); the groups
+ *               are a balanced partition of the N slots, ceil(N/group_size)
+ *               of them; 1 <= group_size <= n.
+ *   cuda_stream cudaStream_t to enqueue on (NULL = legacy default stream).
+ *   out         receives the context; untouched on error.
+ * Errors: PPF_EINVAL (sizes, radius > 8, non-positive sigma_PSF / sigma_xi,
+ * unknown dtype), PPF_ENOMEM, PPF_ECUDA. */
+ppf_status ppf_create(const ppf_model *model, int64_t n, int32_t group_size,
+                      void *cuda_stream, ppf_ctx **out);
+
+/* Frees every buffer of the context (synchronises its stream).  NULL is a no-op. */
+void ppf_destroy(ppf_ctx *ctx);
+
+/* One SIS step of Alg. 1 for frame k: every slot draws its particle from the
+ * dynamics applied to its ancestor (bootstrap proposal), is weighted by the
+ * patch likelihood eq. 4, and the weights are normalised (log-sum-exp with an
+ * FP64 cross-group total), giving the estimate, N_eff and log-evidence.
+ *   frame_dev   device pointer, H x W of model.frame_dtype; must stay valid
+ *               until the stream has run the step.
+ *   k           frame index (counter word of the random stream), k >= 1.
+ * A step that follows another step without ppf_resample keeps the weights
+ * (pure SIS).  Errors: PPF_EINVAL (NULL frame, k < 1), PPF_ECUDA. */
+ppf_status ppf_step(ppf_ctx *ctx, const void *frame_dev, int32_t k);
+
+/* ppf_step for a frame in host memory: the frame is copied into a
+ * library-owned device buffer on the context's stream first (pinned memory
+ * makes that copy asynchronous). */
+ppf_status ppf_step_host(ppf_ctx *ctx, const void *frame_host, int32_t k);
+
+/* The resampling step of Alg. 1 on the weights of the last step, using the
+ * scheme's allocation (Sec. 3) and, for RPA, the scheme's routing schedule
+ * (Sec. 4).  exchange_ratio: RNA only, the fraction alpha of the smallest
+ * group that migrates to the next group of the ring (0 <= alpha <= 1).
+ * Systematic and RPA reset the weights to equal; RNA gives every offspring
+ * its group's weight / group size.  LGS may leave the groups unequal.
+ * Errors: PPF_ESTATE (no step since the last resample), PPF_EINVAL, PPF_ECUDA.
+ * All-zero or NaN weights are reported as PPF_EDEGENERATE by the next
+ * ppf_estimate; the particles are then kept as they are. */
+ppf_status ppf_resample(ppf_ctx *ctx, ppf_scheme scheme, float exchange_ratio);
+
+/* Copies the results of the last step and of the last resample to the host
+ * (synchronises the stream).  Returns PPF_EDEGENERATE / PPF_ETIMEOUT when the
+ * device flagged such a condition since the previous call, PPF_EINVAL when it
+ * found a caller-supplied ancestor out of range or an inconsistent routing
+ * schedule (the values are still filled in; the flags are then cleared), and
+ * PPF_ESTATE before the first step. */
+ppf_status ppf_estimate(ppf_ctx *ctx, ppf_estimate_t *out);
+
+/* Copies the current particles (those of the last step, or the initial ones)
+ * into caller-owned device buffers, each optional (NULL = skip):
+ *   state_dev   6 x N float32 SoA (x, y, vx, vy, I0, lw),
+ *   anc_dev     N int32 ancestors the next step will use (identity if none),
+ *   lw_prev_dev N float32 log-weights the next step starts from.
+ * Enqueued on the context's stream. */
+ppf_status ppf_get_particles(ppf_ctx *ctx, float *state_dev, int32_t *anc_dev, float *lw_prev_dev);
+
+/* Replaces the current particles (test and restart hook), enqueued on the
+ * context's stream; the buffers are copied:
+ *   state_dev   6 x N float32 SoA, required,
+ *   anc_dev     ancestors for the next step, NULL = identity,
+ *   lw_prev_dev N float32 starting log-weights for the next step; NULL means
+ *               "carry lw" when anc_dev is NULL (pure SIS) and "equal
+ *               weights" (as after systematic resampling) when it is not.
+ * The next call must be ppf_step.  Errors: PPF_EINVAL, PPF_ECUDA. */
+ppf_status ppf_set_particles(ppf_ctx *ctx, const float *state_dev, const int32_t *anc_dev,
+                             const float *lw_prev_dev);
+
+/* Number of groups G and their current slot offsets (G + 1 int64 values to a
+ * host buffer; synchronises).  offsets may be NULL to query G only. */
+ppf_status ppf_get_groups(ppf_ctx *ctx, int32_t *n_groups, int64_t *offsets_host);
+
+/* Phase timing and launch counting (measurement hook; no effect on results).
+ * When enabled, a pair of CUDA events is recorded on the context's stream
+ * around each phase of every step / resample (up to `capacity` calls per
+ * phase; later calls are counted but not timed). */
+typedef struct {
+    int64_t launches;        /* kernels launched by the library since enabling     */
+    int64_t steps;           /* ppf_step calls                                      */
+    int64_t resamples;       /* ppf_resample calls                                  */
+    int64_t timed_steps;     /* steps whose events were recorded                    */
+    double prepare_ms;       /* frame preparation kernels, summed device time       */
+    double step_ms;          /* fused propagate + likelihood + partials kernels     */
+    double finalize_ms;      /* FP64 normalisation kernels                          */
+    double resample_ms;      /* all kernels of the resampling calls                 */
+    int64_t h2d_bytes;       /* host-to-device bytes copied by ppf_step_host        */
+    int64_t d2h_bytes;       /* device-to-host bytes copied by ppf_estimate         */
+} ppf_profile_t;
+
+/* enable != 0: reset the counters and start recording (capacity >= 1);
+ * enable == 0: stop recording.  Errors: PPF_EINVAL, PPF_ENOMEM, PPF_ECUDA. */
+ppf_status ppf_profile_enable(ppf_ctx *ctx, int enable, int32_t capacity);
+
+/* Synchronises the stream and sums the recorded event pairs. */
+ppf_status ppf_profile_read(ppf_ctx *ctx, ppf_profile_t *out);
+
+/* Human-readable name of a status code (static string). */
+const char *ppf_status_string(ppf_status s);
+
+/* Text of the last error recorded on this context ("" if none).  Valid until
+ * the next call on the context. */
+const char *ppf_last_error(const ppf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPF_H */

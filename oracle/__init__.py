@@ -95,6 +95,8 @@ def lib():
                 "orc_init": (None, [mp, C.c_int64, dp]),
                 "orc_propagate": (None, [mp, C.c_int64, C.c_int32, dp, i32p, dp, dp]),
                 "orc_loglik": (C.c_double, [mp, dp, C.c_double, C.c_double, C.c_double]),
+                "orc_propagate_slots": (None, [mp, C.c_int64, C.c_int32, i64p, dp, dp]),
+                "orc_loglik_many": (None, [mp, dp, C.c_int64, dp, dp, dp, dp]),
                 "orc_weight": (None, [mp, C.c_int64, dp, dp]),
                 "orc_summary": (None, [C.c_int64, dp, dp, dp]),
                 "orc_scale_bits": (C.c_int, [C.c_int64]),
@@ -163,6 +165,28 @@ def propagate(m: Model, frame: int, parent: np.ndarray, anc: np.ndarray, lw_prev
     lib().orc_propagate(C.byref(m.c()), N, frame, _p(par.reshape(-1), C.c_double), _p(a, C.c_int32),
                         _p(lp, C.c_double), _p(st, C.c_double))
     return st.reshape(6, N)
+
+
+def propagate_slots(m: Model, frame: int, slots: np.ndarray, parents5: np.ndarray) -> np.ndarray:
+    """Propagate only the given slots; parents5: (5, n) parent x, y, vx, vy, I0 per slot."""
+    sl = np.ascontiguousarray(slots, dtype=np.int64)
+    n = sl.shape[0]
+    par = np.ascontiguousarray(parents5, dtype=np.float64).reshape(5, n)
+    out = np.zeros((5, n))
+    lib().orc_propagate_slots(C.byref(m.c()), n, frame, _p(sl, C.c_int64), _p(par.reshape(-1), C.c_double),
+                              _p(out.reshape(-1), C.c_double))
+    return out
+
+
+def loglik_many(m: Model, frame: np.ndarray, x, y, I0) -> np.ndarray:
+    fr = np.ascontiguousarray(frame, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    ii = np.ascontiguousarray(I0, dtype=np.float64)
+    out = np.zeros(xx.shape[0])
+    lib().orc_loglik_many(C.byref(m.c()), _p(fr, C.c_double), xx.shape[0], _p(xx, C.c_double),
+                          _p(yy, C.c_double), _p(ii, C.c_double), _p(out, C.c_double))
+    return out
 
 
 def loglik(m: Model, frame: np.ndarray, x: float, y: float, I0: float) -> float:

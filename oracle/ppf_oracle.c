@@ -163,6 +163,32 @@ void orc_propagate(const orc_model *m, int64_t N, int32_t frame, const double *p
     }
 }
 
+/* S1 for a sample of slots: parents5 holds, for each sampled slot, its parent's
+ * (x, y, vx, vy, I0) as a 5 x n SoA; the noise is keyed by the slot index. */
+void orc_propagate_slots(const orc_model *m, int64_t n, int32_t frame, const int64_t *slots,
+                         const double *parents5, double *out5)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        double e[5];
+        orc_normals5(m->seed, (uint32_t)slots[k], (uint32_t)frame, m->filter_id, e);
+        const double x = parents5[k], y = parents5[n + k], vx = parents5[2 * n + k];
+        const double vy = parents5[3 * n + k], I0 = parents5[4 * n + k];
+        out5[k] = x + vx + m->sigma_m * e[0];
+        out5[n + k] = y + vy + m->sigma_m * e[1];
+        out5[2 * n + k] = vx + m->sigma_v * e[2];
+        out5[3 * n + k] = vy + m->sigma_v * e[3];
+        out5[4 * n + k] = I0 + m->sigma_I * e[4];
+    }
+}
+
+/* S3 for many particles: l[k] = loglik(x[k], y[k], I0[k]) */
+void orc_loglik_many(const orc_model *m, const double *frame, int64_t n, const double *x, const double *y,
+                     const double *I0, double *l)
+{
+    for (int64_t k = 0; k < n; ++k)
+        l[k] = orc_loglik(m, frame, x[k], y[k], I0[k]);
+}
+
 /* ------------------------------------------------------------------------ */
 /* S3: log-likelihood of one particle, eq. 4 with the appearance model eq. 3 */
 /* I(p) = I0 exp(-|p - (x,y)|^2 / (2 sigma^2)) + I_bg over the (2r+1)^2      */
@@ -218,6 +244,8 @@ void orc_weight(const orc_model *m, int64_t N, const double *frame, double *st)
 /* ------------------------------------------------------------------------ */
 void orc_summary(int64_t N, const double *st, const double *lw_prev, double out[8])
 {
+    /* a particle whose log-weight is -inf or NaN has zero weight: it is not
+     * part of the weighted-sample approximation and adds nothing to any sum */
     const double *lw = st + 5 * N;
     double M = -INFINITY, Mp = -INFINITY;
     for (int64_t i = 0; i < N; ++i) {
@@ -226,12 +254,18 @@ void orc_summary(int64_t N, const double *st, const double *lw_prev, double out[
     }
     double total = 0.0, totalp = 0.0;
     for (int64_t i = 0; i < N; ++i) {
-        total += exp(lw[i] - M);
-        totalp += exp(lw_prev[i] - Mp);
+        if (lw[i] > -INFINITY)
+            total += exp(lw[i] - M);
+        if (lw_prev[i] > -INFINITY)
+            totalp += exp(lw_prev[i] - Mp);
     }
     double mean[5] = {0, 0, 0, 0, 0}, sumsq = 0.0;
     for (int64_t i = 0; i < N; ++i) {
+        if (!(lw[i] > -INFINITY))
+            continue;
         double w = exp(lw[i] - M) / total;
+        if (w == 0.0)
+            continue;
         for (int c = 0; c < 5; ++c)
             mean[c] += w * st[c * N + i];
         sumsq += w * w;
@@ -503,7 +537,7 @@ int orc_resample(const orc_model *m, int scheme, double alpha, int64_t N, int32_
         free(q);
         for (int32_t g = 0; g <= G; ++g)
             goff_out[g] = goff_in[g];
-        stats[0] = G > 1 ? G : 0;
+        stats[0] = (G > 1 && mig > 0) ? G : 0; /* ring links that carry particles */
         stats[1] = G > 1 ? mig * G : 0;
         stats[2] = maxsz;
         stats[3] = minsz;

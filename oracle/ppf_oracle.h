@@ -25,6 +25,10 @@ void orc_normals5(uint64_t seed, uint32_t slot, uint32_t frame, uint32_t filter,
 void orc_init(const orc_model *m, int64_t N, double *st);
 void orc_propagate(const orc_model *m, int64_t N, int32_t frame, const double *par,
                    const int32_t *anc, const double *lw_prev, double *st);
+void orc_propagate_slots(const orc_model *m, int64_t n, int32_t frame, const int64_t *slots,
+                         const double *parents5, double *out5);
+void orc_loglik_many(const orc_model *m, const double *frame, int64_t n, const double *x, const double *y,
+                     const double *I0, double *l);
 double orc_loglik(const orc_model *m, const double *frame, double x, double y, double I0);
 void orc_weight(const orc_model *m, int64_t N, const double *frame, double *st);
 void orc_summary(int64_t N, const double *st, const double *lw_prev, double out[8]);

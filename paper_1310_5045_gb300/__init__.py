@@ -1,0 +1,29 @@
+"""GB300-native SIR particle filter for single-spot tracking (PPF, Demirel et
+al.): propagation, patch likelihood, normalisation, estimate and the
+systematic / RPA (GS, SGS, LGS) / RNA resampling steps as hand-written CUDA
+kernels for sm_103a behind the C ABI of ``include/ppf.h``."""
+
+from ._binding import (  # noqa: F401
+    BF16,
+    EDEGENERATE,
+    EINVAL,
+    ENOMEM,
+    ESTATE,
+    F16,
+    F32,
+    OK,
+    RNA,
+    RPA_GS,
+    RPA_LGS,
+    RPA_SGS,
+    SCHEMES,
+    SYSTEMATIC,
+    Estimate,
+    Model,
+    ParticleFilter,
+    PPFError,
+    load,
+    lib_path,
+    status_string,
+)
+from ._build import build  # noqa: F401

@@ -1,0 +1,259 @@
+"""ctypes binding of ``include/ppf.h`` (argument marshalling only).
+
+Every step of the filter runs in libppf's CUDA kernels; torch only provides
+device memory and the CUDA stream.  There is no CPU fallback: if the library
+or a GPU is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import math
+import os
+import threading
+
+from . import _build
+
+SYSTEMATIC, RPA_GS, RPA_SGS, RPA_LGS, RNA = 0, 1, 2, 3, 4
+F32, BF16, F16 = 0, 1, 2
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEGENERATE, ESTATE = range(7)
+SCHEMES = {"systematic": SYSTEMATIC, "rpa_gs": RPA_GS, "rpa_sgs": RPA_SGS, "rpa_lgs": RPA_LGS, "rna": RNA}
+
+EXPORTS = ["ppf_create", "ppf_destroy", "ppf_step", "ppf_step_host", "ppf_resample", "ppf_estimate",
+           "ppf_get_particles", "ppf_set_particles", "ppf_get_groups", "ppf_status_string",
+           "ppf_last_error", "ppf_profile_enable", "ppf_profile_read"]
+
+
+class PPFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class _Model(C.Structure):
+    _fields_ = [
+        ("width", C.c_int32), ("height", C.c_int32), ("patch_radius", C.c_int32), ("frame_dtype", C.c_int32),
+        ("psf_sigma", C.c_float), ("amplitude", C.c_float), ("background", C.c_float), ("sigma_xi", C.c_float),
+        ("sigma_m", C.c_float), ("sigma_v", C.c_float), ("sigma_I", C.c_float), ("v0_max", C.c_float),
+        ("seed", C.c_uint64), ("filter_id", C.c_uint32), ("reserved", C.c_uint32),
+    ]
+
+
+class _Estimate(C.Structure):
+    _fields_ = [
+        ("mean", C.c_double * 5), ("log_evidence", C.c_double), ("ess", C.c_double),
+        ("max_log_weight", C.c_double), ("frame", C.c_int32), ("status_flags", C.c_int32),
+        ("links", C.c_int64), ("moved", C.c_int64), ("max_group", C.c_int64), ("min_group", C.c_int64),
+    ]
+
+
+class _Profile(C.Structure):
+    _fields_ = [
+        ("launches", C.c_int64), ("steps", C.c_int64), ("resamples", C.c_int64), ("timed_steps", C.c_int64),
+        ("prepare_ms", C.c_double), ("step_ms", C.c_double), ("finalize_ms", C.c_double),
+        ("resample_ms", C.c_double), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
+    ]
+
+
+@dataclasses.dataclass
+class Model:
+    """Single-spot tracking model (Sec. 7.1-7.2); mirrors ``ppf_model``."""
+    width: int = 128
+    height: int = 128
+    patch_radius: int = 4
+    psf_sigma: float = 1.5
+    amplitude: float = 50.0
+    background: float = 10.0
+    sigma_xi: float = math.sqrt(10.0)
+    sigma_m: float = 0.5
+    sigma_v: float = 0.1
+    sigma_I: float = 1.0
+    v0_max: float = 1.0
+    seed: int = 0
+    filter_id: int = 0
+    frame_dtype: int = F32
+
+    def c(self) -> _Model:
+        return _Model(self.width, self.height, self.patch_radius, self.frame_dtype, self.psf_sigma,
+                      self.amplitude, self.background, self.sigma_xi, self.sigma_m, self.sigma_v,
+                      self.sigma_I, self.v0_max, self.seed & 0xFFFFFFFFFFFFFFFF, self.filter_id, 0)
+
+
+@dataclasses.dataclass
+class Estimate:
+    mean: tuple
+    log_evidence: float
+    ess: float
+    max_log_weight: float
+    frame: int
+    status_flags: int
+    links: int
+    moved: int
+    max_group: int
+    min_group: int
+    status: int = OK
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libppf.so (building it in-tree first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libppf.so not built ({_build.LIB}); run paper_1310_5045_gb300._build.build()")
+        L = C.CDLL(_build.LIB)
+        P = C.POINTER
+        vp, ctxp = C.c_void_p, C.c_void_p
+        sig = {
+            "ppf_create": (C.c_int, [P(_Model), C.c_int64, C.c_int32, vp, P(ctxp)]),
+            "ppf_destroy": (None, [ctxp]),
+            "ppf_step": (C.c_int, [ctxp, vp, C.c_int32]),
+            "ppf_step_host": (C.c_int, [ctxp, vp, C.c_int32]),
+            "ppf_resample": (C.c_int, [ctxp, C.c_int, C.c_float]),
+            "ppf_estimate": (C.c_int, [ctxp, P(_Estimate)]),
+            "ppf_get_particles": (C.c_int, [ctxp, vp, vp, vp]),
+            "ppf_set_particles": (C.c_int, [ctxp, vp, vp, vp]),
+            "ppf_get_groups": (C.c_int, [ctxp, P(C.c_int32), vp]),
+            "ppf_status_string": (C.c_char_p, [C.c_int]),
+            "ppf_last_error": (C.c_char_p, [ctxp]),
+            "ppf_profile_enable": (C.c_int, [ctxp, C.c_int, C.c_int32]),
+            "ppf_profile_read": (C.c_int, [ctxp, P(_Profile)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def status_string(s: int) -> str:
+    return load().ppf_status_string(s).decode()
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+class ParticleFilter:
+    """One SIR filter of N particles on the current CUDA device (``ppf_ctx``)."""
+
+    def __init__(self, model: Model, n: int, group_size: int = 4096, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("ParticleFilter needs a CUDA GPU: the filter runs only in libppf's kernels")
+        self._torch = torch
+        self.L = load()
+        self.model = model
+        self.n = int(n)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ctx = C.c_void_p()
+        st = self.L.ppf_create(C.byref(model.c()), self.n, int(group_size),
+                               C.c_void_p(self.stream.cuda_stream), C.byref(self._ctx))
+        self._check(st, "ppf_create")
+        self.frame = 0
+
+    # ------------------------------------------------------------------ utils
+    def _check(self, st: int, what: str):
+        if st != OK:
+            detail = ""
+            if self._ctx:
+                detail = self.L.ppf_last_error(self._ctx).decode()
+            raise PPFError(st, f"{what}: {status_string(st)} {detail}".strip())
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self.L.ppf_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------- calls
+    def step(self, frame, k: int | None = None):
+        """``ppf_step``: frame is a CUDA tensor (H, W) of the model's dtype."""
+        k = self.frame + 1 if k is None else int(k)
+        if not frame.is_cuda or not frame.is_contiguous():
+            raise ValueError("frame must be a contiguous CUDA tensor")
+        self._check(self.L.ppf_step(self._ctx, C.c_void_p(frame.data_ptr()), k), "ppf_step")
+        self.frame = k
+
+    def step_host(self, frame, k: int | None = None):
+        """``ppf_step_host``: frame is a host tensor/array (pinned for async copies)."""
+        k = self.frame + 1 if k is None else int(k)
+        ptr = frame.data_ptr() if hasattr(frame, "data_ptr") else frame.ctypes.data
+        self._check(self.L.ppf_step_host(self._ctx, C.c_void_p(ptr), k), "ppf_step_host")
+        self.frame = k
+
+    def resample(self, scheme=SYSTEMATIC, exchange_ratio: float = 0.1):
+        if isinstance(scheme, str):
+            scheme = SCHEMES[scheme]
+        self._check(self.L.ppf_resample(self._ctx, int(scheme), float(exchange_ratio)), "ppf_resample")
+
+    def estimate(self, raise_on_flags: bool = False) -> Estimate:
+        e = _Estimate()
+        st = self.L.ppf_estimate(self._ctx, C.byref(e))
+        if st not in (OK, EDEGENERATE, ETIMEOUT) or (raise_on_flags and st != OK):
+            self._check(st, "ppf_estimate")
+        return Estimate(tuple(e.mean), e.log_evidence, e.ess, e.max_log_weight, e.frame, e.status_flags,
+                        e.links, e.moved, e.max_group, e.min_group, st)
+
+    def get_particles(self, state=True, anc=False, lw_prev=False):
+        torch = self._torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        s = torch.empty((6, self.n), dtype=torch.float32, device=dev) if state else None
+        a = torch.empty(self.n, dtype=torch.int32, device=dev) if anc else None
+        p = torch.empty(self.n, dtype=torch.float32, device=dev) if lw_prev else None
+        self._check(self.L.ppf_get_particles(self._ctx, C.c_void_p(_ptr(s)), C.c_void_p(_ptr(a)),
+                                             C.c_void_p(_ptr(p))), "ppf_get_particles")
+        self.stream.synchronize()
+        return s, a, p
+
+    def set_particles(self, state, anc=None, lw_prev=None):
+        torch = self._torch
+        state = state.to(device="cuda", dtype=torch.float32).contiguous()
+        if state.shape != (6, self.n):
+            raise ValueError("state must be (6, N)")
+        if anc is not None:
+            anc = anc.to(device="cuda", dtype=torch.int32).contiguous()
+        if lw_prev is not None:
+            lw_prev = lw_prev.to(device="cuda", dtype=torch.float32).contiguous()
+        self._check(self.L.ppf_set_particles(self._ctx, C.c_void_p(_ptr(state)), C.c_void_p(_ptr(anc)),
+                                             C.c_void_p(_ptr(lw_prev))), "ppf_set_particles")
+        self.stream.synchronize()
+
+    def groups(self):
+        import numpy as np
+        g = C.c_int32()
+        self._check(self.L.ppf_get_groups(self._ctx, C.byref(g), None), "ppf_get_groups")
+        off = np.zeros(g.value + 1, dtype=np.int64)
+        self._check(self.L.ppf_get_groups(self._ctx, C.byref(g), C.c_void_p(off.ctypes.data)), "ppf_get_groups")
+        return off
+
+    def profile_enable(self, enable: bool = True, capacity: int = 4096):
+        self._check(self.L.ppf_profile_enable(self._ctx, 1 if enable else 0, int(capacity)), "ppf_profile_enable")
+
+    def profile_read(self) -> dict:
+        p = _Profile()
+        self._check(self.L.ppf_profile_read(self._ctx, C.byref(p)), "ppf_profile_read")
+        return {name: getattr(p, name) for name, _ in _Profile._fields_}

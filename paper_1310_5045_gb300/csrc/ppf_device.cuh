@@ -1,0 +1,206 @@
+// ppf_device.cuh -- device-side building blocks of the SIR step (sm_103a).
+//
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+// numbers: as easy as 1, 2, 3", SC'11), keyed by the model seed, counter
+// (index, frame, filter, purpose << 8 | block).  Uniforms are odd multiples of
+// 2^-24 (exact in float32), normals by the Box-Muller transform.
+//
+// Resampling weights (Alg. 1 resampling step) are 64-bit fixed point:
+// q = floor(2^(s + t)), t = (lw - M) log2(e), computed by one fixed float32
+// operation sequence (round-to-nearest, no contraction) so that the integer
+// result is fully determined by lw and M.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ppf {
+
+typedef unsigned __int128 u128;
+
+enum : uint32_t { PURPOSE_INIT = 0, PURPOSE_PROP = 1, PURPOSE_RESAMPLE = 2, PURPOSE_GROUP = 3 };
+
+// One Philox4x32-10 block: ten rounds of two 32x32->64 multiplications of
+// counter words 0 and 2, the high halves xor-ed with the other counter words
+// and the key, the key advanced by the Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t index, uint32_t frame, uint32_t filter,
+                                      uint32_t purpose, uint32_t block)
+{
+    return philox(make_uint4(index, frame, filter, (purpose << 8) | block), (uint32_t)seed,
+                  (uint32_t)(seed >> 32));
+}
+
+// odd multiple of 2^-24 in (0, 1); the integer is < 2^24, so this is exact
+__device__ __forceinline__ float u01(uint32_t r)
+{
+    return __uint2float_rn(2u * (r >> 9) + 1u) * 0x1p-24f;
+}
+
+__device__ __forceinline__ void box_muller(uint32_t r1, uint32_t r2, float &z0, float &z1)
+{
+    const float u1 = u01(r1), u2 = u01(r2);
+    const float rho = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    z0 = rho * c;
+    z1 = rho * s;
+}
+
+// ceil(log2 n) complement: s = 63 - ceil(log2 n), so that n * 2^s <= 2^63
+__host__ __device__ inline int scale_bits(int64_t n)
+{
+    int c = 0;
+    while (((int64_t)1 << c) < n)
+        ++c;
+    return 63 - c;
+}
+
+// 2^f for f in [0, 1): Taylor polynomial of e^(f ln 2) to degree 9, the
+// coefficients (ln 2)^n / n! rounded to float32, evaluated by Horner's rule
+// with fused multiply-adds.
+__device__ __forceinline__ float exp2_frac(float f)
+{
+    float p = 0x1.b5253ep-24f;
+    p = __fmaf_rn(p, f, 0x1.62c022p-20f);
+    p = __fmaf_rn(p, f, 0x1.ffcbfcp-17f);
+    p = __fmaf_rn(p, f, 0x1.430912p-13f);
+    p = __fmaf_rn(p, f, 0x1.5d87fep-10f);
+    p = __fmaf_rn(p, f, 0x1.3b2ab6p-7f);
+    p = __fmaf_rn(p, f, 0x1.c6b08ep-5f);
+    p = __fmaf_rn(p, f, 0x1.ebfbep-3f);
+    p = __fmaf_rn(p, f, 0x1.62e43p-1f);
+    p = __fmaf_rn(p, f, 1.0f);
+    return p;
+}
+
+__device__ __forceinline__ uint64_t quantise(float lw, float M, int s)
+{
+    const float d = __fsub_rn(lw, M);
+    const float t = __fmul_rn(d, 0x1.715476p+0f);
+    if (!(t > -64.0f))
+        return 0ull;
+    const float kf = floorf(t);
+    const float f = __fsub_rn(t, kf);
+    const float p = exp2_frac(f);
+    const int e = s + (int)kf;
+    const uint64_t P = (uint64_t)__float2ull_rz(__fmul_rn(p, 0x1p23f));
+    if (e < -25)
+        return 0ull;
+    if (e >= 23)
+        return P << (e - 23);
+    return P >> (23 - e);
+}
+
+// Number of systematic tickets below cumulative weight c:
+// #{j in [0, n) : u + j Q < n c} = clamp(ceil((n c - u) / Q), 0, n).
+// The quotient is estimated in double and made exact with 128-bit corrections.
+__device__ __forceinline__ int64_t tickets_below(uint64_t c, int64_t n, uint64_t u, uint64_t Q)
+{
+    const u128 nc = (u128)c * (u128)(uint64_t)n;
+    if (nc <= (u128)u)
+        return 0;
+    const u128 num = nc - (u128)u;
+    const double est = ((double)(uint64_t)(num >> 64) * 18446744073709551616.0 + (double)(uint64_t)num) /
+                       (double)Q;
+    if (est > (double)n + 2.0)
+        return n;
+    uint64_t qh = (uint64_t)est;
+    u128 prod = (u128)qh * (u128)Q;
+    while (prod > num) {
+        --qh;
+        prod -= Q;
+    }
+    while (num - prod >= (u128)Q) {
+        ++qh;
+        prod += Q;
+    }
+    if (num != prod)
+        ++qh;
+    return qh > (uint64_t)n ? n : (int64_t)qh;
+}
+
+// u = floor(r64 * Q / 2^64): a uniform ticket offset in [0, Q)
+__device__ __forceinline__ uint64_t ticket_offset(uint64_t seed, uint32_t filter, uint32_t frame,
+                                                  uint32_t purpose, uint32_t index, uint64_t Q)
+{
+    const uint4 r = draw(seed, index, frame, filter, purpose, 0);
+    const uint64_t r64 = ((uint64_t)r.y << 32) | (uint64_t)r.x;
+    return __umul64hi(r64, Q);
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o)
+            v += t;
+    }
+    return v;
+}
+
+// exclusive scan over the block (blockDim.x a multiple of 32, <= 1024);
+// smem: 32 u64.  Returns the exclusive prefix; *total gets the block sum.
+__device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t v, uint64_t *smem, uint64_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint64_t incl = warp_incl_scan_u64(v);
+    __syncthreads();
+    if (lane == 31)
+        smem[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t w = lane < nw ? smem[lane] : 0ull;
+        const uint64_t wi = warp_incl_scan_u64(w);
+        smem[lane] = wi - w;
+        if (lane == 31)
+            smem[32] = wi;
+    }
+    __syncthreads();
+    const uint64_t res = smem[warp] + incl - v;
+    *total = smem[32];
+    return res;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace ppf

@@ -1,0 +1,118 @@
+// ppf_internal.h -- context layout and kernel launchers of the GB300 SIR filter.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ppf.h"
+
+namespace ppf {
+
+constexpr int TILE = 4096;          // particles per resampling tile (256 threads x 16)
+constexpr int TILE_THREADS = 256;
+constexpr int TILE_ITEMS = TILE / TILE_THREADS;
+constexpr int FILL_CHUNK = 4096;    // tickets per fill work item
+constexpr int COPY_CHUNK = 2048;    // slots per routing-copy work item
+constexpr int MAX_RADIUS = 8;
+constexpr int MAX_SCHED_GROUPS = 16384;
+
+// How the next step forms a slot's starting log-weight.
+enum StepMode : int {
+    MODE_CARRY = 0,     // identity ancestry, weight carried (no resampling since the last step)
+    MODE_UNIFORM = 1,   // resampled: equal weights (lw_prev = 0)
+    MODE_EXPLICIT = 2   // resampled: per-slot lw_prev buffer (RNA, restarts)
+};
+
+enum : int { FLAG_DEGENERATE = 1, FLAG_TIMEOUT = 2, FLAG_INTERNAL = 4, FLAG_BAD_ANCESTOR = 8 };
+
+// per-block weight statistics of one step (online log-sum-exp partials)
+struct Partial {
+    float m, s0, s[5], s2, mp, sp;
+};
+
+// device-side per-frame results and resampling scalars
+struct DevSummary {
+    double mean[5];
+    double log_evidence;
+    double ess;
+    double max_lw;
+    double log_total;          // M + log sum e^(lw - M), FP64
+    float M;                   // max lw (exact float): the quantiser reference
+    int32_t frame;
+    int32_t flags;             // sticky FLAG_* bits, cleared by ppf_estimate
+    int32_t degenerate;        // last resample found no usable weight
+    int64_t links, moved, max_group, min_group;
+    uint64_t Q, u;             // last global resample: total fixed-point weight, offset
+    int32_t n_items;           // fill work items of the last resample
+    int32_t n_chunks;          // routing-copy work items of the last RPA resample
+    int64_t mig;               // RNA: slots migrating to the next group
+};
+
+struct Scratch {
+    uint64_t *Qt;      // [T]   tile totals
+    uint64_t *Ct;      // [T+1] exclusive tile prefix
+    int64_t *Tt;       // [T+1] tickets below each tile start
+    int32_t *item_off; // [T+1] fill work-item prefix per tile
+    uint64_t *Cbl;     // [G+1] local prefix at group starts (within their tile)
+    int64_t *Tg;       // [G+1] tickets below each group start
+    // scheduler (RPA)
+    uint64_t *skey;    // [2G] sort / merge buffers
+    int64_t *sval;     // [5G]
+    int32_t *seg_src;  // segments: ticket start, slot start, length, chunk prefix
+    int64_t *seg_tick;
+    int64_t *seg_dst;
+    int64_t *seg_len;
+    int32_t *seg_chunk; // [2G+1]
+};
+
+}  // namespace ppf
+
+struct ppf_ctx {
+    ppf_model m;
+    int64_t N;
+    int32_t group_size, G, T;     // groups, resampling tiles
+    cudaStream_t stream;
+    int device, num_sms;
+    float *state[2];              // 6 x N SoA each
+    int cur;                      // index of the current particles
+    int32_t *anc;                 // pending ancestors
+    int32_t *anc_sys;             // systematic ancestors before RPA routing
+    float *lwp;                   // per-slot starting log-weights (MODE_EXPLICIT)
+    int64_t *goff, *goff_new;     // group offsets [G+1]
+    float *Zp;                    // padded frame minus background
+    int32_t Wp, Hp, pad;
+    void *frame_buf;              // device copy for ppf_step_host
+    size_t frame_bytes;
+    ppf::Partial *part;
+    int n_part;
+    ppf::DevSummary *sum;
+    ppf::DevSummary *sum_host;    // pinned mirror for ppf_estimate
+    ppf::Scratch sc;
+    int mode;                     // StepMode of the next step
+    bool stepped;                 // at least one step since create/set
+    bool weighted;                // a step happened since the last resample
+    int32_t last_frame;
+    // profiling (ppf_profile_enable)
+    bool prof_on;
+    int32_t prof_cap;
+    cudaEvent_t *prof_ev;         // [4 phases][cap][2]
+    int32_t prof_n[4];
+    int64_t launches, n_steps, n_resamples, h2d_bytes, d2h_bytes;
+    char err[512];
+};
+
+namespace ppf {
+enum Phase { PH_PREPARE = 0, PH_STEP = 1, PH_FINALIZE = 2, PH_RESAMPLE = 3 };
+// record the start / end event of a phase when profiling is on
+void prof_mark(ppf_ctx *c, int phase, int end);
+// launchers (each enqueues on ctx->stream; return cudaGetLastError())
+cudaError_t launch_init(ppf_ctx *c);
+cudaError_t launch_prepare_frame(ppf_ctx *c, const void *frame);
+cudaError_t launch_step(ppf_ctx *c, int32_t k);
+cudaError_t launch_resample_global(ppf_ctx *c, int scheme);
+cudaError_t launch_resample_rna(ppf_ctx *c, float alpha);
+cudaError_t launch_identity(ppf_ctx *c, int32_t *dst);
+cudaError_t launch_pending(ppf_ctx *c, int32_t *anc_out, float *lwp_out);
+cudaError_t launch_fill_f32(ppf_ctx *c, float *dst, float v);
+int step_grid(ppf_ctx *c);
+}  // namespace ppf

@@ -1,0 +1,903 @@
+// ppf_resample.cu -- the resampling step of Alg. 1 on 64-bit fixed-point
+// weights, and the distributed schemes of Sec. 3-4 mapped onto particle groups:
+//   systematic  one global offset u, ticket j at (u + jQ)/N of the cumulative
+//               weight; the parent of ticket j is the first particle whose
+//               cumulative weight C_i satisfies N C_i > u + jQ.
+//   RPA         the same global tickets (proportional allocation); group g
+//               holds the tickets of its own cumulative range, keeps the first
+//               ones and routes its surplus to receivers following the Greedy
+//               (Alg. 2), Sorted Greedy (Alg. 3) or Largest Gradient (Alg. 4)
+//               schedule.
+//   RNA         every group resamples its own slots from its own weights with
+//               its own offset (non-proportional allocation); its offspring
+//               carry the group weight, and the last floor(alpha min n_g) slots
+//               of every group migrate to the next group of the ring.
+#include <cmath>
+
+#include "ppf_device.cuh"
+#include "ppf_internal.h"
+
+namespace ppf {
+
+// Load one tile's quantised weights: thread t owns items [16t, 16t+16).
+__device__ __forceinline__ void tile_weights(const float *__restrict__ lw, int64_t lo, int n, float M, int s,
+                                             uint64_t q[TILE_ITEMS])
+{
+    const int base = threadIdx.x * TILE_ITEMS;
+#pragma unroll
+    for (int k = 0; k < TILE_ITEMS; ++k) {
+        const int i = base + k;
+        q[k] = (i < n) ? quantise(__ldg(lw + lo + i), M, s) : 0ull;
+    }
+}
+
+// Inclusive scan of a tile's weights into smem C[0..TILE).  Returns the total.
+__device__ __forceinline__ uint64_t tile_scan(const uint64_t q[TILE_ITEMS], uint64_t *C, uint64_t *red)
+{
+    uint64_t loc[TILE_ITEMS];
+    uint64_t run = 0;
+#pragma unroll
+    for (int k = 0; k < TILE_ITEMS; ++k) {
+        run += q[k];
+        loc[k] = run;
+    }
+    uint64_t total;
+    const uint64_t pre = block_excl_scan_u64(run, red, &total);
+    const int base = threadIdx.x * TILE_ITEMS;
+#pragma unroll
+    for (int k = 0; k < TILE_ITEMS; ++k)
+        C[base + k] = pre + loc[k];
+    __syncthreads();
+    return total;
+}
+
+// ---------------------------------------------------------------- R1 tiles
+// Tile totals Q_t; for RPA also the local prefix at every group start that
+// falls inside the tile.
+__global__ void __launch_bounds__(TILE_THREADS) tile_totals_kernel(
+    const float *__restrict__ lw, int64_t N, const DevSummary *__restrict__ sum, uint64_t *__restrict__ Qt,
+    const int64_t *__restrict__ goff, int32_t G, uint64_t *__restrict__ Cbl)
+{
+    __shared__ uint64_t C[TILE];
+    __shared__ uint64_t red[33];
+    __shared__ int32_t gfirst;
+    const int64_t lo = (int64_t)blockIdx.x * TILE;
+    const int n = (int)(N - lo < TILE ? N - lo : TILE);
+    uint64_t q[TILE_ITEMS];
+    tile_weights(lw, lo, n, sum->M, scale_bits(N), q);
+    const uint64_t total = tile_scan(q, C, red);
+    if (threadIdx.x == 0)
+        Qt[blockIdx.x] = total;
+    if (goff == nullptr)
+        return;
+    if (threadIdx.x == 0) {
+        int32_t a = 0, b = G + 1;  // first g with goff[g] >= lo
+        while (a < b) {
+            const int32_t mid = (a + b) >> 1;
+            if (goff[mid] < lo)
+                a = mid + 1;
+            else
+                b = mid;
+        }
+        gfirst = a;
+    }
+    __syncthreads();
+    for (int32_t g = gfirst + threadIdx.x; g <= G; g += blockDim.x) {
+        const int64_t pos = goff[g];
+        if (pos >= lo + n)
+            break;
+        const int64_t k = pos - lo;
+        Cbl[g] = (k == 0) ? 0ull : C[k - 1];
+    }
+}
+
+// ---------------------------------------------------------------- R2 scan
+// One block: exclusive tile prefix, total Q, ticket offset u, tickets below
+// each tile start, fill work items; for RPA the tickets below each group start.
+__global__ void __launch_bounds__(1024) tile_scan_kernel(
+    int64_t N, int32_t T, const uint64_t *__restrict__ Qt, uint64_t *__restrict__ Ct, int64_t *__restrict__ Tt,
+    int32_t *__restrict__ item_off, DevSummary *sum, uint64_t seed, uint32_t fid, uint32_t frame,
+    const int64_t *__restrict__ goff, int32_t G, int rpa, const uint64_t *__restrict__ Cbl,
+    int64_t *__restrict__ Tg)
+{
+    __shared__ uint64_t red[33];
+    __shared__ uint64_t sQ, su;
+    const int per = (T + blockDim.x - 1) / blockDim.x;
+    const int t0 = threadIdx.x * per;
+    uint64_t s = 0;
+    for (int k = 0; k < per; ++k)
+        if (t0 + k < T)
+            s += Qt[t0 + k];
+    uint64_t total;
+    uint64_t run = block_excl_scan_u64(s, red, &total);
+    for (int k = 0; k < per; ++k)
+        if (t0 + k < T) {
+            Ct[t0 + k] = run;
+            run += Qt[t0 + k];
+        }
+    if (threadIdx.x == 0) {
+        Ct[T] = total;
+        sQ = total;
+        const int deg = (total == 0ull);
+        sum->degenerate = deg;
+        if (deg)
+            sum->flags |= FLAG_DEGENERATE;
+        sum->Q = total;
+        su = deg ? 0ull : ticket_offset(seed, fid, frame, PURPOSE_RESAMPLE, 0u, total);
+        sum->u = su;
+    }
+    __syncthreads();
+    const uint64_t Q = sQ, u = su;
+    if (Q == 0ull) {
+        if (threadIdx.x == 0)
+            sum->n_items = 0;
+        return;
+    }
+    for (int t = threadIdx.x; t <= T; t += blockDim.x)
+        Tt[t] = (t == T) ? N : tickets_below(Ct[t], N, u, Q);
+    __syncthreads();
+    // fill work items: ceil(tickets / FILL_CHUNK) per tile
+    uint64_t cnt = 0;
+    for (int k = 0; k < per; ++k)
+        if (t0 + k < T)
+            cnt += (uint64_t)((Tt[t0 + k + 1] - Tt[t0 + k] + FILL_CHUNK - 1) / FILL_CHUNK);
+    uint64_t items_total;
+    uint64_t irun = block_excl_scan_u64(cnt, red, &items_total);
+    for (int k = 0; k < per; ++k)
+        if (t0 + k < T) {
+            item_off[t0 + k] = (int32_t)irun;
+            irun += (uint64_t)((Tt[t0 + k + 1] - Tt[t0 + k] + FILL_CHUNK - 1) / FILL_CHUNK);
+        }
+    if (threadIdx.x == 0) {
+        item_off[T] = (int32_t)items_total;
+        sum->n_items = (int32_t)items_total;
+    }
+    if (rpa) {
+        for (int g = threadIdx.x; g <= G; g += blockDim.x) {
+            const int64_t pos = goff[g];
+            const uint64_t c = (pos >= N) ? Q : Ct[pos / TILE] + Cbl[g];
+            Tg[g] = (pos >= N) ? N : tickets_below(c, N, u, Q);
+        }
+    } else {
+        // systematic keeps the group layout: report its extent, no routing
+        __shared__ long long smx[32], smn[32];
+        long long mx = 0, mn = INT64_MAX;
+        for (int g = threadIdx.x; g < G; g += blockDim.x) {
+            const long long sz = goff[g + 1] - goff[g];
+            mx = sz > mx ? sz : mx;
+            mn = sz < mn ? sz : mn;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long a = __shfl_xor_sync(0xffffffffu, mx, o);
+            const long long b = __shfl_xor_sync(0xffffffffu, mn, o);
+            mx = a > mx ? a : mx;
+            mn = b < mn ? b : mn;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            smx[threadIdx.x >> 5] = mx;
+            smn[threadIdx.x >> 5] = mn;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long a = 0, b = INT64_MAX;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                a = smx[w] > a ? smx[w] : a;
+                b = smn[w] < b ? smn[w] : b;
+            }
+            sum->max_group = a;
+            sum->min_group = b;
+            sum->links = 0;
+            sum->moved = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- R3 fill
+// Work item b covers tickets [j_lo, j_hi) of one tile; every ticket finds its
+// parent in the tile's cumulative weights by binary search.
+__global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
+    const float *__restrict__ lw, int64_t N, int32_t T, const DevSummary *__restrict__ sum,
+    const uint64_t *__restrict__ Ct, const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
+    int32_t *__restrict__ out)
+{
+    __shared__ uint64_t C[TILE];
+    __shared__ uint64_t red[33];
+    __shared__ int32_t st;
+    const int32_t b = blockIdx.x;
+    if (b >= sum->n_items)
+        return;
+    if (threadIdx.x == 0) {
+        int32_t a = 0, e = T;  // last t with item_off[t] <= b
+        while (a < e) {
+            const int32_t mid = (a + e + 1) >> 1;
+            if (item_off[mid] <= b)
+                a = mid;
+            else
+                e = mid - 1;
+        }
+        st = a;
+    }
+    __syncthreads();
+    const int32_t t = st;
+    const int64_t lo = (int64_t)t * TILE;
+    const int n = (int)(N - lo < TILE ? N - lo : TILE);
+    uint64_t q[TILE_ITEMS];
+    tile_weights(lw, lo, n, sum->M, scale_bits(N), q);
+    tile_scan(q, C, red);
+    const uint64_t Q = sum->Q, u = sum->u, c0 = Ct[t];
+    const int64_t j_lo = Tt[t] + (int64_t)(b - item_off[t]) * FILL_CHUNK;
+    const int64_t j_hi = (Tt[t + 1] < j_lo + FILL_CHUNK) ? Tt[t + 1] : j_lo + FILL_CHUNK;
+    const u128 NN = (u128)(uint64_t)N;
+    for (int64_t j = j_lo + threadIdx.x; j < j_hi; j += blockDim.x) {
+        const u128 V = (u128)u + (u128)(uint64_t)j * (u128)Q;
+        int a = 0, e = n - 1;  // first i with N (c0 + C[i]) > V
+        while (a < e) {
+            const int mid = (a + e) >> 1;
+            if (NN * (u128)(c0 + C[mid]) > V)
+                e = mid;
+            else
+                a = mid + 1;
+        }
+        out[j] = (int32_t)(lo + a);
+    }
+}
+
+// ------------------------------------------------------------ RPA schedule
+// One block.  Senders / receivers from the offspring counts o_g = T_{g+1} -
+// T_g and the balanced targets n_g; SGS and LGS sort both lists by amount,
+// descending, ties by group index (bitonic sort in shared memory).  GS/SGS
+// links are the pieces of [0, D) cut at every sender and receiver prefix
+// boundary (D = total surplus = total deficit); LGS pairs the i-th sender
+// with the i-th receiver.  Output: new group offsets and the routing
+// segments (ticket start, slot start, length) with their copy work items.
+struct SchedArgs {
+    int64_t N;
+    int32_t G;
+    int scheme;
+    const int64_t *goff;
+    int64_t *goff_new;
+    const int64_t *Tg;
+    uint64_t *key;      // [2 * G]  (sender keys, receiver keys)
+    int64_t *val;       // [5 * G]  (PS, PR, sent, recv, merge buffer)
+    int32_t *seg_chunk; // [2G + 2]
+    int64_t *seg_tick, *seg_dst, *seg_len;  // [2G + 1]
+    DevSummary *sum;
+};
+
+__device__ __forceinline__ int64_t target_of(int64_t N, int32_t G, int32_t g)
+{
+    return N / G + ((int64_t)g < N % G ? 1 : 0);
+}
+
+// block-wide exclusive scan of an int64 array in place (single block)
+__device__ void block_scan_i64(int64_t *a, int n, uint64_t *red, int64_t *total_out)
+{
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int i0 = threadIdx.x * per;
+    uint64_t s = 0;
+    for (int k = 0; k < per; ++k)
+        if (i0 + k < n)
+            s += (uint64_t)a[i0 + k];
+    uint64_t total;
+    uint64_t run = block_excl_scan_u64(s, red, &total);
+    __syncthreads();
+    for (int k = 0; k < per; ++k)
+        if (i0 + k < n) {
+            const int64_t v = a[i0 + k];
+            a[i0 + k] = (int64_t)run;
+            run += (uint64_t)v;
+        }
+    if (total_out)
+        *total_out = (int64_t)total;
+    __syncthreads();
+}
+
+// bitonic sort (ascending) of n <= MAX_SCHED_GROUPS u64 keys in shared memory
+__device__ void block_sort_u64(uint64_t *g, int n, uint64_t *sm)
+{
+    int P = 1;
+    while (P < n)
+        P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x)
+        sm[i] = (i < n) ? g[i] : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a = sm[i], b = sm[ixj];
+                    const bool up = ((i & k) == 0);
+                    if ((a > b) == up) {
+                        sm[i] = b;
+                        sm[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        g[i] = sm[i];
+    __syncthreads();
+}
+
+// first index in sorted a[0..n) with a[i] > v
+__device__ __forceinline__ int upper_bound_i64(const int64_t *a, int n, int64_t v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] > v)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int lower_bound_i64(const int64_t *a, int n, int64_t v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
+{
+    extern __shared__ uint64_t sm[];   // MAX_SCHED_GROUPS keys
+    __shared__ uint64_t red[33];
+    __shared__ int nS_s, nR_s, L_s;
+    const int32_t G = A.G;
+    const int64_t N = A.N;
+    DevSummary *sum = A.sum;
+    if (sum->degenerate) {
+        for (int g = threadIdx.x; g <= G; g += blockDim.x)
+            A.goff_new[g] = A.goff[g];
+        if (threadIdx.x == 0) {
+            sum->n_chunks = 0;
+            sum->links = 0;
+            sum->moved = 0;
+        }
+        return;
+    }
+    uint64_t *Skey = A.key, *Rkey = A.key + G;
+    int64_t *PS = A.val, *PR = A.val + G;
+    // 1. senders / receivers, compacted in group order.  key = amount << 24 | g
+    //    (amount <= N < 2^31 fits 40 bits; g < 2^24).  For sorting by amount
+    //    descending then g ascending we sort ((2^40-1-amount) << 24 | g).
+    if (threadIdx.x == 0) {
+        nS_s = 0;
+        nR_s = 0;
+    }
+    __syncthreads();
+    // stable compaction via block scan of flags over contiguous per-thread ranges
+    {
+        const int per = (G + blockDim.x - 1) / blockDim.x;
+        const int g0 = threadIdx.x * per;
+        uint64_t cs = 0, cr = 0;
+        for (int k = 0; k < per; ++k) {
+            const int g = g0 + k;
+            if (g < G) {
+                const int64_t o = A.Tg[g + 1] - A.Tg[g], t = target_of(N, G, g);
+                cs += (o > t);
+                cr += (o < t);
+            }
+        }
+        uint64_t ts, tr;
+        uint64_t ps = block_excl_scan_u64(cs, red, &ts);
+        uint64_t pr = block_excl_scan_u64(cr, red, &tr);
+        const bool sorted = (A.scheme != PPF_RPA_GS);
+        for (int k = 0; k < per; ++k) {
+            const int g = g0 + k;
+            if (g < G) {
+                const int64_t o = A.Tg[g + 1] - A.Tg[g], t = target_of(N, G, g);
+                if (o > t) {
+                    const uint64_t amt = (uint64_t)(o - t);
+                    Skey[ps++] = sorted ? (((0xFFFFFFFFFFull - amt) << 24) | (uint64_t)g) : ((amt << 24) | (uint64_t)g);
+                }
+                if (o < t) {
+                    const uint64_t amt = (uint64_t)(t - o);
+                    Rkey[pr++] = sorted ? (((0xFFFFFFFFFFull - amt) << 24) | (uint64_t)g) : ((amt << 24) | (uint64_t)g);
+                }
+            }
+        }
+        if (threadIdx.x == 0) {
+            nS_s = (int)ts;
+            nR_s = (int)tr;
+        }
+    }
+    __syncthreads();
+    const int nS = nS_s, nR = nR_s;
+    const bool sorted = (A.scheme != PPF_RPA_GS);
+    if (sorted) {
+        block_sort_u64(Skey, nS, sm);
+        block_sort_u64(Rkey, nR, sm);
+    }
+    auto amount = [&](uint64_t k) -> int64_t {
+        return sorted ? (int64_t)(0xFFFFFFFFFFull - (k >> 24)) : (int64_t)(k >> 24);
+    };
+    auto group = [&](uint64_t k) -> int32_t { return (int32_t)(k & 0xFFFFFFull); };
+    // per-group sent / received totals
+    int64_t *sent = A.val + 2 * G, *recv = A.val + 3 * G;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        sent[g] = 0;
+        recv[g] = 0;
+    }
+    __syncthreads();
+    int L = 0;
+    if (A.scheme == PPF_RPA_LGS) {
+        L = nS < nR ? nS : nR;
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            const int64_t a = amount(Skey[i]), b = amount(Rkey[i]);
+            const int64_t c = a < b ? a : b;
+            sent[group(Skey[i])] = c;
+            recv[group(Rkey[i])] = c;
+        }
+    } else {
+        for (int i = threadIdx.x; i < nS; i += blockDim.x)
+            sent[group(Skey[i])] = amount(Skey[i]);
+        for (int i = threadIdx.x; i < nR; i += blockDim.x)
+            recv[group(Rkey[i])] = amount(Rkey[i]);
+    }
+    __syncthreads();
+    // 2. new sizes and offsets: m'_g = o_g - sent_g + recv_g
+    int64_t *off = A.goff_new;
+    for (int g = threadIdx.x; g < G; g += blockDim.x)
+        off[g] = (A.Tg[g + 1] - A.Tg[g]) - sent[g] + recv[g];
+    __syncthreads();
+    {
+        int64_t mx = 0, mn = INT64_MAX;
+        for (int g = threadIdx.x; g < G; g += blockDim.x) {
+            mx = off[g] > mx ? off[g] : mx;
+            mn = off[g] < mn ? off[g] : mn;
+        }
+        __shared__ long long smx[32], smn[32];
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long a = __shfl_xor_sync(0xffffffffu, (long long)mx, o);
+            const long long b = __shfl_xor_sync(0xffffffffu, (long long)mn, o);
+            mx = a > mx ? a : mx;
+            mn = b < mn ? b : mn;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            smx[threadIdx.x >> 5] = mx;
+            smn[threadIdx.x >> 5] = mn;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long a = 0, b = INT64_MAX;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                a = smx[w] > a ? smx[w] : a;
+                b = smn[w] < b ? smn[w] : b;
+            }
+            sum->max_group = a;
+            sum->min_group = b;
+        }
+        __syncthreads();
+    }
+    int64_t tot;
+    block_scan_i64(off, G, red, &tot);
+    if (threadIdx.x == 0)
+        off[G] = tot;
+    __syncthreads();
+    // 3. kept segments: group g keeps its first o_g - sent_g tickets
+    int64_t *seg_len = A.seg_len, *seg_tick = A.seg_tick, *seg_dst = A.seg_dst;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        seg_tick[g] = A.Tg[g];
+        seg_dst[g] = off[g];
+        seg_len[g] = (A.Tg[g + 1] - A.Tg[g]) - sent[g];
+    }
+    // 4. links
+    if (A.scheme == PPF_RPA_LGS) {
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            const int32_t s = group(Skey[i]), r = group(Rkey[i]);
+            const int64_t c = sent[s];
+            const int64_t keep_s = (A.Tg[s + 1] - A.Tg[s]) - c;
+            const int64_t keep_r = A.Tg[r + 1] - A.Tg[r];
+            seg_tick[G + i] = A.Tg[s] + keep_s;
+            seg_dst[G + i] = off[r] + keep_r;
+            seg_len[G + i] = c;
+        }
+        if (threadIdx.x == 0)
+            L_s = L;
+        __syncthreads();
+    } else {
+        // prefix sums of the amounts in list order (inclusive)
+        for (int i = threadIdx.x; i < nS; i += blockDim.x)
+            PS[i] = amount(Skey[i]);
+        for (int i = threadIdx.x; i < nR; i += blockDim.x)
+            PR[i] = amount(Rkey[i]);
+        __syncthreads();
+        int64_t d1, d2;
+        block_scan_i64(PS, nS, red, &d1);
+        block_scan_i64(PR, nR, red, &d2);
+        // now PS[i], PR[j] are exclusive starts; piece starts are the union of
+        // both start sets (0 is in both).  Merge them (PS first on ties).
+        int64_t *MG = A.val + 4 * G;  // at most nS + nR <= G entries
+        __syncthreads();
+        for (int i = threadIdx.x; i < nS; i += blockDim.x)
+            MG[i + lower_bound_i64(PR, nR, PS[i])] = PS[i];
+        for (int j = threadIdx.x; j < nR; j += blockDim.x)
+            MG[j + upper_bound_i64(PS, nS, PR[j])] = PR[j];
+        __syncthreads();
+        const int nm = nS + nR;
+        // distinct starts -> links; store compacted into seg arrays after G
+        {
+            const int per = (nm + blockDim.x - 1) / blockDim.x;
+            const int i0 = threadIdx.x * per;
+            uint64_t c = 0;
+            for (int k = 0; k < per; ++k) {
+                const int i = i0 + k;
+                if (i < nm && (i == 0 || MG[i] != MG[i - 1]))
+                    ++c;
+            }
+            uint64_t tl;
+            uint64_t pos = block_excl_scan_u64(c, red, &tl);
+            for (int k = 0; k < per; ++k) {
+                const int i = i0 + k;
+                if (i < nm && (i == 0 || MG[i] != MG[i - 1])) {
+                    const int64_t a = MG[i];
+                    const int si = upper_bound_i64(PS, nS, a) - 1;  // sender piece contains a
+                    const int rj = upper_bound_i64(PR, nR, a) - 1;
+                    const int64_t se = PS[si] + amount(Skey[si]);
+                    const int64_t re = PR[rj] + amount(Rkey[rj]);
+                    const int64_t e = se < re ? se : re;
+                    const int32_t s = group(Skey[si]), r = group(Rkey[rj]);
+                    const int64_t keep_s = (A.Tg[s + 1] - A.Tg[s]) - sent[s];
+                    const int64_t keep_r = A.Tg[r + 1] - A.Tg[r];
+                    seg_tick[G + pos] = A.Tg[s] + keep_s + (a - PS[si]);
+                    seg_dst[G + pos] = off[r] + keep_r + (a - PR[rj]);
+                    seg_len[G + pos] = e - a;
+                    ++pos;
+                }
+            }
+            if (threadIdx.x == 0)
+                L_s = (nm > 0) ? (int)tl : 0;
+        }
+        __syncthreads();
+    }
+    L = L_s;
+    const int nseg = G + L;
+    // 5. copy work items per segment
+    {
+        const int per = (nseg + blockDim.x - 1) / blockDim.x;
+        const int i0 = threadIdx.x * per;
+        uint64_t c = 0, mv = 0;
+        for (int k = 0; k < per; ++k) {
+            const int i = i0 + k;
+            if (i < nseg) {
+                c += (uint64_t)((seg_len[i] + COPY_CHUNK - 1) / COPY_CHUNK);
+                if (i >= G)
+                    mv += (uint64_t)seg_len[i];
+            }
+        }
+        uint64_t tc, tmv;
+        uint64_t run = block_excl_scan_u64(c, red, &tc);
+        block_excl_scan_u64(mv, red, &tmv);
+        for (int k = 0; k < per; ++k) {
+            const int i = i0 + k;
+            if (i < nseg) {
+                A.seg_chunk[i] = (int32_t)run;
+                run += (uint64_t)((seg_len[i] + COPY_CHUNK - 1) / COPY_CHUNK);
+            }
+        }
+        if (threadIdx.x == 0) {
+            A.seg_chunk[nseg] = (int32_t)tc;
+            sum->n_chunks = (int32_t)tc;
+            sum->links = L;
+            sum->moved = (int64_t)tmv;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        A.seg_chunk[2 * G + 1] = nseg;  // remember the segment count
+}
+
+// routing copy: anc[dst + k] = anc_sys[tick + k] for every segment
+__global__ void __launch_bounds__(256) route_copy_kernel(const int32_t *__restrict__ anc_sys,
+                                                         int32_t *__restrict__ anc, int32_t G,
+                                                         const int32_t *__restrict__ seg_chunk,
+                                                         const int64_t *__restrict__ seg_tick,
+                                                         const int64_t *__restrict__ seg_dst,
+                                                         const int64_t *__restrict__ seg_len, int64_t N,
+                                                         DevSummary *__restrict__ sum)
+{
+    __shared__ int32_t sseg;
+    const int32_t b = blockIdx.x;
+    if (b >= sum->n_chunks)
+        return;
+    const int32_t nseg = seg_chunk[2 * G + 1];
+    if (threadIdx.x == 0) {
+        int32_t a = 0, e = nseg - 1;  // last segment with seg_chunk <= b
+        while (a < e) {
+            const int32_t mid = (a + e + 1) >> 1;
+            if (seg_chunk[mid] <= b)
+                a = mid;
+            else
+                e = mid - 1;
+        }
+        sseg = a;
+    }
+    __syncthreads();
+    const int32_t s = sseg;
+    const int64_t k0 = (int64_t)(b - seg_chunk[s]) * COPY_CHUNK;
+    const int64_t len = seg_len[s];
+    const int64_t k1 = (k0 + COPY_CHUNK < len) ? k0 + COPY_CHUNK : len;
+    const int64_t src = seg_tick[s], dst = seg_dst[s];
+    if (src < 0 || dst < 0 || src + k1 > N || dst + k1 > N) {
+        if (threadIdx.x == 0)
+            atomicOr(&sum->flags, FLAG_INTERNAL);  // inconsistent schedule: never write out of bounds
+        return;
+    }
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x)
+        anc[dst + k] = anc_sys[src + k];
+}
+
+// ------------------------------------------------------------------- RNA
+// One block per group: group max, fixed-point weights, local total and group
+// weight (FP64 against the global total of the step), local systematic
+// tickets, then every offspring is written to its slot -- the last `mig`
+// slots of the group go to the tail of the next group of the ring.
+__global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
+    const float *__restrict__ lw, int64_t N, int32_t G, const int64_t *__restrict__ goff, DevSummary *sum,
+    uint64_t seed, uint32_t fid, uint32_t frame, int32_t *__restrict__ anc, float *__restrict__ lwp)
+{
+    const int64_t mig = sum->mig;
+    __shared__ uint64_t C[TILE];
+    __shared__ uint64_t red[33];
+    __shared__ float smf[8];
+    __shared__ double lwg_s;
+    __shared__ uint64_t Qs, us;
+    const int32_t g = blockIdx.x;
+    const int64_t lo = goff[g], sz = goff[g + 1] - lo;
+    if (sz <= 0)
+        return;
+    const int32_t gn = (g + 1) % G;
+    const int64_t gn_lo = goff[gn], gn_sz = goff[gn + 1] - gn_lo;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // pass 1: group maximum
+    float m = -INFINITY;
+    for (int64_t i = threadIdx.x; i < sz; i += blockDim.x)
+        m = fmaxf(m, __ldg(lw + lo + i));
+    m = warp_max(m);
+    if (lane == 0)
+        smf[warp] = m;
+    __syncthreads();
+    float Mg = -INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+        Mg = fmaxf(Mg, smf[w]);
+    __syncthreads();
+    const int s = scale_bits(sz);
+    // pass 2: total fixed-point weight and sum of e^(lw - Mg)
+    uint64_t qs = 0;
+    float es = 0.0f;
+    for (int64_t i = threadIdx.x; i < sz; i += blockDim.x) {
+        const float v = __ldg(lw + lo + i);
+        qs += quantise(v, Mg, s);
+        if (v > -INFINITY)
+            es += __expf(v - Mg);
+    }
+    uint64_t Qg;
+    block_excl_scan_u64(qs, red, &Qg);
+    es = warp_sum(es);
+    if (lane == 0)
+        smf[warp] = es;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float e = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            e += smf[w];
+        Qs = Qg;
+        if (Qg == 0ull) {
+            lwg_s = -INFINITY;
+            us = 0ull;
+        } else {
+            lwg_s = ((double)Mg + log((double)e)) - sum->log_total - log((double)sz);
+            us = ticket_offset(seed, fid, frame, PURPOSE_GROUP, (uint32_t)g, Qg);
+        }
+    }
+    __syncthreads();
+    const uint64_t Q = Qs, u = us;
+    const float lwg = (float)lwg_s;
+    auto dest = [&](int64_t s2) -> int64_t {
+        return (s2 < sz - mig) ? lo + s2 : gn_lo + gn_sz - mig + (s2 - (sz - mig));
+    };
+    if (Q == 0ull) {  // no usable weight in the group: it keeps its slots
+        for (int64_t s2 = threadIdx.x; s2 < sz; s2 += blockDim.x) {
+            const int64_t d = dest(s2);
+            anc[d] = (int32_t)(lo + s2);
+            lwp[d] = lwg;
+        }
+        return;
+    }
+    // pass 3: chunks of TILE particles; the tickets of chunk [c0, c1) are
+    // [T(C_c0), T(C_c1)) with T the local ticket count of n = sz tickets.
+    uint64_t carry = 0;
+    for (int64_t c0 = 0; c0 < sz; c0 += TILE) {
+        const int n = (int)(sz - c0 < TILE ? sz - c0 : TILE);
+        uint64_t q[TILE_ITEMS];
+        tile_weights(lw, lo + c0, n, Mg, s, q);
+        const uint64_t tot = tile_scan(q, C, red);
+        const int64_t j_lo = tickets_below(carry, sz, u, Q);
+        const int64_t j_hi = tickets_below(carry + tot, sz, u, Q);
+        const u128 NN = (u128)(uint64_t)sz;
+        for (int64_t j = j_lo + threadIdx.x; j < j_hi; j += blockDim.x) {
+            const u128 V = (u128)u + (u128)(uint64_t)j * (u128)Q;
+            int a = 0, e = n - 1;
+            while (a < e) {
+                const int mid = (a + e) >> 1;
+                if (NN * (u128)(carry + C[mid]) > V)
+                    e = mid;
+                else
+                    a = mid + 1;
+            }
+            const int64_t d = dest(j);
+            anc[d] = (int32_t)(lo + c0 + a);
+            lwp[d] = lwg;
+        }
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+// RNA set-up: migration count floor(alpha * min_g n_g) and the ring's routing
+// statistics; also clears the degenerate flag (RNA handles empty groups locally).
+__global__ void __launch_bounds__(1024) rna_prep_kernel(const int64_t *__restrict__ goff, int32_t G, float alpha,
+                                                        DevSummary *sum)
+{
+    __shared__ long long smx[32], smn[32];
+    long long mx = 0, mn = INT64_MAX;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        const long long sz = goff[g + 1] - goff[g];
+        mx = sz > mx ? sz : mx;
+        mn = sz < mn ? sz : mn;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long a = __shfl_xor_sync(0xffffffffu, mx, o);
+        const long long b = __shfl_xor_sync(0xffffffffu, mn, o);
+        mx = a > mx ? a : mx;
+        mn = b < mn ? b : mn;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        smx[threadIdx.x >> 5] = mx;
+        smn[threadIdx.x >> 5] = mn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long a = 0, b = INT64_MAX;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a = smx[w] > a ? smx[w] : a;
+            b = smn[w] < b ? smn[w] : b;
+        }
+        const int64_t mig = (int64_t)floor((double)alpha * (double)b);
+        sum->mig = mig;
+        sum->max_group = a;
+        sum->min_group = b;
+        sum->links = (G > 1 && mig > 0) ? G : 0;
+        sum->moved = (G > 1) ? mig * G : 0;
+        sum->degenerate = 0;
+    }
+}
+
+// ancestors / starting log-weights the next step will use
+__global__ void pending_kernel(int64_t N, int mode, const int32_t *__restrict__ anc, const float *__restrict__ lwp,
+                               const float *__restrict__ lw_cur, const int32_t *__restrict__ degenerate,
+                               int32_t *__restrict__ anc_out, float *__restrict__ lwp_out)
+{
+    const int m = (mode != MODE_CARRY && *degenerate) ? MODE_CARRY : mode;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        if (anc_out)
+            anc_out[i] = (m == MODE_CARRY) ? (int32_t)i : anc[i];
+        if (lwp_out)
+            lwp_out[i] = (m == MODE_CARRY) ? lw_cur[i] : (m == MODE_UNIFORM ? 0.0f : lwp[i]);
+    }
+}
+
+__global__ void identity_kernel(int32_t *__restrict__ a, int64_t N)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (int32_t)i;
+}
+
+__global__ void fill_f32_kernel(float *__restrict__ a, int64_t N, float v)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_resample_global(ppf_ctx *c, int scheme)
+{
+    const bool rpa = (scheme != PPF_SYSTEMATIC);
+    const float *lw = c->state[c->cur] + 5 * c->N;
+    const int T = c->T;
+    prof_mark(c, PH_RESAMPLE, 0);
+    c->launches += rpa ? 5 : 3;
+    tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, c->sc.Qt, rpa ? c->goff : nullptr,
+                                                          c->G, c->sc.Cbl);
+    tile_scan_kernel<<<1, 1024, 0, c->stream>>>(c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sum,
+                                                c->m.seed, c->m.filter_id, (uint32_t)c->last_frame,
+                                                c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg);
+    const int max_items = T + (int)((c->N + FILL_CHUNK - 1) / FILL_CHUNK);
+    int32_t *out = rpa ? c->anc_sys : c->anc;
+    fill_kernel<<<max_items, TILE_THREADS, 0, c->stream>>>(lw, c->N, T, c->sum, c->sc.Ct, c->sc.Tt,
+                                                           c->sc.item_off, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !rpa) {
+        prof_mark(c, PH_RESAMPLE, 1);
+        return e;
+    }
+    SchedArgs A;
+    A.N = c->N;
+    A.G = c->G;
+    A.scheme = scheme;
+    A.goff = c->goff;
+    A.goff_new = c->goff_new;
+    A.Tg = c->sc.Tg;
+    A.key = c->sc.skey;
+    A.val = c->sc.sval;
+    A.seg_chunk = c->sc.seg_chunk;
+    A.seg_tick = c->sc.seg_tick;
+    A.seg_dst = c->sc.seg_dst;
+    A.seg_len = c->sc.seg_len;
+    A.sum = c->sum;
+    const size_t smem = sizeof(uint64_t) * MAX_SCHED_GROUPS;
+    static bool attr_set = false;
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(schedule_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        attr_set = true;
+    }
+    schedule_kernel<<<1, 1024, smem, c->stream>>>(A);
+    const int max_chunks = 2 * c->G + 1 + (int)((c->N + COPY_CHUNK - 1) / COPY_CHUNK);
+    route_copy_kernel<<<max_chunks, 256, 0, c->stream>>>(c->anc_sys, c->anc, c->G, c->sc.seg_chunk,
+                                                         c->sc.seg_tick, c->sc.seg_dst, c->sc.seg_len, c->N,
+                                                         c->sum);
+    prof_mark(c, PH_RESAMPLE, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample_rna(ppf_ctx *c, float alpha)
+{
+    const float *lw = c->state[c->cur] + 5 * c->N;
+    prof_mark(c, PH_RESAMPLE, 0);
+    rna_prep_kernel<<<1, 1024, 0, c->stream>>>(c->goff, c->G, alpha, c->sum);
+    rna_kernel<<<c->G, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->G, c->goff, c->sum, c->m.seed,
+                                                     c->m.filter_id, (uint32_t)c->last_frame, c->anc, c->lwp);
+    prof_mark(c, PH_RESAMPLE, 1);
+    c->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pending(ppf_ctx *c, int32_t *anc_out, float *lwp_out)
+{
+    const int grid = (int)((c->N + 255) / 256 < 8192 ? (c->N + 255) / 256 : 8192);
+    c->launches += 1;
+    pending_kernel<<<grid, 256, 0, c->stream>>>(c->N, c->mode, c->anc, c->lwp, c->state[c->cur] + 5 * c->N,
+                                                &c->sum->degenerate, anc_out, lwp_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_identity(ppf_ctx *c, int32_t *dst)
+{
+    const int grid = (int)((c->N + 255) / 256 < 8192 ? (c->N + 255) / 256 : 8192);
+    c->launches += 1;
+    identity_kernel<<<grid, 256, 0, c->stream>>>(dst, c->N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_f32(ppf_ctx *c, float *dst, float v)
+{
+    const int grid = (int)((c->N + 255) / 256 < 8192 ? (c->N + 255) / 256 : 8192);
+    fill_f32_kernel<<<grid, 256, 0, c->stream>>>(dst, c->N, v);
+    return cudaGetLastError();
+}
+
+}  // namespace ppf

@@ -1,0 +1,440 @@
+// ppf_step.cu -- S0 initialisation and the fused SIS step of Alg. 1:
+// propagation (Sec. 7.1 NCV dynamics, bootstrap proposal), patch likelihood
+// (eq. 3 appearance, eq. 4 likelihood over the (2r+1)^2 box S_x) and the
+// normalisation statistics (log-sum-exp partials per block, FP64 total).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+
+#include "ppf_device.cuh"
+#include "ppf_internal.h"
+
+namespace ppf {
+
+// ------------------------------------------------------------------- S0 init
+// Alg. 1 initialisation: equal weights, particles drawn uniformly (Sec. 7.3).
+__global__ void init_kernel(float *__restrict__ st, int64_t N, uint64_t seed, uint32_t fid, float W,
+                            float H, float v0, float A)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 a = draw(seed, (uint32_t)i, 0u, fid, PURPOSE_INIT, 0);
+        const uint4 b = draw(seed, (uint32_t)i, 0u, fid, PURPOSE_INIT, 1);
+        st[i] = -0.5f + W * u01(a.x);
+        st[N + i] = -0.5f + H * u01(a.y);
+        st[2 * N + i] = v0 * (2.0f * u01(a.z) - 1.0f);
+        st[3 * N + i] = v0 * (2.0f * u01(a.w) - 1.0f);
+        st[4 * N + i] = A * (0.5f + u01(b.x));
+        st[5 * N + i] = 0.0f;
+    }
+}
+
+// --------------------------------------------------------- frame preparation
+// Zp = Z - I_bg inside the image, 0 in a border of width pad = 2r, so that a
+// patch anchored up to r pixels outside the image never leaves the buffer.
+template <typename T>
+__device__ __forceinline__ float to_f32(T v);
+template <>
+__device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+
+template <typename T>
+__global__ void prepare_frame_kernel(const T *__restrict__ Z, float *__restrict__ Zp, int W, int H, int Wp,
+                                     int Hp, int pad, float bg)
+{
+    const int n = Wp * Hp;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int py = idx / Wp - pad, px = idx % Wp - pad;
+        float v = 0.0f;
+        if (px >= 0 && px < W && py >= 0 && py < H)
+            v = to_f32<T>(Z[(int64_t)py * W + px]) - bg;
+        Zp[idx] = v;
+    }
+}
+
+// ------------------------------------------------------------ the SIS step
+struct StepArgs {
+    int64_t N;
+    int W, H, Wp, pad;
+    float inv2s2;      // 1 / (2 sigma_PSF^2)
+    float inv_sxi2;    // 1 / sigma_xi^2
+    float sm, sv, sI;
+    uint64_t seed;
+    uint32_t fid, frame;
+    const float *__restrict__ src;
+    float *__restrict__ dst;
+    const int32_t *__restrict__ anc;
+    const float *__restrict__ lwp;
+    const int32_t *__restrict__ degenerate;
+    int32_t *flags;
+    int mode;
+    const float *__restrict__ Zp;
+    Partial *__restrict__ part;
+};
+
+// Online log-sum-exp accumulator of the weight statistics.
+struct Acc {
+    float m, s0, s[5], s2, mp, sp;
+    __device__ __forceinline__ void init()
+    {
+        m = mp = -INFINITY;
+        s0 = s2 = sp = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+            s[c] = 0.0f;
+    }
+    __device__ __forceinline__ void add(float lw, float lwp, const float v[5])
+    {
+        if (lw > m) {
+            const float sc = __expf(m - lw);
+            s0 *= sc;
+            s2 *= sc * sc;
+#pragma unroll
+            for (int c = 0; c < 5; ++c)
+                s[c] *= sc;
+            m = lw;
+        }
+        if (lw > -INFINITY) {
+            const float e = __expf(lw - m);
+            s0 += e;
+            s2 = fmaf(e, e, s2);
+#pragma unroll
+            for (int c = 0; c < 5; ++c)
+                s[c] = fmaf(e, v[c], s[c]);
+        }
+        if (lwp > mp) {
+            sp *= __expf(mp - lwp);
+            mp = lwp;
+        }
+        if (lwp > -INFINITY)
+            sp += __expf(lwp - mp);
+    }
+    __device__ __forceinline__ void merge(const Acc &o)
+    {
+        const float nm = fmaxf(m, o.m);
+        const float fa = (m == -INFINITY) ? 0.0f : __expf(m - nm);
+        const float fb = (o.m == -INFINITY) ? 0.0f : __expf(o.m - nm);
+        s0 = s0 * fa + o.s0 * fb;
+        s2 = s2 * fa * fa + o.s2 * fb * fb;
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+            s[c] = s[c] * fa + o.s[c] * fb;
+        m = (nm == -INFINITY) ? -INFINITY : nm;
+        const float nmp = fmaxf(mp, o.mp);
+        const float ga = (mp == -INFINITY) ? 0.0f : __expf(mp - nmp);
+        const float gb = (o.mp == -INFINITY) ? 0.0f : __expf(o.mp - nmp);
+        sp = sp * ga + o.sp * gb;
+        mp = nmp;
+    }
+    __device__ __forceinline__ void shfl_merge(int o)
+    {
+        Acc b;
+        b.m = __shfl_xor_sync(0xffffffffu, m, o);
+        b.s0 = __shfl_xor_sync(0xffffffffu, s0, o);
+        b.s2 = __shfl_xor_sync(0xffffffffu, s2, o);
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+            b.s[c] = __shfl_xor_sync(0xffffffffu, s[c], o);
+        b.mp = __shfl_xor_sync(0xffffffffu, mp, o);
+        b.sp = __shfl_xor_sync(0xffffffffu, sp, o);
+        merge(b);
+    }
+};
+
+// Eq. 4 over S_x with the eq. 3 model, pixels outside S_x modelled as
+// background: l = -sum_{S_x} [(Zb - a)^2 - Zb^2] / (2 sigma_xi^2) with
+// Zb = Z - I_bg and a = I0 g, g separable: g = gx(col) gy(row).  Expanded,
+// l = I0 (B - I0 C / 2) / sigma_xi^2 with B = sum gy_j sum_i gx_i Zb and
+// C = sum gx_i^2 sum gy_j^2 (masks make pixels outside the image vanish).
+template <int R>
+__device__ __forceinline__ float patch_loglik(const StepArgs &a, float x, float y, float I0)
+{
+    if (!isfinite(x) || !isfinite(y) || !isfinite(I0))
+        return -INFINITY;
+    const float cxf = floorf(x + 0.5f), cyf = floorf(y + 0.5f);
+    if (cxf < -(float)R || cxf > (float)(a.W - 1 + R) || cyf < -(float)R || cyf > (float)(a.H - 1 + R))
+        return 0.0f;
+    const int cx = (int)cxf, cy = (int)cyf;
+    const float fx = cxf - x, fy = cyf - y;
+    constexpr int P = 2 * R + 1;
+    float gx[P];
+    float sxx = 0.0f, syy = 0.0f;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        const float d = fx + (float)(i - R);
+        float g = expf(-d * d * a.inv2s2);
+        const int px = cx + i - R;
+        g = (px >= 0 && px < a.W) ? g : 0.0f;
+        gx[i] = g;
+        sxx = fmaf(g, g, sxx);
+    }
+    const float *row = a.Zp + (int64_t)(cy - R + a.pad) * a.Wp + (cx - R + a.pad);
+    float B = 0.0f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const float d = fy + (float)(j - R);
+        float g = expf(-d * d * a.inv2s2);
+        const int py = cy + j - R;
+        g = (py >= 0 && py < a.H) ? g : 0.0f;
+        syy = fmaf(g, g, syy);
+        float rj = 0.0f;
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+            rj = fmaf(gx[i], __ldg(row + i), rj);
+        B = fmaf(g, rj, B);
+        row += a.Wp;
+    }
+    const float C = sxx * syy;
+    return I0 * fmaf(-0.5f * I0, C, B) * a.inv_sxi2;
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) step_kernel(StepArgs a)
+{
+    int mode = a.mode;
+    if (mode != MODE_CARRY && *a.degenerate)
+        mode = MODE_CARRY;  // the last resample kept every particle
+    const int64_t N = a.N;
+    Acc acc;
+    acc.init();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = (mode == MODE_CARRY) ? i : (int64_t)__ldg(a.anc + i);
+        if ((uint64_t)p >= (uint64_t)N) {  // caller-supplied ancestors are checked, never trusted
+            atomicOr(a.flags, FLAG_BAD_ANCESTOR);
+            p = i;
+        }
+        const float x = __ldg(a.src + p), y = __ldg(a.src + N + p);
+        const float vx = __ldg(a.src + 2 * N + p), vy = __ldg(a.src + 3 * N + p);
+        const float I0 = __ldg(a.src + 4 * N + p);
+        float lwp;
+        if (mode == MODE_CARRY)
+            lwp = __ldg(a.src + 5 * N + p);
+        else if (mode == MODE_UNIFORM)
+            lwp = 0.0f;
+        else
+            lwp = __ldg(a.lwp + i);
+        const uint4 r0 = draw(a.seed, (uint32_t)i, a.frame, a.fid, PURPOSE_PROP, 0);
+        const uint4 r1 = draw(a.seed, (uint32_t)i, a.frame, a.fid, PURPOSE_PROP, 1);
+        float e0, e1, e2, e3, e4, e5;
+        box_muller(r0.x, r0.y, e0, e1);
+        box_muller(r0.z, r0.w, e2, e3);
+        box_muller(r1.x, r1.y, e4, e5);
+        float v[5];
+        v[0] = fmaf(a.sm, e0, x + vx);
+        v[1] = fmaf(a.sm, e1, y + vy);
+        v[2] = fmaf(a.sv, e2, vx);
+        v[3] = fmaf(a.sv, e3, vy);
+        v[4] = fmaf(a.sI, e4, I0);
+        const float l = patch_loglik<R>(a, v[0], v[1], v[4]);
+        const float lw = lwp + l;
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+            a.dst[c * N + i] = v[c];
+        a.dst[5 * N + i] = lw;
+        acc.add(lw, lwp, v);
+    }
+    // block reduction of the partial statistics
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        acc.shfl_merge(o);
+    __shared__ Acc sh[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        sh[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        if (lane < nw)
+            acc = sh[lane];
+        else
+            acc.init();
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1)
+            acc.shfl_merge(o);
+        if (lane == 0) {
+            Partial q;
+            q.m = acc.m;
+            q.s0 = acc.s0;
+            q.s2 = acc.s2;
+#pragma unroll
+            for (int c = 0; c < 5; ++c)
+                q.s[c] = acc.s[c];
+            q.mp = acc.mp;
+            q.sp = acc.sp;
+            a.part[blockIdx.x] = q;
+        }
+    }
+}
+
+// --------------------------------------------------------------- finalise
+// Cross-block totals in FP64 (the paper's global sum for normalisation):
+// estimate, N_eff, log-evidence.
+__global__ void __launch_bounds__(1024) finalize_kernel(const Partial *__restrict__ part, int n,
+                                                        DevSummary *sum, int32_t frame)
+{
+    __shared__ float smf[32];
+    __shared__ double smd[32][9];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float m = -INFINITY, mp = -INFINITY;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        m = fmaxf(m, part[b].m);
+        mp = fmaxf(mp, part[b].mp);
+    }
+    m = warp_max(m);
+    if (lane == 0)
+        smf[warp] = m;
+    __syncthreads();
+    float M = -INFINITY;
+    for (int w = 0; w < nw; ++w)
+        M = fmaxf(M, smf[w]);
+    __syncthreads();
+    mp = warp_max(mp);
+    if (lane == 0)
+        smf[warp] = mp;
+    __syncthreads();
+    float Mp = -INFINITY;
+    for (int w = 0; w < nw; ++w)
+        Mp = fmaxf(Mp, smf[w]);
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // s0, s[5], s2, sp
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        const Partial q = part[b];
+        if (q.m > -INFINITY) {
+            const double f = exp((double)q.m - (double)M);
+            acc[0] += q.s0 * f;
+            for (int c = 0; c < 5; ++c)
+                acc[1 + c] += q.s[c] * f;
+            acc[6] += q.s2 * f * f;
+        }
+        if (q.mp > -INFINITY)
+            acc[7] += q.sp * exp((double)q.mp - (double)Mp);
+    }
+    for (int c = 0; c < 8; ++c)
+        acc[c] = warp_sum_d(acc[c]);
+    if (lane == 0)
+        for (int c = 0; c < 8; ++c)
+            smd[warp][c] = acc[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < nw; ++w)
+            for (int c = 0; c < 8; ++c)
+                t[c] += smd[w][c];
+        for (int c = 0; c < 5; ++c)
+            sum->mean[c] = t[1 + c] / t[0];
+        sum->ess = t[0] * t[0] / t[6];
+        sum->log_total = (double)M + log(t[0]);
+        sum->log_evidence = sum->log_total - ((double)Mp + log(t[7]));
+        sum->max_lw = (double)M;
+        sum->M = M;
+        sum->frame = frame;
+        if (!(t[0] > 0.0))
+            sum->flags |= FLAG_DEGENERATE;
+    }
+}
+
+// --------------------------------------------------------------- launchers
+int step_grid(ppf_ctx *c)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<5>, 256, 0);
+    if (per_sm < 1)
+        per_sm = 1;
+    int64_t need = (c->N + 255) / 256;
+    int64_t g = (int64_t)c->num_sms * per_sm;
+    return (int)(need < g ? need : g);
+}
+
+cudaError_t launch_init(ppf_ctx *c)
+{
+    const int grid = (int)((c->N + 255) / 256 < 65536 ? (c->N + 255) / 256 : 65536);
+    init_kernel<<<grid, 256, 0, c->stream>>>(c->state[c->cur], c->N, c->m.seed, c->m.filter_id,
+                                              (float)c->m.width, (float)c->m.height, c->m.v0_max,
+                                              c->m.amplitude);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_frame(ppf_ctx *c, const void *frame)
+{
+    prof_mark(c, PH_PREPARE, 0);
+    c->launches += 1;
+    const int n = c->Wp * c->Hp;
+    const int grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    const float bg = c->m.background;
+    switch (c->m.frame_dtype) {
+    case PPF_BF16:
+        prepare_frame_kernel<__nv_bfloat16><<<grid, 256, 0, c->stream>>>(
+            (const __nv_bfloat16 *)frame, c->Zp, c->m.width, c->m.height, c->Wp, c->Hp, c->pad, bg);
+        break;
+    case PPF_F16:
+        prepare_frame_kernel<__half><<<grid, 256, 0, c->stream>>>(
+            (const __half *)frame, c->Zp, c->m.width, c->m.height, c->Wp, c->Hp, c->pad, bg);
+        break;
+    default:
+        prepare_frame_kernel<float><<<grid, 256, 0, c->stream>>>(
+            (const float *)frame, c->Zp, c->m.width, c->m.height, c->Wp, c->Hp, c->pad, bg);
+    }
+    prof_mark(c, PH_PREPARE, 1);
+    return cudaGetLastError();
+}
+
+template <int R>
+static void launch_step_r(const StepArgs &a, int grid, cudaStream_t s)
+{
+    step_kernel<R><<<grid, 256, 0, s>>>(a);
+}
+
+cudaError_t launch_step(ppf_ctx *c, int32_t k)
+{
+    StepArgs a;
+    a.N = c->N;
+    a.W = c->m.width;
+    a.H = c->m.height;
+    a.Wp = c->Wp;
+    a.pad = c->pad;
+    a.inv2s2 = 1.0f / (2.0f * c->m.psf_sigma * c->m.psf_sigma);
+    a.inv_sxi2 = 1.0f / (c->m.sigma_xi * c->m.sigma_xi);
+    a.sm = c->m.sigma_m;
+    a.sv = c->m.sigma_v;
+    a.sI = c->m.sigma_I;
+    a.seed = c->m.seed;
+    a.fid = c->m.filter_id;
+    a.frame = (uint32_t)k;
+    a.src = c->state[c->cur];
+    a.dst = c->state[c->cur ^ 1];
+    a.anc = c->anc;
+    a.lwp = c->lwp;
+    a.degenerate = &c->sum->degenerate;
+    a.flags = &c->sum->flags;
+    a.mode = c->mode;
+    a.Zp = c->Zp;
+    a.part = c->part;
+    const int grid = step_grid(c);
+    prof_mark(c, PH_STEP, 0);
+    switch (c->m.patch_radius) {
+    case 0: launch_step_r<0>(a, grid, c->stream); break;
+    case 1: launch_step_r<1>(a, grid, c->stream); break;
+    case 2: launch_step_r<2>(a, grid, c->stream); break;
+    case 3: launch_step_r<3>(a, grid, c->stream); break;
+    case 4: launch_step_r<4>(a, grid, c->stream); break;
+    case 5: launch_step_r<5>(a, grid, c->stream); break;
+    case 6: launch_step_r<6>(a, grid, c->stream); break;
+    case 7: launch_step_r<7>(a, grid, c->stream); break;
+    default: launch_step_r<8>(a, grid, c->stream); break;
+    }
+    prof_mark(c, PH_STEP, 1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    prof_mark(c, PH_FINALIZE, 0);
+    finalize_kernel<<<1, 1024, 0, c->stream>>>(c->part, grid, c->sum, k);
+    prof_mark(c, PH_FINALIZE, 1);
+    c->launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace ppf

@@ -1,0 +1,167 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs (tolerances derived in tests/gpu_common.py)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ppf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1310_5045_gb300 as p
+    p.load()
+    return p
+
+
+@pytest.fixture(scope="module")
+def movie():
+    return synth.make_movie(W=128, H=128, K=6, sigma=1.5, amplitude=50.0, background=10.0, seed=0)
+
+
+def gpu_frames(movie, dtype=None):
+    import torch
+    t = torch.from_numpy(movie.frames).cuda()
+    return t if dtype is None else t.to(dtype)
+
+
+def test_init_matches_oracle(ppf):
+    from gpu_common import paired_models
+    gm, om = paired_models(ppf, width=100, height=77, v0_max=0.75, amplitude=20.0)
+    N = 10001
+    pf = ppf.ParticleFilter(gm, N, group_size=1000)
+    st, anc, lwp = pf.get_particles(state=True, anc=True, lw_prev=True)
+    ref = orc.init(om, N)
+    got = st.cpu().double().numpy()
+    assert np.allclose(got, ref, rtol=2e-7, atol=1e-7)
+    assert np.array_equal(anc.cpu().numpy(), np.arange(N))
+    assert np.all(lwp.cpu().numpy() == 0.0)
+    pf.close()
+
+
+@pytest.mark.parametrize("scheme", [orc.SYSTEMATIC, orc.RPA_GS, orc.RPA_SGS, orc.RPA_LGS, orc.RNA])
+@pytest.mark.parametrize("N,gs", [(16384, 4096), (10000, 777)])
+def test_lockstep_frames(ppf, movie, scheme, N, gs):
+    from gpu_common import lockstep, paired_models
+    gm, om = paired_models(ppf, seed=3)
+    pf = ppf.ParticleFilter(gm, N, group_size=gs)
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), scheme, K=6, alpha=0.25)
+    pf.close()
+
+
+@pytest.mark.parametrize("r", [0, 1, 5, 8])
+def test_patch_radius_and_ragged_tile(ppf, movie, r):
+    from gpu_common import lockstep, paired_models
+    gm, om = paired_models(ppf, patch_radius=r, seed=5)
+    pf = ppf.ParticleFilter(gm, 4097, group_size=4097)
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), orc.SYSTEMATIC, K=3)
+    pf.close()
+
+
+def test_single_particle(ppf, movie):
+    from gpu_common import lockstep, paired_models
+    gm, om = paired_models(ppf, seed=1)
+    pf = ppf.ParticleFilter(gm, 1, group_size=1)
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), orc.RPA_LGS, K=3)
+    pf.close()
+
+
+@pytest.mark.parametrize("dtype_name", ["bfloat16", "float16"])
+def test_reduced_precision_frames(ppf, movie, dtype_name):
+    """Frames stored in BF16 / FP16; the oracle sees the same stored values."""
+    import torch
+    from gpu_common import lockstep, paired_models
+    dt = getattr(torch, dtype_name)
+    gm, om = paired_models(ppf, seed=2, frame_dtype=ppf.BF16 if dtype_name == "bfloat16" else ppf.F16)
+    fr = gpu_frames(movie, dt)
+    stored = fr.float().cpu().numpy()
+    pf = ppf.ParticleFilter(gm, 8192, group_size=2048)
+    lockstep(pf, gm, om, stored, fr, orc.SYSTEMATIC, K=4)
+    pf.close()
+
+
+def test_sis_without_resampling_carries_weights(ppf, movie):
+    from gpu_common import lockstep, paired_models
+    gm, om = paired_models(ppf, seed=4)
+    pf = ppf.ParticleFilter(gm, 3000, group_size=1000)
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), None, K=3)
+    pf.close()
+
+
+def test_particles_outside_image(ppf, movie):
+    """Particles whose patch leaves the image: partial patches and empty sums."""
+    import torch
+    from gpu_common import lockstep, paired_models
+    gm, om = paired_models(ppf, seed=6, sigma_m=0.0, sigma_v=0.0, sigma_I=0.0)
+    N = 2048
+    rng = np.random.default_rng(0)
+    st = np.zeros((6, N), dtype=np.float32)
+    st[0] = rng.uniform(-14, 142, N)
+    st[1] = rng.uniform(-14, 142, N)
+    st[4] = rng.uniform(10, 80, N)
+    st[0, :4] = [np.nan, np.inf, 1e30, -1e30]
+    pf = ppf.ParticleFilter(gm, N, group_size=512)
+    pf.set_particles(torch.from_numpy(st))
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), orc.SYSTEMATIC, K=2)
+    pf.close()
+
+
+def test_degenerate_weights_keep_particles(ppf, movie):
+    import torch
+    from gpu_common import paired_models
+    gm, om = paired_models(ppf)
+    N = 5000
+    pf = ppf.ParticleFilter(gm, N, group_size=1000)
+    st, _, _ = pf.get_particles()
+    pf.set_particles(st, lw_prev=torch.full((N,), float("nan")))
+    pf.step(gpu_frames(movie)[0], 1)
+    e = pf.estimate()
+    assert e.status == ppf.EDEGENERATE
+    before, _, _ = pf.get_particles()
+    pf.resample(ppf.SYSTEMATIC)
+    e = pf.estimate()
+    assert e.status == ppf.EDEGENERATE
+    _, anc, lwp = pf.get_particles(state=False, anc=True, lw_prev=True)
+    assert np.array_equal(anc.cpu().numpy(), np.arange(N))
+    assert torch.isnan(lwp).all()
+    assert pf.estimate().status == ppf.OK  # flags are cleared once reported
+    pf.close()
+
+
+def test_state_errors(ppf):
+    from gpu_common import paired_models
+    gm, _ = paired_models(ppf)
+    pf = ppf.ParticleFilter(gm, 100, group_size=10)
+    with pytest.raises(ppf.PPFError) as e:
+        pf.resample(ppf.SYSTEMATIC)
+    assert e.value.status == ppf.ESTATE
+    with pytest.raises(ppf.PPFError) as e:
+        pf.estimate(raise_on_flags=True)
+    assert e.value.status == ppf.ESTATE
+    pf.close()
+
+
+def test_free_running_tracks_the_spot(ppf):
+    """End to end (no lockstep): the GPU filter tracks the synthetic spot."""
+    import torch
+    from gpu_common import paired_models
+    mv = synth.make_movie(W=128, H=128, K=20, sigma=1.5, amplitude=50.0, background=10.0, seed=0)
+    gm, om = paired_models(ppf, seed=0, sigma_xi=math.sqrt(200.0))
+    fr = torch.from_numpy(mv.frames).cuda()
+    pf = ppf.ParticleFilter(gm, 16384, group_size=4096)
+    est = []
+    for k in range(1, 21):
+        pf.step(fr[k - 1], k)
+        est.append(pf.estimate().mean)
+        pf.resample(ppf.SYSTEMATIC)
+    est = np.array(est)
+    err = est[5:, :2] - mv.truth[5:, :2]
+    assert np.sqrt((err ** 2).sum(1).mean()) < 0.5
+    pf.close()

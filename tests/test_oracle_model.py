@@ -168,3 +168,33 @@ def test_summary_special_cases(orc):
     s = orc.summary(st, np.zeros(N))
     assert s["ess"] == 1.0 and s["mean"][0] == 17.0
     assert s["log_evidence"] == pytest.approx(2.0 - math.log(N), abs=1e-13)
+
+
+def test_sampled_propagation_and_likelihood_match_full(orc):
+    """The per-slot helpers used at full size equal the whole-array routines."""
+    m = model(orc, sigma_m=0.4, sigma_v=0.1, sigma_I=0.7)
+    rng = np.random.default_rng(9)
+    N = 300
+    parent = rng.normal(size=(6, N)) * [[4], [4], [1], [1], [5], [1]] + [[15], [11], [0], [0], [30], [0]]
+    anc = rng.integers(0, N, size=N).astype(np.int32)
+    full = orc.propagate(m, 6, parent, anc, np.zeros(N))
+    slots = np.array([0, 7, 299, 123])
+    got = orc.propagate_slots(m, 6, slots, parent[:5, anc[slots]])
+    assert np.array_equal(got, full[:5, slots])
+    Z = rng.poisson(12.0, size=(m.height, m.width)).astype(np.float64)
+    l = orc.loglik_many(m, Z, full[0], full[1], full[4])
+    w = orc.weight(m, Z, full)
+    assert np.array_equal(l, w[5] - full[5])
+
+
+def test_summary_ignores_zero_weight_particles(orc):
+    """Zero-weight particles (lw = -inf or NaN) are outside the weighted-sample
+    approximation: their state, even non-finite, does not enter the estimate."""
+    N = 6
+    st = np.zeros((6, N))
+    st[0] = [1.0, 3.0, np.inf, np.nan, 1e300, 5.0]
+    st[5] = [0.0, 0.0, -np.inf, np.nan, -1e6, -np.inf]
+    s = orc.summary(st, np.zeros(N))
+    assert s["mean"][0] == pytest.approx(2.0, abs=1e-12)
+    assert s["ess"] == pytest.approx(2.0, rel=1e-12)
+    assert s["log_evidence"] == pytest.approx(math.log(2.0) - math.log(6.0), abs=1e-12)
