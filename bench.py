@@ -178,7 +178,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     n = args.n
     K, Wm = args.steps, args.warmup
-    extra = 0 if args.no_schemes else 5 * (args.scheme_steps + 2)
+    extra = 0 if args.no_schemes else 6 * (args.scheme_steps + 2)
     k_total = Wm + K + extra + (args.e2e_steps if not args.no_e2e else 0) + 2
     mv, params = make_workload(k_total, seed=0)
     model = ppf.Model(**params, seed=rank, filter_id=rank)

@@ -91,6 +91,8 @@ def lib():
             sig = {
                 "orc_philox": (None, [u32p, u32p, u32p]),
                 "orc_u01": (C.c_double, [C.c_uint32]),
+                "orc_u21": (C.c_double, [C.c_uint32]),
+                "orc_prop_fields": (None, [u32p, u32p]),
                 "orc_normals5": (None, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, dp]),
                 "orc_init": (None, [mp, C.c_int64, dp]),
                 "orc_propagate": (None, [mp, C.c_int64, C.c_int32, dp, i32p, dp, dp]),
@@ -139,6 +141,17 @@ def philox(ctr, key) -> np.ndarray:
 
 def u01(r: int) -> float:
     return lib().orc_u01(int(r))
+
+
+def u21(field: int) -> float:
+    return lib().orc_u21(int(field))
+
+
+def prop_fields(words) -> np.ndarray:
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    f = np.zeros(6, dtype=np.uint32)
+    lib().orc_prop_fields(_p(w, C.c_uint32), _p(f, C.c_uint32))
+    return f
 
 
 def normals5(seed: int, slot: int, frame: int, filter_id: int = 0) -> np.ndarray:

@@ -37,7 +37,9 @@
  *     winning with an empty sum.)
  *   - random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
  *     key = (seed_lo, seed_hi), counter = (index, frame, filter, purpose<<8|block);
- *     uniform u = (2*(r>>9)+1) * 2^-24 (exact in float32); Box-Muller normals.
+ *     prior uniforms u = (2*(r>>9)+1) * 2^-24 from 32-bit words; propagation
+ *     uniforms from six 21-bit fields of one block, u = (2 f + 1) 2^-22 (both
+ *     exact in float32); Box-Muller normals.
  *   - resampling weights: q_i = floor(2^(s + t_i)) with t_i = (lw_i - M) log2 e,
  *     evaluated in float32 by a fixed operation sequence (a float decides an
  *     integer here, so the oracle takes that decision in the kernel's float32
@@ -101,10 +103,26 @@ double orc_u01(uint32_t r)
     return (double)(2u * (r >> 9) + 1u) * (1.0 / 16777216.0);
 }
 
-static void box_muller(uint32_t r1, uint32_t r2, double *z0, double *z1)
+/* The propagation noise of one slot comes from one Philox block: its 128 bits
+ * (word 0 least significant) are cut into six 21-bit fields, field k holding
+ * bits [21k, 21k + 21); each becomes u = (2 field + 1) 2^-22 (exact in float32)
+ * and the three Box-Muller pairs (u0,u1), (u2,u3), (u4,u5) give the normals. */
+double orc_u21(uint32_t field)
+{
+    return (double)(2u * (field & 0x1FFFFFu) + 1u) * (1.0 / 4194304.0);
+}
+
+void orc_prop_fields(const uint32_t r[4], uint32_t f[6])
+{
+    unsigned __int128 b = (unsigned __int128)r[0] | ((unsigned __int128)r[1] << 32) |
+                          ((unsigned __int128)r[2] << 64) | ((unsigned __int128)r[3] << 96);
+    for (int k = 0; k < 6; ++k)
+        f[k] = (uint32_t)((b >> (21 * k)) & 0x1FFFFFu);
+}
+
+static void box_muller_u(double u1, double u2, double *z0, double *z1)
 {
     const double two_pi = 6.283185307179586476925286766559;
-    double u1 = orc_u01(r1), u2 = orc_u01(r2);
     double rho = sqrt(-2.0 * log(u1));
     *z0 = rho * cos(two_pi * u2);
     *z1 = rho * sin(two_pi * u2);
@@ -112,13 +130,13 @@ static void box_muller(uint32_t r1, uint32_t r2, double *z0, double *z1)
 
 void orc_normals5(uint64_t seed, uint32_t slot, uint32_t frame, uint32_t filter, double e[5])
 {
-    uint32_t a[4], b[4];
-    draw(seed, slot, frame, filter, ORC_PURPOSE_PROP, 0, a);
-    draw(seed, slot, frame, filter, ORC_PURPOSE_PROP, 1, b);
+    uint32_t r[4], f[6];
+    draw(seed, slot, frame, filter, ORC_PURPOSE_PROP, 0, r);
+    orc_prop_fields(r, f);
     double spare;
-    box_muller(a[0], a[1], &e[0], &e[1]);
-    box_muller(a[2], a[3], &e[2], &e[3]);
-    box_muller(b[0], b[1], &e[4], &spare);
+    box_muller_u(orc_u21(f[0]), orc_u21(f[1]), &e[0], &e[1]);
+    box_muller_u(orc_u21(f[2]), orc_u21(f[3]), &e[2], &e[3]);
+    box_muller_u(orc_u21(f[4]), orc_u21(f[5]), &e[4], &spare);
 }
 
 /* ------------------------------------------------------------------------ */

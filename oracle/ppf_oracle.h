@@ -21,6 +21,8 @@ typedef struct {
 
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_u01(uint32_t r);
+double orc_u21(uint32_t field);
+void orc_prop_fields(const uint32_t r[4], uint32_t f[6]);
 void orc_normals5(uint64_t seed, uint32_t slot, uint32_t frame, uint32_t filter, double e[5]);
 void orc_init(const orc_model *m, int64_t N, double *st);
 void orc_propagate(const orc_model *m, int64_t N, int32_t frame, const double *par,

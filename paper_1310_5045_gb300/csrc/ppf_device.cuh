@@ -2,8 +2,10 @@
 //
 // Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
 // numbers: as easy as 1, 2, 3", SC'11), keyed by the model seed, counter
-// (index, frame, filter, purpose << 8 | block).  Uniforms are odd multiples of
-// 2^-24 (exact in float32), normals by the Box-Muller transform.
+// (index, frame, filter, purpose << 8 | block).  Prior uniforms are odd
+// multiples of 2^-24 from 32-bit words; the propagation noise takes six 21-bit
+// fields of one block as odd multiples of 2^-22 (all exact in float32);
+// normals by the Box-Muller transform.
 //
 // Resampling weights (Alg. 1 resampling step) are 64-bit fixed point:
 // q = floor(2^(s + t)), t = (lw - M) log2(e), computed by one fixed float32
@@ -51,14 +53,36 @@ __device__ __forceinline__ float u01(uint32_t r)
     return __uint2float_rn(2u * (r >> 9) + 1u) * 0x1p-24f;
 }
 
-__device__ __forceinline__ void box_muller(uint32_t r1, uint32_t r2, float &z0, float &z1)
+// odd multiple of 2^-22 in (0, 1) from a 21-bit field; exact in float32
+__device__ __forceinline__ float u21(uint32_t f)
 {
-    const float u1 = u01(r1), u2 = u01(r2);
+    return __uint2float_rn(2u * f + 1u) * 0x1p-22f;
+}
+
+// The six 21-bit fields of one Philox block (word 0 least significant):
+// field k holds bits [21k, 21k + 21) of the 128-bit block.
+__device__ __forceinline__ void prop_fields(uint4 r, uint32_t f[6])
+{
+    const uint64_t lo = (uint64_t)r.x | ((uint64_t)r.y << 32);
+    const uint64_t hi = (uint64_t)r.z | ((uint64_t)r.w << 32);
+    const uint64_t m = 0x1FFFFFull;
+    f[0] = (uint32_t)(lo & m);
+    f[1] = (uint32_t)((lo >> 21) & m);
+    f[2] = (uint32_t)((lo >> 42) & m);
+    f[3] = (uint32_t)(((lo >> 63) | (hi << 1)) & m);
+    f[4] = (uint32_t)((hi >> 20) & m);
+    f[5] = (uint32_t)((hi >> 41) & m);
+}
+
+// Box-Muller: rho = sqrt(-2 ln u1) (accurate log: u1 -> 1 needs it), angle
+// 2 pi u2 = theta + pi with theta in (-pi, pi) for the hardware sine/cosine.
+__device__ __forceinline__ void box_muller(float u1, float u2, float &z0, float &z1)
+{
     const float rho = sqrtf(-2.0f * logf(u1));
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    z0 = rho * c;
-    z1 = rho * s;
+    __sincosf(__fmaf_rn(6.28318530717958647692f, u2, -3.14159265358979323846f), &s, &c);
+    z0 = -rho * c;
+    z1 = -rho * s;
 }
 
 // ceil(log2 n) complement: s = 63 - ceil(log2 n), so that n * 2^s <= 2^63
@@ -108,30 +132,41 @@ __device__ __forceinline__ uint64_t quantise(float lw, float M, int s)
 
 // Number of systematic tickets below cumulative weight c:
 // #{j in [0, n) : u + j Q < n c} = clamp(ceil((n c - u) / Q), 0, n).
-// The quotient is estimated in double and made exact with 128-bit corrections.
+// Exact integer result: the quotient (at most n < 2^31) is estimated twice
+// with a float reciprocal of Q (the second time on the remainder) and then
+// corrected with 128-bit arithmetic.
+__device__ __forceinline__ float u128_to_float(u128 v)
+{
+    return (float)(uint64_t)(v >> 64) * 18446744073709551616.0f + (float)(uint64_t)v;
+}
+
 __device__ __forceinline__ int64_t tickets_below(uint64_t c, int64_t n, uint64_t u, uint64_t Q)
 {
+    typedef __int128 s128;
     const u128 nc = (u128)c * (u128)(uint64_t)n;
     if (nc <= (u128)u)
         return 0;
     const u128 num = nc - (u128)u;
-    const double est = ((double)(uint64_t)(num >> 64) * 18446744073709551616.0 + (double)(uint64_t)num) /
-                       (double)Q;
-    if (est > (double)n + 2.0)
+    if (num > (u128)Q * (u128)(uint64_t)n)
         return n;
-    uint64_t qh = (uint64_t)est;
-    u128 prod = (u128)qh * (u128)Q;
-    while (prod > num) {
-        --qh;
-        prod -= Q;
+    const float rq = 1.0f / (float)Q;
+    int64_t q = (int64_t)(u128_to_float(num) * rq);
+    s128 r = (s128)num - (s128)q * (s128)Q;
+    const float rf = (r < 0) ? -u128_to_float((u128)(-r)) : u128_to_float((u128)r);
+    const int64_t dq = (int64_t)floorf(rf * rq);
+    q += dq;
+    r -= (s128)dq * (s128)Q;
+    while (r < 0) {
+        --q;
+        r += (s128)Q;
     }
-    while (num - prod >= (u128)Q) {
-        ++qh;
-        prod += Q;
+    while (r >= (s128)Q) {
+        ++q;
+        r -= (s128)Q;
     }
-    if (num != prod)
-        ++qh;
-    return qh > (uint64_t)n ? n : (int64_t)qh;
+    if (r != 0)
+        ++q;
+    return q > n ? n : q;
 }
 
 // u = floor(r64 * Q / 2^64): a uniform ticket offset in [0, Q)

@@ -4,14 +4,15 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/ppf.h"
+#include "ppf.h"  // include/ppf.h (the build passes -I include)
 
 namespace ppf {
 
 constexpr int TILE = 4096;          // particles per resampling tile (256 threads x 16)
 constexpr int TILE_THREADS = 256;
 constexpr int TILE_ITEMS = TILE / TILE_THREADS;
-constexpr int FILL_CHUNK = 4096;    // tickets per fill work item
+constexpr int FILL_CHUNK = 2048;    // tickets per fill pass (8 per thread)
+constexpr int ITEM_TICKETS = 8192;  // tickets per fill work item (4 passes)
 constexpr int COPY_CHUNK = 2048;    // slots per routing-copy work item
 constexpr int MAX_RADIUS = 8;
 constexpr int MAX_SCHED_GROUPS = 16384;
@@ -46,6 +47,7 @@ struct DevSummary {
     int32_t n_items;           // fill work items of the last resample
     int32_t n_chunks;          // routing-copy work items of the last RPA resample
     int64_t mig;               // RNA: slots migrating to the next group
+    uint32_t blocks_done;      // step kernel: blocks that published partials
 };
 
 struct Scratch {

@@ -19,19 +19,31 @@
 
 namespace ppf {
 
-// Load one tile's quantised weights: thread t owns items [16t, 16t+16).
+// Shared-memory layout of one tile: the float32 weights are staged with one
+// pad word per 32 (thread t then reads its 16 consecutive weights without bank
+// conflicts) and the u64 inclusive sums with one pad per 16 (conflict-free for
+// the per-thread writes); both live in the same buffer, one after the other.
+__device__ __forceinline__ int padf(int i) { return i + (i >> 5); }
+__device__ __forceinline__ int padc(int i) { return i + (i >> 4); }
+constexpr int TILE_SMEM_U64 = TILE + TILE / 16;  // >= (TILE + TILE/32) / 2 floats
+
+// Quantised weights of particles [lo, lo + n): coalesced loads into smem, then
+// thread t takes items [16t, 16t + 16).  q = 0 beyond n.
 __device__ __forceinline__ void tile_weights(const float *__restrict__ lw, int64_t lo, int n, float M, int s,
-                                             uint64_t q[TILE_ITEMS])
+                                             uint64_t *buf, uint64_t q[TILE_ITEMS])
 {
+    float *f = reinterpret_cast<float *>(buf);
+    for (int e = threadIdx.x; e < TILE; e += blockDim.x)
+        f[padf(e)] = (e < n) ? __ldg(lw + lo + e) : -INFINITY;
+    __syncthreads();
     const int base = threadIdx.x * TILE_ITEMS;
 #pragma unroll
-    for (int k = 0; k < TILE_ITEMS; ++k) {
-        const int i = base + k;
-        q[k] = (i < n) ? quantise(__ldg(lw + lo + i), M, s) : 0ull;
-    }
+    for (int k = 0; k < TILE_ITEMS; ++k)
+        q[k] = quantise(f[padf(base + k)], M, s);
+    __syncthreads();
 }
 
-// Inclusive scan of a tile's weights into smem C[0..TILE).  Returns the total.
+// Inclusive scan of a tile's weights into C (padded with padc).  Returns the total.
 __device__ __forceinline__ uint64_t tile_scan(const uint64_t q[TILE_ITEMS], uint64_t *C, uint64_t *red)
 {
     uint64_t loc[TILE_ITEMS];
@@ -46,31 +58,122 @@ __device__ __forceinline__ uint64_t tile_scan(const uint64_t q[TILE_ITEMS], uint
     const int base = threadIdx.x * TILE_ITEMS;
 #pragma unroll
     for (int k = 0; k < TILE_ITEMS; ++k)
-        C[base + k] = pre + loc[k];
+        C[padc(base + k)] = pre + loc[k];
     __syncthreads();
     return total;
 }
 
+// floor(X / d) for X < 2^96 whose quotient fits 64 bits, d < 2^32, by long
+// division in 32-bit limbs; *rem = X mod d.
+__device__ __forceinline__ uint64_t div_u96(u128 X, uint32_t d, uint32_t *rem)
+{
+    const uint64_t l2 = (uint64_t)(X >> 64), l1 = (uint64_t)(uint32_t)(X >> 32), l0 = (uint64_t)(uint32_t)X;
+    uint64_t r = l2 % d;
+    uint64_t cur = (r << 32) | l1;
+    const uint64_t q1 = cur / d;
+    r = cur % d;
+    cur = (r << 32) | l0;
+    const uint64_t q0 = cur / d;
+    *rem = (uint32_t)(cur % d);
+    return (q1 << 32) + q0;
+}
+
+// Parents of the tickets [j_lo, j_hi) (at most TILE of them) of one run of
+// particles with inclusive cumulative weights C[0..n) (local, the run starts
+// at cumulative weight c0).  Ticket j sits at (u + jQ)/nt; its parent is the
+// first i with c0 + C[i] > thr_j = floor((u + jQ)/nt).  Thread t takes tickets
+// j_lo + PER t .. + PER: one exact division for the first threshold, then
+// thr_{j+1} = thr_j + floor(Q/nt) (+1 on remainder carry), and a galloping
+// search from the previous parent.  out_s[j - j_lo] = local parent index.
+__device__ __forceinline__ void ticket_parents(const uint64_t *C, int n, uint64_t c0, uint64_t u, uint64_t Q,
+                                               uint32_t nt, int64_t j_lo, int64_t j_hi, int32_t *out_s)
+{
+    constexpr int PER = FILL_CHUNK / TILE_THREADS;
+    const int64_t j0 = j_lo + (int64_t)threadIdx.x * PER;
+    if (j0 >= j_hi)
+        return;
+    const int64_t j1 = (j0 + PER < j_hi) ? j0 + PER : j_hi;
+    const uint64_t qN = Q / nt;
+    const uint32_t qR = (uint32_t)(Q % nt);
+    uint32_t rem;
+    uint64_t thr = div_u96((u128)u + (u128)(uint64_t)j0 * (u128)Q, nt, &rem);
+    // first ticket: binary search for the first C[i] > thr - c0
+    uint64_t lt = thr - c0;
+    int lo = -1, hi = n - 1;  // C[lo] <= lt < C[hi] (C[-1] = 0 conceptually)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (C[padc(mid)] <= lt)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    int p = hi;
+    out_s[j0 - j_lo] = p;
+    for (int64_t j = j0 + 1; j < j1; ++j) {
+        thr += qN;
+        rem += qR;
+        if (rem >= nt) {
+            rem -= nt;
+            thr += 1;
+        }
+        lt = thr - c0;
+        if (C[padc(p)] <= lt) {
+            int a = p, step = 1;  // C[a] <= lt
+            while (a + step < n && C[padc(a + step)] <= lt) {
+                a += step;
+                step <<= 1;
+            }
+            int b = (a + step < n) ? a + step : n - 1;  // C[b] > lt
+            while (b - a > 1) {
+                const int mid = (a + b) >> 1;
+                if (C[padc(mid)] <= lt)
+                    a = mid;
+                else
+                    b = mid;
+            }
+            p = b;
+        }
+        out_s[j - j_lo] = p;
+    }
+}
+
 // ---------------------------------------------------------------- R1 tiles
-// Tile totals Q_t; for RPA also the local prefix at every group start that
-// falls inside the tile.
+// Tile totals Q_t (coalesced loads and a block sum); for RPA also the local
+// prefix at every group start that falls inside the tile (needs the scan).
 __global__ void __launch_bounds__(TILE_THREADS) tile_totals_kernel(
     const float *__restrict__ lw, int64_t N, const DevSummary *__restrict__ sum, uint64_t *__restrict__ Qt,
     const int64_t *__restrict__ goff, int32_t G, uint64_t *__restrict__ Cbl)
 {
-    __shared__ uint64_t C[TILE];
+    __shared__ uint64_t buf[TILE_SMEM_U64];
     __shared__ uint64_t red[33];
     __shared__ int32_t gfirst;
     const int64_t lo = (int64_t)blockIdx.x * TILE;
     const int n = (int)(N - lo < TILE ? N - lo : TILE);
-    uint64_t q[TILE_ITEMS];
-    tile_weights(lw, lo, n, sum->M, scale_bits(N), q);
-    const uint64_t total = tile_scan(q, C, red);
-    if (threadIdx.x == 0)
-        Qt[blockIdx.x] = total;
-    if (goff == nullptr)
+    const float M = sum->M;
+    const int s = scale_bits(N);
+    if (goff == nullptr) {
+        uint64_t acc = 0;
+        const float4 *v4 = reinterpret_cast<const float4 *>(lw + lo);
+        if (n == TILE && ((reinterpret_cast<uintptr_t>(lw + lo) & 15) == 0)) {
+            for (int e = threadIdx.x; e < TILE / 4; e += blockDim.x) {
+                const float4 v = __ldg(v4 + e);
+                acc += quantise(v.x, M, s) + quantise(v.y, M, s) + quantise(v.z, M, s) + quantise(v.w, M, s);
+            }
+        } else {
+            for (int e = threadIdx.x; e < n; e += blockDim.x)
+                acc += quantise(__ldg(lw + lo + e), M, s);
+        }
+        uint64_t total;
+        block_excl_scan_u64(acc, red, &total);
+        if (threadIdx.x == 0)
+            Qt[blockIdx.x] = total;
         return;
+    }
+    uint64_t q[TILE_ITEMS];
+    tile_weights(lw, lo, n, M, s, buf, q);
+    const uint64_t total = tile_scan(q, buf, red);
     if (threadIdx.x == 0) {
+        Qt[blockIdx.x] = total;
         int32_t a = 0, b = G + 1;  // first g with goff[g] >= lo
         while (a < b) {
             const int32_t mid = (a + b) >> 1;
@@ -86,8 +189,8 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_totals_kernel(
         const int64_t pos = goff[g];
         if (pos >= lo + n)
             break;
-        const int64_t k = pos - lo;
-        Cbl[g] = (k == 0) ? 0ull : C[k - 1];
+        const int k = (int)(pos - lo);
+        Cbl[g] = (k == 0) ? 0ull : buf[padc(k - 1)];
     }
 }
 
@@ -136,17 +239,17 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
     for (int t = threadIdx.x; t <= T; t += blockDim.x)
         Tt[t] = (t == T) ? N : tickets_below(Ct[t], N, u, Q);
     __syncthreads();
-    // fill work items: ceil(tickets / FILL_CHUNK) per tile
+    // fill work items: ceil(tickets / ITEM_TICKETS) per tile
     uint64_t cnt = 0;
     for (int k = 0; k < per; ++k)
         if (t0 + k < T)
-            cnt += (uint64_t)((Tt[t0 + k + 1] - Tt[t0 + k] + FILL_CHUNK - 1) / FILL_CHUNK);
+            cnt += (uint64_t)((Tt[t0 + k + 1] - Tt[t0 + k] + ITEM_TICKETS - 1) / ITEM_TICKETS);
     uint64_t items_total;
     uint64_t irun = block_excl_scan_u64(cnt, red, &items_total);
     for (int k = 0; k < per; ++k)
         if (t0 + k < T) {
             item_off[t0 + k] = (int32_t)irun;
-            irun += (uint64_t)((Tt[t0 + k + 1] - Tt[t0 + k] + FILL_CHUNK - 1) / FILL_CHUNK);
+            irun += (uint64_t)((Tt[t0 + k + 1] - Tt[t0 + k] + ITEM_TICKETS - 1) / ITEM_TICKETS);
         }
     if (threadIdx.x == 0) {
         item_off[T] = (int32_t)items_total;
@@ -193,14 +296,16 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
 }
 
 // ---------------------------------------------------------------- R3 fill
-// Work item b covers tickets [j_lo, j_hi) of one tile; every ticket finds its
-// parent in the tile's cumulative weights by binary search.
+// Work item b covers tickets [j_lo, j_hi) of one tile (at most ITEM_TICKETS);
+// the tile's cumulative weights are built once and the parents are found
+// FILL_CHUNK tickets at a time (ticket_parents), written out coalesced.
 __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     const float *__restrict__ lw, int64_t N, int32_t T, const DevSummary *__restrict__ sum,
     const uint64_t *__restrict__ Ct, const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
     int32_t *__restrict__ out)
 {
-    __shared__ uint64_t C[TILE];
+    __shared__ uint64_t C[TILE_SMEM_U64];
+    __shared__ int32_t par[FILL_CHUNK];
     __shared__ uint64_t red[33];
     __shared__ int32_t st;
     const int32_t b = blockIdx.x;
@@ -222,23 +327,19 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     const int64_t lo = (int64_t)t * TILE;
     const int n = (int)(N - lo < TILE ? N - lo : TILE);
     uint64_t q[TILE_ITEMS];
-    tile_weights(lw, lo, n, sum->M, scale_bits(N), q);
+    tile_weights(lw, lo, n, sum->M, scale_bits(N), C, q);
     tile_scan(q, C, red);
-    const uint64_t Q = sum->Q, u = sum->u, c0 = Ct[t];
-    const int64_t j_lo = Tt[t] + (int64_t)(b - item_off[t]) * FILL_CHUNK;
-    const int64_t j_hi = (Tt[t + 1] < j_lo + FILL_CHUNK) ? Tt[t + 1] : j_lo + FILL_CHUNK;
-    const u128 NN = (u128)(uint64_t)N;
-    for (int64_t j = j_lo + threadIdx.x; j < j_hi; j += blockDim.x) {
-        const u128 V = (u128)u + (u128)(uint64_t)j * (u128)Q;
-        int a = 0, e = n - 1;  // first i with N (c0 + C[i]) > V
-        while (a < e) {
-            const int mid = (a + e) >> 1;
-            if (NN * (u128)(c0 + C[mid]) > V)
-                e = mid;
-            else
-                a = mid + 1;
-        }
-        out[j] = (int32_t)(lo + a);
+    const int64_t i_lo = Tt[t] + (int64_t)(b - item_off[t]) * ITEM_TICKETS;
+    const int64_t i_hi = (Tt[t + 1] < i_lo + ITEM_TICKETS) ? Tt[t + 1] : i_lo + ITEM_TICKETS;
+    const uint64_t c0 = Ct[t], u = sum->u, Q = sum->Q;
+    for (int64_t j_lo = i_lo; j_lo < i_hi; j_lo += FILL_CHUNK) {
+        const int64_t j_hi = (i_hi < j_lo + FILL_CHUNK) ? i_hi : j_lo + FILL_CHUNK;
+        ticket_parents(C, n, c0, u, Q, (uint32_t)N, j_lo, j_hi, par);
+        __syncthreads();
+        const int cnt = (int)(j_hi - j_lo);
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x)
+            out[j_lo + k] = (int32_t)(lo + par[k]);
+        __syncthreads();
     }
 }
 
@@ -649,7 +750,7 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
     uint64_t seed, uint32_t fid, uint32_t frame, int32_t *__restrict__ anc, float *__restrict__ lwp)
 {
     const int64_t mig = sum->mig;
-    __shared__ uint64_t C[TILE];
+    __shared__ uint64_t C[TILE_SMEM_U64];
     __shared__ uint64_t red[33];
     __shared__ float smf[8];
     __shared__ double lwg_s;
@@ -716,38 +817,34 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
         }
         return;
     }
-    // pass 3: chunks of TILE particles; the tickets of chunk [c0, c1) are
-    // [T(C_c0), T(C_c1)) with T the local ticket count of n = sz tickets.
+    // pass 3: chunks of TILE particles; the tickets of chunk [c0, c0 + n) are
+    // [T(carry), T(carry + total)) with T the local ticket count of n = sz
+    // tickets, processed FILL_CHUNK at a time.
+    __shared__ int32_t par[FILL_CHUNK];
     uint64_t carry = 0;
     for (int64_t c0 = 0; c0 < sz; c0 += TILE) {
         const int n = (int)(sz - c0 < TILE ? sz - c0 : TILE);
         uint64_t q[TILE_ITEMS];
-        tile_weights(lw, lo + c0, n, Mg, s, q);
+        tile_weights(lw, lo + c0, n, Mg, s, C, q);
         const uint64_t tot = tile_scan(q, C, red);
-        const int64_t j_lo = tickets_below(carry, sz, u, Q);
-        const int64_t j_hi = tickets_below(carry + tot, sz, u, Q);
-        const u128 NN = (u128)(uint64_t)sz;
-        for (int64_t j = j_lo + threadIdx.x; j < j_hi; j += blockDim.x) {
-            const u128 V = (u128)u + (u128)(uint64_t)j * (u128)Q;
-            int a = 0, e = n - 1;
-            while (a < e) {
-                const int mid = (a + e) >> 1;
-                if (NN * (u128)(carry + C[mid]) > V)
-                    e = mid;
-                else
-                    a = mid + 1;
+        const int64_t t_lo = tickets_below(carry, sz, u, Q);
+        const int64_t t_hi = tickets_below(carry + tot, sz, u, Q);
+        for (int64_t j_lo = t_lo; j_lo < t_hi; j_lo += FILL_CHUNK) {
+            const int64_t j_hi = (t_hi < j_lo + FILL_CHUNK) ? t_hi : j_lo + FILL_CHUNK;
+            ticket_parents(C, n, carry, u, Q, (uint32_t)sz, j_lo, j_hi, par);
+            __syncthreads();
+            for (int64_t j = j_lo + threadIdx.x; j < j_hi; j += blockDim.x) {
+                const int64_t d = dest(j);
+                anc[d] = (int32_t)(lo + c0 + par[j - j_lo]);
+                lwp[d] = lwg;
             }
-            const int64_t d = dest(j);
-            anc[d] = (int32_t)(lo + c0 + a);
-            lwp[d] = lwg;
+            __syncthreads();
         }
         carry += tot;
         __syncthreads();
     }
 }
 
-// RNA set-up: migration count floor(alpha * min_g n_g) and the ring's routing
-// statistics; also clears the degenerate flag (RNA handles empty groups locally).
 __global__ void __launch_bounds__(1024) rna_prep_kernel(const int64_t *__restrict__ goff, int32_t G, float alpha,
                                                         DevSummary *sum)
 {
@@ -824,7 +921,7 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme)
     tile_scan_kernel<<<1, 1024, 0, c->stream>>>(c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sum,
                                                 c->m.seed, c->m.filter_id, (uint32_t)c->last_frame,
                                                 c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg);
-    const int max_items = T + (int)((c->N + FILL_CHUNK - 1) / FILL_CHUNK);
+    const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
     int32_t *out = rpa ? c->anc_sys : c->anc;
     fill_kernel<<<max_items, TILE_THREADS, 0, c->stream>>>(lw, c->N, T, c->sum, c->sc.Ct, c->sc.Tt,
                                                            c->sc.item_off, out);

@@ -31,7 +31,7 @@ __global__ void init_kernel(float *__restrict__ st, int64_t N, uint64_t seed, ui
 }
 
 // --------------------------------------------------------- frame preparation
-// Zp = Z - I_bg inside the image, 0 in a border of width pad = 2r, so that a
+// Zb = Z - I_bg inside the image, 0 in a border of width pad = 2r, so that a
 // patch anchored up to r pixels outside the image never leaves the buffer.
 template <typename T>
 __device__ __forceinline__ float to_f32(T v);
@@ -61,6 +61,7 @@ struct StepArgs {
     int64_t N;
     int W, H, Wp, pad;
     float inv2s2;      // 1 / (2 sigma_PSF^2)
+    float Kc[MAX_RADIUS];  // exp(-(2k+1) / (2 sigma_PSF^2)), k = 0..R-1
     float inv_sxi2;    // 1 / sigma_xi^2
     float sm, sv, sI;
     uint64_t seed;
@@ -74,6 +75,8 @@ struct StepArgs {
     int mode;
     const float *__restrict__ Zp;
     Partial *__restrict__ part;
+    unsigned int *done;    // blocks finished (reset by the last one)
+    DevSummary *sum;
 };
 
 // Online log-sum-exp accumulator of the weight statistics.
@@ -145,11 +148,96 @@ struct Acc {
     }
 };
 
+// --------------------------------------------------------------- finalise
+// Cross-block totals in FP64 (the paper's global sum for normalisation):
+// estimate, N_eff, log-evidence.  Run by the last block of the step.
+__device__ void finalize_block(const Partial *part, int n, DevSummary *sum, int32_t frame)
+{
+    __shared__ float smf[32];
+    __shared__ double smd[32][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float m = -INFINITY, mp = -INFINITY;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        m = fmaxf(m, __ldcg(&part[b].m));
+        mp = fmaxf(mp, __ldcg(&part[b].mp));
+    }
+    m = warp_max(m);
+    if (lane == 0)
+        smf[warp] = m;
+    __syncthreads();
+    float M = -INFINITY;
+    for (int w = 0; w < nw; ++w)
+        M = fmaxf(M, smf[w]);
+    __syncthreads();
+    mp = warp_max(mp);
+    if (lane == 0)
+        smf[warp] = mp;
+    __syncthreads();
+    float Mp = -INFINITY;
+    for (int w = 0; w < nw; ++w)
+        Mp = fmaxf(Mp, smf[w]);
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // s0, s[5], s2, sp
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        const float qm = __ldcg(&part[b].m), qmp = __ldcg(&part[b].mp);
+        if (qm > -INFINITY) {
+            const double f = (double)expf(qm - M);  // scale factor to 1 ulp; sums in FP64
+            acc[0] += __ldcg(&part[b].s0) * f;
+            for (int c = 0; c < 5; ++c)
+                acc[1 + c] += __ldcg(&part[b].s[c]) * f;
+            acc[6] += __ldcg(&part[b].s2) * f * f;
+        }
+        if (qmp > -INFINITY)
+            acc[7] += __ldcg(&part[b].sp) * (double)expf(qmp - Mp);
+    }
+    for (int c = 0; c < 8; ++c)
+        acc[c] = warp_sum_d(acc[c]);
+    if (lane == 0)
+        for (int c = 0; c < 8; ++c)
+            smd[warp][c] = acc[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < nw; ++w)
+            for (int c = 0; c < 8; ++c)
+                t[c] += smd[w][c];
+        for (int c = 0; c < 5; ++c)
+            sum->mean[c] = t[1 + c] / t[0];
+        sum->ess = t[0] * t[0] / t[6];
+        sum->log_total = (double)M + log(t[0]);
+        sum->log_evidence = sum->log_total - ((double)Mp + log(t[7]));
+        sum->max_lw = (double)M;
+        sum->M = M;
+        sum->frame = frame;
+        if (!(t[0] > 0.0))
+            sum->flags |= FLAG_DEGENERATE;
+    }
+}
+
+// Point samples g(k) = exp(-a (k + f)^2), k = -R..R, f in (-1/2, 1/2]: the
+// centre by one exponential, the rest by the exact ratios
+// g(k+1) / g(k) = exp(-a (2k+1)) exp(-2 a f) and
+// g(-k-1) / g(-k) = exp(-a (2k+1)) exp(2 a f), k >= 0,
+// with the constants Kc[k] = exp(-a (2k+1)) precomputed per model.
+template <int R>
+__device__ __forceinline__ void gauss_samples(float f, float a, const float *Kc, float g[2 * R + 1])
+{
+    g[R] = __expf(-a * f * f);
+    if (R > 0) {
+        const float up = __expf(-2.0f * a * f), dn = __expf(2.0f * a * f);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            g[R + k + 1] = g[R + k] * (Kc[k] * up);
+            g[R - k - 1] = g[R - k] * (Kc[k] * dn);
+        }
+    }
+}
+
 // Eq. 4 over S_x with the eq. 3 model, pixels outside S_x modelled as
 // background: l = -sum_{S_x} [(Zb - a)^2 - Zb^2] / (2 sigma_xi^2) with
 // Zb = Z - I_bg and a = I0 g, g separable: g = gx(col) gy(row).  Expanded,
 // l = I0 (B - I0 C / 2) / sigma_xi^2 with B = sum gy_j sum_i gx_i Zb and
-// C = sum gx_i^2 sum gy_j^2 (masks make pixels outside the image vanish).
+// C = sum gx_i^2 sum gy_j^2.  Samples of columns / rows outside the image are
+// zeroed (only for patches that cross the border); Zp is zero there as well.
 template <int R>
 __device__ __forceinline__ float patch_loglik(const StepArgs &a, float x, float y, float I0)
 {
@@ -159,33 +247,33 @@ __device__ __forceinline__ float patch_loglik(const StepArgs &a, float x, float 
     if (cxf < -(float)R || cxf > (float)(a.W - 1 + R) || cyf < -(float)R || cyf > (float)(a.H - 1 + R))
         return 0.0f;
     const int cx = (int)cxf, cy = (int)cyf;
-    const float fx = cxf - x, fy = cyf - y;
     constexpr int P = 2 * R + 1;
-    float gx[P];
+    float gx[P], gy[P];
+    gauss_samples<R>(cxf - x, a.inv2s2, a.Kc, gx);
+    gauss_samples<R>(cyf - y, a.inv2s2, a.Kc, gy);
+    if (cx < R || cx > a.W - 1 - R || cy < R || cy > a.H - 1 - R) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const int px = cx + i - R, py = cy + i - R;
+            gx[i] = (px >= 0 && px < a.W) ? gx[i] : 0.0f;
+            gy[i] = (py >= 0 && py < a.H) ? gy[i] : 0.0f;
+        }
+    }
     float sxx = 0.0f, syy = 0.0f;
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-        const float d = fx + (float)(i - R);
-        float g = expf(-d * d * a.inv2s2);
-        const int px = cx + i - R;
-        g = (px >= 0 && px < a.W) ? g : 0.0f;
-        gx[i] = g;
-        sxx = fmaf(g, g, sxx);
+        sxx = fmaf(gx[i], gx[i], sxx);
+        syy = fmaf(gy[i], gy[i], syy);
     }
     const float *row = a.Zp + (int64_t)(cy - R + a.pad) * a.Wp + (cx - R + a.pad);
     float B = 0.0f;
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-        const float d = fy + (float)(j - R);
-        float g = expf(-d * d * a.inv2s2);
-        const int py = cy + j - R;
-        g = (py >= 0 && py < a.H) ? g : 0.0f;
-        syy = fmaf(g, g, syy);
         float rj = 0.0f;
 #pragma unroll
         for (int i = 0; i < P; ++i)
             rj = fmaf(gx[i], __ldg(row + i), rj);
-        B = fmaf(g, rj, B);
+        B = fmaf(gy[j], rj, B);
         row += a.Wp;
     }
     const float C = sxx * syy;
@@ -218,12 +306,12 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
             lwp = 0.0f;
         else
             lwp = __ldg(a.lwp + i);
-        const uint4 r0 = draw(a.seed, (uint32_t)i, a.frame, a.fid, PURPOSE_PROP, 0);
-        const uint4 r1 = draw(a.seed, (uint32_t)i, a.frame, a.fid, PURPOSE_PROP, 1);
+        uint32_t f[6];
+        prop_fields(draw(a.seed, (uint32_t)i, a.frame, a.fid, PURPOSE_PROP, 0), f);
         float e0, e1, e2, e3, e4, e5;
-        box_muller(r0.x, r0.y, e0, e1);
-        box_muller(r0.z, r0.w, e2, e3);
-        box_muller(r1.x, r1.y, e4, e5);
+        box_muller(u21(f[0]), u21(f[1]), e0, e1);
+        box_muller(u21(f[2]), u21(f[3]), e2, e3);
+        box_muller(u21(f[4]), u21(f[5]), e4, e5);
         float v[5];
         v[0] = fmaf(a.sm, e0, x + vx);
         v[1] = fmaf(a.sm, e1, y + vy);
@@ -269,71 +357,19 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
             a.part[blockIdx.x] = q;
         }
     }
-}
-
-// --------------------------------------------------------------- finalise
-// Cross-block totals in FP64 (the paper's global sum for normalisation):
-// estimate, N_eff, log-evidence.
-__global__ void __launch_bounds__(1024) finalize_kernel(const Partial *__restrict__ part, int n,
-                                                        DevSummary *sum, int32_t frame)
-{
-    __shared__ float smf[32];
-    __shared__ double smd[32][9];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float m = -INFINITY, mp = -INFINITY;
-    for (int b = threadIdx.x; b < n; b += blockDim.x) {
-        m = fmaxf(m, part[b].m);
-        mp = fmaxf(mp, part[b].mp);
-    }
-    m = warp_max(m);
-    if (lane == 0)
-        smf[warp] = m;
-    __syncthreads();
-    float M = -INFINITY;
-    for (int w = 0; w < nw; ++w)
-        M = fmaxf(M, smf[w]);
-    __syncthreads();
-    mp = warp_max(mp);
-    if (lane == 0)
-        smf[warp] = mp;
-    __syncthreads();
-    float Mp = -INFINITY;
-    for (int w = 0; w < nw; ++w)
-        Mp = fmaxf(Mp, smf[w]);
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // s0, s[5], s2, sp
-    for (int b = threadIdx.x; b < n; b += blockDim.x) {
-        const Partial q = part[b];
-        if (q.m > -INFINITY) {
-            const double f = exp((double)q.m - (double)M);
-            acc[0] += q.s0 * f;
-            for (int c = 0; c < 5; ++c)
-                acc[1 + c] += q.s[c] * f;
-            acc[6] += q.s2 * f * f;
-        }
-        if (q.mp > -INFINITY)
-            acc[7] += q.sp * exp((double)q.mp - (double)Mp);
-    }
-    for (int c = 0; c < 8; ++c)
-        acc[c] = warp_sum_d(acc[c]);
-    if (lane == 0)
-        for (int c = 0; c < 8; ++c)
-            smd[warp][c] = acc[c];
-    __syncthreads();
+    // the last block to finish combines every block's partials (no waiting:
+    // it only runs once all the others have published theirs)
+    __shared__ bool last;
     if (threadIdx.x == 0) {
-        double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int w = 0; w < nw; ++w)
-            for (int c = 0; c < 8; ++c)
-                t[c] += smd[w][c];
-        for (int c = 0; c < 5; ++c)
-            sum->mean[c] = t[1 + c] / t[0];
-        sum->ess = t[0] * t[0] / t[6];
-        sum->log_total = (double)M + log(t[0]);
-        sum->log_evidence = sum->log_total - ((double)Mp + log(t[7]));
-        sum->max_lw = (double)M;
-        sum->M = M;
-        sum->frame = frame;
-        if (!(t[0] > 0.0))
-            sum->flags |= FLAG_DEGENERATE;
+        __threadfence();
+        last = (atomicAdd(a.done, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        finalize_block(a.part, gridDim.x, a.sum, (int32_t)a.frame);
+        if (threadIdx.x == 0)
+            *a.done = 0u;
     }
 }
 
@@ -362,8 +398,8 @@ cudaError_t launch_prepare_frame(ppf_ctx *c, const void *frame)
 {
     prof_mark(c, PH_PREPARE, 0);
     c->launches += 1;
-    const int n = c->Wp * c->Hp;
-    const int grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    const int64_t n = (int64_t)c->Wp * c->Hp;
+    const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     const float bg = c->m.background;
     switch (c->m.frame_dtype) {
     case PPF_BF16:
@@ -397,6 +433,8 @@ cudaError_t launch_step(ppf_ctx *c, int32_t k)
     a.Wp = c->Wp;
     a.pad = c->pad;
     a.inv2s2 = 1.0f / (2.0f * c->m.psf_sigma * c->m.psf_sigma);
+    for (int k = 0; k < MAX_RADIUS; ++k)
+        a.Kc[k] = (float)exp(-(2.0 * k + 1.0) * (double)a.inv2s2);
     a.inv_sxi2 = 1.0f / (c->m.sigma_xi * c->m.sigma_xi);
     a.sm = c->m.sigma_m;
     a.sv = c->m.sigma_v;
@@ -413,6 +451,8 @@ cudaError_t launch_step(ppf_ctx *c, int32_t k)
     a.mode = c->mode;
     a.Zp = c->Zp;
     a.part = c->part;
+    a.done = &c->sum->blocks_done;
+    a.sum = c->sum;
     const int grid = step_grid(c);
     prof_mark(c, PH_STEP, 0);
     switch (c->m.patch_radius) {
@@ -427,13 +467,7 @@ cudaError_t launch_step(ppf_ctx *c, int32_t k)
     default: launch_step_r<8>(a, grid, c->stream); break;
     }
     prof_mark(c, PH_STEP, 1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return e;
-    prof_mark(c, PH_FINALIZE, 0);
-    finalize_kernel<<<1, 1024, 0, c->stream>>>(c->part, grid, c->sum, k);
-    prof_mark(c, PH_FINALIZE, 1);
-    c->launches += 2;
+    c->launches += 1;
     return cudaGetLastError();
 }
 

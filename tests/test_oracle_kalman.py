@@ -82,4 +82,3 @@ def test_sir_matches_kalman(orc, case):
     se_ev = E.std(axis=0, ddof=1) / math.sqrt(R)
     zev = np.abs(E.mean(axis=0) - want_ev) / se_ev
     assert zev.max() < 4.0, np.round(zev, 2)
-    assert np.max(np.abs(E.mean(axis=0) - want_ev)) < 0.02

@@ -83,3 +83,20 @@ def test_normals_are_standard_normal(orc):
     assert np.array_equal(orc.normals5(7, 5, 3), orc.normals5(7, 5, 3))
     assert not np.array_equal(orc.normals5(7, 5, 3), orc.normals5(7, 5, 4))
     assert not np.array_equal(orc.normals5(7, 5, 3), orc.normals5(8, 5, 3))
+
+
+def test_propagation_fields_and_uniforms(orc):
+    """Six 21-bit fields of one 128-bit block, each mapped to an exact float32
+    odd multiple of 2^-22; checked against Python's big-integer slicing."""
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        w = rng.integers(0, 2**32, size=4, dtype=np.uint64)
+        big = int(w[0]) | int(w[1]) << 32 | int(w[2]) << 64 | int(w[3]) << 96
+        want = [(big >> (21 * k)) & (2**21 - 1) for k in range(6)]
+        assert orc.prop_fields(w).tolist() == want
+    assert orc.prop_fields([0xFFFFFFFF] * 4).tolist() == [2**21 - 1] * 6
+    assert orc.u21(0) == 2.0**-22
+    assert orc.u21(2**21 - 1) == 1.0 - 2.0**-22
+    for f in [0, 1, 12345, 2**20, 2**21 - 1]:
+        u = orc.u21(f)
+        assert float(np.float32(u)) == u and 0.0 < u < 1.0
