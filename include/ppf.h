@@ -183,6 +183,31 @@ ppf_status ppf_profile_enable(ppf_ctx *ctx, int enable, int32_t capacity);
 /* Synchronises the stream and sums the recorded event pairs. */
 ppf_status ppf_profile_read(ppf_ctx *ctx, ppf_profile_t *out);
 
+/* Systematic resampling of n device log-weights with no device allocation.
+ * (A library addition for callers that cannot allocate; the paper has no
+ * counterpart.)  Some callers cannot call cudaMalloc: serving or real-time
+ * loops that pre-plan all device memory (cudaMalloc may block and
+ * synchronise the device), or hosts whose device memory belongs to another
+ * runtime's allocator.  This call computes exactly what ppf_resample
+ * (PPF_SYSTEMATIC) computes for the same log-weights, seed, filter id and
+ * frame, using a fixed scratch array inside the library instead of
+ * allocated buffers.
+ *   lw_dev     n float32 log-weights (device), read only.
+ *   n          1 <= n <= 16,777,216 (2^24, the scratch array's capacity);
+ *              larger n returns PPF_EINVAL and enqueues nothing.
+ *   anc_dev    n int32 (device, caller-owned): ancestor of every slot; the
+ *              identity when every weight is zero or NaN.
+ *   cuda_stream stream to enqueue on (NULL = legacy default stream).
+ * The scratch array (about 113 KB) lives on every device that loads the
+ * library until the process exits.  The first call on a device looks up its
+ * address (once per device, with that device current); make that first call
+ * before any stream capture.  Every call shares the array and it keeps the
+ * last call's contents (each call clears what must start at zero): calls
+ * whose work overlaps on the GPU race and must be serialised by the caller.
+ * Errors: PPF_EINVAL (NULL pointers, n out of range, frame < 0), PPF_ECUDA. */
+ppf_status ppf_systematic_resample_noalloc(const float *lw_dev, int64_t n, uint64_t seed, uint32_t filter_id,
+                                           int32_t frame, int32_t *anc_dev, void *cuda_stream);
+
 /* Human-readable name of a status code (static string). */
 const char *ppf_status_string(ppf_status s);
 

@@ -21,7 +21,7 @@ SCHEMES = {"systematic": SYSTEMATIC, "rpa_gs": RPA_GS, "rpa_sgs": RPA_SGS, "rpa_
 
 EXPORTS = ["ppf_create", "ppf_destroy", "ppf_step", "ppf_step_host", "ppf_resample", "ppf_estimate",
            "ppf_get_particles", "ppf_set_particles", "ppf_get_groups", "ppf_status_string",
-           "ppf_last_error", "ppf_profile_enable", "ppf_profile_read"]
+           "ppf_last_error", "ppf_profile_enable", "ppf_profile_read", "ppf_systematic_resample_noalloc"]
 
 
 class PPFError(RuntimeError):
@@ -129,6 +129,8 @@ def load(build_if_missing: bool = True):
             "ppf_last_error": (C.c_char_p, [ctxp]),
             "ppf_profile_enable": (C.c_int, [ctxp, C.c_int, C.c_int32]),
             "ppf_profile_read": (C.c_int, [ctxp, P(_Profile)]),
+            "ppf_systematic_resample_noalloc": (C.c_int, [vp, C.c_int64, C.c_uint64, C.c_uint32, C.c_int32, vp,
+                                                          vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -136,6 +138,25 @@ def load(build_if_missing: bool = True):
             f.argtypes = args
         _lib = L
         return L
+
+
+def systematic_resample_noalloc(lw, seed: int, filter_id: int, frame: int, out=None, stream=None):
+    """``ppf_systematic_resample_noalloc``: ancestors of the CUDA float32 log-weights
+    ``lw`` for callers that cannot allocate device memory.  ``out`` (CUDA int32,
+    same length) receives them; if omitted it is allocated here by torch, which
+    a caller that cannot allocate would pass in instead."""
+    import torch
+    if not lw.is_cuda or lw.dtype != torch.float32 or not lw.is_contiguous():
+        raise ValueError("lw must be a contiguous CUDA float32 tensor")
+    if out is None:
+        out = torch.empty(lw.numel(), dtype=torch.int32, device=lw.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = load().ppf_systematic_resample_noalloc(C.c_void_p(lw.data_ptr()), lw.numel(), seed & 0xFFFFFFFFFFFFFFFF,
+                                                filter_id, frame, C.c_void_p(out.data_ptr()),
+                                                C.c_void_p(st.cuda_stream))
+    if rc != OK:
+        raise PPFError(rc, f"ppf_systematic_resample_noalloc: {status_string(rc)}")
+    return out
 
 
 def status_string(s: int) -> str:
