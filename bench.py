@@ -36,6 +36,16 @@ R = 5
 # algorithmic HBM bytes per particle of the fused step kernel after a global
 # resample: ancestor 4 + gathered parent x, y, vx, vy, I0 20 + written state 24
 STEP_BYTES = 48
+# measured DRAM bytes per particle of the same kernel (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum, 9th launch at N = 16M, profiles/step_kernel_spot512_n16m.md),
+# scaled to a launch by N; set to None whenever step_kernel changes
+STEP_TRAFFIC_PER_PARTICLE = 673.76e6 / 16e6
+# algorithmic FP32 flops per particle of the likelihood + propagation (an FMA
+# counts 2): bilinear form 2P^2, row combination 2P, sums of squares 4P, final
+# combination 6, propagation 10, with P = 2r + 1
+STEP_FLOPS = 2 * 11 * 11 + 2 * 11 + 4 * 11 + 6 + 10
+# FP32 peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def workload_desc(n, scheme):
@@ -215,18 +225,25 @@ def run_ours(args):
     if os.path.exists(pp):
         peaks = json.load(open(pp))
     peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic = None if STEP_TRAFFIC_PER_PARTICLE is None else STEP_TRAFFIC_PER_PARTICLE * n
     roofline = {"bound": "hbm", "kernel": "step_kernel<5> (propagate + likelihood + weight partials)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
                 "bytes_per_particle": STEP_BYTES, "step_kernel_ms": step_ms,
-                "traffic": None,
+                "traffic": traffic,
+                "traffic_source": "ncu dram bytes at N=16M scaled by N (profiles/step_kernel_spot512_n16m.md)",
                 "phase_ms_per_step": {kk: prof[kk] / max(1, prof["timed_steps"]) for kk in
                                       ("prepare_ms", "step_ms", "finalize_ms", "resample_ms")}}
+    tflops = STEP_FLOPS * n / (step_ms / 1e3) / 1e12
+    roofline_alu = {"bound": "alu", "kernel": "step_kernel<5>", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS, "flops_per_particle": STEP_FLOPS,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
             "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded Poisson spot movie, random-init particles)",
-            "config": workload_desc(n, args.scheme), "roofline": roofline, "clocks": clk,
+            "config": workload_desc(n, args.scheme), "roofline": roofline, "roofline_alu": roofline_alu,
+            "clocks": clk,
             "gpu_launches": int(prof["launches"]),
             "last_estimate": {"mean": est.mean, "ess": est.ess, "log_evidence": est.log_evidence,
                               "truth": mv.truth[kdone - 1].tolist()}}
@@ -296,7 +313,7 @@ def main():
     ap.add_argument("--scheme-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-n", type=int, default=1 << 20)
-    ap.add_argument("--cpu-frames", type=int, default=3)
+    ap.add_argument("--cpu-frames", type=int, default=4)
     ap.add_argument("--ref-n", type=int, default=1 << 17)
     ap.add_argument("--no-schemes", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

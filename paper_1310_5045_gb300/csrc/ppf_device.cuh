@@ -122,7 +122,10 @@ __device__ __forceinline__ uint64_t quantise(float lw, float M, int s)
     const float f = __fsub_rn(t, kf);
     const float p = exp2_frac(f);
     const int e = s + (int)kf;
-    const uint64_t P = (uint64_t)__float2ull_rz(__fmul_rn(p, 0x1p23f));
+    // P = p 2^23 exactly: p lies in [1, 2], so its mantissa with the implicit
+    // bit, doubled when the exponent is that of 2
+    const uint32_t pb = __float_as_uint(p);
+    const uint64_t P = (uint64_t)((pb & 0x7FFFFFu) | 0x800000u) << ((pb >> 23) - 127u);
     if (e < -25)
         return 0ull;
     if (e >= 23)

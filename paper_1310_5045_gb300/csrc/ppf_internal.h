@@ -12,7 +12,7 @@ constexpr int TILE = 4096;          // particles per resampling tile (256 thread
 constexpr int TILE_THREADS = 256;
 constexpr int TILE_ITEMS = TILE / TILE_THREADS;
 constexpr int FILL_CHUNK = 2048;    // tickets per fill pass (8 per thread)
-constexpr int ITEM_TICKETS = 8192;  // tickets per fill work item (4 passes)
+constexpr int ITEM_TICKETS = 16384; // tickets per fill work item (8 passes)
 constexpr int COPY_CHUNK = 2048;    // slots per routing-copy work item
 constexpr int MAX_RADIUS = 8;
 constexpr int MAX_SCHED_GROUPS = 16384;

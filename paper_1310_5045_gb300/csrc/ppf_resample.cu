@@ -78,62 +78,66 @@ __device__ __forceinline__ uint64_t div_u96(u128 X, uint32_t d, uint32_t *rem)
     return (q1 << 32) + q0;
 }
 
-// Parents of the tickets [j_lo, j_hi) (at most TILE of them) of one run of
-// particles with inclusive cumulative weights C[0..n) (local, the run starts
-// at cumulative weight c0).  Ticket j sits at (u + jQ)/nt; its parent is the
-// first i with c0 + C[i] > thr_j = floor((u + jQ)/nt).  Thread t takes tickets
-// j_lo + PER t .. + PER: one exact division for the first threshold, then
-// thr_{j+1} = thr_j + floor(Q/nt) (+1 on remainder carry), and a galloping
-// search from the previous parent.  out_s[j - j_lo] = local parent index.
-__device__ __forceinline__ void ticket_parents(const uint64_t *C, int n, uint64_t c0, uint64_t u, uint64_t Q,
-                                               uint32_t nt, int64_t j_lo, int64_t j_hi, int32_t *out_s)
+// floor(v / d), v mod d for v < 2^52, d < 2^32: float estimate, exact fix-up
+__device__ __forceinline__ uint64_t div_small(uint64_t v, uint32_t d, float rd, uint32_t *rem)
 {
-    constexpr int PER = FILL_CHUNK / TILE_THREADS;
-    const int64_t j0 = j_lo + (int64_t)threadIdx.x * PER;
-    if (j0 >= j_hi)
-        return;
-    const int64_t j1 = (j0 + PER < j_hi) ? j0 + PER : j_hi;
+    uint64_t q = (uint64_t)((float)v * rd);
+    int64_t r = (int64_t)v - (int64_t)(q * d);
+    while (r < 0) {
+        --q;
+        r += d;
+    }
+    while (r >= (int64_t)d) {
+        ++q;
+        r -= d;
+    }
+    *rem = (uint32_t)r;
+    return q;
+}
+
+// Parents of the tickets [j_lo, j_hi) of one run of particles with inclusive
+// cumulative weights C[0..n) (local; the run starts at cumulative weight c0,
+// n <= TILE).  Ticket j sits at (u + jQ)/nt; its parent is the first i with
+// c0 + C[i] > thr_j = floor((u + jQ)/nt).  One exact 96/32 division gives thr
+// at j_lo; with Q = qN nt + qR, ticket j_lo + o has
+// thr = thr(j_lo) + o qN + floor((rem(j_lo) + o qR) / nt).  Thread t takes
+// tickets j_lo + t, j_lo + t + blockDim, ... (coalesced writes) and finds each
+// parent with a fixed 12-step branch-free binary search (no divergence, no
+// barriers between tickets).  emit(j, i) receives every (ticket, parent).
+// Called by every thread of the block.
+template <typename Emit>
+__device__ __forceinline__ void ticket_parents(const uint64_t *C, int n, uint64_t c0, uint64_t u, uint64_t Q,
+                                               uint32_t nt, int64_t j_lo, int64_t j_hi, Emit emit)
+{
+    __shared__ uint64_t s_thr;
+    __shared__ uint32_t s_rem;
     const uint64_t qN = Q / nt;
     const uint32_t qR = (uint32_t)(Q % nt);
-    uint32_t rem;
-    uint64_t thr = div_u96((u128)u + (u128)(uint64_t)j0 * (u128)Q, nt, &rem);
-    // first ticket: binary search for the first C[i] > thr - c0
-    uint64_t lt = thr - c0;
-    int lo = -1, hi = n - 1;  // C[lo] <= lt < C[hi] (C[-1] = 0 conceptually)
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (C[padc(mid)] <= lt)
-            lo = mid;
-        else
-            hi = mid;
+    const float rnt = 1.0f / (float)nt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t r0;
+        s_thr = div_u96((u128)u + (u128)(uint64_t)j_lo * (u128)Q, nt, &r0);
+        s_rem = r0;
     }
-    int p = hi;
-    out_s[j0 - j_lo] = p;
-    for (int64_t j = j0 + 1; j < j1; ++j) {
-        thr += qN;
-        rem += qR;
-        if (rem >= nt) {
-            rem -= nt;
-            thr += 1;
+    __syncthreads();
+    const uint64_t thr0 = s_thr;
+    const uint64_t rem0 = s_rem;
+    for (int64_t j = j_lo + threadIdx.x; j < j_hi; j += blockDim.x) {
+        const uint64_t o = (uint64_t)(j - j_lo);
+        uint32_t r;
+        const uint64_t thr = thr0 + o * qN + div_small(rem0 + o * qR, nt, rnt, &r);
+        const uint64_t lt = thr - c0;
+        // number of C[i] <= lt over i < TILE (C[i] for i >= n is never reached:
+        // every ticket of this run has lt < C[n-1])
+        int pos = 0;
+#pragma unroll
+        for (int step = TILE / 2; step > 0; step >>= 1) {
+            const int k = pos + step - 1;
+            if (k < n && C[padc(k)] <= lt)
+                pos += step;
         }
-        lt = thr - c0;
-        if (C[padc(p)] <= lt) {
-            int a = p, step = 1;  // C[a] <= lt
-            while (a + step < n && C[padc(a + step)] <= lt) {
-                a += step;
-                step <<= 1;
-            }
-            int b = (a + step < n) ? a + step : n - 1;  // C[b] > lt
-            while (b - a > 1) {
-                const int mid = (a + b) >> 1;
-                if (C[padc(mid)] <= lt)
-                    a = mid;
-                else
-                    b = mid;
-            }
-            p = b;
-        }
-        out_s[j - j_lo] = p;
+        emit(j, pos);
     }
 }
 
@@ -296,16 +300,15 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
 }
 
 // ---------------------------------------------------------------- R3 fill
-// Work item b covers tickets [j_lo, j_hi) of one tile (at most ITEM_TICKETS);
-// the tile's cumulative weights are built once and the parents are found
-// FILL_CHUNK tickets at a time (ticket_parents), written out coalesced.
+// Work item b covers tickets [i_lo, i_hi) of one tile (at most ITEM_TICKETS);
+// the tile's cumulative weights are built once in shared memory and every
+// ticket finds its parent there (ticket_parents), written out coalesced.
 __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     const float *__restrict__ lw, int64_t N, int32_t T, const DevSummary *__restrict__ sum,
     const uint64_t *__restrict__ Ct, const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
     int32_t *__restrict__ out)
 {
     __shared__ uint64_t C[TILE_SMEM_U64];
-    __shared__ int32_t par[FILL_CHUNK];
     __shared__ uint64_t red[33];
     __shared__ int32_t st;
     const int32_t b = blockIdx.x;
@@ -331,16 +334,8 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     tile_scan(q, C, red);
     const int64_t i_lo = Tt[t] + (int64_t)(b - item_off[t]) * ITEM_TICKETS;
     const int64_t i_hi = (Tt[t + 1] < i_lo + ITEM_TICKETS) ? Tt[t + 1] : i_lo + ITEM_TICKETS;
-    const uint64_t c0 = Ct[t], u = sum->u, Q = sum->Q;
-    for (int64_t j_lo = i_lo; j_lo < i_hi; j_lo += FILL_CHUNK) {
-        const int64_t j_hi = (i_hi < j_lo + FILL_CHUNK) ? i_hi : j_lo + FILL_CHUNK;
-        ticket_parents(C, n, c0, u, Q, (uint32_t)N, j_lo, j_hi, par);
-        __syncthreads();
-        const int cnt = (int)(j_hi - j_lo);
-        for (int k = threadIdx.x; k < cnt; k += blockDim.x)
-            out[j_lo + k] = (int32_t)(lo + par[k]);
-        __syncthreads();
-    }
+    ticket_parents(C, n, Ct[t], sum->u, sum->Q, (uint32_t)N, i_lo, i_hi,
+                   [&](int64_t j, int i) { out[j] = (int32_t)(lo + i); });
 }
 
 // ------------------------------------------------------------ RPA schedule
@@ -818,9 +813,7 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
         return;
     }
     // pass 3: chunks of TILE particles; the tickets of chunk [c0, c0 + n) are
-    // [T(carry), T(carry + total)) with T the local ticket count of n = sz
-    // tickets, processed FILL_CHUNK at a time.
-    __shared__ int32_t par[FILL_CHUNK];
+    // [T(carry), T(carry + total)) with T the local ticket count of n = sz.
     uint64_t carry = 0;
     for (int64_t c0 = 0; c0 < sz; c0 += TILE) {
         const int n = (int)(sz - c0 < TILE ? sz - c0 : TILE);
@@ -829,17 +822,11 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
         const uint64_t tot = tile_scan(q, C, red);
         const int64_t t_lo = tickets_below(carry, sz, u, Q);
         const int64_t t_hi = tickets_below(carry + tot, sz, u, Q);
-        for (int64_t j_lo = t_lo; j_lo < t_hi; j_lo += FILL_CHUNK) {
-            const int64_t j_hi = (t_hi < j_lo + FILL_CHUNK) ? t_hi : j_lo + FILL_CHUNK;
-            ticket_parents(C, n, carry, u, Q, (uint32_t)sz, j_lo, j_hi, par);
-            __syncthreads();
-            for (int64_t j = j_lo + threadIdx.x; j < j_hi; j += blockDim.x) {
-                const int64_t d = dest(j);
-                anc[d] = (int32_t)(lo + c0 + par[j - j_lo]);
-                lwp[d] = lwg;
-            }
-            __syncthreads();
-        }
+        ticket_parents(C, n, carry, u, Q, (uint32_t)sz, t_lo, t_hi, [&](int64_t j, int i) {
+            const int64_t d = dest(j);
+            anc[d] = (int32_t)(lo + c0 + i);
+            lwp[d] = lwg;
+        });
         carry += tot;
         __syncthreads();
     }
