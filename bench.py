@@ -286,6 +286,35 @@ def run_ours(args):
                        "h2d_bytes_per_step": pr["h2d_bytes"] // ke, "d2h_bytes_per_step": pr["d2h_bytes"] // ke,
                        "timing": "host wall clock around step_host + resample + estimate (sync) per frame"}
 
+    # gradient of the log marginal likelihood: N = 2^20, 50 frames of 256^2
+    if not args.no_grad:
+        import synth
+        gmv, gp = synth.preset("spot256_k50", seed=1)
+        gmodel = ppf.Model(width=256, height=256, patch_radius=4, psf_sigma=1.5, amplitude=50.0, background=10.0,
+                           sigma_xi=math.sqrt(10.0), sigma_m=0.5, sigma_v=0.1, sigma_I=0.0, seed=rank)
+        gfr = torch.from_numpy(gmv.frames).to(dev)
+        gpf = ppf.ParticleFilter(gmodel, gp["N"], group_size=GROUP, stream=stream)
+        gpf.loglik_grad(gfr)
+        torch.cuda.synchronize()
+        reps = args.grad_evals
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            Lg, gg = gpf.loglik_grad(gfr)
+        e1.record(stream)
+        e1.synchronize()
+        tg = e0.elapsed_time(e1) / reps
+        K5 = gfr.shape[0]
+        line["grad"] = {"workload": f"spot256: 256x256 frames, K={K5}, N={gp['N']}, 9x9 patch, I0 = A, "
+                                    "systematic resampling (stop-gradient)",
+                        "grad_evals_per_sec": 1e3 / tg, "ms_per_eval": tg,
+                        "particle_steps_per_sec": gp["N"] * K5 / (tg / 1e3),
+                        "loglik": Lg, "grad": {"psf_sigma": gg[0], "amplitude": gg[1], "background": gg[2],
+                                               "sigma_m": gg[3]},
+                        }
+        gpf.close()
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cn, ck = args.cpu_n, args.cpu_frames
         rate, dt = oracle_rate(params, mv.frames, cn, ck)
@@ -318,6 +347,8 @@ def main():
     ap.add_argument("--no-schemes", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--grad-evals", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

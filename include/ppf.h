@@ -159,6 +159,32 @@ ppf_status ppf_set_particles(ppf_ctx *ctx, const float *state_dev, const int32_t
  * host buffer; synchronises).  offsets may be NULL to query G only. */
 ppf_status ppf_get_groups(ppf_ctx *ctx, int32_t *n_groups, int64_t *offsets_host);
 
+/* Gradient of the log marginal likelihood estimate (the sum over frames of
+ * the per-frame log-evidence of Alg. 1) with respect to
+ * theta = (sigma_PSF, A, I_bg, sigma_m).  It runs K frames from a fresh prior
+ * draw: propagation, likelihood (intensity fixed at I0 = A, so A is a
+ * parameter), normalisation, and systematic resampling after every frame but
+ * the last.  Resampling is a stop-gradient: ancestors and patch anchors are
+ * held fixed.  The sigma_m derivative follows each particle's ancestry
+ * forward (a per-particle tangent), the others come from the frame
+ * likelihoods; all cross-block sums are FP64.
+ *   frames_dev  K x H x W of model.frame_dtype (device), frames 1..K.
+ *   theta       host float[4] overriding the model's (psf_sigma, amplitude,
+ *               background, sigma_m) for this call; NULL = the model's.
+ *   loglik      receives L = sum_k [log sum_i w_i e^{l_k^i} ... ] (eq. 4 scale).
+ *   grad        receives dL/dtheta (host double[4]).
+ *   anc_dev     optional K x N int32 (device): row k holds the ancestors that
+ *               frame k+1 used (row 0 is the identity) -- the checkpoint of
+ *               the stop-gradient path.
+ *   anchors_dev optional K x 2 x N int32 (device): the patch anchors
+ *               (cx row, cy row) of every frame.
+ * Synchronous.  It re-draws and overwrites the context's particles; afterwards
+ * they are frame K's weighted particles (ppf_resample may follow).
+ * Errors: PPF_EINVAL, PPF_ENOMEM, PPF_ECUDA; PPF_EDEGENERATE if some frame had
+ * no usable weight (the values are still written). */
+ppf_status ppf_loglik_grad(ppf_ctx *ctx, const void *frames_dev, int32_t K, const float *theta, double *loglik,
+                           double *grad, int32_t *anc_dev, int32_t *anchors_dev);
+
 /* Phase timing and launch counting (measurement hook; no effect on results).
  * When enabled, a pair of CUDA events is recorded on the context's stream
  * around each phase of every step / resample (up to `capacity` calls per

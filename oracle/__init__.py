@@ -115,6 +115,9 @@ def lib():
                                            i64p, fp, dp, i32p, dp, i64p, i64p]),
                 "orc_run": (C.c_int, [mp, C.c_int64, C.c_int32, C.c_int, C.c_double, C.c_int32,
                                       dp, dp, dp]),
+                "orc_loglik_partials": (None, [mp, dp, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                               C.c_int32, dp]),
+                "orc_grad_run": (C.c_int, [mp, C.c_int64, C.c_int32, dp, dp, C.c_int, i32p, i32p, dp, dp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -305,3 +308,32 @@ def run(m: Model, N: int, frames: np.ndarray, group_size: int = 4096, scheme: in
     rc = lib().orc_run(C.byref(m.c()), N, group_size, scheme, alpha, K, _p(fr.reshape(-1), C.c_double),
                        _p(est.reshape(-1), C.c_double), _p(st, C.c_double))
     return rc, est, st.reshape(6, N)
+
+
+def loglik_partials(m: Model, frame: np.ndarray, x: float, y: float, I0: float, anchor=None) -> np.ndarray:
+    """(l, dl/dsigma, dl/dI0, dl/dbg, dl/dx, dl/dy) of one particle."""
+    fr = np.ascontiguousarray(frame, dtype=np.float64)
+    out = np.zeros(6)
+    ax, ay = (-2**31, -2**31) if anchor is None else anchor
+    lib().orc_loglik_partials(C.byref(m.c()), _p(fr, C.c_double), x, y, I0, ax, ay, _p(out, C.c_double))
+    return out
+
+
+def grad_run(m: Model, N: int, frames: np.ndarray, theta, anc=None, anchors=None):
+    """Log marginal likelihood estimate over the frames (systematic resampling every
+    frame, I0 = A) and its gradient w.r.t. (sigma_PSF, A, I_bg, sigma_m), reverse mode.
+    Without anc/anchors the run records them (returned); with them it replays them.
+    Returns (rc, L, grad[4], anc (K, N), anchors (K, 2, N))."""
+    fr = np.ascontiguousarray(frames, dtype=np.float64)
+    K = fr.shape[0]
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    replay = anc is not None
+    a = np.zeros((K, N), dtype=np.int32) if anc is None else np.ascontiguousarray(anc, dtype=np.int32).copy()
+    an = (np.zeros((K, 2, N), dtype=np.int32) if anchors is None else
+          np.ascontiguousarray(anchors, dtype=np.int32).copy())
+    L = np.zeros(1)
+    g = np.zeros(4)
+    rc = lib().orc_grad_run(C.byref(m.c()), N, K, _p(fr.reshape(-1), C.c_double), _p(th, C.c_double),
+                            1 if replay else 0, _p(a.reshape(-1), C.c_int32), _p(an.reshape(-1), C.c_int32),
+                            _p(L, C.c_double), _p(g, C.c_double))
+    return rc, float(L[0]), g, a, an

@@ -717,3 +717,175 @@ int orc_run(const orc_model *m, int64_t N, int32_t group_size, int scheme, doubl
     free(cur); free(nxt); free(lw_prev); free(lwf); free(anc); free(goff); free(goff2);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the log marginal likelihood estimate (the sum of the per-    */
+/* frame log-evidences of Alg. 1 with systematic resampling every frame)    */
+/* with respect to theta = (sigma_PSF, A, I_bg, sigma_m), the intensity     */
+/* fixed at I0 = A.  Resampling is a stop-gradient: the ancestors are held  */
+/* fixed; the patch anchors too (the objective is piecewise smooth in the   */
+/* positions).  Reverse mode, FP64.                                         */
+/* ------------------------------------------------------------------------ */
+
+/* l and its partials for one particle, from eq. 3/eq. 4 pixel by pixel:
+ * out = {l, dl/dsigma, dl/dI0, dl/dbg, dl/dx, dl/dy}.  (ax, ay) forces the
+ * anchor when ax != INT32_MIN. */
+void orc_loglik_partials(const orc_model *m, const double *frame, double x, double y, double I0, int32_t ax,
+                         int32_t ay, double out[6])
+{
+    for (int c = 0; c < 6; ++c)
+        out[c] = 0.0;
+    if (!isfinite(x) || !isfinite(y) || !isfinite(I0)) {
+        out[0] = -INFINITY;
+        return;
+    }
+    const int r = m->patch_radius;
+    int64_t cx, cy;
+    if (ax != INT32_MIN) {
+        cx = ax;
+        cy = ay;
+    } else {
+        const double cxd = floor(x + 0.5), cyd = floor(y + 0.5);
+        if (cxd < -r - 1.0 || cxd > m->width + r || cyd < -r - 1.0 || cyd > m->height + r)
+            return;
+        cx = (int64_t)cxd;
+        cy = (int64_t)cyd;
+    }
+    const double s = m->psf_sigma, s2 = s * s, sx2 = m->sigma_xi * m->sigma_xi;
+    for (int64_t py = cy - r; py <= cy + r; ++py) {
+        if (py < 0 || py >= m->height)
+            continue;
+        for (int64_t px = cx - r; px <= cx + r; ++px) {
+            if (px < 0 || px >= m->width)
+                continue;
+            const double dx = (double)px - x, dy = (double)py - y, d2 = dx * dx + dy * dy;
+            const double g = exp(-d2 / (2.0 * s2));
+            const double I = I0 * g + m->background;
+            const double z = frame[py * (int64_t)m->width + px];
+            const double res = z - I, res0 = z - m->background;
+            out[0] += -(res * res - res0 * res0) / (2.0 * sx2);
+            const double dl_dI = res / sx2;               /* d l / d I at this pixel */
+            out[1] += dl_dI * I0 * g * d2 / (s2 * s);     /* dI/dsigma = I0 g d^2 / s^3 */
+            out[2] += dl_dI * g;                          /* dI/dI0 = g */
+            out[3] += (res - res0) / sx2;                 /* I and res0 both move with I_bg */
+            out[4] += dl_dI * I0 * g * dx / s2;           /* dI/dx = I0 g (px - x) / s^2 */
+            out[5] += dl_dI * I0 * g * dy / s2;
+        }
+    }
+}
+
+/* K frames from the prior: L = sum_k [log sum_i e^{l_k^i} - log N] and dL/dtheta.
+ * theta overrides (psf_sigma, amplitude, background, sigma_m) of m.
+ * anc_io (K x N): if replay, slot i of frame k+1 (k = 0..K-1) takes anc_io[k N + i]
+ * (row 0 is the identity of the first step); otherwise it is written.  anchor_io
+ * (K x 2 x N: cx then cy per frame): replayed or written likewise. */
+int orc_grad_run(const orc_model *m0, int64_t N, int32_t K, const double *frames, const double theta[4],
+                 int replay, int32_t *anc_io, int32_t *anchor_io, double *L_out, double grad[4])
+{
+    orc_model m = *m0;
+    m.psf_sigma = theta[0];
+    m.amplitude = theta[1];
+    m.background = theta[2];
+    m.sigma_m = theta[3];
+    const double A = theta[1];
+    const int64_t npix = (int64_t)m.width * m.height;
+    double *cur = (double *)malloc(sizeof(double) * (size_t)(6 * N));
+    double *nxt = (double *)malloc(sizeof(double) * (size_t)(6 * N));
+    double *zero = (double *)calloc((size_t)N, sizeof(double));
+    double *wlx = (double *)malloc(sizeof(double) * (size_t)(K * N)); /* w dl/dx per frame */
+    double *wly = (double *)malloc(sizeof(double) * (size_t)(K * N));
+    double *lam = (double *)calloc((size_t)N, sizeof(double));
+    double *mu = (double *)calloc((size_t)N, sizeof(double));
+    double *lam2 = (double *)malloc(sizeof(double) * (size_t)N);
+    double *mu2 = (double *)malloc(sizeof(double) * (size_t)N);
+    double *part = (double *)malloc(sizeof(double) * (size_t)(6 * N));
+    int32_t *anc = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int rc = ORC_OK;
+    double L = 0.0, gd[3] = {0, 0, 0};
+    orc_init(&m, N, cur);
+    for (int64_t i = 0; i < N; ++i)
+        anc[i] = (int32_t)i;
+    int32_t G = 1;
+    int64_t goff[2] = {0, N}, goff2[2];
+    for (int32_t k = 0; k < K && rc == ORC_OK; ++k) {
+        if (replay)
+            memcpy(anc, anc_io + (int64_t)k * N, sizeof(int32_t) * (size_t)N);
+        else
+            memcpy(anc_io + (int64_t)k * N, anc, sizeof(int32_t) * (size_t)N);
+        orc_propagate(&m, N, k + 1, cur, anc, zero, nxt);
+        const double *fr = frames + (int64_t)k * npix;
+        double M = -INFINITY;
+        for (int64_t i = 0; i < N; ++i) {
+            int32_t ax = INT32_MIN, ay = INT32_MIN;
+            int32_t *an = anchor_io + (int64_t)k * 2 * N;
+            if (replay) {
+                ax = an[i];
+                ay = an[N + i];
+            }
+            orc_loglik_partials(&m, fr, nxt[i], nxt[N + i], A, ax, ay, part + 6 * i);
+            if (!replay) {
+                an[i] = (int32_t)floor(nxt[i] + 0.5);
+                an[N + i] = (int32_t)floor(nxt[N + i] + 0.5);
+            }
+            nxt[5 * N + i] = part[6 * i];
+            if (part[6 * i] > M)
+                M = part[6 * i];
+        }
+        double tot = 0.0;
+        for (int64_t i = 0; i < N; ++i)
+            tot += exp(nxt[5 * N + i] - M);
+        L += M + log(tot) - log((double)N);
+        for (int64_t i = 0; i < N; ++i) {
+            const double w = exp(nxt[5 * N + i] - M) / tot;
+            gd[0] += w * part[6 * i + 1];
+            gd[1] += w * part[6 * i + 2];
+            gd[2] += w * part[6 * i + 3];
+            wlx[(int64_t)k * N + i] = w * part[6 * i + 4];
+            wly[(int64_t)k * N + i] = w * part[6 * i + 5];
+        }
+        if (k + 1 < K && !replay) {
+            float *lwf = (float *)malloc(sizeof(float) * (size_t)N);
+            double *lwr = (double *)malloc(sizeof(double) * (size_t)N);
+            int64_t st[4];
+            for (int64_t i = 0; i < N; ++i)
+                lwf[i] = (float)nxt[5 * N + i];
+            rc = orc_resample(&m, ORC_SYSTEMATIC, 0.0, N, k + 1, G, goff, lwf, nxt + 5 * N, anc, lwr, goff2, st);
+            free(lwf);
+            free(lwr);
+        }
+        double *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    /* reverse sweep over the position adjoints: x_{k+1}^c = x_k^{a(c)} + ... so
+     * the adjoint of x_k^i collects w_k^i dl/dx plus the adjoints of its children */
+    double gsm = 0.0;
+    for (int32_t k = K - 1; k >= 0 && rc == ORC_OK; --k) {
+        for (int64_t i = 0; i < N; ++i) {
+            lam2[i] = wlx[(int64_t)k * N + i];
+            mu2[i] = wly[(int64_t)k * N + i];
+        }
+        if (k + 1 < K) {
+            const int32_t *a = anc_io + (int64_t)(k + 1) * N;
+            for (int64_t c = 0; c < N; ++c) {
+                lam2[a[c]] += lam[c];
+                mu2[a[c]] += mu[c];
+            }
+        }
+        for (int64_t i = 0; i < N; ++i) {
+            double e[5];
+            orc_normals5(m.seed, (uint32_t)i, (uint32_t)(k + 1), m.filter_id, e);
+            gsm += lam2[i] * e[0] + mu2[i] * e[1];  /* dx/dsigma_m = e1, dy/dsigma_m = e2 */
+        }
+        double *t = lam; lam = lam2; lam2 = t;
+        t = mu; mu = mu2; mu2 = t;
+    }
+    *L_out = L;
+    grad[0] = gd[0];
+    grad[1] = gd[1];
+    grad[2] = gd[2];
+    grad[3] = gsm;
+    free(cur); free(nxt); free(zero); free(wlx); free(wly); free(lam); free(mu); free(lam2); free(mu2);
+    free(part); free(anc);
+    return rc;
+}

@@ -23,6 +23,7 @@ from ._binding import (  # noqa: F401
     ParticleFilter,
     PPFError,
     load,
+    log_marginal_likelihood,
     lib_path,
     status_string,
 )

@@ -21,7 +21,8 @@ SCHEMES = {"systematic": SYSTEMATIC, "rpa_gs": RPA_GS, "rpa_sgs": RPA_SGS, "rpa_
 
 EXPORTS = ["ppf_create", "ppf_destroy", "ppf_step", "ppf_step_host", "ppf_resample", "ppf_estimate",
            "ppf_get_particles", "ppf_set_particles", "ppf_get_groups", "ppf_status_string",
-           "ppf_last_error", "ppf_profile_enable", "ppf_profile_read", "ppf_systematic_resample_noalloc"]
+           "ppf_last_error", "ppf_profile_enable", "ppf_profile_read", "ppf_systematic_resample_noalloc",
+           "ppf_loglik_grad"]
 
 
 class PPFError(RuntimeError):
@@ -131,6 +132,8 @@ def load(build_if_missing: bool = True):
             "ppf_profile_read": (C.c_int, [ctxp, P(_Profile)]),
             "ppf_systematic_resample_noalloc": (C.c_int, [vp, C.c_int64, C.c_uint64, C.c_uint32, C.c_int32, vp,
                                                           vp]),
+            "ppf_loglik_grad": (C.c_int, [ctxp, vp, C.c_int32, P(C.c_float), P(C.c_double), P(C.c_double), vp,
+                                          vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -278,3 +281,51 @@ class ParticleFilter:
         p = _Profile()
         self._check(self.L.ppf_profile_read(self._ctx, C.byref(p)), "ppf_profile_read")
         return {name: getattr(p, name) for name, _ in _Profile._fields_}
+
+    def loglik_grad(self, frames, theta=None, return_path=False):
+        """``ppf_loglik_grad``: L = sum of the per-frame log-evidences over the
+        frames (K, H, W CUDA tensor) and dL/d(sigma_PSF, A, I_bg, sigma_m).
+        Returns (L, grad[4]) or, with return_path, also the per-frame ancestors
+        (K, N) and patch anchors (K, 2, N) of the stop-gradient path."""
+        import numpy as np
+        torch = self._torch
+        if not frames.is_cuda or not frames.is_contiguous():
+            raise ValueError("frames must be a contiguous CUDA tensor")
+        K = int(frames.shape[0])
+        th = None
+        if theta is not None:
+            th = (C.c_float * 4)(*[float(v) for v in theta])
+        L = C.c_double()
+        g = (C.c_double * 4)()
+        anc = anchors = None
+        if return_path:
+            anc = torch.empty((K, self.n), dtype=torch.int32, device=frames.device)
+            anchors = torch.empty((K, 2, self.n), dtype=torch.int32, device=frames.device)
+        st = self.L.ppf_loglik_grad(self._ctx, C.c_void_p(frames.data_ptr()), K, th, C.byref(L), g,
+                                    C.c_void_p(_ptr(anc)), C.c_void_p(_ptr(anchors)))
+        if st not in (OK, EDEGENERATE):
+            self._check(st, "ppf_loglik_grad")
+        self.frame = K
+        out = (L.value, np.array(list(g)))
+        return out + (anc, anchors) if return_path else out
+
+
+def log_marginal_likelihood(theta, pf: ParticleFilter, frames):
+    """Differentiable log marginal likelihood estimate of a filter over frames,
+    as a function of theta = (sigma_PSF, A, I_bg, sigma_m) (torch tensor of 4);
+    the gradient comes from ppf_loglik_grad (stop-gradient through resampling)."""
+    import torch
+
+    class _LML(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, th):
+            L, g = pf.loglik_grad(frames, th.detach().cpu().tolist())
+            ctx.save_for_backward(torch.as_tensor(g, dtype=th.dtype, device=th.device))
+            return th.new_tensor(L)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            return gout * g
+
+    return _LML.apply(theta)

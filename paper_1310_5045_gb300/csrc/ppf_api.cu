@@ -57,7 +57,8 @@ cudaError_t dalloc(T **p, size_t count)
 
 void free_all(ppf_ctx *c)
 {
-    void *ptrs[] = {c->state[0], c->state[1], c->anc, c->anc_sys, c->lwp, c->goff, c->goff_new, c->Zp,
+    void *ptrs[] = {c->tang[0], c->tang[1], c->gpart,
+                    c->state[0], c->state[1], c->anc, c->anc_sys, c->lwp, c->goff, c->goff_new, c->Zp,
                     c->frame_buf, c->part, c->sum, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.Cbl,
                     c->sc.Tg, c->sc.skey, c->sc.sval, c->sc.seg_tick, c->sc.seg_dst, c->sc.seg_len,
                     c->sc.seg_chunk};
@@ -424,6 +425,76 @@ ppf_status ppf_profile_read(ppf_ctx *c, ppf_profile_t *out)
     out->resample_ms = ms[PH_RESAMPLE];
     out->timed_steps = c->prof_n[PH_STEP];
     return PPF_OK;
+}
+
+ppf_status ppf_loglik_grad(ppf_ctx *c, const void *frames_dev, int32_t K, const float *theta, double *loglik,
+                           double *grad, int32_t *anc_dev, int32_t *anchors_dev)
+{
+    if (!c || !frames_dev || K < 1 || !loglik || !grad)
+        return PPF_EINVAL;
+    if (theta && !(theta[0] > 0.0f && theta[3] >= 0.0f))
+        return PPF_EINVAL;
+    const int64_t N = c->N;
+    if (!c->tang[0]) {
+        cudaError_t e1 = cudaMalloc((void **)&c->tang[0], sizeof(float) * 2 * N);
+        cudaError_t e2 = cudaMalloc((void **)&c->tang[1], sizeof(float) * 2 * N);
+        cudaError_t e3 = cudaMalloc((void **)&c->gpart, sizeof(GradPartial) * c->n_part);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            set_err(c, "gradient buffers: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3));
+            return PPF_ENOMEM;
+        }
+    }
+    const ppf_model saved = c->m;
+    if (theta) {
+        c->m.psf_sigma = theta[0];
+        c->m.amplitude = theta[1];
+        c->m.background = theta[2];
+        c->m.sigma_m = theta[3];
+    }
+    ppf_status st = PPF_OK;
+    auto run = [&]() -> ppf_status {
+        CK(cudaMemsetAsync((char *)c->sum + offsetof(DevSummary, grad_L), 0, sizeof(double) * 5, c->stream));
+        CK(cudaMemsetAsync((char *)c->sum + offsetof(DevSummary, degenerate), 0, sizeof(int32_t), c->stream));
+        CK(cudaMemsetAsync((char *)c->sum + offsetof(DevSummary, flags), 0, sizeof(int32_t), c->stream));
+        CK(ppf::launch_init(c));
+        c->launches += 1;
+        const char *fr = (const char *)frames_dev;
+        for (int32_t k = 1; k <= K; ++k) {
+            if (anc_dev) {
+                if (k == 1)
+                    CK(ppf::launch_identity(c, anc_dev));
+                else
+                    CK(cudaMemcpyAsync(anc_dev + (int64_t)(k - 1) * N, c->anc, sizeof(int32_t) * N,
+                                       cudaMemcpyDeviceToDevice, c->stream));
+            }
+            CK(ppf::launch_prepare_frame(c, fr + (size_t)(k - 1) * c->frame_bytes));
+            prof_mark(c, PH_STEP, 0);
+            CK(ppf::launch_grad_step(c, k, k == 1, anchors_dev ? anchors_dev + (int64_t)(k - 1) * 2 * N : nullptr));
+            prof_mark(c, PH_STEP, 1);
+            c->cur ^= 1;
+            c->tcur ^= 1;
+            c->last_frame = k;
+            c->n_steps += 1;
+            if (k < K) {
+                CK(ppf::launch_resample_global(c, PPF_SYSTEMATIC));
+                c->n_resamples += 1;
+            }
+        }
+        CK(cudaMemcpyAsync(c->sum_host, c->sum, sizeof(DevSummary), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return PPF_OK;
+    };
+    st = run();
+    c->m = saved;
+    c->mode = MODE_CARRY;
+    c->stepped = true;
+    c->weighted = true;
+    if (st != PPF_OK)
+        return st;
+    *loglik = c->sum_host->grad_L;
+    for (int q = 0; q < 4; ++q)
+        grad[q] = c->sum_host->grad_g[q];
+    return (c->sum_host->flags & FLAG_DEGENERATE) ? PPF_EDEGENERATE : PPF_OK;
 }
 
 }  // extern "C"

@@ -31,6 +31,12 @@ struct Partial {
     float m, s0, s[5], s2, mp, sp;
 };
 
+// per-block statistics of one gradient step: log-sum-exp of l and the
+// weighted sums of dl/d(sigma_PSF, A, I_bg, sigma_m)
+struct GradPartial {
+    float m, s0, s[4];
+};
+
 // device-side per-frame results and resampling scalars
 struct DevSummary {
     double mean[5];
@@ -48,6 +54,8 @@ struct DevSummary {
     int32_t n_chunks;          // routing-copy work items of the last RPA resample
     int64_t mig;               // RNA: slots migrating to the next group
     uint32_t blocks_done;      // step kernel: blocks that published partials
+    double grad_L;             // ppf_loglik_grad: running sum of log-evidences
+    double grad_g[4];          // and of their derivatives
 };
 
 struct Scratch {
@@ -87,6 +95,9 @@ struct ppf_ctx {
     size_t frame_bytes;
     ppf::Partial *part;
     int n_part;
+    float *tang[2];               // gradient: d(x, y)/dsigma_m tangents, 2 x N each
+    int tcur;
+    ppf::GradPartial *gpart;
     ppf::DevSummary *sum;
     ppf::DevSummary *sum_host;    // pinned mirror for ppf_estimate
     ppf::Scratch sc;
@@ -111,6 +122,7 @@ void prof_mark(ppf_ctx *c, int phase, int end);
 cudaError_t launch_init(ppf_ctx *c);
 cudaError_t launch_prepare_frame(ppf_ctx *c, const void *frame);
 cudaError_t launch_step(ppf_ctx *c, int32_t k);
+cudaError_t launch_grad_step(ppf_ctx *c, int32_t k, bool first, int32_t *anchors);
 cudaError_t launch_resample_global(ppf_ctx *c, int scheme);
 cudaError_t launch_resample_rna(ppf_ctx *c, float alpha);
 cudaError_t launch_identity(ppf_ctx *c, int32_t *dst);
