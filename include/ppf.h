@@ -185,6 +185,62 @@ ppf_status ppf_get_groups(ppf_ctx *ctx, int32_t *n_groups, int64_t *offsets_host
 ppf_status ppf_loglik_grad(ppf_ctx *ctx, const void *frames_dev, int32_t K, const float *theta, double *loglik,
                            double *grad, int32_t *anc_dev, int32_t *anchors_dev);
 
+/* ------------------------------------------------------------------------
+ * Batched filters: F independent SIR filters (the bank of independent
+ * filters of Sec. 3, MPF) with uneven particle counts, stepped together.
+ * All filters share the frame size, patch radius and frame dtype; every other
+ * model field is per filter.  Filter f draws its random numbers with its
+ * model's seed and filter_id, so its results equal those of a single-filter
+ * context created with the same model and n_f (systematic resampling).
+ * ------------------------------------------------------------------------ */
+typedef struct ppf_batch ppf_batch;
+
+/* Per-filter results of a step (same meaning as ppf_estimate_t's fields). */
+typedef struct {
+    double mean[5];
+    double log_evidence;
+    double ess;
+    float max_log_weight;
+    int32_t degenerate;      /* 1: no usable weight in this filter */
+} ppf_filter_estimate_t;
+
+/* models: host array of F models; n: host array of F particle counts (>= 1,
+ * sum <= 2^31 - 1).  Draws every filter's prior (synchronises).
+ * Errors: PPF_EINVAL (geometry differs between filters, bad values), PPF_ENOMEM,
+ * PPF_ECUDA. */
+ppf_status ppf_batch_create(const ppf_model *models, const int64_t *n, int32_t F, void *cuda_stream,
+                            ppf_batch **out);
+void ppf_batch_destroy(ppf_batch *b);
+
+/* One SIS step of every filter (frames_dev: F x H x W, filter-major), then
+ * ppf_batch_resample for frame k (systematic, per filter).  A step must follow
+ * the prior draw or a resample (PPF_ESTATE otherwise). */
+ppf_status ppf_batch_step(ppf_batch *b, const void *frames_dev, int32_t k);
+ppf_status ppf_batch_resample(ppf_batch *b, int32_t k);
+
+/* K frames (frames_dev: K x F x H x W) of step + resample, frame indices
+ * k0 .. k0+K-1.  use_graph != 0 captures the whole sequence in one CUDA graph
+ * and launches it once.  est_host (optional, K x F, host) receives every
+ * filter's estimate of every frame.  Synchronous. */
+ppf_status ppf_batch_run(ppf_batch *b, const void *frames_dev, int32_t k0, int32_t K, int32_t use_graph,
+                         ppf_filter_estimate_t *est_host);
+
+/* Estimates of the last step (F entries, host; synchronises).  Returns
+ * PPF_EDEGENERATE when some filter had no usable weight since the last call. */
+ppf_status ppf_batch_estimates(ppf_batch *b, ppf_filter_estimate_t *out_host);
+
+/* Copies the concatenated state (6 x Ntot float32, filter-major slots) and
+ * the pending ancestors (Ntot int32, global slot indices); each optional. */
+ppf_status ppf_batch_get_particles(ppf_batch *b, float *state_dev, int32_t *anc_dev);
+
+/* Times launch shapes of the batched step on frame k (frames_dev F x H x W)
+ * -- work-unit size {512, 1024, 2048, 4096} particles, block {128, 256, 512}
+ * threads, {2, 4, 8} blocks per SM -- and keeps the fastest.  The filters'
+ * state is not advanced.  config_out (optional, 3 ints) receives the choice. */
+ppf_status ppf_batch_autotune(ppf_batch *b, const void *frames_dev, int32_t k, int32_t *config_out);
+
+const char *ppf_batch_last_error(const ppf_batch *b);
+
 /* Phase timing and launch counting (measurement hook; no effect on results).
  * When enabled, a pair of CUDA events is recorded on the context's stream
  * around each phase of every step / resample (up to `capacity` calls per

@@ -18,6 +18,7 @@ from ._binding import (  # noqa: F401
     RPA_SGS,
     SCHEMES,
     SYSTEMATIC,
+    BatchFilter,
     Estimate,
     Model,
     ParticleFilter,

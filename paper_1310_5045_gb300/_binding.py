@@ -22,7 +22,9 @@ SCHEMES = {"systematic": SYSTEMATIC, "rpa_gs": RPA_GS, "rpa_sgs": RPA_SGS, "rpa_
 EXPORTS = ["ppf_create", "ppf_destroy", "ppf_step", "ppf_step_host", "ppf_resample", "ppf_estimate",
            "ppf_get_particles", "ppf_set_particles", "ppf_get_groups", "ppf_status_string",
            "ppf_last_error", "ppf_profile_enable", "ppf_profile_read", "ppf_systematic_resample_noalloc",
-           "ppf_loglik_grad"]
+           "ppf_loglik_grad", "ppf_batch_create", "ppf_batch_destroy", "ppf_batch_step", "ppf_batch_resample",
+           "ppf_batch_run", "ppf_batch_estimates", "ppf_batch_get_particles", "ppf_batch_autotune",
+           "ppf_batch_last_error"]
 
 
 class PPFError(RuntimeError):
@@ -46,6 +48,15 @@ class _Estimate(C.Structure):
         ("max_log_weight", C.c_double), ("frame", C.c_int32), ("status_flags", C.c_int32),
         ("links", C.c_int64), ("moved", C.c_int64), ("max_group", C.c_int64), ("min_group", C.c_int64),
     ]
+
+
+class _FilterEstimate(C.Structure):
+    _fields_ = [("mean", C.c_double * 5), ("log_evidence", C.c_double), ("ess", C.c_double),
+                ("max_log_weight", C.c_float), ("degenerate", C.c_int32)]
+
+
+FILTER_ESTIMATE_DTYPE = [("mean", "<f8", (5,)), ("log_evidence", "<f8"), ("ess", "<f8"),
+                         ("max_log_weight", "<f4"), ("degenerate", "<i4")]
 
 
 class _Profile(C.Structure):
@@ -134,6 +145,15 @@ def load(build_if_missing: bool = True):
                                                           vp]),
             "ppf_loglik_grad": (C.c_int, [ctxp, vp, C.c_int32, P(C.c_float), P(C.c_double), P(C.c_double), vp,
                                           vp]),
+            "ppf_batch_create": (C.c_int, [P(_Model), P(C.c_int64), C.c_int32, vp, P(vp)]),
+            "ppf_batch_destroy": (None, [vp]),
+            "ppf_batch_step": (C.c_int, [vp, vp, C.c_int32]),
+            "ppf_batch_resample": (C.c_int, [vp, C.c_int32]),
+            "ppf_batch_run": (C.c_int, [vp, vp, C.c_int32, C.c_int32, C.c_int32, vp]),
+            "ppf_batch_estimates": (C.c_int, [vp, vp]),
+            "ppf_batch_get_particles": (C.c_int, [vp, vp, vp]),
+            "ppf_batch_autotune": (C.c_int, [vp, vp, C.c_int32, P(C.c_int32)]),
+            "ppf_batch_last_error": (C.c_char_p, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -329,3 +349,79 @@ def log_marginal_likelihood(theta, pf: ParticleFilter, frames):
             return gout * g
 
     return _LML.apply(theta)
+
+
+class BatchFilter:
+    """F independent SIR filters with uneven particle counts (``ppf_batch``)."""
+
+    def __init__(self, models, ns, stream=None):
+        import numpy as np
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("BatchFilter needs a CUDA GPU")
+        self._torch = torch
+        self.L = load()
+        self.F = len(models)
+        self.ns = np.asarray(ns, dtype=np.int64)
+        self.offsets = np.concatenate([[0], np.cumsum(self.ns)])
+        self.ntot = int(self.offsets[-1])
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (_Model * self.F)(*[m.c() for m in models])
+        nn = (C.c_int64 * self.F)(*[int(v) for v in self.ns])
+        self._b = C.c_void_p()
+        st = self.L.ppf_batch_create(arr, nn, self.F, C.c_void_p(self.stream.cuda_stream), C.byref(self._b))
+        if st != OK:
+            raise PPFError(st, f"ppf_batch_create: {status_string(st)}")
+
+    def _check(self, st, what):
+        if st != OK:
+            raise PPFError(st, f"{what}: {status_string(st)} {self.L.ppf_batch_last_error(self._b).decode()}")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self.L.ppf_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, frames, k):
+        self._check(self.L.ppf_batch_step(self._b, C.c_void_p(frames.data_ptr()), int(k)), "ppf_batch_step")
+
+    def resample(self, k):
+        self._check(self.L.ppf_batch_resample(self._b, int(k)), "ppf_batch_resample")
+
+    def run(self, frames, k0=1, use_graph=True, estimates=True):
+        """K frames (K, F, H, W) of step + resample; returns (K, F) estimates."""
+        import numpy as np
+        K = int(frames.shape[0])
+        out = np.zeros((K, self.F), dtype=FILTER_ESTIMATE_DTYPE) if estimates else None
+        st = self.L.ppf_batch_run(self._b, C.c_void_p(frames.data_ptr()), int(k0), K, 1 if use_graph else 0,
+                                  C.c_void_p(out.ctypes.data) if estimates else None)
+        self._check(st, "ppf_batch_run")
+        return out
+
+    def estimates(self):
+        import numpy as np
+        out = np.zeros(self.F, dtype=FILTER_ESTIMATE_DTYPE)
+        st = self.L.ppf_batch_estimates(self._b, C.c_void_p(out.ctypes.data))
+        if st not in (OK, EDEGENERATE):
+            self._check(st, "ppf_batch_estimates")
+        return out
+
+    def get_particles(self, state=True, anc=False):
+        torch = self._torch
+        s = torch.empty((6, self.ntot), dtype=torch.float32, device="cuda") if state else None
+        a = torch.empty(self.ntot, dtype=torch.int32, device="cuda") if anc else None
+        self._check(self.L.ppf_batch_get_particles(self._b, C.c_void_p(_ptr(s)), C.c_void_p(_ptr(a))),
+                    "ppf_batch_get_particles")
+        return s, a
+
+    def autotune(self, frames, k):
+        cfg = (C.c_int32 * 3)()
+        self._check(self.L.ppf_batch_autotune(self._b, C.c_void_p(frames.data_ptr()), int(k), cfg),
+                    "ppf_batch_autotune")
+        return {"unit": cfg[0], "block": cfg[1], "blocks_per_sm": cfg[2]}

@@ -1,0 +1,769 @@
+// ppf_batch.cu -- F independent SIR filters (the paper's bank of particle
+// filters, Sec. 3 "MPF") with uneven particle counts, stepped together:
+//   * all particles of all filters live in one concatenated 6 x Ntot SoA
+//     state; filter f owns slots [off_f, off_f + n_f);
+//   * one persistent kernel per frame walks work units (filter, run of at most
+//     `unit` particles) and writes per-unit weight statistics;
+//   * a per-filter FP64 finalisation (one warp per filter) gives each
+//     filter's estimate, N_eff and log-evidence;
+//   * one block per filter resamples it systematically (Alg. 1) on 64-bit
+//     fixed point, exactly as a single filter with filter id f would;
+//   * a whole movie of K frames can be captured in one CUDA graph;
+//   * an autotuner times launch shapes (block size, blocks per SM, unit size)
+//     on the caller's data and keeps the fastest.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ppf_device.cuh"
+#include "ppf_internal.h"
+#include "ppf_kernels.cuh"
+#include "ppf_tiles.cuh"
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace ppf {
+
+struct FilterParams {
+    int64_t off, n;
+    uint64_t seed;
+    uint32_t fid;
+    float inv2s2, inv_sxi2, sm, sv, sI, bg;
+    float Kc[MAX_RADIUS];
+};
+
+// same layout as ppf_filter_estimate_t
+struct FilterSummary {
+    double mean[5];
+    double log_evidence;
+    double ess;
+    float M;
+    int32_t degenerate;
+};
+static_assert(sizeof(FilterSummary) == sizeof(ppf_filter_estimate_t), "layout");
+
+}  // namespace ppf
+
+struct ppf_batch {
+    int32_t F;
+    int64_t Ntot;
+    int32_t W, H, r, Wp, Hp, pad;
+    int32_t dtype;
+    size_t frame_bytes;                // one filter's frame
+    cudaStream_t stream;
+    int num_sms;
+    std::vector<ppf_model> models;
+    std::vector<int64_t> n, off;
+    ppf::FilterParams *fp;             // device [F]
+    float *state[2];
+    int cur;
+    int32_t *anc;
+    float *Zp;                         // F x Hp x Wp
+    // work units
+    int32_t unit, block, bps;          // tuned launch shape
+    int32_t U;
+    int32_t *unit_f;                   // device [U]
+    int64_t *unit_lo;
+    int32_t *unit_n;
+    int32_t *fu_off;                   // device [F + 1]: units of filter f
+    ppf::Partial *upart;               // device [U]
+    ppf::FilterSummary *fsum;          // device [F]
+    ppf::FilterSummary *fsum_host;     // pinned [F]
+    ppf::FilterSummary *fsum_run;      // device [K x F] of the last graph run
+    int64_t fsum_run_cap;
+    int32_t *flags;                    // device: any degenerate filter
+    bool first;                        // next step starts from the prior draw
+    bool weighted;
+    int64_t launches;
+    char err[256];
+};
+
+namespace ppf {
+namespace {
+
+// ------------------------------------------------------------------ kernels
+__global__ void batch_init_kernel(float *__restrict__ st, int64_t Ntot, const FilterParams *__restrict__ fp,
+                                  const int32_t *__restrict__ unit_f, const int64_t *__restrict__ unit_lo,
+                                  const int32_t *__restrict__ unit_n, int32_t U, float W, float H,
+                                  const float *__restrict__ v0A)
+{
+    for (int32_t u = blockIdx.x; u < U; u += gridDim.x) {
+        const int32_t f = unit_f[u];
+        const FilterParams P = fp[f];
+        const float v0 = v0A[2 * f], A = v0A[2 * f + 1];
+        for (int32_t j = threadIdx.x; j < unit_n[u]; j += blockDim.x) {
+            const int64_t i = unit_lo[u] + j;
+            const uint32_t slot = (uint32_t)(i - P.off);
+            const uint4 a = draw(P.seed, slot, 0u, P.fid, PURPOSE_INIT, 0);
+            const uint4 b = draw(P.seed, slot, 0u, P.fid, PURPOSE_INIT, 1);
+            st[i] = -0.5f + W * u01(a.x);
+            st[Ntot + i] = -0.5f + H * u01(a.y);
+            st[2 * Ntot + i] = v0 * (2.0f * u01(a.z) - 1.0f);
+            st[3 * Ntot + i] = v0 * (2.0f * u01(a.w) - 1.0f);
+            st[4 * Ntot + i] = A * (0.5f + u01(b.x));
+            st[5 * Ntot + i] = 0.0f;
+        }
+    }
+}
+
+// frames F x H x W -> padded F x Hp x Wp, minus each filter's background
+template <typename T>
+__device__ __forceinline__ float tof(T v);
+template <>
+__device__ __forceinline__ float tof<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ float tof<__half>(__half v) { return __half2float(v); }
+
+template <typename T>
+__global__ void batch_prepare_kernel(const T *__restrict__ Z, float *__restrict__ Zp, int32_t F, int W, int H, int Wp,
+                                     int Hp, int pad, const FilterParams *__restrict__ fp)
+{
+    const int64_t plane = (int64_t)Wp * Hp;
+    const int64_t n = plane * F;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t f = (int32_t)(idx / plane);
+        const int64_t rem = idx - f * plane;
+        const int py = (int)(rem / Wp) - pad, px = (int)(rem % Wp) - pad;
+        float v = 0.0f;
+        if (px >= 0 && px < W && py >= 0 && py < H)
+            v = tof<T>(Z[((int64_t)f * H + py) * W + px]) - fp[f].bg;
+        Zp[idx] = v;
+    }
+}
+
+struct BatchStepArgs {
+    int64_t Ntot;
+    int W, H, Wp, Hp, pad;
+    uint32_t frame;
+    int first;
+    const FilterParams *__restrict__ fp;
+    const int32_t *__restrict__ unit_f;
+    const int64_t *__restrict__ unit_lo;
+    const int32_t *__restrict__ unit_n;
+    int32_t U;
+    const float *__restrict__ src;
+    float *__restrict__ dst;
+    const int32_t *__restrict__ anc;
+    const float *__restrict__ Zp;
+    Partial *__restrict__ part;
+};
+
+// persistent SIS step over all units of all filters
+template <int R>
+__global__ void batch_step_kernel(BatchStepArgs a)
+{
+    const int64_t N = a.Ntot;
+    __shared__ FilterParams P;
+    __shared__ Acc sh[32];
+    for (int32_t u = blockIdx.x; u < a.U; u += gridDim.x) {
+        const int32_t f = a.unit_f[u];
+        __syncthreads();
+        if (threadIdx.x == 0)
+            P = a.fp[f];
+        __syncthreads();
+        const PatchGeom geom{a.Zp + (int64_t)f * a.Wp * a.Hp, a.W, a.H, a.Wp, a.pad, P.inv2s2, P.inv_sxi2, P.Kc};
+        Acc acc;
+        acc.init();
+        const int64_t lo = a.unit_lo[u];
+        const int32_t n = a.unit_n[u];
+        for (int32_t j = threadIdx.x; j < n; j += blockDim.x) {
+            const int64_t i = lo + j;
+            int64_t p = a.first ? i : (int64_t)__ldg(a.anc + i);
+            if (p < P.off || p >= P.off + P.n)
+                p = i;  // ancestors never cross filters
+            const float x = __ldg(a.src + p), y = __ldg(a.src + N + p);
+            const float vx = __ldg(a.src + 2 * N + p), vy = __ldg(a.src + 3 * N + p);
+            const float I0 = __ldg(a.src + 4 * N + p);
+            const float lwp = a.first ? __ldg(a.src + 5 * N + p) : 0.0f;
+            uint32_t fl[6];
+            prop_fields(draw(P.seed, (uint32_t)(i - P.off), a.frame, P.fid, PURPOSE_PROP, 0), fl);
+            float e0, e1, e2, e3, e4, e5;
+            box_muller(u21(fl[0]), u21(fl[1]), e0, e1);
+            box_muller(u21(fl[2]), u21(fl[3]), e2, e3);
+            box_muller(u21(fl[4]), u21(fl[5]), e4, e5);
+            float v[5];
+            v[0] = fmaf(P.sm, e0, x + vx);
+            v[1] = fmaf(P.sm, e1, y + vy);
+            v[2] = fmaf(P.sv, e2, vx);
+            v[3] = fmaf(P.sv, e3, vy);
+            v[4] = fmaf(P.sI, e4, I0);
+            const float lw = lwp + patch_loglik<R>(geom, v[0], v[1], v[4]);
+#pragma unroll
+            for (int c = 0; c < 5; ++c)
+                a.dst[c * N + i] = v[c];
+            a.dst[5 * N + i] = lw;
+            acc.add(lw, lwp, v);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            acc.shfl_merge(o);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        if (lane == 0)
+            sh[warp] = acc;
+        __syncthreads();
+        if (warp == 0) {
+            if (lane < nw)
+                acc = sh[lane];
+            else
+                acc.init();
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                acc.shfl_merge(o);
+            if (lane == 0) {
+                Partial q;
+                q.m = acc.m;
+                q.s0 = acc.s0;
+                q.s2 = acc.s2;
+                for (int c = 0; c < 5; ++c)
+                    q.s[c] = acc.s[c];
+                q.mp = acc.mp;
+                q.sp = acc.sp;
+                a.part[u] = q;
+            }
+        }
+    }
+}
+
+// one warp per filter: FP64 combination of its units' partials
+__global__ void batch_finalize_kernel(const Partial *__restrict__ part, const int32_t *__restrict__ fu_off, int32_t F,
+                                      FilterSummary *__restrict__ fs)
+{
+    const int32_t f = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (f >= F)
+        return;
+    const int32_t u0 = fu_off[f], u1 = fu_off[f + 1];
+    float m = -INFINITY, mp = -INFINITY;
+    for (int32_t u = u0 + lane; u < u1; u += 32) {
+        m = fmaxf(m, part[u].m);
+        mp = fmaxf(mp, part[u].mp);
+    }
+    m = warp_max(m);
+    mp = warp_max(mp);
+    double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int32_t u = u0 + lane; u < u1; u += 32) {
+        const Partial q = part[u];
+        if (q.m > -INFINITY) {
+            const double sc = (double)expf(q.m - m);
+            t[0] += q.s0 * sc;
+            for (int c = 0; c < 5; ++c)
+                t[1 + c] += q.s[c] * sc;
+            t[6] += q.s2 * sc * sc;
+        }
+        if (q.mp > -INFINITY)
+            t[7] += q.sp * (double)expf(q.mp - mp);
+    }
+    for (int c = 0; c < 8; ++c)
+        t[c] = warp_sum_d(t[c]);
+    if (lane == 0) {
+        FilterSummary s;
+        for (int c = 0; c < 5; ++c)
+            s.mean[c] = t[1 + c] / t[0];
+        s.ess = t[0] * t[0] / t[6];
+        s.log_evidence = ((double)m + log(t[0])) - ((double)mp + log(t[7]));
+        s.M = m;
+        s.degenerate = (t[0] > 0.0) ? 0 : 1;
+        fs[f] = s;
+    }
+}
+
+// one block per filter: systematic resampling of its n_f slots (Alg. 1) on
+// 64-bit fixed point, the same tickets as a single filter with filter id f
+__global__ void __launch_bounds__(TILE_THREADS) batch_resample_kernel(const float *__restrict__ lw,
+                                                                      const FilterParams *__restrict__ fp,
+                                                                      const FilterSummary *__restrict__ fs,
+                                                                      uint32_t frame, int32_t *__restrict__ anc,
+                                                                      int32_t *__restrict__ flags)
+{
+    __shared__ uint64_t C[TILE + TILE / 16];
+    __shared__ uint64_t red[33];
+    __shared__ uint64_t Qs, us;
+    const int32_t f = blockIdx.x;
+    const FilterParams P = fp[f];
+    const int64_t lo = P.off, sz = P.n;
+    const float Mf = fs[f].M;
+    const int s = scale_bits(sz);
+    uint64_t qs = 0;
+    for (int64_t i = threadIdx.x; i < sz; i += blockDim.x)
+        qs += quantise(__ldg(lw + lo + i), Mf, s);
+    uint64_t Q;
+    block_excl_scan_u64(qs, red, &Q);
+    if (threadIdx.x == 0) {
+        Qs = Q;
+        us = (Q == 0ull) ? 0ull : ticket_offset(P.seed, P.fid, frame, PURPOSE_RESAMPLE, 0u, Q);
+        if (Q == 0ull)
+            atomicOr(flags, FLAG_DEGENERATE);
+    }
+    __syncthreads();
+    Q = Qs;
+    const uint64_t u = us;
+    if (Q == 0ull) {  // no usable weight: the filter keeps its particles
+        for (int64_t j = threadIdx.x; j < sz; j += blockDim.x)
+            anc[lo + j] = (int32_t)(lo + j);
+        return;
+    }
+    uint64_t carry = 0;
+    for (int64_t c0 = 0; c0 < sz; c0 += TILE) {
+        const int n = (int)(sz - c0 < TILE ? sz - c0 : TILE);
+        uint64_t q[TILE_ITEMS];
+        tile_weights(lw, lo + c0, n, Mf, s, C, q);
+        const uint64_t tot = tile_scan(q, C, red);
+        const int64_t t_lo = tickets_below(carry, sz, u, Q);
+        const int64_t t_hi = tickets_below(carry + tot, sz, u, Q);
+        ticket_parents(C, n, carry, u, Q, (uint32_t)sz, t_lo, t_hi,
+                       [&](int64_t j, int i) { anc[lo + j] = (int32_t)(lo + c0 + i); });
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ host side
+template <typename T>
+cudaError_t dmalloc(T **p, size_t n)
+{
+    *p = nullptr;
+    return cudaMalloc((void **)p, sizeof(T) * (n ? n : 1));
+}
+
+cudaError_t build_units(ppf_batch *b, int32_t unit)
+{
+    std::vector<int32_t> uf, un, fo(b->F + 1);
+    std::vector<int64_t> ul;
+    for (int32_t f = 0; f < b->F; ++f) {
+        fo[f] = (int32_t)uf.size();
+        for (int64_t s = 0; s < b->n[f]; s += unit) {
+            uf.push_back(f);
+            ul.push_back(b->off[f] + s);
+            un.push_back((int32_t)((b->n[f] - s) < unit ? (b->n[f] - s) : unit));
+        }
+    }
+    fo[b->F] = (int32_t)uf.size();
+    if (b->unit_f) {
+        cudaFree(b->unit_f);
+        cudaFree(b->unit_lo);
+        cudaFree(b->unit_n);
+        cudaFree(b->upart);
+    }
+    b->U = (int32_t)uf.size();
+    cudaError_t e;
+    if ((e = dmalloc(&b->unit_f, b->U)) != cudaSuccess) return e;
+    if ((e = dmalloc(&b->unit_lo, b->U)) != cudaSuccess) return e;
+    if ((e = dmalloc(&b->unit_n, b->U)) != cudaSuccess) return e;
+    if ((e = dmalloc(&b->upart, b->U)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b->unit_f, uf.data(), sizeof(int32_t) * b->U, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b->unit_lo, ul.data(), sizeof(int64_t) * b->U, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b->unit_n, un.data(), sizeof(int32_t) * b->U, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b->fu_off, fo.data(), sizeof(int32_t) * (b->F + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    b->unit = unit;
+    return cudaSuccess;
+}
+
+template <int R>
+void launch_batch_step_r(const BatchStepArgs &a, int grid, int block, cudaStream_t s)
+{
+    batch_step_kernel<R><<<grid, block, 0, s>>>(a);
+}
+
+cudaError_t launch_batch_step(ppf_batch *b, int32_t k, bool commit)
+{
+    BatchStepArgs a;
+    a.Ntot = b->Ntot;
+    a.W = b->W;
+    a.H = b->H;
+    a.Wp = b->Wp;
+    a.Hp = b->Hp;
+    a.pad = b->pad;
+    a.frame = (uint32_t)k;
+    a.first = b->first ? 1 : 0;
+    a.fp = b->fp;
+    a.unit_f = b->unit_f;
+    a.unit_lo = b->unit_lo;
+    a.unit_n = b->unit_n;
+    a.U = b->U;
+    a.src = b->state[b->cur];
+    a.dst = b->state[b->cur ^ 1];
+    a.anc = b->anc;
+    a.Zp = b->Zp;
+    a.part = b->upart;
+    int grid = b->num_sms * b->bps;
+    if (grid > b->U)
+        grid = b->U;
+    switch (b->r) {
+    case 0: launch_batch_step_r<0>(a, grid, b->block, b->stream); break;
+    case 1: launch_batch_step_r<1>(a, grid, b->block, b->stream); break;
+    case 2: launch_batch_step_r<2>(a, grid, b->block, b->stream); break;
+    case 3: launch_batch_step_r<3>(a, grid, b->block, b->stream); break;
+    case 4: launch_batch_step_r<4>(a, grid, b->block, b->stream); break;
+    case 5: launch_batch_step_r<5>(a, grid, b->block, b->stream); break;
+    case 6: launch_batch_step_r<6>(a, grid, b->block, b->stream); break;
+    case 7: launch_batch_step_r<7>(a, grid, b->block, b->stream); break;
+    default: launch_batch_step_r<8>(a, grid, b->block, b->stream); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !commit)
+        return e;
+    const int fgrid = (b->F * 32 + 255) / 256;
+    batch_finalize_kernel<<<fgrid, 256, 0, b->stream>>>(b->upart, b->fu_off, b->F, b->fsum);
+    b->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_prepare(ppf_batch *b, const void *frames)
+{
+    const int64_t n = (int64_t)b->F * b->Wp * b->Hp;
+    const int grid = (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
+    switch (b->dtype) {
+    case PPF_BF16:
+        batch_prepare_kernel<__nv_bfloat16><<<grid, 256, 0, b->stream>>>((const __nv_bfloat16 *)frames, b->Zp, b->F,
+                                                                         b->W, b->H, b->Wp, b->Hp, b->pad, b->fp);
+        break;
+    case PPF_F16:
+        batch_prepare_kernel<__half><<<grid, 256, 0, b->stream>>>((const __half *)frames, b->Zp, b->F, b->W, b->H,
+                                                                  b->Wp, b->Hp, b->pad, b->fp);
+        break;
+    default:
+        batch_prepare_kernel<float><<<grid, 256, 0, b->stream>>>((const float *)frames, b->Zp, b->F, b->W, b->H,
+                                                                 b->Wp, b->Hp, b->pad, b->fp);
+    }
+    b->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_resample(ppf_batch *b, int32_t k)
+{
+    batch_resample_kernel<<<b->F, TILE_THREADS, 0, b->stream>>>(b->state[b->cur] + 5 * b->Ntot, b->fp, b->fsum,
+                                                                (uint32_t)k, b->anc, b->flags);
+    b->launches += 1;
+    return cudaGetLastError();
+}
+
+void free_batch(ppf_batch *b)
+{
+    void *p[] = {b->fp, b->state[0], b->state[1], b->anc, b->Zp, b->unit_f, b->unit_lo, b->unit_n, b->fu_off,
+                 b->upart, b->fsum, b->flags, b->fsum_run};
+    for (void *q : p)
+        if (q)
+            cudaFree(q);
+    if (b->fsum_host)
+        cudaFreeHost(b->fsum_host);
+}
+
+}  // namespace
+}  // namespace ppf
+
+using namespace ppf;
+
+#define BCK(call)                                                                  \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            snprintf(b->err, sizeof(b->err), "%s: %s", #call, cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? PPF_ENOMEM : PPF_ECUDA;       \
+        }                                                                          \
+    } while (0)
+
+extern "C" {
+
+ppf_status ppf_batch_create(const ppf_model *models, const int64_t *n, int32_t F, void *cuda_stream, ppf_batch **out)
+{
+    if (!models || !n || !out || F < 1)
+        return PPF_EINVAL;
+    const ppf_model &m0 = models[0];
+    int64_t Ntot = 0;
+    for (int32_t f = 0; f < F; ++f) {
+        const ppf_model &m = models[f];
+        if (m.width != m0.width || m.height != m0.height || m.patch_radius != m0.patch_radius ||
+            m.frame_dtype != m0.frame_dtype)
+            return PPF_EINVAL;
+        if (!(m.psf_sigma > 0.0f) || !(m.sigma_xi > 0.0f) || !(m.sigma_m >= 0.0f) || !(m.sigma_v >= 0.0f) ||
+            !(m.sigma_I >= 0.0f) || !(m.v0_max >= 0.0f))
+            return PPF_EINVAL;
+        if (n[f] < 1)
+            return PPF_EINVAL;
+        Ntot += n[f];
+    }
+    if (Ntot > 2147483647LL || m0.width < 1 || m0.height < 1 || m0.patch_radius < 0 || m0.patch_radius > MAX_RADIUS)
+        return PPF_EINVAL;
+    if (m0.frame_dtype != PPF_F32 && m0.frame_dtype != PPF_BF16 && m0.frame_dtype != PPF_F16)
+        return PPF_EINVAL;
+    ppf_batch *b = new (std::nothrow) ppf_batch();
+    if (!b)
+        return PPF_ENOMEM;
+    b->F = F;
+    b->Ntot = Ntot;
+    b->W = m0.width;
+    b->H = m0.height;
+    b->r = m0.patch_radius;
+    b->pad = 2 * b->r;
+    b->Wp = b->W + 2 * b->pad;
+    b->Hp = b->H + 2 * b->pad;
+    b->dtype = m0.frame_dtype;
+    b->frame_bytes = (size_t)b->W * b->H * (b->dtype == PPF_F32 ? 4 : 2);
+    b->stream = (cudaStream_t)cuda_stream;
+    b->models.assign(models, models + F);
+    b->n.assign(n, n + F);
+    b->off.resize(F);
+    int64_t o = 0;
+    for (int32_t f = 0; f < F; ++f) {
+        b->off[f] = o;
+        o += n[f];
+    }
+    b->block = 256;
+    b->bps = 4;
+    b->first = true;
+    auto fail = [&](ppf_status st) {
+        free_batch(b);
+        delete b;
+        return st;
+    };
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return fail(PPF_ECUDA);
+    std::vector<FilterParams> hp(F);
+    std::vector<float> v0A(2 * (size_t)F);
+    for (int32_t f = 0; f < F; ++f) {
+        const ppf_model &m = models[f];
+        FilterParams &P = hp[f];
+        P.off = b->off[f];
+        P.n = n[f];
+        P.seed = m.seed;
+        P.fid = m.filter_id;
+        P.inv2s2 = 1.0f / (2.0f * m.psf_sigma * m.psf_sigma);
+        P.inv_sxi2 = 1.0f / (m.sigma_xi * m.sigma_xi);
+        P.sm = m.sigma_m;
+        P.sv = m.sigma_v;
+        P.sI = m.sigma_I;
+        P.bg = m.background;
+        for (int k = 0; k < MAX_RADIUS; ++k)
+            P.Kc[k] = (float)exp(-(2.0 * k + 1.0) * (double)P.inv2s2);
+        v0A[2 * f] = m.v0_max;
+        v0A[2 * f + 1] = m.amplitude;
+    }
+    float *dv0A = nullptr;
+    if (dmalloc(&b->fp, F) != cudaSuccess || dmalloc(&b->state[0], 6 * Ntot) != cudaSuccess ||
+        dmalloc(&b->state[1], 6 * Ntot) != cudaSuccess || dmalloc(&b->anc, Ntot) != cudaSuccess ||
+        dmalloc(&b->Zp, (size_t)F * b->Wp * b->Hp) != cudaSuccess || dmalloc(&b->fu_off, F + 1) != cudaSuccess ||
+        dmalloc(&b->fsum, F) != cudaSuccess || dmalloc(&b->flags, 1) != cudaSuccess ||
+        cudaMallocHost((void **)&b->fsum_host, sizeof(FilterSummary) * F) != cudaSuccess ||
+        dmalloc(&dv0A, 2 * (size_t)F) != cudaSuccess)
+        return (dv0A ? cudaFree(dv0A) : cudaSuccess), fail(PPF_ENOMEM);
+    if (cudaMemcpy(b->fp, hp.data(), sizeof(FilterParams) * F, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dv0A, v0A.data(), sizeof(float) * 2 * F, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->flags, 0, sizeof(int32_t)) != cudaSuccess || build_units(b, 1024) != cudaSuccess) {
+        cudaFree(dv0A);
+        return fail(PPF_ECUDA);
+    }
+    batch_init_kernel<<<4 * b->num_sms, 256, 0, b->stream>>>(b->state[0], Ntot, b->fp, b->unit_f, b->unit_lo,
+                                                               b->unit_n, b->U, (float)b->W, (float)b->H, dv0A);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(b->stream);
+    cudaFree(dv0A);
+    if (e != cudaSuccess)
+        return fail(PPF_ECUDA);
+    *out = b;
+    return PPF_OK;
+}
+
+void ppf_batch_destroy(ppf_batch *b)
+{
+    if (!b)
+        return;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    delete b;
+}
+
+ppf_status ppf_batch_step(ppf_batch *b, const void *frames_dev, int32_t k)
+{
+    if (!b || !frames_dev || k < 1)
+        return PPF_EINVAL;
+    if (b->weighted)
+        return PPF_ESTATE;  // every batched step follows a resample (or the prior)
+    BCK(launch_batch_prepare(b, frames_dev));
+    BCK(launch_batch_step(b, k, true));
+    b->cur ^= 1;
+    b->first = false;
+    b->weighted = true;
+    return PPF_OK;
+}
+
+ppf_status ppf_batch_resample(ppf_batch *b, int32_t k)
+{
+    if (!b)
+        return PPF_EINVAL;
+    if (!b->weighted)
+        return PPF_ESTATE;
+    BCK(launch_batch_resample(b, k));
+    b->weighted = false;
+    return PPF_OK;
+}
+
+ppf_status ppf_batch_run(ppf_batch *b, const void *frames_dev, int32_t k0, int32_t K, int32_t use_graph,
+                         ppf_filter_estimate_t *est_host)
+{
+    if (!b || !frames_dev || k0 < 1 || K < 1)
+        return PPF_EINVAL;
+    if (b->weighted)
+        return PPF_ESTATE;
+    if (est_host && b->fsum_run_cap < (int64_t)K * b->F) {
+        if (b->fsum_run)
+            cudaFree(b->fsum_run);
+        b->fsum_run = nullptr;
+        BCK(cudaMalloc((void **)&b->fsum_run, sizeof(FilterSummary) * (size_t)K * b->F));
+        b->fsum_run_cap = (int64_t)K * b->F;
+    }
+    const size_t per_frame = b->frame_bytes * (size_t)b->F;
+    const char *fr = (const char *)frames_dev;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = b->stream;
+    bool own = false;
+    if (use_graph && cap == nullptr) {  // the legacy stream cannot be captured
+        BCK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        BCK(cudaStreamSynchronize(nullptr));
+        own = true;
+    }
+    cudaStream_t saved = b->stream;
+    b->stream = cap;
+    if (use_graph)
+        BCK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    ppf_status st = PPF_OK;
+    for (int32_t t = 0; t < K && st == PPF_OK; ++t) {
+        cudaError_t e = launch_batch_prepare(b, fr + per_frame * t);
+        if (e == cudaSuccess)
+            e = launch_batch_step(b, k0 + t, true);
+        b->cur ^= 1;
+        b->first = false;
+        if (e == cudaSuccess)
+            e = launch_batch_resample(b, k0 + t);
+        if (e == cudaSuccess && est_host)
+            e = cudaMemcpyAsync(b->fsum_run + (size_t)t * b->F, b->fsum, sizeof(FilterSummary) * b->F,
+                                cudaMemcpyDeviceToDevice, cap);
+        if (e != cudaSuccess) {
+            snprintf(b->err, sizeof(b->err), "batch frame %d: %s", k0 + t, cudaGetErrorString(e));
+            st = PPF_ECUDA;
+        }
+    }
+    if (use_graph) {
+        cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        if (st == PPF_OK && e == cudaSuccess)
+            e = cudaGraphInstantiate(&exec, graph, 0);
+        if (st == PPF_OK && e == cudaSuccess)
+            e = cudaGraphLaunch(exec, cap);
+        if (st == PPF_OK && e != cudaSuccess) {
+            snprintf(b->err, sizeof(b->err), "graph: %s", cudaGetErrorString(e));
+            st = PPF_ECUDA;
+        }
+    }
+    if (st == PPF_OK && est_host) {
+        cudaError_t e2 = cudaMemcpyAsync(est_host, b->fsum_run, sizeof(FilterSummary) * (size_t)K * b->F,
+                                         cudaMemcpyDeviceToHost, cap);
+        if (e2 != cudaSuccess)
+            st = PPF_ECUDA;
+    }
+    cudaError_t e = cudaStreamSynchronize(cap);
+    if (exec)
+        cudaGraphExecDestroy(exec);
+    if (graph)
+        cudaGraphDestroy(graph);
+    if (own)
+        cudaStreamDestroy(cap);
+    b->stream = saved;
+    if (st == PPF_OK && e != cudaSuccess) {
+        snprintf(b->err, sizeof(b->err), "run: %s", cudaGetErrorString(e));
+        st = PPF_ECUDA;
+    }
+    return st;
+}
+
+ppf_status ppf_batch_estimates(ppf_batch *b, ppf_filter_estimate_t *out_host)
+{
+    if (!b || !out_host)
+        return PPF_EINVAL;
+    BCK(cudaMemcpyAsync(b->fsum_host, b->fsum, sizeof(FilterSummary) * b->F, cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    memcpy(out_host, b->fsum_host, sizeof(FilterSummary) * b->F);
+    int32_t fl = 0;
+    BCK(cudaMemcpy(&fl, b->flags, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (fl) {
+        BCK(cudaMemset(b->flags, 0, sizeof(int32_t)));
+        return PPF_EDEGENERATE;
+    }
+    return PPF_OK;
+}
+
+ppf_status ppf_batch_get_particles(ppf_batch *b, float *state_dev, int32_t *anc_dev)
+{
+    if (!b)
+        return PPF_EINVAL;
+    if (state_dev)
+        BCK(cudaMemcpyAsync(state_dev, b->state[b->cur], sizeof(float) * 6 * b->Ntot, cudaMemcpyDeviceToDevice,
+                            b->stream));
+    if (anc_dev)
+        BCK(cudaMemcpyAsync(anc_dev, b->anc, sizeof(int32_t) * b->Ntot, cudaMemcpyDeviceToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return PPF_OK;
+}
+
+ppf_status ppf_batch_autotune(ppf_batch *b, const void *frames_dev, int32_t k, int32_t *config_out)
+{
+    if (!b || !frames_dev || k < 1)
+        return PPF_EINVAL;
+    BCK(launch_batch_prepare(b, frames_dev));
+    const int32_t units[] = {512, 1024, 2048, 4096};
+    const int32_t blocks[] = {128, 256, 512};
+    const int32_t bpss[] = {2, 4, 8};
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int32_t bu = b->unit, bb = b->block, bs = b->bps;
+    for (int32_t un : units) {
+        BCK(build_units(b, un));
+        for (int32_t bl : blocks)
+            for (int32_t bp : bpss) {
+                b->block = bl;
+                b->bps = bp;
+                // the step writes the other state buffer only (no swap): re-running it is harmless
+                BCK(launch_batch_step(b, k, false));
+                BCK(cudaEventRecord(e0, b->stream));
+                for (int rep = 0; rep < 3; ++rep)
+                    BCK(launch_batch_step(b, k, false));
+                BCK(cudaEventRecord(e1, b->stream));
+                BCK(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                BCK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    bu = un;
+                    bb = bl;
+                    bs = bp;
+                }
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    BCK(build_units(b, bu));
+    b->block = bb;
+    b->bps = bs;
+    if (config_out) {
+        config_out[0] = bu;
+        config_out[1] = bb;
+        config_out[2] = bs;
+    }
+    return PPF_OK;
+}
+
+const char *ppf_batch_last_error(const ppf_batch *b)
+{
+    return b ? b->err : "";
+}
+
+}  // extern "C"

@@ -9,6 +9,7 @@
 
 #include "ppf_device.cuh"
 #include "ppf_internal.h"
+#include "ppf_kernels.cuh"
 
 namespace ppf {
 
@@ -79,75 +80,6 @@ struct StepArgs {
     DevSummary *sum;
 };
 
-// Online log-sum-exp accumulator of the weight statistics.
-struct Acc {
-    float m, s0, s[5], s2, mp, sp;
-    __device__ __forceinline__ void init()
-    {
-        m = mp = -INFINITY;
-        s0 = s2 = sp = 0.0f;
-#pragma unroll
-        for (int c = 0; c < 5; ++c)
-            s[c] = 0.0f;
-    }
-    __device__ __forceinline__ void add(float lw, float lwp, const float v[5])
-    {
-        if (lw > m) {
-            const float sc = __expf(m - lw);
-            s0 *= sc;
-            s2 *= sc * sc;
-#pragma unroll
-            for (int c = 0; c < 5; ++c)
-                s[c] *= sc;
-            m = lw;
-        }
-        if (lw > -INFINITY) {
-            const float e = __expf(lw - m);
-            s0 += e;
-            s2 = fmaf(e, e, s2);
-#pragma unroll
-            for (int c = 0; c < 5; ++c)
-                s[c] = fmaf(e, v[c], s[c]);
-        }
-        if (lwp > mp) {
-            sp *= __expf(mp - lwp);
-            mp = lwp;
-        }
-        if (lwp > -INFINITY)
-            sp += __expf(lwp - mp);
-    }
-    __device__ __forceinline__ void merge(const Acc &o)
-    {
-        const float nm = fmaxf(m, o.m);
-        const float fa = (m == -INFINITY) ? 0.0f : __expf(m - nm);
-        const float fb = (o.m == -INFINITY) ? 0.0f : __expf(o.m - nm);
-        s0 = s0 * fa + o.s0 * fb;
-        s2 = s2 * fa * fa + o.s2 * fb * fb;
-#pragma unroll
-        for (int c = 0; c < 5; ++c)
-            s[c] = s[c] * fa + o.s[c] * fb;
-        m = (nm == -INFINITY) ? -INFINITY : nm;
-        const float nmp = fmaxf(mp, o.mp);
-        const float ga = (mp == -INFINITY) ? 0.0f : __expf(mp - nmp);
-        const float gb = (o.mp == -INFINITY) ? 0.0f : __expf(o.mp - nmp);
-        sp = sp * ga + o.sp * gb;
-        mp = nmp;
-    }
-    __device__ __forceinline__ void shfl_merge(int o)
-    {
-        Acc b;
-        b.m = __shfl_xor_sync(0xffffffffu, m, o);
-        b.s0 = __shfl_xor_sync(0xffffffffu, s0, o);
-        b.s2 = __shfl_xor_sync(0xffffffffu, s2, o);
-#pragma unroll
-        for (int c = 0; c < 5; ++c)
-            b.s[c] = __shfl_xor_sync(0xffffffffu, s[c], o);
-        b.mp = __shfl_xor_sync(0xffffffffu, mp, o);
-        b.sp = __shfl_xor_sync(0xffffffffu, sp, o);
-        merge(b);
-    }
-};
-
 // --------------------------------------------------------------- finalise
 // Cross-block totals in FP64 (the paper's global sum for normalisation):
 // estimate, N_eff, log-evidence.  Run by the last block of the step.
@@ -213,79 +145,13 @@ __device__ void finalize_block(const Partial *part, int n, DevSummary *sum, int3
     }
 }
 
-// Point samples g(k) = exp(-a (k + f)^2), k = -R..R, f in (-1/2, 1/2]: the
-// centre by one exponential, the rest by the exact ratios
-// g(k+1) / g(k) = exp(-a (2k+1)) exp(-2 a f) and
-// g(-k-1) / g(-k) = exp(-a (2k+1)) exp(2 a f), k >= 0,
-// with the constants Kc[k] = exp(-a (2k+1)) precomputed per model.
-template <int R>
-__device__ __forceinline__ void gauss_samples(float f, float a, const float *Kc, float g[2 * R + 1])
-{
-    g[R] = __expf(-a * f * f);
-    if (R > 0) {
-        const float up = __expf(-2.0f * a * f), dn = __expf(2.0f * a * f);
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            g[R + k + 1] = g[R + k] * (Kc[k] * up);
-            g[R - k - 1] = g[R - k] * (Kc[k] * dn);
-        }
-    }
-}
-
-// Eq. 4 over S_x with the eq. 3 model, pixels outside S_x modelled as
-// background: l = -sum_{S_x} [(Zb - a)^2 - Zb^2] / (2 sigma_xi^2) with
-// Zb = Z - I_bg and a = I0 g, g separable: g = gx(col) gy(row).  Expanded,
-// l = I0 (B - I0 C / 2) / sigma_xi^2 with B = sum gy_j sum_i gx_i Zb and
-// C = sum gx_i^2 sum gy_j^2.  Samples of columns / rows outside the image are
-// zeroed (only for patches that cross the border); Zp is zero there as well.
-template <int R>
-__device__ __forceinline__ float patch_loglik(const StepArgs &a, float x, float y, float I0)
-{
-    if (!isfinite(x) || !isfinite(y) || !isfinite(I0))
-        return -INFINITY;
-    const float cxf = floorf(x + 0.5f), cyf = floorf(y + 0.5f);
-    if (cxf < -(float)R || cxf > (float)(a.W - 1 + R) || cyf < -(float)R || cyf > (float)(a.H - 1 + R))
-        return 0.0f;
-    const int cx = (int)cxf, cy = (int)cyf;
-    constexpr int P = 2 * R + 1;
-    float gx[P], gy[P];
-    gauss_samples<R>(cxf - x, a.inv2s2, a.Kc, gx);
-    gauss_samples<R>(cyf - y, a.inv2s2, a.Kc, gy);
-    if (cx < R || cx > a.W - 1 - R || cy < R || cy > a.H - 1 - R) {
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-            const int px = cx + i - R, py = cy + i - R;
-            gx[i] = (px >= 0 && px < a.W) ? gx[i] : 0.0f;
-            gy[i] = (py >= 0 && py < a.H) ? gy[i] : 0.0f;
-        }
-    }
-    float sxx = 0.0f, syy = 0.0f;
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-        sxx = fmaf(gx[i], gx[i], sxx);
-        syy = fmaf(gy[i], gy[i], syy);
-    }
-    const float *row = a.Zp + (int64_t)(cy - R + a.pad) * a.Wp + (cx - R + a.pad);
-    float B = 0.0f;
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-        float rj = 0.0f;
-#pragma unroll
-        for (int i = 0; i < P; ++i)
-            rj = fmaf(gx[i], __ldg(row + i), rj);
-        B = fmaf(gy[j], rj, B);
-        row += a.Wp;
-    }
-    const float C = sxx * syy;
-    return I0 * fmaf(-0.5f * I0, C, B) * a.inv_sxi2;
-}
-
 template <int R>
 __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
 {
     int mode = a.mode;
     if (mode != MODE_CARRY && *a.degenerate)
         mode = MODE_CARRY;  // the last resample kept every particle
+    const PatchGeom geom{a.Zp, a.W, a.H, a.Wp, a.pad, a.inv2s2, a.inv_sxi2, a.Kc};
     const int64_t N = a.N;
     Acc acc;
     acc.init();
@@ -318,7 +184,7 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
         v[2] = fmaf(a.sv, e2, vx);
         v[3] = fmaf(a.sv, e3, vy);
         v[4] = fmaf(a.sI, e4, I0);
-        const float l = patch_loglik<R>(a, v[0], v[1], v[4]);
+        const float l = patch_loglik<R>(geom, v[0], v[1], v[4]);
         const float lw = lwp + l;
 #pragma unroll
         for (int c = 0; c < 5; ++c)

@@ -1,0 +1,128 @@
+"""Batched filters (ppf_batch_*): every filter against the FP64 oracle in
+lockstep (same tolerances as tests/gpu_common.py, bit-exact ancestors),
+bitwise equality with single-filter contexts, CUDA-graph runs identical to
+plain launches, and autotuned launch shapes that leave the results unchanged."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ppf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1310_5045_gb300 as p
+    p.load()
+    return p
+
+
+def make(ppf, F, ns, K=4, seed=0, W=48):
+    import torch
+    from gpu_common import f32
+    mb = synth.make_movie_batch(F=F, W=W, H=W, K=K, n_range=(256, 1024), seed=seed)
+    gms, oms = [], []
+    for f in range(F):
+        kw = dict(width=W, height=W, patch_radius=4, psf_sigma=f32(mb.sigma[f]), amplitude=f32(mb.amplitude[f]),
+                  background=10.0, sigma_xi=f32(math.sqrt(10.0)), sigma_m=0.5, sigma_v=0.1, sigma_I=1.0,
+                  v0_max=1.0, seed=seed, filter_id=f)
+        gms.append(ppf.Model(**kw))
+        oms.append(orc.Model(**kw))
+    frames = torch.from_numpy(np.ascontiguousarray(mb.frames)).cuda()   # (K, F, H, W)
+    return mb, gms, oms, frames
+
+
+def test_batch_lockstep_against_oracle(ppf):
+    F = 9
+    ns = [1, 7, 300, 4095, 4096, 4097, 9000, 250, 2]
+    mb, gms, oms, frames = make(ppf, F, ns)
+    bf = ppf.BatchFilter(gms, ns)
+    off = bf.offsets
+    for k in range(1, 4):
+        st0, anc0 = bf.get_particles(state=True, anc=(k > 1))
+        st0 = st0.double().cpu().numpy()
+        a0 = anc0.cpu().numpy() if anc0 is not None else np.arange(bf.ntot, dtype=np.int32)
+        bf.step(frames[k - 1], k)
+        est = bf.estimates()
+        st1, _ = bf.get_particles()
+        S = st1.double().cpu().numpy()
+        bf.resample(k)
+        _, anc1 = bf.get_particles(state=False, anc=True)
+        a1 = anc1.cpu().numpy()
+        for f in range(F):
+            lo, hi = off[f], off[f + 1]
+            n = hi - lo
+            par = st0[:, lo:hi]
+            anc = a0[lo:hi] - lo
+            ref = orc.propagate(oms[f], k, par, anc, np.zeros(n) if k > 1 else par[5])
+            assert np.all(np.abs(S[:5, lo:hi] - ref[:5]) <= 2e-6 * (np.abs(ref[:5]) + 10.0)), f
+            fr = mb.frames[k - 1, f].astype(np.float64)
+            lp = np.zeros(n) if k > 1 else par[5][anc]
+            l_ref = orc.loglik_many(oms[f], fr, S[0, lo:hi], S[1, lo:hi], S[4, lo:hi])
+            tol = 1e-5 * np.maximum(1.0, np.abs(l_ref)) + 1e-6 * S[4, lo:hi] ** 2 * 81 / 10.0
+            assert np.all(np.abs(S[5, lo:hi] - (lp + l_ref)) <= tol + 1e-6 * np.abs(l_ref)), f
+            so_st = S[:, lo:hi].copy()
+            so_st[5] = lp + l_ref
+            so = orc.summary(so_st, lp)
+            scale = np.array([48.0, 48.0, 1.0, 1.0, gms[f].amplitude])
+            assert np.all(np.abs(est[f]["mean"] - so["mean"]) <= 1e-4 * np.maximum(np.abs(so["mean"]), scale)), f
+            assert abs(est[f]["log_evidence"] - so["log_evidence"]) <= 1e-5 * max(1.0, abs(so["log_evidence"]))
+            lwf = st1[5, lo:hi].cpu().numpy()
+            rc, want, _, _, _ = orc.resample(oms[f], orc.SYSTEMATIC, n, k, np.array([0, n]), lwf)
+            assert rc == 0 and np.array_equal(a1[lo:hi] - lo, want), f
+    bf.close()
+
+
+def test_batch_equals_single_filter_contexts(ppf):
+    F = 5
+    ns = [513, 64, 5000, 1, 2048]
+    mb, gms, oms, frames = make(ppf, F, ns, seed=3)
+    bf = ppf.BatchFilter(gms, ns)
+    singles = [ppf.ParticleFilter(gms[f], ns[f], group_size=ns[f]) for f in range(F)]
+    for k in range(1, 4):
+        bf.step(frames[k - 1], k)
+        for f in range(F):
+            singles[f].step(frames[k - 1, f].contiguous(), k)
+        sb, _ = bf.get_particles()
+        for f in range(F):
+            s1, _, _ = singles[f].get_particles()
+            assert np.array_equal(sb[:, bf.offsets[f]:bf.offsets[f + 1]].cpu().numpy(), s1.cpu().numpy()), (k, f)
+        bf.resample(k)
+        _, ab = bf.get_particles(state=False, anc=True)
+        for f in range(F):
+            singles[f].resample(ppf.SYSTEMATIC)
+            _, a1, _ = singles[f].get_particles(state=False, anc=True)
+            assert np.array_equal(ab[bf.offsets[f]:bf.offsets[f + 1]].cpu().numpy() - bf.offsets[f],
+                                  a1.cpu().numpy()), (k, f)
+    for s in singles:
+        s.close()
+    bf.close()
+
+
+def test_graph_run_matches_plain_launches_and_autotune(ppf):
+    import torch
+    F = 40
+    rng = np.random.default_rng(1)
+    ns = [int(v) for v in np.floor(np.exp(rng.uniform(np.log(256), np.log(6000), F)))]
+    mb, gms, oms, frames = make(ppf, F, ns, K=5, seed=5)
+    a = ppf.BatchFilter(gms, ns)
+    b = ppf.BatchFilter(gms, ns)
+    cfg = b.autotune(frames[0], 1)
+    assert cfg["unit"] in (512, 1024, 2048, 4096) and cfg["block"] in (128, 256, 512)
+    ea = a.run(frames, 1, use_graph=False)
+    eb = b.run(frames, 1, use_graph=True)
+    sa, aa = a.get_particles(anc=True)
+    sb, ab = b.get_particles(anc=True)
+    assert torch.equal(sa, sb) and torch.equal(aa, ab)
+    # a different work-unit size groups the float32 partial sums differently:
+    # the estimates agree to the summation-order error
+    assert np.allclose(ea["mean"], eb["mean"], rtol=1e-5, atol=1e-5)
+    assert np.allclose(ea["log_evidence"], eb["log_evidence"], rtol=1e-6)
+    a.close()
+    b.close()
