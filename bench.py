@@ -248,6 +248,26 @@ def run_ours(args):
             "last_estimate": {"mean": est.mean, "ess": est.ess, "log_evidence": est.log_evidence,
                               "truth": mv.truth[kdone - 1].tolist()}}
 
+    # end to end through the C ABI with host frames (pinned), estimate read back
+    if not args.no_e2e:
+        ke = args.e2e_steps
+        host = torch.from_numpy(mv.frames[kdone:kdone + ke]).pin_memory()  # the frames right after the timed ones
+        torch.cuda.synchronize()
+        pf.profile_enable(True, capacity=ke + 8)
+        t0 = time.perf_counter()
+        for i in range(ke):
+            pf.step_host(host[i], kdone + 1 + i)
+            pf.resample(scheme, args.alpha)
+            pf.estimate()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        pr = pf.profile_read()
+        line["e2e"] = {"value": n * ke * world / dt, "unit": UNIT, "steps": ke,
+                       "h2d_bytes_per_step": pr["h2d_bytes"] // ke, "d2h_bytes_per_step": pr["d2h_bytes"] // ke,
+                       "timing": "host wall clock around step_host + resample + estimate (sync) per frame, "
+                                 "on the frames that follow the timed ones"}
+        kdone += ke
+
     # every allocation / routing scheme of Sec. 3-4 on the same workload
     if not args.no_schemes:
         sch = {}
@@ -268,23 +288,88 @@ def run_ours(args):
         line["schemes"] = sch
         kdone = k - 1
 
-    # end to end through the C ABI with host frames (pinned), estimate read back
-    if not args.no_e2e:
-        ke = args.e2e_steps
-        host = torch.from_numpy(mv.frames[kdone:kdone + ke]).pin_memory()
-        torch.cuda.synchronize()
-        pf.profile_enable(True, capacity=ke + 8)
-        t0 = time.perf_counter()
-        for i in range(ke):
-            pf.step_host(host[i], kdone + 1 + i)
-            pf.resample(scheme, args.alpha)
-            pf.estimate()
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        pr = pf.profile_read()
-        line["e2e"] = {"value": n * ke * world / dt, "unit": UNIT, "steps": ke,
-                       "h2d_bytes_per_step": pr["h2d_bytes"] // ke, "d2h_bytes_per_step": pr["d2h_bytes"] // ke,
-                       "timing": "host wall clock around step_host + resample + estimate (sync) per frame"}
+    # batched filters: 4096 filters, N_f log-uniform in [256, 65536], 64^2 frames
+    if not args.no_batch:
+        import synth
+        Kb = 2 + args.batch_steps
+        mb = synth.make_movie_batch(F=args.batch_filters, W=64, H=64, K=Kb, n_range=(256, 65536), seed=0)
+        bmodels = [ppf.Model(width=64, height=64, patch_radius=5, psf_sigma=float(mb.sigma[f]),
+                             amplitude=float(mb.amplitude[f]), background=10.0, sigma_xi=math.sqrt(10.0),
+                             sigma_m=0.5, sigma_v=0.1, sigma_I=1.0, seed=rank, filter_id=f)
+                   for f in range(args.batch_filters)]
+        bfr = torch.from_numpy(mb.frames).to(dev)
+        bres = {}
+        for mode in ("graph", "launches"):
+            bf = ppf.BatchFilter(bmodels, mb.n_particles, stream=stream)
+            cfg = bf.autotune(bfr[0], 1) if mode == "graph" else None
+            bf.run(bfr[:2], 1, use_graph=(mode == "graph"), estimates=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bf.run(bfr[2:], 3, use_graph=(mode == "graph"), estimates=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            bres[mode] = {"particle_steps_per_sec": bf.ntot * args.batch_steps / dt,
+                          "ms_per_frame": 1e3 * dt / args.batch_steps}
+            if cfg:
+                bres[mode]["autotuned"] = cfg
+            ntot = bf.ntot
+            bf.close()
+        line["batched"] = {"workload": f"{args.batch_filters} filters, N_f log-uniform in [256, 65536] "
+                                       f"(total {ntot:,}), 64x64 frames, 11x11 patch, systematic per filter",
+                           "filters": args.batch_filters, "particles": ntot, "frames_timed": args.batch_steps,
+                           "timing": "host wall clock around one ppf_batch_run (synchronous)", **bres,
+                           "vs_plain_fp32_path": bres["graph"]["particle_steps_per_sec"] / value}
+        del bfr
+
+    # reduced-precision frames: BF16 / FP16 against the FP32 path, per frame in
+    # lockstep (both start every frame from the FP32 run's particles)
+    if not args.no_precision:
+        prec = {}
+        pn = args.precision_n
+        gain = torch.from_numpy(mv.frames[: args.precision_frames + 1]).to(dev) * 1.37 + 0.29
+        base = ppf.ParticleFilter(ppf.Model(**params, seed=rank), pn, group_size=GROUP, stream=stream)
+        others = {}
+        for name, dt_, code in (("bf16", torch.bfloat16, ppf.BF16), ("fp16", torch.float16, ppf.F16)):
+            others[name] = (ppf.ParticleFilter(ppf.Model(**params, seed=rank, frame_dtype=code), pn, group_size=GROUP,
+                                               stream=stream), gain.to(dt_).contiguous())
+        errs = {name: {"mean_rel": 0.0, "log_evidence_rel": 0.0} for name in others}
+        for k in range(1, args.precision_frames + 1):
+            st, an, lp = base.get_particles(state=True, anc=True, lw_prev=True)
+            for name, (pf2, fr2) in others.items():
+                pf2.set_particles(st, an if k > 1 else None, lp if k > 1 else None)
+            base.step(gain[k - 1].contiguous(), k)
+            e32 = base.estimate()
+            for name, (pf2, fr2) in others.items():
+                pf2.step(fr2[k - 1], k)
+                e2 = pf2.estimate()
+                scales = np.array([W, H, 1.0, 1.0, params["amplitude"]])
+                m = np.max(np.abs(np.array(e2.mean) - np.array(e32.mean)) / np.maximum(np.abs(e32.mean), scales))
+                errs[name]["mean_rel"] = max(errs[name]["mean_rel"], float(m))
+                errs[name]["log_evidence_rel"] = max(errs[name]["log_evidence_rel"],
+                                                     abs(e2.log_evidence - e32.log_evidence) / abs(e32.log_evidence))
+            base.resample(ppf.SYSTEMATIC)
+        for name, (pf2, fr2) in others.items():
+            # throughput of the reduced-precision path on the same frames
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            pf2.resample(ppf.SYSTEMATIC)
+            e0.record(stream)
+            for k in range(1, args.precision_frames + 1):
+                pf2.step(fr2[k - 1], 100 + k)
+                pf2.resample(ppf.SYSTEMATIC)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / args.precision_frames
+            prec[name] = {"max_rel_err_mean_vs_fp32": errs[name]["mean_rel"],
+                          "max_rel_err_log_evidence_vs_fp32": errs[name]["log_evidence_rel"],
+                          "ms_per_frame": ms, "particle_steps_per_sec": pn / (ms / 1e3)}
+            pf2.close()
+        base.close()
+        line["precision"] = {"workload": f"N={pn:,}, the 512x512 movie scaled by 1.37 and offset by 0.29 "
+                                         "(non-integer counts, so BF16/FP16 storage rounds them)",
+                             "frames": args.precision_frames, **prec,
+                             "note": "integer photon counts <= 256 are exact in BF16 (<= 2048 in FP16): on the "
+                                     "unscaled movie the reduced-precision paths reproduce FP32 bit for bit"}
 
     # gradient of the log marginal likelihood: N = 2^20, 50 frames of 256^2
     if not args.no_grad:
@@ -341,13 +426,19 @@ def main():
     ap.add_argument("--alpha", type=float, default=0.1)
     ap.add_argument("--scheme-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=30)
-    ap.add_argument("--cpu-n", type=int, default=1 << 20)
-    ap.add_argument("--cpu-frames", type=int, default=4)
+    ap.add_argument("--cpu-n", type=int, default=1 << 22)
+    ap.add_argument("--cpu-frames", type=int, default=3)
     ap.add_argument("--ref-n", type=int, default=1 << 17)
     ap.add_argument("--no-schemes", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-filters", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--precision-n", type=int, default=N_FULL)
+    ap.add_argument("--precision-frames", type=int, default=5)
     ap.add_argument("--grad-evals", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -45,6 +45,19 @@ struct FilterSummary {
 };
 static_assert(sizeof(FilterSummary) == sizeof(ppf_filter_estimate_t), "layout");
 
+// Device-resident position in a frame sequence: the kernels of one frame
+// iteration read their frame index, frame and estimate slot from here, so a
+// single captured iteration can be replayed frame after frame.
+struct BatchCursor {
+    const char *frames;       // K x F x H x W (or one F x H x W frame)
+    int64_t frame_bytes;      // bytes of one F x H x W frame
+    FilterSummary *est;       // optional K x F estimates
+    int32_t k;                // frame index of the current iteration
+    int32_t t;                // position in the sequence
+    int32_t cur;              // state buffer holding the particles the step starts from
+    int32_t first;            // the step starts from the prior draw (identity ancestry)
+};
+
 }  // namespace ppf
 
 struct ppf_batch {
@@ -69,14 +82,28 @@ struct ppf_batch {
     int64_t *unit_lo;
     int32_t *unit_n;
     int32_t *fu_off;                   // device [F + 1]: units of filter f
+    // resampling tiles: every filter cut into runs of at most TILE particles
+    int32_t T;
+    int32_t *tile_f;                   // device [T]
+    int64_t *tile_lo;
+    int32_t *tile_n;
+    int32_t *ft_off;                   // device [F + 1]: tiles of filter f
+    uint64_t *tQ;                      // device [T] tile totals
+    uint64_t *tC;                      // device [T] exclusive prefix within the filter
+    int64_t *tT;                       // device [T + 1]: first ticket of the tile (filter-local)
+    uint64_t *fQu;                     // device [2F]: per filter Q_f, u_f
     ppf::Partial *upart;               // device [U]
     ppf::FilterSummary *fsum;          // device [F]
     ppf::FilterSummary *fsum_host;     // pinned [F]
     ppf::FilterSummary *fsum_run;      // device [K x F] of the last graph run
     int64_t fsum_run_cap;
     int32_t *flags;                    // device: any degenerate filter
+    ppf::BatchCursor *cursor;          // device
+    cudaStream_t gstream;              // stream the cached graph runs on
+    cudaGraphExec_t gexec;             // cached one-frame iteration
     bool first;                        // next step starts from the prior draw
     bool weighted;
+    int32_t last_k;
     int64_t launches;
     char err[256];
 };
@@ -119,10 +146,35 @@ __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __
 template <>
 __device__ __forceinline__ float tof<__half>(__half v) { return __half2float(v); }
 
-template <typename T>
-__global__ void batch_prepare_kernel(const T *__restrict__ Z, float *__restrict__ Zp, int32_t F, int W, int H, int Wp,
-                                     int Hp, int pad, const FilterParams *__restrict__ fp)
+__global__ void batch_set_cursor(BatchCursor *c, const char *frames, int64_t frame_bytes, FilterSummary *est,
+                                 int32_t k, int32_t t, int32_t cur, int32_t first)
 {
+    c->frames = frames;
+    c->frame_bytes = frame_bytes;
+    c->est = est;
+    c->k = k;
+    c->t = t;
+    c->cur = cur;
+    c->first = first;
+}
+
+// start of one frame iteration of a sequence: next frame; after the first
+// iteration the particles of the previous one are current and resampled
+__global__ void batch_advance(BatchCursor *c)
+{
+    c->k += 1;
+    c->t += 1;
+    if (c->t > 0) {
+        c->cur ^= 1;
+        c->first = 0;
+    }
+}
+
+template <typename T>
+__global__ void batch_prepare_kernel(const BatchCursor *__restrict__ cur, float *__restrict__ Zp, int32_t F, int W,
+                                     int H, int Wp, int Hp, int pad, const FilterParams *__restrict__ fp)
+{
+    const T *Z = reinterpret_cast<const T *>(cur->frames + cur->frame_bytes * cur->t);
     const int64_t plane = (int64_t)Wp * Hp;
     const int64_t n = plane * F;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
@@ -139,15 +191,13 @@ __global__ void batch_prepare_kernel(const T *__restrict__ Z, float *__restrict_
 struct BatchStepArgs {
     int64_t Ntot;
     int W, H, Wp, Hp, pad;
-    uint32_t frame;
-    int first;
+    const BatchCursor *cur;
     const FilterParams *__restrict__ fp;
     const int32_t *__restrict__ unit_f;
     const int64_t *__restrict__ unit_lo;
     const int32_t *__restrict__ unit_n;
     int32_t U;
-    const float *__restrict__ src;
-    float *__restrict__ dst;
+    float *st0, *st1;           // the two state buffers; the cursor says which is current
     const int32_t *__restrict__ anc;
     const float *__restrict__ Zp;
     Partial *__restrict__ part;
@@ -158,6 +208,10 @@ template <int R>
 __global__ void batch_step_kernel(BatchStepArgs a)
 {
     const int64_t N = a.Ntot;
+    const uint32_t frame = (uint32_t)a.cur->k;
+    const bool first = a.cur->first != 0;
+    const float *__restrict__ src = a.cur->cur ? a.st1 : a.st0;
+    float *__restrict__ dst = a.cur->cur ? a.st0 : a.st1;
     __shared__ FilterParams P;
     __shared__ Acc sh[32];
     for (int32_t u = blockIdx.x; u < a.U; u += gridDim.x) {
@@ -173,15 +227,15 @@ __global__ void batch_step_kernel(BatchStepArgs a)
         const int32_t n = a.unit_n[u];
         for (int32_t j = threadIdx.x; j < n; j += blockDim.x) {
             const int64_t i = lo + j;
-            int64_t p = a.first ? i : (int64_t)__ldg(a.anc + i);
+            int64_t p = first ? i : (int64_t)__ldg(a.anc + i);
             if (p < P.off || p >= P.off + P.n)
                 p = i;  // ancestors never cross filters
-            const float x = __ldg(a.src + p), y = __ldg(a.src + N + p);
-            const float vx = __ldg(a.src + 2 * N + p), vy = __ldg(a.src + 3 * N + p);
-            const float I0 = __ldg(a.src + 4 * N + p);
-            const float lwp = a.first ? __ldg(a.src + 5 * N + p) : 0.0f;
+            const float x = src[p], y = src[N + p];
+            const float vx = src[2 * N + p], vy = src[3 * N + p];
+            const float I0 = src[4 * N + p];
+            const float lwp = first ? src[5 * N + p] : 0.0f;
             uint32_t fl[6];
-            prop_fields(draw(P.seed, (uint32_t)(i - P.off), a.frame, P.fid, PURPOSE_PROP, 0), fl);
+            prop_fields(draw(P.seed, (uint32_t)(i - P.off), frame, P.fid, PURPOSE_PROP, 0), fl);
             float e0, e1, e2, e3, e4, e5;
             box_muller(u21(fl[0]), u21(fl[1]), e0, e1);
             box_muller(u21(fl[2]), u21(fl[3]), e2, e3);
@@ -195,8 +249,8 @@ __global__ void batch_step_kernel(BatchStepArgs a)
             const float lw = lwp + patch_loglik<R>(geom, v[0], v[1], v[4]);
 #pragma unroll
             for (int c = 0; c < 5; ++c)
-                a.dst[c * N + i] = v[c];
-            a.dst[5 * N + i] = lw;
+                dst[c * N + i] = v[c];
+            dst[5 * N + i] = lw;
             acc.add(lw, lwp, v);
         }
 #pragma unroll
@@ -231,7 +285,7 @@ __global__ void batch_step_kernel(BatchStepArgs a)
 
 // one warp per filter: FP64 combination of its units' partials
 __global__ void batch_finalize_kernel(const Partial *__restrict__ part, const int32_t *__restrict__ fu_off, int32_t F,
-                                      FilterSummary *__restrict__ fs)
+                                      FilterSummary *__restrict__ fs, const BatchCursor *__restrict__ cur)
 {
     const int32_t f = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -269,57 +323,107 @@ __global__ void batch_finalize_kernel(const Partial *__restrict__ part, const in
         s.M = m;
         s.degenerate = (t[0] > 0.0) ? 0 : 1;
         fs[f] = s;
+        if (cur->est)
+            cur->est[(int64_t)cur->t * F + f] = s;
     }
 }
 
-// one block per filter: systematic resampling of its n_f slots (Alg. 1) on
-// 64-bit fixed point, the same tickets as a single filter with filter id f
-__global__ void __launch_bounds__(TILE_THREADS) batch_resample_kernel(const float *__restrict__ lw,
-                                                                      const FilterParams *__restrict__ fp,
-                                                                      const FilterSummary *__restrict__ fs,
-                                                                      uint32_t frame, int32_t *__restrict__ anc,
-                                                                      int32_t *__restrict__ flags)
+// Systematic resampling of every filter (Alg. 1) on 64-bit fixed point,
+// the same tickets as a single filter with filter id f, in three balanced
+// passes over tiles of at most TILE particles:
+//   1. tile totals of the fixed-point weights (one block per tile);
+//   2. per filter (one warp): exclusive prefix over its tiles, total Q_f,
+//      ticket offset u_f and each tile's first ticket;
+//   3. one block per tile: its cumulative weights and the parents of its
+//      tickets.  A filter with no usable weight keeps its particles.
+__global__ void __launch_bounds__(TILE_THREADS) batch_tile_totals(const float *st0, const float *st1, int64_t Ntot,
+                                                                  const FilterParams *__restrict__ fp,
+                                                                  const FilterSummary *__restrict__ fs,
+                                                                  const BatchCursor *__restrict__ cur,
+                                                                  const int32_t *__restrict__ tile_f,
+                                                                  const int64_t *__restrict__ tile_lo,
+                                                                  const int32_t *__restrict__ tile_n,
+                                                                  uint64_t *__restrict__ tQ)
 {
-    __shared__ uint64_t C[TILE + TILE / 16];
     __shared__ uint64_t red[33];
-    __shared__ uint64_t Qs, us;
-    const int32_t f = blockIdx.x;
-    const FilterParams P = fp[f];
-    const int64_t lo = P.off, sz = P.n;
+    const float *__restrict__ lw = (cur->cur ? st0 : st1) + 5 * Ntot;
+    const int32_t t = blockIdx.x, f = tile_f[t];
     const float Mf = fs[f].M;
-    const int s = scale_bits(sz);
-    uint64_t qs = 0;
-    for (int64_t i = threadIdx.x; i < sz; i += blockDim.x)
-        qs += quantise(__ldg(lw + lo + i), Mf, s);
-    uint64_t Q;
-    block_excl_scan_u64(qs, red, &Q);
-    if (threadIdx.x == 0) {
-        Qs = Q;
-        us = (Q == 0ull) ? 0ull : ticket_offset(P.seed, P.fid, frame, PURPOSE_RESAMPLE, 0u, Q);
+    const int s = scale_bits(fp[f].n);
+    uint64_t acc = 0;
+    for (int i = threadIdx.x; i < tile_n[t]; i += blockDim.x)
+        acc += quantise(__ldg(lw + tile_lo[t] + i), Mf, s);
+    uint64_t total;
+    block_excl_scan_u64(acc, red, &total);
+    if (threadIdx.x == 0)
+        tQ[t] = total;
+}
+
+__global__ void batch_tile_scan(const FilterParams *__restrict__ fp, const BatchCursor *__restrict__ cur,
+                                const int32_t *__restrict__ ft_off, int32_t F, const uint64_t *__restrict__ tQ,
+                                uint64_t *__restrict__ tC, int64_t *__restrict__ tT, uint64_t *__restrict__ fQu,
+                                int32_t *__restrict__ flags)
+{
+    const int32_t f = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (f >= F)
+        return;
+    const int32_t t0 = ft_off[f], t1 = ft_off[f + 1];
+    const FilterParams P = fp[f];
+    uint64_t carry = 0;
+    for (int32_t base = t0; base < t1; base += 32) {
+        const int32_t t = base + lane;
+        const uint64_t v = (t < t1) ? tQ[t] : 0ull;
+        const uint64_t incl = warp_incl_scan_u64(v);
+        if (t < t1)
+            tC[t] = carry + incl - v;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    const uint64_t Q = carry;
+    const uint64_t u = (Q == 0ull) ? 0ull : ticket_offset(P.seed, P.fid, (uint32_t)cur->k, PURPOSE_RESAMPLE, 0u, Q);
+    if (lane == 0) {
+        fQu[2 * f] = Q;
+        fQu[2 * f + 1] = u;
         if (Q == 0ull)
             atomicOr(flags, FLAG_DEGENERATE);
     }
-    __syncthreads();
-    Q = Qs;
-    const uint64_t u = us;
-    if (Q == 0ull) {  // no usable weight: the filter keeps its particles
-        for (int64_t j = threadIdx.x; j < sz; j += blockDim.x)
-            anc[lo + j] = (int32_t)(lo + j);
+    for (int32_t t = t0 + lane; t < t1; t += 32)
+        tT[t] = (Q == 0ull) ? 0 : tickets_below(tC[t], P.n, u, Q);
+}
+
+__global__ void __launch_bounds__(TILE_THREADS) batch_fill(const float *st0, const float *st1, int64_t Ntot,
+                                                           const FilterParams *__restrict__ fp,
+                                                           const FilterSummary *__restrict__ fs,
+                                                           const BatchCursor *__restrict__ cur,
+                                                           const int32_t *__restrict__ tile_f,
+                                                           const int64_t *__restrict__ tile_lo,
+                                                           const int32_t *__restrict__ tile_n,
+                                                           const int32_t *__restrict__ ft_off,
+                                                           const uint64_t *__restrict__ tC,
+                                                           const int64_t *__restrict__ tT,
+                                                           const uint64_t *__restrict__ fQu, int32_t *__restrict__ anc)
+{
+    __shared__ uint64_t C[TILE_SMEM_U64];
+    __shared__ uint64_t red[33];
+    const float *__restrict__ lw = (cur->cur ? st0 : st1) + 5 * Ntot;
+    const int32_t t = blockIdx.x, f = tile_f[t];
+    const FilterParams P = fp[f];
+    const int64_t lo = tile_lo[t];
+    const int n = tile_n[t];
+    const uint64_t Q = fQu[2 * f], u = fQu[2 * f + 1];
+    if (Q == 0ull) {  // no usable weight in the filter: it keeps its particles
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            anc[lo + i] = (int32_t)(lo + i);
         return;
     }
-    uint64_t carry = 0;
-    for (int64_t c0 = 0; c0 < sz; c0 += TILE) {
-        const int n = (int)(sz - c0 < TILE ? sz - c0 : TILE);
-        uint64_t q[TILE_ITEMS];
-        tile_weights(lw, lo + c0, n, Mf, s, C, q);
-        const uint64_t tot = tile_scan(q, C, red);
-        const int64_t t_lo = tickets_below(carry, sz, u, Q);
-        const int64_t t_hi = tickets_below(carry + tot, sz, u, Q);
-        ticket_parents(C, n, carry, u, Q, (uint32_t)sz, t_lo, t_hi,
-                       [&](int64_t j, int i) { anc[lo + j] = (int32_t)(lo + c0 + i); });
-        carry += tot;
-        __syncthreads();
-    }
+    const int32_t tl = ft_off[f + 1] - 1;
+    const int64_t j_lo = tT[t];
+    const int64_t j_hi = (t < tl) ? tT[t + 1] : P.n;
+    uint64_t q[TILE_ITEMS];
+    tile_weights(lw, lo, n, fs[f].M, scale_bits(P.n), C, q);
+    tile_scan(q, C, red);
+    ticket_parents(C, n, tC[t], u, Q, (uint32_t)P.n, j_lo, j_hi,
+                   [&](int64_t j, int i) { anc[P.off + j] = (int32_t)(lo + i); });
 }
 
 // ------------------------------------------------------------------ host side
@@ -364,13 +468,42 @@ cudaError_t build_units(ppf_batch *b, int32_t unit)
     return cudaSuccess;
 }
 
+cudaError_t build_tiles(ppf_batch *b)
+{
+    std::vector<int32_t> tf, tn, fo(b->F + 1);
+    std::vector<int64_t> tl;
+    for (int32_t f = 0; f < b->F; ++f) {
+        fo[f] = (int32_t)tf.size();
+        for (int64_t s = 0; s < b->n[f]; s += TILE) {
+            tf.push_back(f);
+            tl.push_back(b->off[f] + s);
+            tn.push_back((int32_t)((b->n[f] - s) < TILE ? (b->n[f] - s) : TILE));
+        }
+    }
+    fo[b->F] = (int32_t)tf.size();
+    b->T = (int32_t)tf.size();
+    cudaError_t e;
+    if ((e = dmalloc(&b->tile_f, b->T)) != cudaSuccess) return e;
+    if ((e = dmalloc(&b->tile_lo, b->T)) != cudaSuccess) return e;
+    if ((e = dmalloc(&b->tile_n, b->T)) != cudaSuccess) return e;
+    if ((e = dmalloc(&b->ft_off, b->F + 1)) != cudaSuccess) return e;
+    if ((e = dmalloc(&b->tQ, b->T)) != cudaSuccess) return e;
+    if ((e = dmalloc(&b->tC, b->T)) != cudaSuccess) return e;
+    if ((e = dmalloc(&b->tT, b->T + 1)) != cudaSuccess) return e;
+    if ((e = dmalloc(&b->fQu, 2 * (size_t)b->F)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b->tile_f, tf.data(), sizeof(int32_t) * b->T, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b->tile_lo, tl.data(), sizeof(int64_t) * b->T, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b->tile_n, tn.data(), sizeof(int32_t) * b->T, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    return cudaMemcpy(b->ft_off, fo.data(), sizeof(int32_t) * (b->F + 1), cudaMemcpyHostToDevice);
+}
+
 template <int R>
 void launch_batch_step_r(const BatchStepArgs &a, int grid, int block, cudaStream_t s)
 {
     batch_step_kernel<R><<<grid, block, 0, s>>>(a);
 }
 
-cudaError_t launch_batch_step(ppf_batch *b, int32_t k, bool commit)
+cudaError_t launch_batch_step(ppf_batch *b, bool commit)
 {
     BatchStepArgs a;
     a.Ntot = b->Ntot;
@@ -379,15 +512,14 @@ cudaError_t launch_batch_step(ppf_batch *b, int32_t k, bool commit)
     a.Wp = b->Wp;
     a.Hp = b->Hp;
     a.pad = b->pad;
-    a.frame = (uint32_t)k;
-    a.first = b->first ? 1 : 0;
+    a.cur = b->cursor;
     a.fp = b->fp;
     a.unit_f = b->unit_f;
     a.unit_lo = b->unit_lo;
     a.unit_n = b->unit_n;
     a.U = b->U;
-    a.src = b->state[b->cur];
-    a.dst = b->state[b->cur ^ 1];
+    a.st0 = b->state[0];
+    a.st1 = b->state[1];
     a.anc = b->anc;
     a.Zp = b->Zp;
     a.part = b->upart;
@@ -409,44 +541,84 @@ cudaError_t launch_batch_step(ppf_batch *b, int32_t k, bool commit)
     if (e != cudaSuccess || !commit)
         return e;
     const int fgrid = (b->F * 32 + 255) / 256;
-    batch_finalize_kernel<<<fgrid, 256, 0, b->stream>>>(b->upart, b->fu_off, b->F, b->fsum);
+    batch_finalize_kernel<<<fgrid, 256, 0, b->stream>>>(b->upart, b->fu_off, b->F, b->fsum, b->cursor);
     b->launches += 2;
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_prepare(ppf_batch *b, const void *frames)
+cudaError_t launch_batch_prepare(ppf_batch *b)
 {
     const int64_t n = (int64_t)b->F * b->Wp * b->Hp;
     const int grid = (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
     switch (b->dtype) {
     case PPF_BF16:
-        batch_prepare_kernel<__nv_bfloat16><<<grid, 256, 0, b->stream>>>((const __nv_bfloat16 *)frames, b->Zp, b->F,
-                                                                         b->W, b->H, b->Wp, b->Hp, b->pad, b->fp);
+        batch_prepare_kernel<__nv_bfloat16><<<grid, 256, 0, b->stream>>>(b->cursor, b->Zp, b->F, b->W, b->H, b->Wp,
+                                                                         b->Hp, b->pad, b->fp);
         break;
     case PPF_F16:
-        batch_prepare_kernel<__half><<<grid, 256, 0, b->stream>>>((const __half *)frames, b->Zp, b->F, b->W, b->H,
-                                                                  b->Wp, b->Hp, b->pad, b->fp);
+        batch_prepare_kernel<__half><<<grid, 256, 0, b->stream>>>(b->cursor, b->Zp, b->F, b->W, b->H, b->Wp, b->Hp,
+                                                                  b->pad, b->fp);
         break;
     default:
-        batch_prepare_kernel<float><<<grid, 256, 0, b->stream>>>((const float *)frames, b->Zp, b->F, b->W, b->H,
-                                                                 b->Wp, b->Hp, b->pad, b->fp);
+        batch_prepare_kernel<float><<<grid, 256, 0, b->stream>>>(b->cursor, b->Zp, b->F, b->W, b->H, b->Wp, b->Hp,
+                                                                 b->pad, b->fp);
     }
     b->launches += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_resample(ppf_batch *b, int32_t k)
+cudaError_t set_cursor(ppf_batch *b, const void *frames, FilterSummary *est, int32_t k, int32_t t)
 {
-    batch_resample_kernel<<<b->F, TILE_THREADS, 0, b->stream>>>(b->state[b->cur] + 5 * b->Ntot, b->fp, b->fsum,
-                                                                (uint32_t)k, b->anc, b->flags);
+    batch_set_cursor<<<1, 1, 0, b->stream>>>(b->cursor, (const char *)frames, (int64_t)(b->frame_bytes * b->F), est,
+                                             k, t, b->cur, b->first ? 1 : 0);
     b->launches += 1;
     return cudaGetLastError();
 }
 
+cudaError_t launch_batch_resample(ppf_batch *b)
+{
+    batch_tile_totals<<<b->T, TILE_THREADS, 0, b->stream>>>(b->state[0], b->state[1], b->Ntot, b->fp, b->fsum,
+                                                            b->cursor, b->tile_f, b->tile_lo, b->tile_n, b->tQ);
+    batch_tile_scan<<<(b->F * 32 + 255) / 256, 256, 0, b->stream>>>(b->fp, b->cursor, b->ft_off, b->F, b->tQ, b->tC,
+                                                                      b->tT, b->fQu, b->flags);
+    batch_fill<<<b->T, TILE_THREADS, 0, b->stream>>>(b->state[0], b->state[1], b->Ntot, b->fp, b->fsum, b->cursor,
+                                                     b->tile_f, b->tile_lo, b->tile_n, b->ft_off, b->tC, b->tT, b->fQu,
+                                                     b->anc);
+    b->launches += 3;
+    return cudaGetLastError();
+}
+
+// one frame iteration of a sequence: advance, prepare, step, finalise, resample
+cudaError_t launch_iteration(ppf_batch *b)
+{
+    batch_advance<<<1, 1, 0, b->stream>>>(b->cursor);
+    b->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_batch_prepare(b);
+    if (e == cudaSuccess)
+        e = launch_batch_step(b, true);
+    if (e == cudaSuccess)
+        e = launch_batch_resample(b);
+    return e;
+}
+
+void drop_graph(ppf_batch *b)
+{
+    if (b->gexec)
+        cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+}
+
 void free_batch(ppf_batch *b)
 {
+    if (b->gexec)
+        cudaGraphExecDestroy(b->gexec);
+    if (b->gstream)
+        cudaStreamDestroy(b->gstream);
     void *p[] = {b->fp, b->state[0], b->state[1], b->anc, b->Zp, b->unit_f, b->unit_lo, b->unit_n, b->fu_off,
-                 b->upart, b->fsum, b->flags, b->fsum_run};
+                 b->upart, b->fsum, b->flags, b->fsum_run, b->cursor, b->tile_f, b->tile_lo, b->tile_n, b->ft_off,
+                 b->tQ, b->tC, b->tT, b->fQu};
     for (void *q : p)
         if (q)
             cudaFree(q);
@@ -550,12 +722,14 @@ ppf_status ppf_batch_create(const ppf_model *models, const int64_t *n, int32_t F
         dmalloc(&b->state[1], 6 * Ntot) != cudaSuccess || dmalloc(&b->anc, Ntot) != cudaSuccess ||
         dmalloc(&b->Zp, (size_t)F * b->Wp * b->Hp) != cudaSuccess || dmalloc(&b->fu_off, F + 1) != cudaSuccess ||
         dmalloc(&b->fsum, F) != cudaSuccess || dmalloc(&b->flags, 1) != cudaSuccess ||
+        dmalloc(&b->cursor, 1) != cudaSuccess ||
         cudaMallocHost((void **)&b->fsum_host, sizeof(FilterSummary) * F) != cudaSuccess ||
         dmalloc(&dv0A, 2 * (size_t)F) != cudaSuccess)
         return (dv0A ? cudaFree(dv0A) : cudaSuccess), fail(PPF_ENOMEM);
     if (cudaMemcpy(b->fp, hp.data(), sizeof(FilterParams) * F, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(dv0A, v0A.data(), sizeof(float) * 2 * F, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(b->flags, 0, sizeof(int32_t)) != cudaSuccess || build_units(b, 1024) != cudaSuccess) {
+        cudaMemset(b->flags, 0, sizeof(int32_t)) != cudaSuccess || build_units(b, 1024) != cudaSuccess ||
+        build_tiles(b) != cudaSuccess) {
         cudaFree(dv0A);
         return fail(PPF_ECUDA);
     }
@@ -586,11 +760,13 @@ ppf_status ppf_batch_step(ppf_batch *b, const void *frames_dev, int32_t k)
         return PPF_EINVAL;
     if (b->weighted)
         return PPF_ESTATE;  // every batched step follows a resample (or the prior)
-    BCK(launch_batch_prepare(b, frames_dev));
-    BCK(launch_batch_step(b, k, true));
+    BCK(set_cursor(b, frames_dev, nullptr, k, 0));
+    BCK(launch_batch_prepare(b));
+    BCK(launch_batch_step(b, true));
     b->cur ^= 1;
     b->first = false;
     b->weighted = true;
+    b->last_k = k;
     return PPF_OK;
 }
 
@@ -600,7 +776,9 @@ ppf_status ppf_batch_resample(ppf_batch *b, int32_t k)
         return PPF_EINVAL;
     if (!b->weighted)
         return PPF_ESTATE;
-    BCK(launch_batch_resample(b, k));
+    if (k != b->last_k)
+        return PPF_EINVAL;  // the cursor still holds the last step's frame
+    BCK(launch_batch_resample(b));
     b->weighted = false;
     return PPF_OK;
 }
@@ -619,66 +797,54 @@ ppf_status ppf_batch_run(ppf_batch *b, const void *frames_dev, int32_t k0, int32
         BCK(cudaMalloc((void **)&b->fsum_run, sizeof(FilterSummary) * (size_t)K * b->F));
         b->fsum_run_cap = (int64_t)K * b->F;
     }
-    const size_t per_frame = b->frame_bytes * (size_t)b->F;
-    const char *fr = (const char *)frames_dev;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaStream_t cap = b->stream;
-    bool own = false;
-    if (use_graph && cap == nullptr) {  // the legacy stream cannot be captured
-        BCK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t user = b->stream;
+    if (use_graph && user == nullptr) {  // the legacy stream cannot be captured
+        if (!b->gstream)
+            BCK(cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking));
         BCK(cudaStreamSynchronize(nullptr));
-        own = true;
+        b->stream = b->gstream;
     }
-    cudaStream_t saved = b->stream;
-    b->stream = cap;
-    if (use_graph)
-        BCK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     ppf_status st = PPF_OK;
-    for (int32_t t = 0; t < K && st == PPF_OK; ++t) {
-        cudaError_t e = launch_batch_prepare(b, fr + per_frame * t);
+    cudaError_t e = set_cursor(b, frames_dev, est_host ? b->fsum_run : nullptr, k0 - 1, -1);
+    if (e == cudaSuccess && use_graph && !b->gexec) {
+        // capture one iteration; every replay advances the cursor to the next frame
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const int64_t launches = b->launches;
+            cudaError_t ec = launch_iteration(b);
+            b->launches = launches;
+            e = cudaStreamEndCapture(b->stream, &g);
+            if (e == cudaSuccess)
+                e = ec;
+        }
         if (e == cudaSuccess)
-            e = launch_batch_step(b, k0 + t, true);
-        b->cur ^= 1;
-        b->first = false;
-        if (e == cudaSuccess)
-            e = launch_batch_resample(b, k0 + t);
-        if (e == cudaSuccess && est_host)
-            e = cudaMemcpyAsync(b->fsum_run + (size_t)t * b->F, b->fsum, sizeof(FilterSummary) * b->F,
-                                cudaMemcpyDeviceToDevice, cap);
-        if (e != cudaSuccess) {
-            snprintf(b->err, sizeof(b->err), "batch frame %d: %s", k0 + t, cudaGetErrorString(e));
-            st = PPF_ECUDA;
+            e = cudaGraphInstantiate(&b->gexec, g, 0);
+        if (g)
+            cudaGraphDestroy(g);
+    }
+    for (int32_t t = 0; t < K && e == cudaSuccess; ++t) {
+        if (use_graph) {
+            e = cudaGraphLaunch(b->gexec, b->stream);
+            b->launches += 7;
+        } else {
+            e = launch_iteration(b);
         }
     }
-    if (use_graph) {
-        cudaError_t e = cudaStreamEndCapture(cap, &graph);
-        if (st == PPF_OK && e == cudaSuccess)
-            e = cudaGraphInstantiate(&exec, graph, 0);
-        if (st == PPF_OK && e == cudaSuccess)
-            e = cudaGraphLaunch(exec, cap);
-        if (st == PPF_OK && e != cudaSuccess) {
-            snprintf(b->err, sizeof(b->err), "graph: %s", cudaGetErrorString(e));
-            st = PPF_ECUDA;
-        }
-    }
-    if (st == PPF_OK && est_host) {
-        cudaError_t e2 = cudaMemcpyAsync(est_host, b->fsum_run, sizeof(FilterSummary) * (size_t)K * b->F,
-                                         cudaMemcpyDeviceToHost, cap);
-        if (e2 != cudaSuccess)
-            st = PPF_ECUDA;
-    }
-    cudaError_t e = cudaStreamSynchronize(cap);
-    if (exec)
-        cudaGraphExecDestroy(exec);
-    if (graph)
-        cudaGraphDestroy(graph);
-    if (own)
-        cudaStreamDestroy(cap);
-    b->stream = saved;
-    if (st == PPF_OK && e != cudaSuccess) {
-        snprintf(b->err, sizeof(b->err), "run: %s", cudaGetErrorString(e));
+    if (e == cudaSuccess && est_host)
+        e = cudaMemcpyAsync(est_host, b->fsum_run, sizeof(FilterSummary) * (size_t)K * b->F, cudaMemcpyDeviceToHost,
+                            b->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        snprintf(b->err, sizeof(b->err), "batch run: %s", cudaGetErrorString(e));
         st = PPF_ECUDA;
+    }
+    b->stream = user;
+    if (st == PPF_OK) {
+        b->cur ^= (K & 1);
+        b->first = false;
+        b->last_k = k0 + K - 1;
     }
     return st;
 }
@@ -716,38 +882,60 @@ ppf_status ppf_batch_autotune(ppf_batch *b, const void *frames_dev, int32_t k, i
 {
     if (!b || !frames_dev || k < 1)
         return PPF_EINVAL;
-    BCK(launch_batch_prepare(b, frames_dev));
+    if (b->weighted)
+        return PPF_ESTATE;
+    drop_graph(b);  // the launch shape is baked into a captured graph
+    BCK(set_cursor(b, frames_dev, nullptr, k, 0));
+    BCK(launch_batch_prepare(b));
     const int32_t units[] = {512, 1024, 2048, 4096};
     const int32_t blocks[] = {128, 256, 512};
     const int32_t bpss[] = {2, 4, 8};
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int32_t bu = b->unit, bb = b->block, bs = b->bps;
-    for (int32_t un : units) {
-        BCK(build_units(b, un));
+    // each candidate: one untimed launch, then the best of 3 timings of 3 launches
+    auto time_cfg = [&](int32_t un, int32_t bl, int32_t bp, float *out) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        if (un != b->unit)
+            e = build_units(b, un);
+        b->block = bl;
+        b->bps = bp;
+        if (e == cudaSuccess)
+            e = launch_batch_step(b, false);
+        float best_ms = 1e30f;
+        for (int trial = 0; trial < 3 && e == cudaSuccess; ++trial) {
+            e = cudaEventRecord(e0, b->stream);
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
+                e = launch_batch_step(b, false);
+            if (e == cudaSuccess)
+                e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess)
+                e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess)
+                e = cudaEventElapsedTime(&ms, e0, e1);
+            best_ms = ms < best_ms ? ms : best_ms;
+        }
+        *out = best_ms;
+        return e;
+    };
+    float base_ms;
+    const int32_t du = 1024, db = 256, dp = 4;  // the default shape
+    BCK(time_cfg(du, db, dp, &base_ms));
+    float best = base_ms;
+    int32_t bu = du, bb = db, bs = dp;
+    for (int32_t un : units)
         for (int32_t bl : blocks)
             for (int32_t bp : bpss) {
-                b->block = bl;
-                b->bps = bp;
-                // the step writes the other state buffer only (no swap): re-running it is harmless
-                BCK(launch_batch_step(b, k, false));
-                BCK(cudaEventRecord(e0, b->stream));
-                for (int rep = 0; rep < 3; ++rep)
-                    BCK(launch_batch_step(b, k, false));
-                BCK(cudaEventRecord(e1, b->stream));
-                BCK(cudaEventSynchronize(e1));
-                float ms = 0.0f;
-                BCK(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best) {
+                float ms;
+                BCK(time_cfg(un, bl, bp, &ms));
+                if (ms < 0.98f * best) {  // a change must win by 2 %
                     best = ms;
                     bu = un;
                     bb = bl;
                     bs = bp;
                 }
             }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     BCK(build_units(b, bu));

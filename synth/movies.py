@@ -5,8 +5,10 @@ Readings used here (all data-side only):
   * Pixel (i, j) is column i <-> x and row j <-> y, pixel centres at integer
     coordinates 0..W-1, and the PSF is point-sampled at the centres (eq. 3).
   * Truth dynamics per frame: x_k = x_{k-1} + v_{k-1} + sigma_m * e,
-    v_k = v_{k-1} + sigma_v * e', the spot intensity is constant.  The truth is
-    reflected at a margin so the spot stays inside the image.
+    v_k = 0.98 v_{k-1} + sigma_v * e' - kappa (x_{k-1} - centre), the spot
+    intensity constant.  The weak pull kappa = (v0 / 0.3 W)^2 and the light
+    damping keep long sequences in view with smooth turns; a reflection at a
+    margin is the safety net.
   * SNR is the Poisson peak SNR I0 / sqrt(I0 + I_bg) (an amplitude ratio,
     "SNR 2 (6 dB)" in Sec. 7.3), so I0 solves I0^2 = SNR^2 (I0 + I_bg).
   * Frames are float32 photon counts.  Reduced-precision copies are made by the
@@ -64,13 +66,19 @@ def _trajectory(rng, K, W, H, start_lo, start_hi, v0, sigma_m, sigma_v, amp, mar
     y = rng.uniform(start_lo[1], start_hi[1])
     vx = rng.uniform(-v0, v0)
     vy = rng.uniform(-v0, v0)
+    # a weak pull toward the image centre turns the spot smoothly, so long
+    # sequences stay in view (swing of about 0.3 of the image for |v| <= v0)
+    kx = (max(v0, 1e-3) / (0.3 * W)) ** 2
+    ky = (max(v0, 1e-3) / (0.3 * H)) ** 2
+    cx, cy = 0.5 * (W - 1), 0.5 * (H - 1)
+    damp = 0.02  # keeps the velocity spread stationary (about sigma_v / sqrt(2 damp))
     truth = np.empty((K, 5), dtype=np.float64)
     for k in range(K):
         e = rng.standard_normal(4)
         nx = x + vx + sigma_m * e[0]
         ny = y + vy + sigma_m * e[1]
-        vx = vx + sigma_v * e[2]
-        vy = vy + sigma_v * e[3]
+        vx = (1.0 - damp) * vx + sigma_v * e[2] - kx * (x - cx)
+        vy = (1.0 - damp) * vy + sigma_v * e[3] - ky * (y - cy)
         # keep the spot inside the image (generator-side only)
         if nx < margin:
             nx, vx = 2 * margin - nx, abs(vx)

@@ -115,8 +115,11 @@ def test_graph_run_matches_plain_launches_and_autotune(ppf):
     b = ppf.BatchFilter(gms, ns)
     cfg = b.autotune(frames[0], 1)
     assert cfg["unit"] in (512, 1024, 2048, 4096) and cfg["block"] in (128, 256, 512)
-    ea = a.run(frames, 1, use_graph=False)
-    eb = b.run(frames, 1, use_graph=True)
+    # two runs: the second replays the graph cached by the first, from the next frame
+    a.run(frames[:2], 1, use_graph=False)
+    b.run(frames[:2], 1, use_graph=True)
+    ea = a.run(frames[2:], 3, use_graph=False)
+    eb = b.run(frames[2:], 3, use_graph=True)
     sa, aa = a.get_particles(anc=True)
     sb, ab = b.get_particles(anc=True)
     assert torch.equal(sa, sb) and torch.equal(aa, ab)
@@ -124,5 +127,25 @@ def test_graph_run_matches_plain_launches_and_autotune(ppf):
     # the estimates agree to the summation-order error
     assert np.allclose(ea["mean"], eb["mean"], rtol=1e-5, atol=1e-5)
     assert np.allclose(ea["log_evidence"], eb["log_evidence"], rtol=1e-6)
+    a.close()
+    b.close()
+
+
+def test_step_api_matches_run(ppf):
+    import torch
+    F = 6
+    ns = [100, 4097, 7, 3000, 1, 512]
+    mb, gms, oms, frames = make(ppf, F, ns, K=3, seed=9)
+    a = ppf.BatchFilter(gms, ns)
+    b = ppf.BatchFilter(gms, ns)
+    for k in range(1, 4):
+        a.step(frames[k - 1], k)
+        a.resample(k)
+    b.run(frames, 1, use_graph=True)
+    sa, aa = a.get_particles(anc=True)
+    sb, ab = b.get_particles(anc=True)
+    assert torch.equal(sa, sb) and torch.equal(aa, ab)
+    with pytest.raises(ppf.PPFError):
+        a.resample(3)  # no step since the last resample
     a.close()
     b.close()
