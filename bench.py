@@ -159,6 +159,25 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- ranks
+def max_over_ranks(t_ms, dist, device):
+    """Barrier, then the largest of every rank's time: the job ends with its
+    slowest rank."""
+    if dist is None:
+        return t_ms
+    import torch
+    dist.barrier()
+    t = torch.tensor([t_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(n_per_rank, steps, world, t_ms):
+    """Whole-job particle-steps/s: every rank's particles over the slowest
+    rank's time."""
+    return n_per_rank * steps * world / (t_ms / 1e3)
+
+
 # ---------------------------------------------------------------- ours
 def timed_frames(pf, frames, k0, K, scheme, alpha, stream):
     import torch
@@ -208,15 +227,11 @@ def run_ours(args):
     t_ms = timed_frames(pf, frames, Wm + 1, K, scheme, args.alpha, stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    if dist:
-        dist.barrier()
-        t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = max_over_ranks(t_ms, dist, dev)
     prof = pf.profile_read()
     est = pf.estimate()
     kdone = Wm + K
-    value = n * K * world / (t_ms / 1e3)
+    value = job_rate(n, K, world, t_ms)
 
     step_ms = prof["step_ms"] / max(1, prof["timed_steps"])
     achieved = STEP_BYTES * n / (step_ms / 1e3) / 1e9
@@ -253,6 +268,8 @@ def run_ours(args):
         ke = args.e2e_steps
         host = torch.from_numpy(mv.frames[kdone:kdone + ke]).pin_memory()  # the frames right after the timed ones
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         pf.profile_enable(True, capacity=ke + 8)
         t0 = time.perf_counter()
         for i in range(ke):
@@ -260,9 +277,9 @@ def run_ours(args):
             pf.resample(scheme, args.alpha)
             pf.estimate()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
         pr = pf.profile_read()
-        line["e2e"] = {"value": n * ke * world / dt, "unit": UNIT, "steps": ke,
+        line["e2e"] = {"value": job_rate(n, ke, world, 1e3 * dt), "unit": UNIT, "steps": ke,
                        "h2d_bytes_per_step": pr["h2d_bytes"] // ke, "d2h_bytes_per_step": pr["d2h_bytes"] // ke,
                        "timing": "host wall clock around step_host + resample + estimate (sync) per frame, "
                                  "on the frames that follow the timed ones"}

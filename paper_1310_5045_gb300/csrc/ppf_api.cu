@@ -202,6 +202,8 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
         }
     }
     if (st == PPF_OK)
+        chk(ppf::resample_kernel_attributes(), "kernel attributes");
+    if (st == PPF_OK)
         chk(ppf::launch_init(c), "init_kernel");
     if (st == PPF_OK)
         chk(ppf::launch_identity(c, c->anc), "identity");

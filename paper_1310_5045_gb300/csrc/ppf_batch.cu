@@ -403,7 +403,9 @@ __global__ void __launch_bounds__(TILE_THREADS) batch_fill(const float *st0, con
                                                            const int64_t *__restrict__ tT,
                                                            const uint64_t *__restrict__ fQu, int32_t *__restrict__ anc)
 {
-    __shared__ uint64_t C[TILE_SMEM_U64];
+    extern __shared__ uint64_t fill_smem[];  // FILL_SMEM_BYTES
+    uint64_t *C = fill_smem;
+    uint16_t *stage = reinterpret_cast<uint16_t *>(fill_smem + TILE_SMEM_U64);
     __shared__ uint64_t red[33];
     const float *__restrict__ lw = (cur->cur ? st0 : st1) + 5 * Ntot;
     const int32_t t = blockIdx.x, f = tile_f[t];
@@ -422,8 +424,8 @@ __global__ void __launch_bounds__(TILE_THREADS) batch_fill(const float *st0, con
     uint64_t q[TILE_ITEMS];
     tile_weights(lw, lo, n, fs[f].M, scale_bits(P.n), C, q);
     tile_scan(q, C, red);
-    ticket_parents(C, n, tC[t], u, Q, (uint32_t)P.n, j_lo, j_hi,
-                   [&](int64_t j, int i) { anc[P.off + j] = (int32_t)(lo + i); });
+    ticket_parents_staged(C, n, tC[t], u, Q, (uint32_t)P.n, j_lo, j_hi, stage,
+                          [&](int64_t j, int i) { anc[P.off + j] = (int32_t)(lo + i); });
 }
 
 // ------------------------------------------------------------------ host side
@@ -581,7 +583,7 @@ cudaError_t launch_batch_resample(ppf_batch *b)
                                                             b->cursor, b->tile_f, b->tile_lo, b->tile_n, b->tQ);
     batch_tile_scan<<<(b->F * 32 + 255) / 256, 256, 0, b->stream>>>(b->fp, b->cursor, b->ft_off, b->F, b->tQ, b->tC,
                                                                       b->tT, b->fQu, b->flags);
-    batch_fill<<<b->T, TILE_THREADS, 0, b->stream>>>(b->state[0], b->state[1], b->Ntot, b->fp, b->fsum, b->cursor,
+    batch_fill<<<b->T, TILE_THREADS, FILL_SMEM_BYTES, b->stream>>>(b->state[0], b->state[1], b->Ntot, b->fp, b->fsum, b->cursor,
                                                      b->tile_f, b->tile_lo, b->tile_n, b->ft_off, b->tC, b->tT, b->fQu,
                                                      b->anc);
     b->launches += 3;
@@ -729,7 +731,9 @@ ppf_status ppf_batch_create(const ppf_model *models, const int64_t *n, int32_t F
     if (cudaMemcpy(b->fp, hp.data(), sizeof(FilterParams) * F, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(dv0A, v0A.data(), sizeof(float) * 2 * F, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->flags, 0, sizeof(int32_t)) != cudaSuccess || build_units(b, 1024) != cudaSuccess ||
-        build_tiles(b) != cudaSuccess) {
+        build_tiles(b) != cudaSuccess ||
+        cudaFuncSetAttribute(batch_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILL_SMEM_BYTES) !=
+            cudaSuccess) {
         cudaFree(dv0A);
         return fail(PPF_ECUDA);
     }

@@ -11,8 +11,7 @@ namespace ppf {
 constexpr int TILE = 4096;          // particles per resampling tile (256 threads x 16)
 constexpr int TILE_THREADS = 256;
 constexpr int TILE_ITEMS = TILE / TILE_THREADS;
-constexpr int FILL_CHUNK = 2048;    // tickets per fill pass (8 per thread)
-constexpr int ITEM_TICKETS = 16384; // tickets per fill work item (8 passes)
+constexpr int ITEM_TICKETS = 8192;  // tickets per fill work item
 constexpr int COPY_CHUNK = 2048;    // slots per routing-copy work item
 constexpr int MAX_RADIUS = 8;
 constexpr int MAX_SCHED_GROUPS = 16384;
@@ -123,6 +122,7 @@ cudaError_t launch_init(ppf_ctx *c);
 cudaError_t launch_prepare_frame(ppf_ctx *c, const void *frame);
 cudaError_t launch_step(ppf_ctx *c, int32_t k);
 cudaError_t launch_grad_step(ppf_ctx *c, int32_t k, bool first, int32_t *anchors);
+cudaError_t resample_kernel_attributes();
 cudaError_t launch_resample_global(ppf_ctx *c, int scheme);
 cudaError_t launch_resample_rna(ppf_ctx *c, float alpha);
 cudaError_t launch_identity(ppf_ctx *c, int32_t *dst);

@@ -20,6 +20,7 @@
 
 #include "ppf_device.cuh"
 #include "ppf_internal.h"
+#include "ppf_tiles.cuh"
 
 namespace ppf {
 
@@ -129,6 +130,10 @@ unsigned char *scratch_address(int dev, cudaError_t *err)
         *err = cudaGetSymbolAddress(&p, g_scratch);
         if (*err != cudaSuccess)
             return nullptr;
+        // the fill kernel's dynamic shared memory size (an attribute, no allocation)
+        *err = resample_kernel_attributes();
+        if (*err != cudaSuccess)
+            return nullptr;
         g_addr[dev] = static_cast<unsigned char *>(p);
     }
     *err = cudaSuccess;
@@ -166,7 +171,7 @@ extern "C" ppf_status ppf_systematic_resample_noalloc(const float *lw_dev, int64
     tile_scan_kernel<<<1, 1024, 0, st>>>(n, T, Qt, Ct, Tt, item_off, sum, seed, filter_id, (uint32_t)frame,
                                          nullptr, 0, 0, nullptr, nullptr);
     const int max_items = T + (int)((n + ITEM_TICKETS - 1) / ITEM_TICKETS);
-    fill_kernel<<<max_items, TILE_THREADS, 0, st>>>(lw_dev, n, T, sum, Ct, Tt, item_off, anc_dev);
+    fill_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, st>>>(lw_dev, n, T, sum, Ct, Tt, item_off, anc_dev);
     noalloc_identity_if_degenerate<<<gmax, 256, 0, st>>>(anc_dev, n, s);
     return cudaGetLastError() == cudaSuccess ? PPF_OK : PPF_ECUDA;
 }

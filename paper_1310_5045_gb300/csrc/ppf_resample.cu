@@ -180,14 +180,17 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
 
 // ---------------------------------------------------------------- R3 fill
 // Work item b covers tickets [i_lo, i_hi) of one tile (at most ITEM_TICKETS);
-// the tile's cumulative weights are built once in shared memory and every
-// ticket finds its parent there (ticket_parents), written out coalesced.
+// the tile's cumulative weights are built once in shared memory, the parents
+// of the item's tickets are staged there and written out coalesced.
+// Dynamic shared memory: FILL_SMEM_BYTES.
 __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     const float *__restrict__ lw, int64_t N, int32_t T, const DevSummary *__restrict__ sum,
     const uint64_t *__restrict__ Ct, const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
     int32_t *__restrict__ out)
 {
-    __shared__ uint64_t C[TILE_SMEM_U64];
+    extern __shared__ uint64_t fill_smem[];
+    uint64_t *C = fill_smem;
+    uint16_t *stage = reinterpret_cast<uint16_t *>(fill_smem + TILE_SMEM_U64);
     __shared__ uint64_t red[33];
     __shared__ int32_t st;
     const int32_t b = blockIdx.x;
@@ -213,8 +216,8 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     tile_scan(q, C, red);
     const int64_t i_lo = Tt[t] + (int64_t)(b - item_off[t]) * ITEM_TICKETS;
     const int64_t i_hi = (Tt[t + 1] < i_lo + ITEM_TICKETS) ? Tt[t + 1] : i_lo + ITEM_TICKETS;
-    ticket_parents(C, n, Ct[t], sum->u, sum->Q, (uint32_t)N, i_lo, i_hi,
-                   [&](int64_t j, int i) { out[j] = (int32_t)(lo + i); });
+    ticket_parents_staged(C, n, Ct[t], sum->u, sum->Q, (uint32_t)N, i_lo, i_hi, stage,
+                          [&](int64_t j, int i) { out[j] = (int32_t)(lo + i); });
 }
 
 // ------------------------------------------------------------ RPA schedule
@@ -624,7 +627,9 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
     uint64_t seed, uint32_t fid, uint32_t frame, int32_t *__restrict__ anc, float *__restrict__ lwp)
 {
     const int64_t mig = sum->mig;
-    __shared__ uint64_t C[TILE_SMEM_U64];
+    extern __shared__ uint64_t fill_smem[];  // FILL_SMEM_BYTES
+    uint64_t *C = fill_smem;
+    uint16_t *stage = reinterpret_cast<uint16_t *>(fill_smem + TILE_SMEM_U64);
     __shared__ uint64_t red[33];
     __shared__ float smf[8];
     __shared__ double lwg_s;
@@ -701,7 +706,7 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
         const uint64_t tot = tile_scan(q, C, red);
         const int64_t t_lo = tickets_below(carry, sz, u, Q);
         const int64_t t_hi = tickets_below(carry + tot, sz, u, Q);
-        ticket_parents(C, n, carry, u, Q, (uint32_t)sz, t_lo, t_hi, [&](int64_t j, int i) {
+        ticket_parents_staged(C, n, carry, u, Q, (uint32_t)sz, t_lo, t_hi, stage, [&](int64_t j, int i) {
             const int64_t d = dest(j);
             anc[d] = (int32_t)(lo + c0 + i);
             lwp[d] = lwg;
@@ -775,6 +780,20 @@ __global__ void fill_f32_kernel(float *__restrict__ a, int64_t N, float v)
 }
 
 // ---------------------------------------------------------------- launchers
+// Opt the dynamic-shared-memory kernels of this file into their sizes (current
+// device; called when a context is created).
+cudaError_t resample_kernel_attributes()
+{
+    cudaError_t e = cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)FILL_SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rna_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILL_SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(schedule_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(uint64_t) * MAX_SCHED_GROUPS));
+    return e;
+}
+
 cudaError_t launch_resample_global(ppf_ctx *c, int scheme)
 {
     const bool rpa = (scheme != PPF_SYSTEMATIC);
@@ -789,7 +808,7 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme)
                                                 c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg);
     const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
     int32_t *out = rpa ? c->anc_sys : c->anc;
-    fill_kernel<<<max_items, TILE_THREADS, 0, c->stream>>>(lw, c->N, T, c->sum, c->sc.Ct, c->sc.Tt,
+    fill_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(lw, c->N, T, c->sum, c->sc.Ct, c->sc.Tt,
                                                            c->sc.item_off, out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !rpa) {
@@ -811,13 +830,6 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme)
     A.seg_len = c->sc.seg_len;
     A.sum = c->sum;
     const size_t smem = sizeof(uint64_t) * MAX_SCHED_GROUPS;
-    static bool attr_set = false;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(schedule_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        attr_set = true;
-    }
     schedule_kernel<<<1, 1024, smem, c->stream>>>(A);
     const int max_chunks = 2 * c->G + 1 + (int)((c->N + COPY_CHUNK - 1) / COPY_CHUNK);
     route_copy_kernel<<<max_chunks, 256, 0, c->stream>>>(c->anc_sys, c->anc, c->G, c->sc.seg_chunk,
@@ -832,7 +844,7 @@ cudaError_t launch_resample_rna(ppf_ctx *c, float alpha)
     const float *lw = c->state[c->cur] + 5 * c->N;
     prof_mark(c, PH_RESAMPLE, 0);
     rna_prep_kernel<<<1, 1024, 0, c->stream>>>(c->goff, c->G, alpha, c->sum);
-    rna_kernel<<<c->G, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->G, c->goff, c->sum, c->m.seed,
+    rna_kernel<<<c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(lw, c->N, c->G, c->goff, c->sum, c->m.seed,
                                                      c->m.filter_id, (uint32_t)c->last_frame, c->anc, c->lwp);
     prof_mark(c, PH_RESAMPLE, 1);
     c->launches += 2;

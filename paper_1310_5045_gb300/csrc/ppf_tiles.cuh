@@ -90,46 +90,108 @@ __device__ __forceinline__ uint64_t div_small(uint64_t v, uint32_t d, float rd, 
 // Parents of the tickets [j_lo, j_hi) of one run of particles with inclusive
 // cumulative weights C[0..n) (local; the run starts at cumulative weight c0,
 // n <= TILE).  Ticket j sits at (u + jQ)/nt; its parent is the first i with
-// c0 + C[i] > thr_j = floor((u + jQ)/nt).  One exact 96/32 division gives thr
-// at j_lo; with Q = qN nt + qR, ticket j_lo + o has
-// thr = thr(j_lo) + o qN + floor((rem(j_lo) + o qR) / nt).  Thread t takes
-// tickets j_lo + t, j_lo + t + blockDim, ... (coalesced writes) and finds each
-// parent with a fixed 12-step branch-free binary search (no divergence, no
-// barriers between tickets).  emit(j, i) receives every (ticket, parent).
-// Called by every thread of the block.
+// c0 + C[i] > thr_j = floor((u + jQ)/nt).  With Q = qN nt + qR the thresholds
+// step as thr_{j+1} = thr_j + qN + [rem_j + qR >= nt] (rem_j = (u + jQ) mod nt).
+//
+// The parents are a merge of two sorted sequences: particle i comes before
+// ticket j iff C[i] <= thr_j - c0, and a ticket's parent is the particle that
+// follows it.  The merged sequence (n + L elements, L = j_hi - j_lo) is cut
+// into equal pieces, one per thread (merge path): a binary search along the
+// thread's cross diagonal finds where its piece starts, then the thread walks
+// its piece, advancing either the particle or the ticket at every step.  Every
+// thread does the same number of steps whatever the weights.
+// emit(j, i) receives every (ticket, parent), a thread's tickets in
+// increasing order.  Called by every thread of the block; contains barriers.
 template <typename Emit>
 __device__ __forceinline__ void ticket_parents(const uint64_t *C, int n, uint64_t c0, uint64_t u, uint64_t Q,
                                                uint32_t nt, int64_t j_lo, int64_t j_hi, Emit emit)
 {
-    __shared__ uint64_t s_thr;
-    __shared__ uint32_t s_rem;
-    const uint64_t qN = Q / nt;
-    const uint32_t qR = (uint32_t)(Q % nt);
-    const float rnt = 1.0f / (float)nt;
+    __shared__ uint64_t s_thr, s_qN;
+    __shared__ uint32_t s_rem, s_qR;
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t r0;
         s_thr = div_u96((u128)u + (u128)(uint64_t)j_lo * (u128)Q, nt, &r0);
         s_rem = r0;
+        s_qN = Q / nt;
+        s_qR = (uint32_t)(Q % nt);
     }
     __syncthreads();
-    const uint64_t thr0 = s_thr;
-    const uint64_t rem0 = s_rem;
-    for (int64_t j = j_lo + threadIdx.x; j < j_hi; j += blockDim.x) {
-        const uint64_t o = (uint64_t)(j - j_lo);
-        uint32_t r;
-        const uint64_t thr = thr0 + o * qN + div_small(rem0 + o * qR, nt, rnt, &r);
-        const uint64_t lt = thr - c0;
-        // number of C[i] <= lt over i < TILE (C[i] for i >= n is never reached:
-        // every ticket of this run has lt < C[n-1])
-        int pos = 0;
-#pragma unroll
-        for (int step = TILE / 2; step > 0; step >>= 1) {
-            const int k = pos + step - 1;
-            if (k < n && C[padc(k)] <= lt)
-                pos += step;
+    const int64_t L = j_hi - j_lo;
+    const int64_t D = (int64_t)n + L;
+    const int64_t K = (D + blockDim.x - 1) / blockDim.x;
+    const int64_t d0 = (int64_t)threadIdx.x * K;
+    if (L <= 0 || d0 >= D)
+        return;
+    const uint64_t thr0 = s_thr, qN = s_qN;
+    const uint32_t rem0 = s_rem, qR = s_qR;
+    const float rnt = 1.0f / (float)nt;
+    // thr_{j_lo + b} - c0 and rem_{j_lo + b}
+    auto lt_at = [&](int64_t b, uint32_t *rem) -> uint64_t {
+        uint64_t t;
+        if (b < (1 << 21))  // quotient < 2^21: the float estimate is off by at most 1
+            t = thr0 + (uint64_t)b * qN + div_small((uint64_t)rem0 + (uint64_t)b * qR, nt, rnt, rem);
+        else
+            t = div_u96((u128)u + (u128)(uint64_t)(j_lo + b) * (u128)Q, nt, rem);
+        return t - c0;
+    };
+    // particles among the first d0 merged elements: the first a in
+    // [max(0, d0 - L), min(d0, n)] with C[a] > lt(d0 - a - 1)
+    int64_t lo = d0 > L ? d0 - L : 0, hi = d0 < n ? d0 : n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        uint32_t rm;
+        if (C[padc((int)mid)] <= lt_at(d0 - mid - 1, &rm))
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    int i = (int)lo;
+    int64_t b = d0 - lo;
+    if (b >= L)
+        return;
+    uint32_t r;
+    uint64_t lt = lt_at(b, &r);
+    const int64_t steps = (D - d0 < K) ? D - d0 : K;
+    // every ticket has lt < C[n-1], so i stays below n while tickets remain
+    for (int64_t s = 0; s < steps; ++s) {
+        if (C[padc(i)] <= lt) {
+            ++i;
+        } else {
+            emit(j_lo + b, i);
+            if (++b >= L)
+                break;
+            lt += qN;
+            r += qR;
+            if (r >= nt) {
+                r -= nt;
+                ++lt;
+            }
         }
-        emit(j, pos);
+    }
+}
+
+// Shared memory of the fill kernels: the tile's cumulative weights, then the
+// staged parents (local indices) of up to STAGE_TICKETS tickets.
+constexpr int STAGE_TICKETS = ITEM_TICKETS;
+constexpr size_t FILL_SMEM_BYTES = sizeof(uint64_t) * TILE_SMEM_U64 + sizeof(uint16_t) * STAGE_TICKETS;
+
+// ticket_parents in chunks of STAGE_TICKETS tickets: the parents are staged in
+// shared memory and handed to store(j, i) in ticket order, thread k taking
+// tickets k, k + blockDim, ... of the chunk (coalesced global writes).
+template <typename Store>
+__device__ __forceinline__ void ticket_parents_staged(const uint64_t *C, int n, uint64_t c0, uint64_t u, uint64_t Q,
+                                                      uint32_t nt, int64_t j_lo, int64_t j_hi, uint16_t *stage,
+                                                      Store store)
+{
+    for (int64_t c = j_lo; c < j_hi; c += STAGE_TICKETS) {
+        const int64_t ce = (j_hi - c < STAGE_TICKETS) ? j_hi : c + STAGE_TICKETS;
+        ticket_parents(C, n, c0, u, Q, nt, c, ce, [&](int64_t j, int i) { stage[j - c] = (uint16_t)i; });
+        __syncthreads();
+        const int m = (int)(ce - c);
+        for (int k = threadIdx.x; k < m; k += blockDim.x)
+            store(c + k, (int)stage[k]);
+        __syncthreads();
     }
 }
 
