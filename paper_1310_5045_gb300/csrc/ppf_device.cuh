@@ -116,21 +116,19 @@ __device__ __forceinline__ uint64_t quantise(float lw, float M, int s)
 {
     const float d = __fsub_rn(lw, M);
     const float t = __fmul_rn(d, 0x1.715476p+0f);
-    if (!(t > -64.0f))
-        return 0ull;
-    const float kf = floorf(t);
+    const float kf = fmaxf(floorf(t), -64.0f);  // the clamp only affects results that are 0 anyway
     const float f = __fsub_rn(t, kf);
     const float p = exp2_frac(f);
     const int e = s + (int)kf;
-    // P = p 2^23 exactly: p lies in [1, 2], so its mantissa with the implicit
-    // bit, doubled when the exponent is that of 2
+    // p lies in [1, 2]: P = p 2^23 is its mantissa with the implicit bit,
+    // doubled when p = 2.  q = floor(P 2^(e - 23)) without branches:
+    // X = P 2^39 < 2^64, q = X / 2^(62 - e); e = 63 only for p = 1 (t = 0),
+    // and q = 0 for e < -1.
     const uint32_t pb = __float_as_uint(p);
-    const uint64_t P = (uint64_t)((pb & 0x7FFFFFu) | 0x800000u) << ((pb >> 23) - 127u);
-    if (e < -25)
-        return 0ull;
-    if (e >= 23)
-        return P << (e - 23);
-    return P >> (23 - e);
+    const uint64_t X = ((uint64_t)((pb & 0x7FFFFFu) | 0x800000u) << (((pb >> 23) - 127u) & 1u)) << 39;
+    const int sh = 62 - e;
+    const uint64_t q = (sh < 0) ? (X << 1) : (X >> (sh < 63 ? sh : 63));
+    return (t > -64.0f && e >= -1) ? q : 0ull;  // t <= -64 or NaN: zero weight
 }
 
 // Number of systematic tickets below cumulative weight c:

@@ -80,6 +80,8 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_totals_kernel(
 // ---------------------------------------------------------------- R2 scan
 // One block: exclusive tile prefix, total Q, ticket offset u, tickets below
 // each tile start, fill work items; for RPA the tickets below each group start.
+// Every array is walked in rounds of blockDim consecutive entries (coalesced),
+// each round closed by a block scan.
 __global__ void __launch_bounds__(1024) tile_scan_kernel(
     int64_t N, int32_t T, const uint64_t *__restrict__ Qt, uint64_t *__restrict__ Ct, int64_t *__restrict__ Tt,
     int32_t *__restrict__ item_off, DevSummary *sum, uint64_t seed, uint32_t fid, uint32_t frame,
@@ -87,23 +89,19 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
     int64_t *__restrict__ Tg)
 {
     __shared__ uint64_t red[33];
-    __shared__ uint64_t sQ, su;
-    const int per = (T + blockDim.x - 1) / blockDim.x;
-    const int t0 = threadIdx.x * per;
-    uint64_t s = 0;
-    for (int k = 0; k < per; ++k)
-        if (t0 + k < T)
-            s += Qt[t0 + k];
-    uint64_t total;
-    uint64_t run = block_excl_scan_u64(s, red, &total);
-    for (int k = 0; k < per; ++k)
-        if (t0 + k < T) {
-            Ct[t0 + k] = run;
-            run += Qt[t0 + k];
-        }
+    __shared__ uint64_t su;
+    uint64_t total = 0;
+    for (int base = 0; base < T; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        const uint64_t v = (t < T) ? Qt[t] : 0ull;
+        uint64_t tot;
+        const uint64_t ex = block_excl_scan_u64(v, red, &tot);
+        if (t < T)
+            Ct[t] = total + ex;
+        total += tot;
+    }
     if (threadIdx.x == 0) {
         Ct[T] = total;
-        sQ = total;
         const int deg = (total == 0ull);
         sum->degenerate = deg;
         if (deg)
@@ -113,7 +111,7 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
         sum->u = su;
     }
     __syncthreads();
-    const uint64_t Q = sQ, u = su;
+    const uint64_t Q = total, u = su;
     if (Q == 0ull) {
         if (threadIdx.x == 0)
             sum->n_items = 0;
@@ -123,17 +121,16 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
         Tt[t] = (t == T) ? N : tickets_below(Ct[t], N, u, Q);
     __syncthreads();
     // fill work items: ceil(tickets / ITEM_TICKETS) per tile
-    uint64_t cnt = 0;
-    for (int k = 0; k < per; ++k)
-        if (t0 + k < T)
-            cnt += (uint64_t)((Tt[t0 + k + 1] - Tt[t0 + k] + ITEM_TICKETS - 1) / ITEM_TICKETS);
-    uint64_t items_total;
-    uint64_t irun = block_excl_scan_u64(cnt, red, &items_total);
-    for (int k = 0; k < per; ++k)
-        if (t0 + k < T) {
-            item_off[t0 + k] = (int32_t)irun;
-            irun += (uint64_t)((Tt[t0 + k + 1] - Tt[t0 + k] + ITEM_TICKETS - 1) / ITEM_TICKETS);
-        }
+    uint64_t items_total = 0;
+    for (int base = 0; base < T; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        const uint64_t cnt = (t < T) ? (uint64_t)((Tt[t + 1] - Tt[t] + ITEM_TICKETS - 1) / ITEM_TICKETS) : 0ull;
+        uint64_t tot;
+        const uint64_t ex = block_excl_scan_u64(cnt, red, &tot);
+        if (t < T)
+            item_off[t] = (int32_t)(items_total + ex);
+        items_total += tot;
+    }
     if (threadIdx.x == 0) {
         item_off[T] = (int32_t)items_total;
         sum->n_items = (int32_t)items_total;
