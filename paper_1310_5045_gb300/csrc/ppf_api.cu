@@ -59,7 +59,7 @@ void free_all(ppf_ctx *c)
 {
     void *ptrs[] = {c->tang[0], c->tang[1], c->gpart,
                     c->state[0], c->state[1], c->anc, c->anc_sys, c->lwp, c->goff, c->goff_new, c->Zp,
-                    c->frame_buf, c->part, c->sum, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.Cbl,
+                    c->frame_buf, c->part, c->sum, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sc.Cbl,
                     c->sc.Tg, c->sc.skey, c->sc.sval, c->sc.seg_tick, c->sc.seg_dst, c->sc.seg_len,
                     c->sc.seg_chunk};
     for (void *p : ptrs)
@@ -176,6 +176,7 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
         chk(dalloc(&c->sc.Ct, T + 1), "Ct");
         chk(dalloc(&c->sc.Tt, T + 1), "Tt");
         chk(dalloc(&c->sc.item_off, T + 1), "item_off");
+        chk(dalloc(&c->sc.item_tile, T + (N + ppf::ITEM_TICKETS - 1) / ppf::ITEM_TICKETS), "item_tile");
         chk(dalloc(&c->sc.Cbl, G + 1), "Cbl");
         chk(dalloc(&c->sc.Tg, G + 1), "Tg");
         chk(dalloc(&c->sc.skey, 2 * G), "skey");

@@ -30,6 +30,7 @@ namespace ppf {
 struct FilterParams {
     int64_t off, n;
     uint64_t seed;
+    Divisor ndiv;             // n as a divisor of the ticket grid
     uint32_t fid;
     float inv2s2, inv_sxi2, sm, sv, sI, bg;
     float Kc[MAX_RADIUS];
@@ -91,7 +92,7 @@ struct ppf_batch {
     uint64_t *tQ;                      // device [T] tile totals
     uint64_t *tC;                      // device [T] exclusive prefix within the filter
     int64_t *tT;                       // device [T + 1]: first ticket of the tile (filter-local)
-    uint64_t *fQu;                     // device [2F]: per filter Q_f, u_f
+    uint64_t *fQu;                     // device [4F]: per filter Q_f, u_f, Q_f / n_f, Q_f mod n_f
     ppf::Partial *upart;               // device [U]
     ppf::FilterSummary *fsum;          // device [F]
     ppf::FilterSummary *fsum_host;     // pinned [F]
@@ -382,8 +383,10 @@ __global__ void batch_tile_scan(const FilterParams *__restrict__ fp, const Batch
     const uint64_t Q = carry;
     const uint64_t u = (Q == 0ull) ? 0ull : ticket_offset(P.seed, P.fid, (uint32_t)cur->k, PURPOSE_RESAMPLE, 0u, Q);
     if (lane == 0) {
-        fQu[2 * f] = Q;
-        fQu[2 * f + 1] = u;
+        fQu[4 * f] = Q;
+        fQu[4 * f + 1] = u;
+        fQu[4 * f + 2] = Q / (uint64_t)P.n;
+        fQu[4 * f + 3] = Q % (uint64_t)P.n;
         if (Q == 0ull)
             atomicOr(flags, FLAG_DEGENERATE);
     }
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(TILE_THREADS) batch_fill(const float *st0, con
     const FilterParams P = fp[f];
     const int64_t lo = tile_lo[t];
     const int n = tile_n[t];
-    const uint64_t Q = fQu[2 * f], u = fQu[2 * f + 1];
+    const uint64_t Q = fQu[4 * f], u = fQu[4 * f + 1];
     if (Q == 0ull) {  // no usable weight in the filter: it keeps its particles
         for (int i = threadIdx.x; i < n; i += blockDim.x)
             anc[lo + i] = (int32_t)(lo + i);
@@ -424,7 +427,8 @@ __global__ void __launch_bounds__(TILE_THREADS) batch_fill(const float *st0, con
     uint64_t q[TILE_ITEMS];
     tile_weights(lw, lo, n, fs[f].M, scale_bits(P.n), C, q);
     tile_scan(q, C, red);
-    ticket_parents_staged(C, n, tC[t], u, Q, (uint32_t)P.n, j_lo, j_hi, stage,
+    const TicketGrid tg = ticket_grid(Q, u, fQu[4 * f + 2], (uint32_t)fQu[4 * f + 3], P.ndiv);
+    ticket_parents_staged(C, n, tC[t], tg, j_lo, j_hi, stage,
                           [&](int64_t j, int i) { anc[P.off + j] = (int32_t)(lo + i); });
 }
 
@@ -492,7 +496,7 @@ cudaError_t build_tiles(ppf_batch *b)
     if ((e = dmalloc(&b->tQ, b->T)) != cudaSuccess) return e;
     if ((e = dmalloc(&b->tC, b->T)) != cudaSuccess) return e;
     if ((e = dmalloc(&b->tT, b->T + 1)) != cudaSuccess) return e;
-    if ((e = dmalloc(&b->fQu, 2 * (size_t)b->F)) != cudaSuccess) return e;
+    if ((e = dmalloc(&b->fQu, 4 * (size_t)b->F)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(b->tile_f, tf.data(), sizeof(int32_t) * b->T, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(b->tile_lo, tl.data(), sizeof(int64_t) * b->T, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(b->tile_n, tn.data(), sizeof(int32_t) * b->T, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
@@ -706,6 +710,7 @@ ppf_status ppf_batch_create(const ppf_model *models, const int64_t *n, int32_t F
         FilterParams &P = hp[f];
         P.off = b->off[f];
         P.n = n[f];
+        P.ndiv = make_divisor((uint32_t)n[f]);
         P.seed = m.seed;
         P.fid = m.filter_id;
         P.inv2s2 = 1.0f / (2.0f * m.psf_sigma * m.psf_sigma);

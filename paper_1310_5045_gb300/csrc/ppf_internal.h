@@ -49,6 +49,8 @@ struct DevSummary {
     int32_t degenerate;        // last resample found no usable weight
     int64_t links, moved, max_group, min_group;
     uint64_t Q, u;             // last global resample: total fixed-point weight, offset
+    uint64_t qN;               // and Q = qN N + qR (the ticket spacing in whole and remainder)
+    uint32_t qR;
     int32_t n_items;           // fill work items of the last resample
     int32_t n_chunks;          // routing-copy work items of the last RPA resample
     int64_t mig;               // RNA: slots migrating to the next group
@@ -62,6 +64,7 @@ struct Scratch {
     uint64_t *Ct;      // [T+1] exclusive tile prefix
     int64_t *Tt;       // [T+1] tickets below each tile start
     int32_t *item_off; // [T+1] fill work-item prefix per tile
+    int32_t *item_tile; // [T + ceil(N / ITEM_TICKETS)] tile of every fill work item
     uint64_t *Cbl;     // [G+1] local prefix at group starts (within their tile)
     int64_t *Tg;       // [G+1] tickets below each group start
     // scheduler (RPA)

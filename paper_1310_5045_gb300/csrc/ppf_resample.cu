@@ -79,13 +79,14 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_totals_kernel(
 
 // ---------------------------------------------------------------- R2 scan
 // One block: exclusive tile prefix, total Q, ticket offset u, tickets below
-// each tile start, fill work items; for RPA the tickets below each group start.
+// each tile start, fill work items (and the tile of each item when item_tile
+// is given); for RPA the tickets below each group start.
 // Every array is walked in rounds of blockDim consecutive entries (coalesced),
 // each round closed by a block scan.
 __global__ void __launch_bounds__(1024) tile_scan_kernel(
     int64_t N, int32_t T, const uint64_t *__restrict__ Qt, uint64_t *__restrict__ Ct, int64_t *__restrict__ Tt,
-    int32_t *__restrict__ item_off, DevSummary *sum, uint64_t seed, uint32_t fid, uint32_t frame,
-    const int64_t *__restrict__ goff, int32_t G, int rpa, const uint64_t *__restrict__ Cbl,
+    int32_t *__restrict__ item_off, int32_t *__restrict__ item_tile, DevSummary *sum, uint64_t seed, uint32_t fid,
+    uint32_t frame, const int64_t *__restrict__ goff, int32_t G, int rpa, const uint64_t *__restrict__ Cbl,
     int64_t *__restrict__ Tg)
 {
     __shared__ uint64_t red[33];
@@ -107,6 +108,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
         if (deg)
             sum->flags |= FLAG_DEGENERATE;
         sum->Q = total;
+        sum->qN = total / (uint64_t)N;
+        sum->qR = (uint32_t)(total % (uint64_t)N);
         su = deg ? 0ull : ticket_offset(seed, fid, frame, PURPOSE_RESAMPLE, 0u, total);
         sum->u = su;
     }
@@ -127,8 +130,12 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
         const uint64_t cnt = (t < T) ? (uint64_t)((Tt[t + 1] - Tt[t] + ITEM_TICKETS - 1) / ITEM_TICKETS) : 0ull;
         uint64_t tot;
         const uint64_t ex = block_excl_scan_u64(cnt, red, &tot);
-        if (t < T)
+        if (t < T) {
             item_off[t] = (int32_t)(items_total + ex);
+            if (item_tile)
+                for (uint64_t k = 0; k < cnt; ++k)
+                    item_tile[items_total + ex + k] = t;
+        }
         items_total += tot;
     }
     if (threadIdx.x == 0) {
@@ -181,9 +188,9 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
 // of the item's tickets are staged there and written out coalesced.
 // Dynamic shared memory: FILL_SMEM_BYTES.
 __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
-    const float *__restrict__ lw, int64_t N, int32_t T, const DevSummary *__restrict__ sum,
+    const float *__restrict__ lw, int64_t N, int32_t T, Divisor ndiv, const DevSummary *__restrict__ sum,
     const uint64_t *__restrict__ Ct, const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
-    int32_t *__restrict__ out)
+    const int32_t *__restrict__ item_tile, int32_t *__restrict__ out)
 {
     extern __shared__ uint64_t fill_smem[];
     uint64_t *C = fill_smem;
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     const int32_t b = blockIdx.x;
     if (b >= sum->n_items)
         return;
-    if (threadIdx.x == 0) {
+    if (item_tile == nullptr && threadIdx.x == 0) {
         int32_t a = 0, e = T;  // last t with item_off[t] <= b
         while (a < e) {
             const int32_t mid = (a + e + 1) >> 1;
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
         st = a;
     }
     __syncthreads();
-    const int32_t t = st;
+    const int32_t t = item_tile ? item_tile[b] : st;
     const int64_t lo = (int64_t)t * TILE;
     const int n = (int)(N - lo < TILE ? N - lo : TILE);
     uint64_t q[TILE_ITEMS];
@@ -213,8 +220,8 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     tile_scan(q, C, red);
     const int64_t i_lo = Tt[t] + (int64_t)(b - item_off[t]) * ITEM_TICKETS;
     const int64_t i_hi = (Tt[t + 1] < i_lo + ITEM_TICKETS) ? Tt[t + 1] : i_lo + ITEM_TICKETS;
-    ticket_parents_staged(C, n, Ct[t], sum->u, sum->Q, (uint32_t)N, i_lo, i_hi, stage,
-                          [&](int64_t j, int i) { out[j] = (int32_t)(lo + i); });
+    const TicketGrid tg = ticket_grid(sum->Q, sum->u, sum->qN, sum->qR, ndiv);
+    ticket_parents_staged(C, n, Ct[t], tg, i_lo, i_hi, stage, [&](int64_t j, int i) { out[j] = (int32_t)(lo + i); });
 }
 
 // ------------------------------------------------------------ RPA schedule
@@ -630,7 +637,9 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
     __shared__ uint64_t red[33];
     __shared__ float smf[8];
     __shared__ double lwg_s;
-    __shared__ uint64_t Qs, us;
+    __shared__ uint64_t Qs, us, qNs;
+    __shared__ uint32_t qRs;
+    __shared__ Divisor dvs;
     const int32_t g = blockIdx.x;
     const int64_t lo = goff[g], sz = goff[g + 1] - lo;
     if (sz <= 0)
@@ -671,6 +680,9 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
             e += smf[w];
         Qs = Qg;
+        dvs = make_divisor((uint32_t)sz);
+        qNs = Qg / (uint64_t)sz;
+        qRs = (uint32_t)(Qg % (uint64_t)sz);
         if (Qg == 0ull) {
             lwg_s = -INFINITY;
             us = 0ull;
@@ -693,6 +705,7 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
         }
         return;
     }
+    const TicketGrid tg = ticket_grid(Q, u, qNs, qRs, dvs);
     // pass 3: chunks of TILE particles; the tickets of chunk [c0, c0 + n) are
     // [T(carry), T(carry + total)) with T the local ticket count of n = sz.
     uint64_t carry = 0;
@@ -703,7 +716,7 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
         const uint64_t tot = tile_scan(q, C, red);
         const int64_t t_lo = tickets_below(carry, sz, u, Q);
         const int64_t t_hi = tickets_below(carry + tot, sz, u, Q);
-        ticket_parents_staged(C, n, carry, u, Q, (uint32_t)sz, t_lo, t_hi, stage, [&](int64_t j, int i) {
+        ticket_parents_staged(C, n, carry, tg, t_lo, t_hi, stage, [&](int64_t j, int i) {
             const int64_t d = dest(j);
             anc[d] = (int32_t)(lo + c0 + i);
             lwp[d] = lwg;
@@ -800,13 +813,14 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme)
     c->launches += rpa ? 5 : 3;
     tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, c->sc.Qt, rpa ? c->goff : nullptr,
                                                           c->G, c->sc.Cbl);
-    tile_scan_kernel<<<1, 1024, 0, c->stream>>>(c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sum,
+    tile_scan_kernel<<<1, 1024, 0, c->stream>>>(c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off,
+                                                c->sc.item_tile, c->sum,
                                                 c->m.seed, c->m.filter_id, (uint32_t)c->last_frame,
                                                 c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg);
     const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
     int32_t *out = rpa ? c->anc_sys : c->anc;
-    fill_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(lw, c->N, T, c->sum, c->sc.Ct, c->sc.Tt,
-                                                           c->sc.item_off, out);
+    fill_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
+        lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !rpa) {
         prof_mark(c, PH_RESAMPLE, 1);

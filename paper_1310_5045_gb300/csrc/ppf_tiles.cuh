@@ -55,21 +55,6 @@ __device__ __forceinline__ uint64_t tile_scan(const uint64_t q[TILE_ITEMS], uint
     return total;
 }
 
-// floor(X / d) for X < 2^96 whose quotient fits 64 bits, d < 2^32, by long
-// division in 32-bit limbs; *rem = X mod d.
-__device__ __forceinline__ uint64_t div_u96(u128 X, uint32_t d, uint32_t *rem)
-{
-    const uint64_t l2 = (uint64_t)(X >> 64), l1 = (uint64_t)(uint32_t)(X >> 32), l0 = (uint64_t)(uint32_t)X;
-    uint64_t r = l2 % d;
-    uint64_t cur = (r << 32) | l1;
-    const uint64_t q1 = cur / d;
-    r = cur % d;
-    cur = (r << 32) | l0;
-    const uint64_t q0 = cur / d;
-    *rem = (uint32_t)(cur % d);
-    return (q1 << 32) + q0;
-}
-
 // floor(v / d), v mod d for v < 2^52, d < 2^32: float estimate, exact fix-up
 __device__ __forceinline__ uint64_t div_small(uint64_t v, uint32_t d, float rd, uint32_t *rem)
 {
@@ -87,11 +72,59 @@ __device__ __forceinline__ uint64_t div_small(uint64_t v, uint32_t d, float rd, 
     return q;
 }
 
+// floor(x / d) for a fixed divisor d >= 1 and any x < 2^64, from the
+// precomputed m = floor((2^64 - 1) / d): the product estimate floor(x m / 2^64)
+// lies within 2 below the quotient and never above it.
+struct Divisor {
+    uint64_t m;
+    uint32_t d;
+};
+
+__host__ __device__ inline Divisor make_divisor(uint32_t d)
+{
+    Divisor v;
+    v.m = ~0ull / d;
+    v.d = d;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t div_by(uint64_t x, Divisor v, uint32_t *rem)
+{
+    uint64_t q = __umul64hi(x, v.m);
+    uint64_t r = x - q * v.d;
+    while (r >= v.d) {
+        ++q;
+        r -= v.d;
+    }
+    *rem = (uint32_t)r;
+    return q;
+}
+
+// The ticket grid of one systematic draw: nt tickets at (u + jQ)/nt of the
+// cumulative fixed-point weight, Q = qN nt + qR.
+struct TicketGrid {
+    uint64_t Q, u, qN;
+    uint32_t qR;
+    Divisor nt;
+};
+
+__device__ __forceinline__ TicketGrid ticket_grid(uint64_t Q, uint64_t u, uint64_t qN, uint32_t qR, Divisor nt)
+{
+    TicketGrid g;
+    g.Q = Q;
+    g.u = u;
+    g.qN = qN;
+    g.qR = qR;
+    g.nt = nt;
+    return g;
+}
+
 // Parents of the tickets [j_lo, j_hi) of one run of particles with inclusive
 // cumulative weights C[0..n) (local; the run starts at cumulative weight c0,
 // n <= TILE).  Ticket j sits at (u + jQ)/nt; its parent is the first i with
-// c0 + C[i] > thr_j = floor((u + jQ)/nt).  With Q = qN nt + qR the thresholds
-// step as thr_{j+1} = thr_j + qN + [rem_j + qR >= nt] (rem_j = (u + jQ) mod nt).
+// c0 + C[i] > thr_j = floor((u + jQ)/nt) = j qN + floor((u + j qR)/nt), and the
+// thresholds step as thr_{j+1} = thr_j + qN + [rem_j + qR >= nt]
+// (rem_j = (u + jQ) mod nt).
 //
 // The parents are a merge of two sorted sequences: particle i comes before
 // ticket j iff C[i] <= thr_j - c0, and a ticket's parent is the particle that
@@ -103,18 +136,23 @@ __device__ __forceinline__ uint64_t div_small(uint64_t v, uint32_t d, float rd, 
 // emit(j, i) receives every (ticket, parent), a thread's tickets in
 // increasing order.  Called by every thread of the block; contains barriers.
 template <typename Emit>
-__device__ __forceinline__ void ticket_parents(const uint64_t *C, int n, uint64_t c0, uint64_t u, uint64_t Q,
-                                               uint32_t nt, int64_t j_lo, int64_t j_hi, Emit emit)
+__device__ __forceinline__ void ticket_parents(const uint64_t *C, int n, uint64_t c0, const TicketGrid &tg,
+                                               int64_t j_lo, int64_t j_hi, Emit emit)
 {
-    __shared__ uint64_t s_thr, s_qN;
-    __shared__ uint32_t s_rem, s_qR;
+    __shared__ uint64_t s_thr;
+    __shared__ uint32_t s_rem;
+    const uint32_t nt = tg.nt.d;
+    const uint64_t qN = tg.qN;
+    const uint32_t qR = tg.qR;
+    // threshold and remainder of ticket j (j < nt < 2^31): u + j qR < 2^63 + 2^62
+    auto thr_of = [&](int64_t j, uint32_t *rem) -> uint64_t {
+        return (uint64_t)j * qN + div_by(tg.u + (uint64_t)j * qR, tg.nt, rem);
+    };
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t r0;
-        s_thr = div_u96((u128)u + (u128)(uint64_t)j_lo * (u128)Q, nt, &r0);
+        s_thr = thr_of(j_lo, &r0);
         s_rem = r0;
-        s_qN = Q / nt;
-        s_qR = (uint32_t)(Q % nt);
     }
     __syncthreads();
     const int64_t L = j_hi - j_lo;
@@ -123,8 +161,8 @@ __device__ __forceinline__ void ticket_parents(const uint64_t *C, int n, uint64_
     const int64_t d0 = (int64_t)threadIdx.x * K;
     if (L <= 0 || d0 >= D)
         return;
-    const uint64_t thr0 = s_thr, qN = s_qN;
-    const uint32_t rem0 = s_rem, qR = s_qR;
+    const uint64_t thr0 = s_thr;
+    const uint32_t rem0 = s_rem;
     const float rnt = 1.0f / (float)nt;
     // thr_{j_lo + b} - c0 and rem_{j_lo + b}
     auto lt_at = [&](int64_t b, uint32_t *rem) -> uint64_t {
@@ -132,7 +170,7 @@ __device__ __forceinline__ void ticket_parents(const uint64_t *C, int n, uint64_
         if (b < (1 << 21))  // quotient < 2^21: the float estimate is off by at most 1
             t = thr0 + (uint64_t)b * qN + div_small((uint64_t)rem0 + (uint64_t)b * qR, nt, rnt, rem);
         else
-            t = div_u96((u128)u + (u128)(uint64_t)(j_lo + b) * (u128)Q, nt, rem);
+            t = thr_of(j_lo + b, rem);
         return t - c0;
     };
     // particles among the first d0 merged elements: the first a in
@@ -180,13 +218,12 @@ constexpr size_t FILL_SMEM_BYTES = sizeof(uint64_t) * TILE_SMEM_U64 + sizeof(uin
 // shared memory and handed to store(j, i) in ticket order, thread k taking
 // tickets k, k + blockDim, ... of the chunk (coalesced global writes).
 template <typename Store>
-__device__ __forceinline__ void ticket_parents_staged(const uint64_t *C, int n, uint64_t c0, uint64_t u, uint64_t Q,
-                                                      uint32_t nt, int64_t j_lo, int64_t j_hi, uint16_t *stage,
-                                                      Store store)
+__device__ __forceinline__ void ticket_parents_staged(const uint64_t *C, int n, uint64_t c0, const TicketGrid &tg,
+                                                      int64_t j_lo, int64_t j_hi, uint16_t *stage, Store store)
 {
     for (int64_t c = j_lo; c < j_hi; c += STAGE_TICKETS) {
         const int64_t ce = (j_hi - c < STAGE_TICKETS) ? j_hi : c + STAGE_TICKETS;
-        ticket_parents(C, n, c0, u, Q, nt, c, ce, [&](int64_t j, int i) { stage[j - c] = (uint16_t)i; });
+        ticket_parents(C, n, c0, tg, c, ce, [&](int64_t j, int i) { stage[j - c] = (uint16_t)i; });
         __syncthreads();
         const int m = (int)(ce - c);
         for (int k = threadIdx.x; k < m; k += blockDim.x)
