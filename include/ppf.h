@@ -74,7 +74,9 @@ typedef struct {
     int32_t frame;            /* frame index of the last ppf_step                */
     int32_t status_flags;     /* bit 0 degenerate weights, 1 wait timeout,
                                  2 inconsistent routing (copy skipped),
-                                 3 caller ancestor out of range (identity used) */
+                                 3 caller ancestor out of range (identity used),
+                                 4 resampling skipped by the N_eff test
+                                   (ppf_resample_if)                            */
     int64_t links;            /* routing links of the last resample (Sec. 4-5)   */
     int64_t moved;            /* particles moved between groups by that resample */
     int64_t max_group;        /* largest / smallest group after it               */
@@ -127,6 +129,17 @@ ppf_status ppf_step_host(ppf_ctx *ctx, const void *frame_host, int32_t k);
  * All-zero or NaN weights are reported as PPF_EDEGENERATE by the next
  * ppf_estimate; the particles are then kept as they are. */
 ppf_status ppf_resample(ppf_ctx *ctx, ppf_scheme scheme, float exchange_ratio);
+
+/* The resampling step of Alg. 1 under its effective-sample-size test: the
+ * particles are resampled (as by ppf_resample) only when the N_eff of the
+ * last step is below ess_threshold.  Otherwise they are kept -- identity
+ * ancestry, group layout unchanged -- and the next step carries their
+ * weights, as in sequential importance sampling.  The test runs on the
+ * device (no host round trip); ppf_estimate reports a kept step in bit 4 of
+ * status_flags and with links = moved = 0.  ess_threshold = +inf resamples
+ * every time (ppf_resample), 0 never.
+ * Errors: as ppf_resample; PPF_EINVAL for a NaN threshold. */
+ppf_status ppf_resample_if(ppf_ctx *ctx, ppf_scheme scheme, float exchange_ratio, double ess_threshold);
 
 /* Copies the results of the last step and of the last resample to the host
  * (synchronises the stream).  Returns PPF_EDEGENERATE / PPF_ETIMEOUT when the
@@ -191,7 +204,9 @@ ppf_status ppf_loglik_grad(ppf_ctx *ctx, const void *frames_dev, int32_t K, cons
  * All filters share the frame size, patch radius and frame dtype; every other
  * model field is per filter.  Filter f draws its random numbers with its
  * model's seed and filter_id, so its results equal those of a single-filter
- * context created with the same model and n_f (systematic resampling).
+ * context created with the same model and n_f (systematic resampling).  A
+ * filter whose resample keeps its particles (no usable weight, or the N_eff
+ * test of ppf_batch_set_ess_threshold) continues them with their weights.
  * ------------------------------------------------------------------------ */
 typedef struct ppf_batch ppf_batch;
 
@@ -238,6 +253,15 @@ ppf_status ppf_batch_get_particles(ppf_batch *b, float *state_dev, int32_t *anc_
  * threads, {2, 4, 8} blocks per SM -- and keeps the fastest.  The filters'
  * state is not advanced.  config_out (optional, 3 ints) receives the choice. */
 ppf_status ppf_batch_autotune(ppf_batch *b, const void *frames_dev, int32_t k, int32_t *config_out);
+
+/* Alg. 1's effective-sample-size test for every filter of the batch: from
+ * the next resample on, filter f is resampled only while its N_eff is below
+ * fraction x n_f; otherwise it keeps its particles and its next step carries
+ * their weights (as ppf_resample_if does for one filter).  fraction = +inf
+ * (the default) resamples every frame, 0 never.  Synchronises the batch's
+ * stream; a cached graph of ppf_batch_run stays valid.
+ * Errors: PPF_EINVAL (NaN or negative fraction), PPF_ECUDA. */
+ppf_status ppf_batch_set_ess_threshold(ppf_batch *b, double fraction);
 
 const char *ppf_batch_last_error(const ppf_batch *b);
 

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes as C
 import dataclasses
+import math
 import os
 import subprocess
 import threading
@@ -113,7 +114,7 @@ def lib():
                 "orc_balanced_offsets": (None, [C.c_int64, C.c_int32, i64p]),
                 "orc_resample": (C.c_int, [mp, C.c_int, C.c_double, C.c_int64, C.c_int32, C.c_int32,
                                            i64p, fp, dp, i32p, dp, i64p, i64p]),
-                "orc_run": (C.c_int, [mp, C.c_int64, C.c_int32, C.c_int, C.c_double, C.c_int32,
+                "orc_run": (C.c_int, [mp, C.c_int64, C.c_int32, C.c_int, C.c_double, C.c_double, C.c_int32,
                                       dp, dp, dp]),
                 "orc_loglik_partials": (None, [mp, dp, C.c_double, C.c_double, C.c_double, C.c_int32,
                                                C.c_int32, dp]),
@@ -299,14 +300,15 @@ def resample(m: Model, scheme: int, N: int, frame: int, goff: np.ndarray, lw: np
 
 
 def run(m: Model, N: int, frames: np.ndarray, group_size: int = 4096, scheme: int = SYSTEMATIC,
-        alpha: float = 0.1):
-    """Whole SIR run (Alg. 1); returns (rc, est[K, 8], last weighted state (6, N))."""
+        alpha: float = 0.1, ess_threshold: float = math.inf):
+    """Whole SIR run (Alg. 1), resampling when N_eff < ess_threshold (every
+    frame by default); returns (rc, est[K, 8], last weighted state (6, N))."""
     fr = np.ascontiguousarray(frames, dtype=np.float64)
     K = fr.shape[0]
     est = np.zeros((K, 8))
     st = np.zeros(6 * N)
-    rc = lib().orc_run(C.byref(m.c()), N, group_size, scheme, alpha, K, _p(fr.reshape(-1), C.c_double),
-                       _p(est.reshape(-1), C.c_double), _p(st, C.c_double))
+    rc = lib().orc_run(C.byref(m.c()), N, group_size, scheme, alpha, ess_threshold, K,
+                       _p(fr.reshape(-1), C.c_double), _p(est.reshape(-1), C.c_double), _p(st, C.c_double))
     return rc, est, st.reshape(6, N)
 
 

@@ -677,11 +677,12 @@ int orc_resample(const orc_model *m, int scheme, double alpha, int64_t N, int32_
 
 /* ------------------------------------------------------------------------ */
 /* A whole SIR run (Alg. 1): init, then for each frame propagate, weight,    */
-/* summarise, resample.  frames: K x H x W doubles.  est: K x 8 (mean[5],    */
+/* summarise, resample (when N_eff < ess_threshold; +inf: every frame).     */
+/* frames: K x H x W doubles.  est: K x 8 (mean[5],                          */
 /* log-evidence, ess, max lw).  st (6N) holds the last weighted particles.   */
 /* ------------------------------------------------------------------------ */
 int orc_run(const orc_model *m, int64_t N, int32_t group_size, int scheme, double alpha,
-            int32_t K, const double *frames, double *est, double *st_out)
+            double ess_threshold, int32_t K, const double *frames, double *est, double *st_out)
 {
     int32_t G = (int32_t)((N + group_size - 1) / group_size);
     double *cur = (double *)malloc(sizeof(double) * (size_t)(6 * N));
@@ -703,13 +704,22 @@ int orc_run(const orc_model *m, int64_t N, int32_t group_size, int scheme, doubl
         orc_propagate(m, N, k + 1, cur, anc, lw_prev, nxt);
         orc_weight(m, N, frames + (int64_t)k * npix, nxt);
         orc_summary(N, nxt, lw_prev, est + 8 * (int64_t)k);
-        for (int64_t i = 0; i < N; ++i)
-            lwf[i] = (float)nxt[5 * N + i];
-        int64_t stats[4];
-        rc = orc_resample(m, scheme, alpha, N, k + 1, G, goff, lwf, nxt + 5 * N, anc, lw_prev, goff2, stats);
-        if (rc != ORC_OK)
-            break;
-        memcpy(goff, goff2, sizeof(int64_t) * (size_t)(G + 1));
+        /* Alg. 1: resample only while the effective sample size is below
+         * the threshold; otherwise keep the particles and carry the weights */
+        if (!(est[8 * (int64_t)k + 6] < ess_threshold)) {
+            for (int64_t i = 0; i < N; ++i) {
+                anc[i] = (int32_t)i;
+                lw_prev[i] = nxt[5 * N + i];
+            }
+        } else {
+            for (int64_t i = 0; i < N; ++i)
+                lwf[i] = (float)nxt[5 * N + i];
+            int64_t stats[4];
+            rc = orc_resample(m, scheme, alpha, N, k + 1, G, goff, lwf, nxt + 5 * N, anc, lw_prev, goff2, stats);
+            if (rc != ORC_OK)
+                break;
+            memcpy(goff, goff2, sizeof(int64_t) * (size_t)(G + 1));
+        }
         double *t = cur; cur = nxt; nxt = t;
     }
     if (st_out)

@@ -49,7 +49,7 @@ int orc_resample(const orc_model *m, int scheme, double alpha, int64_t N, int32_
                  int32_t G, const int64_t *goff_in, const float *lw, const double *lw_sum,
                  int32_t *anc, double *lw_reset, int64_t *goff_out, int64_t stats[4]);
 int orc_run(const orc_model *m, int64_t N, int32_t group_size, int scheme, double alpha,
-            int32_t K, const double *frames, double *est, double *st_out);
+            double ess_threshold, int32_t K, const double *frames, double *est, double *st_out);
 void orc_loglik_partials(const orc_model *m, const double *frame, double x, double y, double I0, int32_t ax,
                          int32_t ay, double out[6]);
 int orc_grad_run(const orc_model *m0, int64_t N, int32_t K, const double *frames, const double theta[4],

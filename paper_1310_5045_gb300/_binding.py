@@ -19,12 +19,13 @@ F32, BF16, F16 = 0, 1, 2
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEGENERATE, ESTATE = range(7)
 SCHEMES = {"systematic": SYSTEMATIC, "rpa_gs": RPA_GS, "rpa_sgs": RPA_SGS, "rpa_lgs": RPA_LGS, "rna": RNA}
 
-EXPORTS = ["ppf_create", "ppf_destroy", "ppf_step", "ppf_step_host", "ppf_resample", "ppf_estimate",
+EXPORTS = ["ppf_create", "ppf_destroy", "ppf_step", "ppf_step_host", "ppf_resample", "ppf_resample_if",
+           "ppf_estimate",
            "ppf_get_particles", "ppf_set_particles", "ppf_get_groups", "ppf_status_string",
            "ppf_last_error", "ppf_profile_enable", "ppf_profile_read", "ppf_systematic_resample_noalloc",
            "ppf_loglik_grad", "ppf_batch_create", "ppf_batch_destroy", "ppf_batch_step", "ppf_batch_resample",
            "ppf_batch_run", "ppf_batch_estimates", "ppf_batch_get_particles", "ppf_batch_autotune",
-           "ppf_batch_last_error"]
+           "ppf_batch_set_ess_threshold", "ppf_batch_last_error"]
 
 
 class PPFError(RuntimeError):
@@ -133,6 +134,7 @@ def load(build_if_missing: bool = True):
             "ppf_step": (C.c_int, [ctxp, vp, C.c_int32]),
             "ppf_step_host": (C.c_int, [ctxp, vp, C.c_int32]),
             "ppf_resample": (C.c_int, [ctxp, C.c_int, C.c_float]),
+            "ppf_resample_if": (C.c_int, [ctxp, C.c_int, C.c_float, C.c_double]),
             "ppf_estimate": (C.c_int, [ctxp, P(_Estimate)]),
             "ppf_get_particles": (C.c_int, [ctxp, vp, vp, vp]),
             "ppf_set_particles": (C.c_int, [ctxp, vp, vp, vp]),
@@ -153,6 +155,7 @@ def load(build_if_missing: bool = True):
             "ppf_batch_estimates": (C.c_int, [vp, vp]),
             "ppf_batch_get_particles": (C.c_int, [vp, vp, vp]),
             "ppf_batch_autotune": (C.c_int, [vp, vp, C.c_int32, P(C.c_int32)]),
+            "ppf_batch_set_ess_threshold": (C.c_int, [vp, C.c_double]),
             "ppf_batch_last_error": (C.c_char_p, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -249,10 +252,16 @@ class ParticleFilter:
         self._check(self.L.ppf_step_host(self._ctx, C.c_void_p(ptr), k), "ppf_step_host")
         self.frame = k
 
-    def resample(self, scheme=SYSTEMATIC, exchange_ratio: float = 0.1):
+    def resample(self, scheme=SYSTEMATIC, exchange_ratio: float = 0.1, ess_threshold: float | None = None):
+        """Resampling step of Alg. 1; with ess_threshold, only when the last
+        step's N_eff is below it (decided on the device)."""
         if isinstance(scheme, str):
             scheme = SCHEMES[scheme]
-        self._check(self.L.ppf_resample(self._ctx, int(scheme), float(exchange_ratio)), "ppf_resample")
+        if ess_threshold is None:
+            self._check(self.L.ppf_resample(self._ctx, int(scheme), float(exchange_ratio)), "ppf_resample")
+        else:
+            self._check(self.L.ppf_resample_if(self._ctx, int(scheme), float(exchange_ratio),
+                                               float(ess_threshold)), "ppf_resample_if")
 
     def estimate(self, raise_on_flags: bool = False) -> Estimate:
         e = _Estimate()
@@ -393,6 +402,11 @@ class BatchFilter:
 
     def resample(self, k):
         self._check(self.L.ppf_batch_resample(self._b, int(k)), "ppf_batch_resample")
+
+    def set_ess_threshold(self, fraction: float):
+        """Alg. 1's N_eff test per filter: resample filter f only while its
+        N_eff < fraction * n_f (inf: every frame, the default)."""
+        self._check(self.L.ppf_batch_set_ess_threshold(self._b, float(fraction)), "ppf_batch_set_ess_threshold")
 
     def run(self, frames, k0=1, use_graph=True, estimates=True):
         """K frames (K, F, H, W) of step + resample; returns (K, F) estimates."""

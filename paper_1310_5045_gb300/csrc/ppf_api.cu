@@ -256,7 +256,14 @@ ppf_status ppf_step_host(ppf_ctx *c, const void *frame_host, int32_t k)
 
 ppf_status ppf_resample(ppf_ctx *c, ppf_scheme scheme, float alpha)
 {
+    return ppf_resample_if(c, scheme, alpha, INFINITY);
+}
+
+ppf_status ppf_resample_if(ppf_ctx *c, ppf_scheme scheme, float alpha, double ess_threshold)
+{
     if (!c)
+        return PPF_EINVAL;
+    if (ess_threshold != ess_threshold)  // NaN
         return PPF_EINVAL;
     if (scheme < PPF_SYSTEMATIC || scheme > PPF_RNA)
         return PPF_EINVAL;
@@ -269,10 +276,10 @@ ppf_status ppf_resample(ppf_ctx *c, ppf_scheme scheme, float alpha)
     if (!c->weighted)
         return PPF_ESTATE;
     if (scheme == PPF_RNA) {
-        CK(ppf::launch_resample_rna(c, alpha));
+        CK(ppf::launch_resample_rna(c, alpha, ess_threshold));
         c->mode = MODE_EXPLICIT;
     } else {
-        CK(ppf::launch_resample_global(c, (int)scheme));
+        CK(ppf::launch_resample_global(c, (int)scheme, ess_threshold));
         if (scheme != PPF_SYSTEMATIC) {
             int64_t *t = c->goff;
             c->goff = c->goff_new;
@@ -317,9 +324,12 @@ ppf_status ppf_estimate(ppf_ctx *c, ppf_estimate_t *out)
                                                   : "inconsistent routing schedule (copy skipped)");
             return PPF_EINVAL;
         }
-        return (s.flags & FLAG_DEGENERATE) ? PPF_EDEGENERATE : PPF_ETIMEOUT;
+        if (s.flags & FLAG_DEGENERATE)
+            return PPF_EDEGENERATE;
+        if (s.flags & FLAG_TIMEOUT)
+            return PPF_ETIMEOUT;
     }
-    return PPF_OK;
+    return PPF_OK;  // FLAG_KEPT (N_eff test) is information, not an error
 }
 
 ppf_status ppf_get_particles(ppf_ctx *c, float *state_dev, int32_t *anc_dev, float *lwp_dev)
@@ -479,7 +489,7 @@ ppf_status ppf_loglik_grad(ppf_ctx *c, const void *frames_dev, int32_t K, const 
             c->last_frame = k;
             c->n_steps += 1;
             if (k < K) {
-                CK(ppf::launch_resample_global(c, PPF_SYSTEMATIC));
+                CK(ppf::launch_resample_global(c, PPF_SYSTEMATIC, INFINITY));
                 c->n_resamples += 1;
             }
         }

@@ -31,6 +31,7 @@ struct FilterParams {
     int64_t off, n;
     uint64_t seed;
     Divisor ndiv;             // n as a divisor of the ticket grid
+    double ess_thr;           // Alg. 1's test: resample only while N_eff < ess_thr (+inf: always)
     uint32_t fid;
     float inv2s2, inv_sxi2, sm, sv, sI, bg;
     float Kc[MAX_RADIUS];
@@ -72,6 +73,8 @@ struct ppf_batch {
     std::vector<ppf_model> models;
     std::vector<int64_t> n, off;
     ppf::FilterParams *fp;             // device [F]
+    std::vector<ppf::FilterParams> hp; // host copy of fp
+    int32_t *fkeep;                    // device [F]: the last resample kept the filter's particles
     float *state[2];
     int cur;
     int32_t *anc;
@@ -200,6 +203,7 @@ struct BatchStepArgs {
     int32_t U;
     float *st0, *st1;           // the two state buffers; the cursor says which is current
     const int32_t *__restrict__ anc;
+    const int32_t *__restrict__ fkeep;
     const float *__restrict__ Zp;
     Partial *__restrict__ part;
 };
@@ -222,19 +226,22 @@ __global__ void batch_step_kernel(BatchStepArgs a)
             P = a.fp[f];
         __syncthreads();
         const PatchGeom geom{a.Zp + (int64_t)f * a.Wp * a.Hp, a.W, a.H, a.Wp, a.pad, P.inv2s2, P.inv_sxi2, P.Kc};
+        // after the prior draw, or when the last resample kept this filter's
+        // particles, every slot continues its own particle with its weight
+        const bool carry = first || a.fkeep[f] != 0;
         Acc acc;
         acc.init();
         const int64_t lo = a.unit_lo[u];
         const int32_t n = a.unit_n[u];
         for (int32_t j = threadIdx.x; j < n; j += blockDim.x) {
             const int64_t i = lo + j;
-            int64_t p = first ? i : (int64_t)__ldg(a.anc + i);
+            int64_t p = carry ? i : (int64_t)__ldg(a.anc + i);
             if (p < P.off || p >= P.off + P.n)
                 p = i;  // ancestors never cross filters
             const float x = src[p], y = src[N + p];
             const float vx = src[2 * N + p], vy = src[3 * N + p];
             const float I0 = src[4 * N + p];
-            const float lwp = first ? src[5 * N + p] : 0.0f;
+            const float lwp = carry ? src[5 * N + p] : 0.0f;
             uint32_t fl[6];
             prop_fields(draw(P.seed, (uint32_t)(i - P.off), frame, P.fid, PURPOSE_PROP, 0), fl);
             float e0, e1, e2, e3, e4, e5;
@@ -349,6 +356,8 @@ __global__ void __launch_bounds__(TILE_THREADS) batch_tile_totals(const float *s
     __shared__ uint64_t red[33];
     const float *__restrict__ lw = (cur->cur ? st0 : st1) + 5 * Ntot;
     const int32_t t = blockIdx.x, f = tile_f[t];
+    if (fs[f].ess >= fp[f].ess_thr)
+        return;  // N_eff test: this filter keeps its particles
     const float Mf = fs[f].M;
     const int s = scale_bits(fp[f].n);
     uint64_t acc = 0;
@@ -360,10 +369,10 @@ __global__ void __launch_bounds__(TILE_THREADS) batch_tile_totals(const float *s
         tQ[t] = total;
 }
 
-__global__ void batch_tile_scan(const FilterParams *__restrict__ fp, const BatchCursor *__restrict__ cur,
-                                const int32_t *__restrict__ ft_off, int32_t F, const uint64_t *__restrict__ tQ,
-                                uint64_t *__restrict__ tC, int64_t *__restrict__ tT, uint64_t *__restrict__ fQu,
-                                int32_t *__restrict__ flags)
+__global__ void batch_tile_scan(const FilterParams *__restrict__ fp, const FilterSummary *__restrict__ fs,
+                                const BatchCursor *__restrict__ cur, const int32_t *__restrict__ ft_off, int32_t F,
+                                const uint64_t *__restrict__ tQ, uint64_t *__restrict__ tC, int64_t *__restrict__ tT,
+                                uint64_t *__restrict__ fQu, int32_t *__restrict__ fkeep, int32_t *__restrict__ flags)
 {
     const int32_t f = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -371,6 +380,13 @@ __global__ void batch_tile_scan(const FilterParams *__restrict__ fp, const Batch
         return;
     const int32_t t0 = ft_off[f], t1 = ft_off[f + 1];
     const FilterParams P = fp[f];
+    if (fs[f].ess >= P.ess_thr) {  // N_eff test: keep the particles, carry the weights
+        if (lane == 0) {
+            fQu[4 * f] = 0ull;
+            fkeep[f] = 1;
+        }
+        return;
+    }
     uint64_t carry = 0;
     for (int32_t base = t0; base < t1; base += 32) {
         const int32_t t = base + lane;
@@ -387,6 +403,7 @@ __global__ void batch_tile_scan(const FilterParams *__restrict__ fp, const Batch
         fQu[4 * f + 1] = u;
         fQu[4 * f + 2] = Q / (uint64_t)P.n;
         fQu[4 * f + 3] = Q % (uint64_t)P.n;
+        fkeep[f] = (Q == 0ull) ? 1 : 0;  // no usable weight: kept as well
         if (Q == 0ull)
             atomicOr(flags, FLAG_DEGENERATE);
     }
@@ -416,7 +433,7 @@ __global__ void __launch_bounds__(TILE_THREADS) batch_fill(const float *st0, con
     const int64_t lo = tile_lo[t];
     const int n = tile_n[t];
     const uint64_t Q = fQu[4 * f], u = fQu[4 * f + 1];
-    if (Q == 0ull) {  // no usable weight in the filter: it keeps its particles
+    if (Q == 0ull) {  // kept by the N_eff test, or no usable weight: identity ancestry
         for (int i = threadIdx.x; i < n; i += blockDim.x)
             anc[lo + i] = (int32_t)(lo + i);
         return;
@@ -527,6 +544,7 @@ cudaError_t launch_batch_step(ppf_batch *b, bool commit)
     a.st0 = b->state[0];
     a.st1 = b->state[1];
     a.anc = b->anc;
+    a.fkeep = b->fkeep;
     a.Zp = b->Zp;
     a.part = b->upart;
     int grid = b->num_sms * b->bps;
@@ -585,8 +603,9 @@ cudaError_t launch_batch_resample(ppf_batch *b)
 {
     batch_tile_totals<<<b->T, TILE_THREADS, 0, b->stream>>>(b->state[0], b->state[1], b->Ntot, b->fp, b->fsum,
                                                             b->cursor, b->tile_f, b->tile_lo, b->tile_n, b->tQ);
-    batch_tile_scan<<<(b->F * 32 + 255) / 256, 256, 0, b->stream>>>(b->fp, b->cursor, b->ft_off, b->F, b->tQ, b->tC,
-                                                                      b->tT, b->fQu, b->flags);
+    batch_tile_scan<<<(b->F * 32 + 255) / 256, 256, 0, b->stream>>>(b->fp, b->fsum, b->cursor, b->ft_off, b->F,
+                                                                      b->tQ, b->tC, b->tT, b->fQu, b->fkeep,
+                                                                      b->flags);
     batch_fill<<<b->T, TILE_THREADS, FILL_SMEM_BYTES, b->stream>>>(b->state[0], b->state[1], b->Ntot, b->fp, b->fsum, b->cursor,
                                                      b->tile_f, b->tile_lo, b->tile_n, b->ft_off, b->tC, b->tT, b->fQu,
                                                      b->anc);
@@ -623,7 +642,8 @@ void free_batch(ppf_batch *b)
     if (b->gstream)
         cudaStreamDestroy(b->gstream);
     void *p[] = {b->fp, b->state[0], b->state[1], b->anc, b->Zp, b->unit_f, b->unit_lo, b->unit_n, b->fu_off,
-                 b->upart, b->fsum, b->flags, b->fsum_run, b->cursor, b->tile_f, b->tile_lo, b->tile_n, b->ft_off,
+                 b->upart, b->fsum, b->flags, b->fkeep, b->fsum_run, b->cursor, b->tile_f, b->tile_lo, b->tile_n,
+                 b->ft_off,
                  b->tQ, b->tC, b->tT, b->fQu};
     for (void *q : p)
         if (q)
@@ -711,6 +731,7 @@ ppf_status ppf_batch_create(const ppf_model *models, const int64_t *n, int32_t F
         P.off = b->off[f];
         P.n = n[f];
         P.ndiv = make_divisor((uint32_t)n[f]);
+        P.ess_thr = INFINITY;
         P.seed = m.seed;
         P.fid = m.filter_id;
         P.inv2s2 = 1.0f / (2.0f * m.psf_sigma * m.psf_sigma);
@@ -729,19 +750,22 @@ ppf_status ppf_batch_create(const ppf_model *models, const int64_t *n, int32_t F
         dmalloc(&b->state[1], 6 * Ntot) != cudaSuccess || dmalloc(&b->anc, Ntot) != cudaSuccess ||
         dmalloc(&b->Zp, (size_t)F * b->Wp * b->Hp) != cudaSuccess || dmalloc(&b->fu_off, F + 1) != cudaSuccess ||
         dmalloc(&b->fsum, F) != cudaSuccess || dmalloc(&b->flags, 1) != cudaSuccess ||
+        dmalloc(&b->fkeep, F) != cudaSuccess ||
         dmalloc(&b->cursor, 1) != cudaSuccess ||
         cudaMallocHost((void **)&b->fsum_host, sizeof(FilterSummary) * F) != cudaSuccess ||
         dmalloc(&dv0A, 2 * (size_t)F) != cudaSuccess)
         return (dv0A ? cudaFree(dv0A) : cudaSuccess), fail(PPF_ENOMEM);
     if (cudaMemcpy(b->fp, hp.data(), sizeof(FilterParams) * F, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(dv0A, v0A.data(), sizeof(float) * 2 * F, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(b->flags, 0, sizeof(int32_t)) != cudaSuccess || build_units(b, 1024) != cudaSuccess ||
+        cudaMemset(b->flags, 0, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(b->fkeep, 0, sizeof(int32_t) * F) != cudaSuccess || build_units(b, 1024) != cudaSuccess ||
         build_tiles(b) != cudaSuccess ||
         cudaFuncSetAttribute(batch_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILL_SMEM_BYTES) !=
             cudaSuccess) {
         cudaFree(dv0A);
         return fail(PPF_ECUDA);
     }
+    b->hp = hp;
     batch_init_kernel<<<4 * b->num_sms, 256, 0, b->stream>>>(b->state[0], Ntot, b->fp, b->unit_f, b->unit_lo,
                                                                b->unit_n, b->U, (float)b->W, (float)b->H, dv0A);
     cudaError_t e = cudaGetLastError();
@@ -955,6 +979,17 @@ ppf_status ppf_batch_autotune(ppf_batch *b, const void *frames_dev, int32_t k, i
         config_out[1] = bb;
         config_out[2] = bs;
     }
+    return PPF_OK;
+}
+
+ppf_status ppf_batch_set_ess_threshold(ppf_batch *b, double fraction)
+{
+    if (!b || fraction != fraction || fraction < 0.0)
+        return PPF_EINVAL;
+    for (int32_t f = 0; f < b->F; ++f)
+        b->hp[f].ess_thr = (fraction == INFINITY) ? INFINITY : fraction * (double)b->n[f];
+    BCK(cudaStreamSynchronize(b->stream));  // no kernel of the batch reads the parameters meanwhile
+    BCK(cudaMemcpy(b->fp, b->hp.data(), sizeof(FilterParams) * b->F, cudaMemcpyHostToDevice));
     return PPF_OK;
 }
 

@@ -23,7 +23,7 @@ enum StepMode : int {
     MODE_EXPLICIT = 2   // resampled: per-slot lw_prev buffer (RNA, restarts)
 };
 
-enum : int { FLAG_DEGENERATE = 1, FLAG_TIMEOUT = 2, FLAG_INTERNAL = 4, FLAG_BAD_ANCESTOR = 8 };
+enum : int { FLAG_DEGENERATE = 1, FLAG_TIMEOUT = 2, FLAG_INTERNAL = 4, FLAG_BAD_ANCESTOR = 8, FLAG_KEPT = 16 };
 
 // per-block weight statistics of one step (online log-sum-exp partials)
 struct Partial {
@@ -46,7 +46,7 @@ struct DevSummary {
     float M;                   // max lw (exact float): the quantiser reference
     int32_t frame;
     int32_t flags;             // sticky FLAG_* bits, cleared by ppf_estimate
-    int32_t degenerate;        // last resample found no usable weight
+    int32_t degenerate;        // last resample kept every particle (no usable weight, or N_eff test)
     int64_t links, moved, max_group, min_group;
     uint64_t Q, u;             // last global resample: total fixed-point weight, offset
     uint64_t qN;               // and Q = qN N + qR (the ticket spacing in whole and remainder)
@@ -126,8 +126,8 @@ cudaError_t launch_prepare_frame(ppf_ctx *c, const void *frame);
 cudaError_t launch_step(ppf_ctx *c, int32_t k);
 cudaError_t launch_grad_step(ppf_ctx *c, int32_t k, bool first, int32_t *anchors);
 cudaError_t resample_kernel_attributes();
-cudaError_t launch_resample_global(ppf_ctx *c, int scheme);
-cudaError_t launch_resample_rna(ppf_ctx *c, float alpha);
+cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr);
+cudaError_t launch_resample_rna(ppf_ctx *c, float alpha, double ess_thr);
 cudaError_t launch_identity(ppf_ctx *c, int32_t *dst);
 cudaError_t launch_pending(ppf_ctx *c, int32_t *anc_out, float *lwp_out);
 cudaError_t launch_fill_f32(ppf_ctx *c, float *dst, float v);

@@ -12,6 +12,9 @@
 //               its own offset (non-proportional allocation); its offspring
 //               carry the group weight, and the last floor(alpha min n_g) slots
 //               of every group migrate to the next group of the ring.
+// Every resampling kernel takes the N_eff threshold of Alg. 1: when the
+// step's effective sample size is not below it, the kernels do nothing but
+// mark the particles as kept (the next step carries their weights).
 #include <cmath>
 
 #include "ppf_device.cuh"
@@ -20,13 +23,22 @@
 
 namespace ppf {
 
+// Alg. 1 resamples only while N_eff < N_threshold (NaN N_eff: resample, which
+// then reports the degenerate weights).
+__device__ __forceinline__ bool kept_by_ess(const DevSummary *sum, double ess_thr)
+{
+    return sum->ess >= ess_thr;
+}
+
 // ---------------------------------------------------------------- R1 tiles
 // Tile totals Q_t (coalesced loads and a block sum); for RPA also the local
 // prefix at every group start that falls inside the tile (needs the scan).
 __global__ void __launch_bounds__(TILE_THREADS) tile_totals_kernel(
-    const float *__restrict__ lw, int64_t N, const DevSummary *__restrict__ sum, uint64_t *__restrict__ Qt,
-    const int64_t *__restrict__ goff, int32_t G, uint64_t *__restrict__ Cbl)
+    const float *__restrict__ lw, int64_t N, const DevSummary *__restrict__ sum, double ess_thr,
+    uint64_t *__restrict__ Qt, const int64_t *__restrict__ goff, int32_t G, uint64_t *__restrict__ Cbl)
 {
+    if (kept_by_ess(sum, ess_thr))
+        return;
     __shared__ uint64_t buf[TILE_SMEM_U64];
     __shared__ uint64_t red[33];
     __shared__ int32_t gfirst;
@@ -85,12 +97,22 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_totals_kernel(
 // each round closed by a block scan.
 __global__ void __launch_bounds__(1024) tile_scan_kernel(
     int64_t N, int32_t T, const uint64_t *__restrict__ Qt, uint64_t *__restrict__ Ct, int64_t *__restrict__ Tt,
-    int32_t *__restrict__ item_off, int32_t *__restrict__ item_tile, DevSummary *sum, uint64_t seed, uint32_t fid,
-    uint32_t frame, const int64_t *__restrict__ goff, int32_t G, int rpa, const uint64_t *__restrict__ Cbl,
-    int64_t *__restrict__ Tg)
+    int32_t *__restrict__ item_off, int32_t *__restrict__ item_tile, DevSummary *sum, double ess_thr, uint64_t seed,
+    uint32_t fid, uint32_t frame, const int64_t *__restrict__ goff, int32_t G, int rpa,
+    const uint64_t *__restrict__ Cbl, int64_t *__restrict__ Tg)
 {
     __shared__ uint64_t red[33];
     __shared__ uint64_t su;
+    if (kept_by_ess(sum, ess_thr)) {  // N_eff test: keep the particles and the layout
+        if (threadIdx.x == 0) {
+            sum->degenerate = 1;
+            sum->flags |= FLAG_KEPT;
+            sum->n_items = 0;
+            sum->links = 0;
+            sum->moved = 0;
+        }
+        return;
+    }
     uint64_t total = 0;
     for (int base = 0; base < T; base += blockDim.x) {
         const int t = base + threadIdx.x;
@@ -628,8 +650,10 @@ __global__ void __launch_bounds__(256) route_copy_kernel(const int32_t *__restri
 // slots of the group go to the tail of the next group of the ring.
 __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
     const float *__restrict__ lw, int64_t N, int32_t G, const int64_t *__restrict__ goff, DevSummary *sum,
-    uint64_t seed, uint32_t fid, uint32_t frame, int32_t *__restrict__ anc, float *__restrict__ lwp)
+    double ess_thr, uint64_t seed, uint32_t fid, uint32_t frame, int32_t *__restrict__ anc, float *__restrict__ lwp)
 {
+    if (kept_by_ess(sum, ess_thr))
+        return;
     const int64_t mig = sum->mig;
     extern __shared__ uint64_t fill_smem[];  // FILL_SMEM_BYTES
     uint64_t *C = fill_smem;
@@ -727,7 +751,7 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
 }
 
 __global__ void __launch_bounds__(1024) rna_prep_kernel(const int64_t *__restrict__ goff, int32_t G, float alpha,
-                                                        DevSummary *sum)
+                                                        DevSummary *sum, double ess_thr)
 {
     __shared__ long long smx[32], smn[32];
     long long mx = 0, mn = INT64_MAX;
@@ -753,13 +777,16 @@ __global__ void __launch_bounds__(1024) rna_prep_kernel(const int64_t *__restric
             a = smx[w] > a ? smx[w] : a;
             b = smn[w] < b ? smn[w] : b;
         }
-        const int64_t mig = (int64_t)floor((double)alpha * (double)b);
+        const bool kept = kept_by_ess(sum, ess_thr);  // N_eff test: no resampling, no exchange
+        const int64_t mig = kept ? 0 : (int64_t)floor((double)alpha * (double)b);
         sum->mig = mig;
         sum->max_group = a;
         sum->min_group = b;
         sum->links = (G > 1 && mig > 0) ? G : 0;
         sum->moved = (G > 1) ? mig * G : 0;
-        sum->degenerate = 0;
+        sum->degenerate = kept ? 1 : 0;
+        if (kept)
+            sum->flags |= FLAG_KEPT;
     }
 }
 
@@ -804,17 +831,17 @@ cudaError_t resample_kernel_attributes()
     return e;
 }
 
-cudaError_t launch_resample_global(ppf_ctx *c, int scheme)
+cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
 {
     const bool rpa = (scheme != PPF_SYSTEMATIC);
     const float *lw = c->state[c->cur] + 5 * c->N;
     const int T = c->T;
     prof_mark(c, PH_RESAMPLE, 0);
     c->launches += rpa ? 5 : 3;
-    tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, c->sc.Qt, rpa ? c->goff : nullptr,
-                                                          c->G, c->sc.Cbl);
+    tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt,
+                                                          rpa ? c->goff : nullptr, c->G, c->sc.Cbl);
     tile_scan_kernel<<<1, 1024, 0, c->stream>>>(c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off,
-                                                c->sc.item_tile, c->sum,
+                                                c->sc.item_tile, c->sum, ess_thr,
                                                 c->m.seed, c->m.filter_id, (uint32_t)c->last_frame,
                                                 c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg);
     const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
@@ -850,12 +877,12 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme)
     return cudaGetLastError();
 }
 
-cudaError_t launch_resample_rna(ppf_ctx *c, float alpha)
+cudaError_t launch_resample_rna(ppf_ctx *c, float alpha, double ess_thr)
 {
     const float *lw = c->state[c->cur] + 5 * c->N;
     prof_mark(c, PH_RESAMPLE, 0);
-    rna_prep_kernel<<<1, 1024, 0, c->stream>>>(c->goff, c->G, alpha, c->sum);
-    rna_kernel<<<c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(lw, c->N, c->G, c->goff, c->sum, c->m.seed,
+    rna_prep_kernel<<<1, 1024, 0, c->stream>>>(c->goff, c->G, alpha, c->sum, ess_thr);
+    rna_kernel<<<c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(lw, c->N, c->G, c->goff, c->sum, ess_thr, c->m.seed,
                                                      c->m.filter_id, (uint32_t)c->last_frame, c->anc, c->lwp);
     prof_mark(c, PH_RESAMPLE, 1);
     c->launches += 2;

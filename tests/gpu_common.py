@@ -75,8 +75,13 @@ def check_estimate(est, so, W, H, A, d_spread=0.0):
     assert abs(est.ess - so["ess"]) <= ess_tol * so["ess"], (est.ess, so["ess"], ess_tol)
 
 
-def lockstep(pf, gm, om, frames_np, frames_gpu, scheme, K, alpha=0.1, check_resample=True, log=None):
-    """Run K frames on the GPU and check every stage against the oracle."""
+def lockstep(pf, gm, om, frames_np, frames_gpu, scheme, K, alpha=0.1, check_resample=True, log=None,
+             ess_threshold=None):
+    """Run K frames on the GPU and check every stage against the oracle.
+    With ess_threshold, resampling follows the N_eff test of Alg. 1: the
+    GPU's decision must match the oracle's wherever N_eff is not within
+    1e-3 of the threshold, and the kept or resampled particles must match
+    the oracle's for the decision the GPU took."""
     N = pf.n
     r = gm.patch_radius
     for k in range(1, K + 1):
@@ -114,13 +119,27 @@ def lockstep(pf, gm, om, frames_np, frames_gpu, scheme, K, alpha=0.1, check_resa
         if scheme is None:
             continue
         # S6-S8: resampling from the same float32 log-weights
-        pf.resample(scheme, alpha)
+        pf.resample(scheme, alpha, ess_threshold)
         _, anc1, lwp1 = pf.get_particles(state=False, anc=True, lw_prev=True)
         goff1 = pf.groups()
         est2 = pf.estimate()
         if not check_resample:
             continue
         lwf = st1[5].cpu().numpy().astype(np.float32)
+        kept = bool(est2.status_flags & 16)
+        if ess_threshold is not None:
+            if abs(so["ess"] - ess_threshold) > 1e-3 * ess_threshold:
+                assert kept == (so["ess"] >= ess_threshold), (k, so["ess"], ess_threshold, kept)
+            if log is not None:
+                log.append(("kept", k, kept))
+        else:
+            assert not kept
+        if kept:  # Alg. 1 without resampling: identity ancestry, weights carried, layout kept
+            assert np.array_equal(anc1.cpu().numpy(), np.arange(N, dtype=np.int32))
+            assert np.array_equal(lwp1.cpu().numpy(), lwf)
+            assert np.array_equal(goff1, goff0)
+            assert (est2.links, est2.moved) == (0, 0)
+            continue
         rc, anc_ref, lwr_ref, goff_ref, stats = orc.resample(om, scheme, N, k, goff0, lwf,
                                                              lwf.astype(np.float64), alpha)
         assert rc == 0

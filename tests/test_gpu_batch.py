@@ -23,14 +23,14 @@ def ppf():
     return p
 
 
-def make(ppf, F, ns, K=4, seed=0, W=48):
+def make(ppf, F, ns, K=4, seed=0, W=48, sigma_xi2=10.0):
     import torch
     from gpu_common import f32
     mb = synth.make_movie_batch(F=F, W=W, H=W, K=K, n_range=(256, 1024), seed=seed)
     gms, oms = [], []
     for f in range(F):
         kw = dict(width=W, height=W, patch_radius=4, psf_sigma=f32(mb.sigma[f]), amplitude=f32(mb.amplitude[f]),
-                  background=10.0, sigma_xi=f32(math.sqrt(10.0)), sigma_m=0.5, sigma_v=0.1, sigma_I=1.0,
+                  background=10.0, sigma_xi=f32(math.sqrt(sigma_xi2)), sigma_m=0.5, sigma_v=0.1, sigma_I=1.0,
                   v0_max=1.0, seed=seed, filter_id=f)
         gms.append(ppf.Model(**kw))
         oms.append(orc.Model(**kw))
@@ -100,6 +100,52 @@ def test_batch_equals_single_filter_contexts(ppf):
             _, a1, _ = singles[f].get_particles(state=False, anc=True)
             assert np.array_equal(ab[bf.offsets[f]:bf.offsets[f + 1]].cpu().numpy() - bf.offsets[f],
                                   a1.cpu().numpy()), (k, f)
+    for s in singles:
+        s.close()
+    bf.close()
+
+
+def test_batch_ess_test_equals_single_filter_contexts(ppf):
+    """Alg. 1's N_eff test per filter: the batch with fraction 0.3 against
+    single-filter contexts resampling only while N_eff < 0.3 n_f (both sides
+    decide from their own N_eff, so a filter is followed only while its N_eff
+    is not within 1e-4 of the threshold)."""
+    F = 6
+    ns = [513, 64, 5000, 3, 2048, 900]
+    K = 8
+    mb, gms, oms, frames = make(ppf, F, ns, K=K, seed=4, sigma_xi2=2000.0)
+    bf = ppf.BatchFilter(gms, ns)
+    bf.set_ess_threshold(0.3)
+    singles = [ppf.ParticleFilter(gms[f], ns[f], group_size=ns[f]) for f in range(F)]
+    live = [True] * F
+    kept_seen = resampled_seen = 0
+    for k in range(1, K + 1):
+        bf.step(frames[k - 1], k)
+        for f in range(F):
+            singles[f].step(frames[k - 1, f].contiguous(), k)
+        sb, _ = bf.get_particles()
+        for f in range(F):
+            if live[f]:
+                s1, _, _ = singles[f].get_particles()
+                assert np.array_equal(sb[:, bf.offsets[f]:bf.offsets[f + 1]].cpu().numpy(), s1.cpu().numpy()), (k, f)
+        bf.resample(k)
+        _, ab = bf.get_particles(state=False, anc=True)
+        for f in range(F):
+            thr = 0.3 * ns[f]
+            ess = singles[f].estimate().ess
+            singles[f].resample(ppf.SYSTEMATIC, ess_threshold=thr)
+            if abs(ess - thr) <= 1e-4 * thr:
+                live[f] = False
+            if not live[f]:
+                continue
+            if ess >= thr:
+                kept_seen += 1
+            else:
+                resampled_seen += 1
+            _, a1, _ = singles[f].get_particles(state=False, anc=True)
+            assert np.array_equal(ab[bf.offsets[f]:bf.offsets[f + 1]].cpu().numpy() - bf.offsets[f],
+                                  a1.cpu().numpy()), (k, f)
+    assert kept_seen > 0 and resampled_seen > 0, (kept_seen, resampled_seen)
     for s in singles:
         s.close()
     bf.close()

@@ -56,6 +56,22 @@ def test_lockstep_frames(ppf, movie, scheme, N, gs):
     pf.close()
 
 
+@pytest.mark.parametrize("scheme", [orc.SYSTEMATIC, orc.RPA_SGS, orc.RNA])
+def test_ess_gated_resampling(ppf, scheme):
+    """Alg. 1's N_eff test on the device: with sigma_xi^2 = 2000 and a
+    threshold of 4000 (N = 16384) the oracle keeps the particles at frames
+    4, 6 and 7 and resamples at the others."""
+    from gpu_common import lockstep, paired_models
+    mv = synth.make_movie(W=128, H=128, K=8, sigma=1.5, amplitude=50.0, background=10.0, seed=0)
+    gm, om = paired_models(ppf, seed=3, sigma_xi=math.sqrt(2000.0))
+    pf = ppf.ParticleFilter(gm, 16384, group_size=4096)
+    log = []
+    lockstep(pf, gm, om, mv.frames, gpu_frames(mv), scheme, K=8, alpha=0.25, log=log, ess_threshold=4000.0)
+    kept = [e[2] for e in log if e[0] == "kept"]
+    assert any(kept) and not all(kept), kept
+    pf.close()
+
+
 @pytest.mark.parametrize("r", [0, 1, 5, 8])
 def test_patch_radius_and_ragged_tile(ppf, movie, r):
     from gpu_common import lockstep, paired_models

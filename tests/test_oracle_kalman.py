@@ -5,6 +5,10 @@ noise, Gaussian prior -- against the Kalman filter, whose posterior mean and
 predictive density are the exact answer (Kalman 1960).  The PSF likelihood is
 pinned separately; here the weight is the linear-Gaussian one.
 
+Case 2 resamples only while the effective sample size is below N/2 (the
+N_eff test of Alg. 1), so the carried-weight path of the recursion is pinned
+as well.
+
 Monte Carlo error: 20 runs with independent random streams (the paper repeats
 each test 20 times, Sec. 7.3); the seed-mean of every posterior-mean component
 and of the log-evidence must lie within 4 standard errors of the closed form,
@@ -32,7 +36,7 @@ def kalman_axis(z, m0, P0, sm, sv, sz):
     return np.array(means), np.array(logp)
 
 
-def run_sir(orc, seed, zs, prior_m, prior_s, sm, sv, sI, sz, N):
+def run_sir(orc, seed, zs, prior_m, prior_s, sm, sv, sI, sz, N, ess_threshold=math.inf):
     m = orc.Model(seed=seed, sigma_m=sm, sigma_v=sv, sigma_I=sI)
     rng = np.random.default_rng(seed)
     st = np.zeros((6, N))
@@ -48,13 +52,17 @@ def run_sir(orc, seed, zs, prior_m, prior_s, sm, sv, sI, sz, N):
         means.append(s["mean"])
         # the weight leaves out the Gaussian normalising constant -log(2 pi sz^2)
         ev.append(s["log_evidence"] - math.log(2 * math.pi * sz * sz))
-        rc, anc, lw_prev, goff, _ = orc.resample(m, orc.SYSTEMATIC, N, k + 1, goff,
-                                                 st[5].astype(np.float32), st[5])
-        assert rc == 0
+        if s["ess"] < ess_threshold:
+            rc, anc, lw_prev, goff, _ = orc.resample(m, orc.SYSTEMATIC, N, k + 1, goff,
+                                                     st[5].astype(np.float32), st[5])
+            assert rc == 0
+        else:  # keep the particles, carry their weights
+            anc = np.arange(N, dtype=np.int32)
+            lw_prev = st[5].copy()
     return np.array(means), np.array(ev)
 
 
-@pytest.mark.parametrize("case", [0, 1])
+@pytest.mark.parametrize("case", [0, 1, 2])
 def test_sir_matches_kalman(orc, case):
     rng = np.random.default_rng(100 + case)
     N, K, R = 1 << 14, 12, 20
@@ -73,7 +81,8 @@ def test_sir_matches_kalman(orc, case):
     ky = kalman_axis(zs[:, 1], [prior_m[1], prior_m[3]], np.diag([prior_s[1] ** 2, prior_s[3] ** 2]), sm, sv, sz)
     want = np.stack([kx[0][:, 0], ky[0][:, 0], kx[0][:, 1], ky[0][:, 1], np.full(K, prior_m[4])], axis=1)
     want_ev = kx[1] + ky[1]
-    runs = [run_sir(orc, 1000 * case + s, zs, prior_m, prior_s, sm, sv, sI, sz, N) for s in range(R)]
+    thr = N / 2 if case == 2 else math.inf
+    runs = [run_sir(orc, 1000 * case + s, zs, prior_m, prior_s, sm, sv, sI, sz, N, thr) for s in range(R)]
     M = np.array([r[0] for r in runs])       # (R, K, 5)
     E = np.array([r[1] for r in runs])       # (R, K)
     se = M.std(axis=0, ddof=1) / math.sqrt(R)
