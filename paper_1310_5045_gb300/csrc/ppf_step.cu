@@ -152,22 +152,37 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
     if (mode != MODE_CARRY && *a.degenerate)
         mode = MODE_CARRY;  // the last resample kept every particle
     const PatchGeom geom{a.Zp, a.W, a.H, a.Wp, a.pad, a.inv2s2, a.inv_sxi2, a.Kc};
-    const int64_t N = a.N;
+    // N < 2^31: 32-bit slot indices into per-component planes
+    const int32_t N = (int32_t)a.N;
+    const float *__restrict__ sx = a.src, *__restrict__ sy = a.src + a.N, *__restrict__ svx = a.src + 2 * a.N;
+    const float *__restrict__ svy = a.src + 3 * a.N, *__restrict__ sI = a.src + 4 * a.N;
+    const float *__restrict__ slw = a.src + 5 * a.N;
+    float *__restrict__ dplane[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+        dplane[c] = a.dst + c * a.N;
     Acc acc;
     acc.init();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t p = (mode == MODE_CARRY) ? i : (int64_t)__ldg(a.anc + i);
-        if ((uint64_t)p >= (uint64_t)N) {  // caller-supplied ancestors are checked, never trusted
+    // unsigned: i + stride stays below 2^32 for any N < 2^31.  The ancestor of
+    // the next slot is loaded one iteration ahead, so the parent-state gather
+    // does not wait on a dependent load.
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t pn = (i0 < (uint32_t)N) ? ((mode == MODE_CARRY) ? i0 : (uint32_t)__ldg(a.anc + i0)) : 0u;
+    for (uint32_t i = i0; i < (uint32_t)N; i += stride) {
+        uint32_t p = pn;
+        if (i + stride < (uint32_t)N)
+            pn = (mode == MODE_CARRY) ? i + stride : (uint32_t)__ldg(a.anc + i + stride);
+        if (p >= (uint32_t)N) {  // caller-supplied ancestors are checked, never trusted
             atomicOr(a.flags, FLAG_BAD_ANCESTOR);
             p = i;
         }
-        const float x = __ldg(a.src + p), y = __ldg(a.src + N + p);
-        const float vx = __ldg(a.src + 2 * N + p), vy = __ldg(a.src + 3 * N + p);
-        const float I0 = __ldg(a.src + 4 * N + p);
+        const float x = __ldg(sx + p), y = __ldg(sy + p);
+        const float vx = __ldg(svx + p), vy = __ldg(svy + p);
+        const float I0 = __ldg(sI + p);
         float lwp;
         if (mode == MODE_CARRY)
-            lwp = __ldg(a.src + 5 * N + p);
+            lwp = __ldg(slw + p);
         else if (mode == MODE_UNIFORM)
             lwp = 0.0f;
         else
@@ -188,8 +203,8 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
         const float lw = lwp + l;
 #pragma unroll
         for (int c = 0; c < 5; ++c)
-            a.dst[c * N + i] = v[c];
-        a.dst[5 * N + i] = lw;
+            dplane[c][i] = v[c];
+        dplane[5][i] = lw;
         acc.add(lw, lwp, v);
     }
     // block reduction of the partial statistics
