@@ -178,17 +178,22 @@ template <typename T>
 __global__ void batch_prepare_kernel(const BatchCursor *__restrict__ cur, float *__restrict__ Zp, int32_t F, int W,
                                      int H, int Wp, int Hp, int pad, const FilterParams *__restrict__ fp)
 {
+    // one warp per padded row (F * Hp rows), lanes across its columns
     const T *Z = reinterpret_cast<const T *>(cur->frames + cur->frame_bytes * cur->t);
-    const int64_t plane = (int64_t)Wp * Hp;
-    const int64_t n = plane * F;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t f = (int32_t)(idx / plane);
-        const int64_t rem = idx - f * plane;
-        const int py = (int)(rem / Wp) - pad, px = (int)(rem % Wp) - pad;
-        float v = 0.0f;
-        if (px >= 0 && px < W && py >= 0 && py < H)
-            v = tof<T>(Z[((int64_t)f * H + py) * W + px]) - fp[f].bg;
-        Zp[idx] = v;
+    const int lane = threadIdx.x & 31;
+    const int32_t rows = F * Hp;
+    const int32_t nw = (int32_t)(gridDim.x * (blockDim.x >> 5));
+    for (int32_t row = (int32_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); row < rows; row += nw) {
+        const int32_t f = row / Hp;
+        const int py = row - f * Hp - pad;
+        const float bg = fp[f].bg;
+        float *__restrict__ out = Zp + (int64_t)row * Wp;
+        const bool in_row = py >= 0 && py < H;
+        const T *zrow = Z + ((int64_t)f * H + (in_row ? py : 0)) * W;
+        for (int c = lane; c < Wp; c += 32) {
+            const int px = c - pad;
+            out[c] = (in_row && px >= 0 && px < W) ? tof<T>(zrow[px]) - bg : 0.0f;
+        }
     }
 }
 
@@ -208,85 +213,89 @@ struct BatchStepArgs {
     Partial *__restrict__ part;
 };
 
-// persistent SIS step over all units of all filters
+// Persistent SIS step over all work units of all filters.  A unit is a run
+// of at most `unit` particles of one filter and belongs to one warp: the warp
+// steps its particles (the next slot's ancestor loaded one iteration ahead)
+// and reduces their weight statistics with shuffles into the unit's partial,
+// with no block-wide synchronisation.
 template <int R>
 __global__ void batch_step_kernel(BatchStepArgs a)
 {
-    const int64_t N = a.Ntot;
+    const uint32_t N = (uint32_t)a.Ntot;  // < 2^31
     const uint32_t frame = (uint32_t)a.cur->k;
     const bool first = a.cur->first != 0;
     const float *__restrict__ src = a.cur->cur ? a.st1 : a.st0;
     float *__restrict__ dst = a.cur->cur ? a.st0 : a.st1;
-    __shared__ FilterParams P;
-    __shared__ Acc sh[32];
-    for (int32_t u = blockIdx.x; u < a.U; u += gridDim.x) {
+    const float *__restrict__ sx = src, *__restrict__ sy = src + N, *__restrict__ svx = src + 2 * (size_t)N;
+    const float *__restrict__ svy = src + 3 * (size_t)N, *__restrict__ sI = src + 4 * (size_t)N;
+    const float *__restrict__ slw = src + 5 * (size_t)N;
+    __shared__ float kcs[32][MAX_RADIUS];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int32_t nwarps = (int32_t)(gridDim.x * (blockDim.x >> 5));
+    for (int32_t u = (int32_t)(blockIdx.x * (blockDim.x >> 5)) + wib; u < a.U; u += nwarps) {
         const int32_t f = a.unit_f[u];
-        __syncthreads();
-        if (threadIdx.x == 0)
-            P = a.fp[f];
-        __syncthreads();
-        const PatchGeom geom{a.Zp + (int64_t)f * a.Wp * a.Hp, a.W, a.H, a.Wp, a.pad, P.inv2s2, P.inv_sxi2, P.Kc};
+        const FilterParams *__restrict__ P = a.fp + f;
+        const uint32_t off = (uint32_t)P->off, nf = (uint32_t)P->n;
+        const uint64_t seed = P->seed;
+        const uint32_t fid = P->fid;
+        const float sm = P->sm, sv = P->sv, sIn = P->sI;
+        __syncwarp();
+        if (lane < R)
+            kcs[wib][lane] = P->Kc[lane];
+        __syncwarp();
+        const PatchGeom geom{a.Zp + (int64_t)f * a.Wp * a.Hp, a.W, a.H, a.Wp, a.pad, P->inv2s2, P->inv_sxi2,
+                             kcs[wib]};
         // after the prior draw, or when the last resample kept this filter's
         // particles, every slot continues its own particle with its weight
         const bool carry = first || a.fkeep[f] != 0;
         Acc acc;
         acc.init();
-        const int64_t lo = a.unit_lo[u];
+        const uint32_t lo = (uint32_t)a.unit_lo[u];
         const int32_t n = a.unit_n[u];
-        for (int32_t j = threadIdx.x; j < n; j += blockDim.x) {
-            const int64_t i = lo + j;
-            int64_t p = carry ? i : (int64_t)__ldg(a.anc + i);
-            if (p < P.off || p >= P.off + P.n)
+        uint32_t pn = (lane < n) ? (carry ? lo + lane : (uint32_t)__ldg(a.anc + lo + lane)) : 0u;
+        for (int32_t j = lane; j < n; j += 32) {
+            const uint32_t i = lo + (uint32_t)j;
+            uint32_t p = pn;
+            if (j + 32 < n)
+                pn = carry ? i + 32 : (uint32_t)__ldg(a.anc + i + 32);
+            if (p < off || p >= off + nf)
                 p = i;  // ancestors never cross filters
-            const float x = src[p], y = src[N + p];
-            const float vx = src[2 * N + p], vy = src[3 * N + p];
-            const float I0 = src[4 * N + p];
-            const float lwp = carry ? src[5 * N + p] : 0.0f;
+            const float x = __ldg(sx + p), y = __ldg(sy + p);
+            const float vx = __ldg(svx + p), vy = __ldg(svy + p);
+            const float I0 = __ldg(sI + p);
+            const float lwp = carry ? __ldg(slw + p) : 0.0f;
             uint32_t fl[6];
-            prop_fields(draw(P.seed, (uint32_t)(i - P.off), frame, P.fid, PURPOSE_PROP, 0), fl);
+            prop_fields(draw(seed, i - off, frame, fid, PURPOSE_PROP, 0), fl);
             float e0, e1, e2, e3, e4, e5;
             box_muller(u21(fl[0]), u21(fl[1]), e0, e1);
             box_muller(u21(fl[2]), u21(fl[3]), e2, e3);
             box_muller(u21(fl[4]), u21(fl[5]), e4, e5);
             float v[5];
-            v[0] = fmaf(P.sm, e0, x + vx);
-            v[1] = fmaf(P.sm, e1, y + vy);
-            v[2] = fmaf(P.sv, e2, vx);
-            v[3] = fmaf(P.sv, e3, vy);
-            v[4] = fmaf(P.sI, e4, I0);
+            v[0] = fmaf(sm, e0, x + vx);
+            v[1] = fmaf(sm, e1, y + vy);
+            v[2] = fmaf(sv, e2, vx);
+            v[3] = fmaf(sv, e3, vy);
+            v[4] = fmaf(sIn, e4, I0);
             const float lw = lwp + patch_loglik<R>(geom, v[0], v[1], v[4]);
 #pragma unroll
             for (int c = 0; c < 5; ++c)
-                dst[c * N + i] = v[c];
-            dst[5 * N + i] = lw;
+                dst[(size_t)c * N + i] = v[c];
+            dst[5 * (size_t)N + i] = lw;
             acc.add(lw, lwp, v);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             acc.shfl_merge(o);
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        if (lane == 0)
-            sh[warp] = acc;
-        __syncthreads();
-        if (warp == 0) {
-            if (lane < nw)
-                acc = sh[lane];
-            else
-                acc.init();
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                acc.shfl_merge(o);
-            if (lane == 0) {
-                Partial q;
-                q.m = acc.m;
-                q.s0 = acc.s0;
-                q.s2 = acc.s2;
-                for (int c = 0; c < 5; ++c)
-                    q.s[c] = acc.s[c];
-                q.mp = acc.mp;
-                q.sp = acc.sp;
-                a.part[u] = q;
-            }
+        if (lane == 0) {
+            Partial q;
+            q.m = acc.m;
+            q.s0 = acc.s0;
+            q.s2 = acc.s2;
+            for (int c = 0; c < 5; ++c)
+                q.s[c] = acc.s[c];
+            q.mp = acc.mp;
+            q.sp = acc.sp;
+            a.part[u] = q;
         }
     }
 }
@@ -360,9 +369,19 @@ __global__ void __launch_bounds__(TILE_THREADS) batch_tile_totals(const float *s
         return;  // N_eff test: this filter keeps its particles
     const float Mf = fs[f].M;
     const int s = scale_bits(fp[f].n);
+    const int n = tile_n[t];
+    const float *__restrict__ w = lw + tile_lo[t];
+    // all loads first (independent, in flight together), then the quantiser
+    float v[TILE_ITEMS];
+#pragma unroll
+    for (int k = 0; k < TILE_ITEMS; ++k) {
+        const int i = threadIdx.x + k * TILE_THREADS;
+        v[k] = (i < n) ? __ldg(w + i) : -INFINITY;
+    }
     uint64_t acc = 0;
-    for (int i = threadIdx.x; i < tile_n[t]; i += blockDim.x)
-        acc += quantise(__ldg(lw + tile_lo[t] + i), Mf, s);
+#pragma unroll
+    for (int k = 0; k < TILE_ITEMS; ++k)
+        acc += quantise(v[k], Mf, s);
     uint64_t total;
     block_excl_scan_u64(acc, red, &total);
     if (threadIdx.x == 0)
@@ -572,8 +591,8 @@ cudaError_t launch_batch_step(ppf_batch *b, bool commit)
 
 cudaError_t launch_batch_prepare(ppf_batch *b)
 {
-    const int64_t n = (int64_t)b->F * b->Wp * b->Hp;
-    const int grid = (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
+    const int64_t rows = (int64_t)b->F * b->Hp;  // one warp per row, 8 warps per block
+    const int grid = (int)((rows + 7) / 8 < 8192 ? (rows + 7) / 8 : 8192);
     switch (b->dtype) {
     case PPF_BF16:
         batch_prepare_kernel<__nv_bfloat16><<<grid, 256, 0, b->stream>>>(b->cursor, b->Zp, b->F, b->W, b->H, b->Wp,
