@@ -319,7 +319,7 @@ def run_ours(args):
         bfr = torch.from_numpy(mb.frames).to(dev)
         bres = {}
         bf = ppf.BatchFilter(bmodels, mb.n_particles, stream=stream)
-        cfg = bf.autotune(bfr[0], 1)
+        cfg = None if args.no_autotune else bf.autotune(bfr[0], 1)
         bf.run(bfr[:2], 1, use_graph=True, estimates=False)
         k0 = 3
         for mode in ("graph", "launches", "graph"):  # same launch shape; the graph twice (first and last)
@@ -335,7 +335,7 @@ def run_ours(args):
             r = {"particle_steps_per_sec": bf.ntot * args.batch_steps / dt, "ms_per_frame": 1e3 * dt / args.batch_steps}
             if mode not in bres or r["ms_per_frame"] < bres[mode]["ms_per_frame"]:
                 bres[mode] = r
-        bres["graph"]["autotuned"] = cfg
+        bres["graph"]["autotuned"] = cfg if cfg else "off (default shape)"
         ntot = bf.ntot
         bf.close()
         line["batched"] = {"workload": f"{args.batch_filters} filters, N_f log-uniform in [256, 65536] "
@@ -461,6 +461,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-filters", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--no-autotune", action="store_true", help="batched stage: keep the default launch shape")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--precision-n", type=int, default=N_FULL)
     ap.add_argument("--precision-frames", type=int, default=5)

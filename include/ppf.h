@@ -234,9 +234,13 @@ ppf_status ppf_batch_step(ppf_batch *b, const void *frames_dev, int32_t k);
 ppf_status ppf_batch_resample(ppf_batch *b, int32_t k);
 
 /* K frames (frames_dev: K x F x H x W) of step + resample, frame indices
- * k0 .. k0+K-1.  use_graph != 0 captures the whole sequence in one CUDA graph
- * and launches it once.  est_host (optional, K x F, host) receives every
- * filter's estimate of every frame.  Synchronous. */
+ * k0 .. k0+K-1.  Every kernel of a frame iteration reads its frame, frame
+ * index and estimate slot from a device-side cursor, so with use_graph != 0
+ * one iteration is captured as a CUDA graph once (on the first such call, or
+ * after the launch shape changed) and replayed K times; use_graph == 0
+ * launches the kernels directly.  Both give identical results.  est_host
+ * (optional, K x F, host) receives every filter's estimate of every frame.
+ * Synchronous. */
 ppf_status ppf_batch_run(ppf_batch *b, const void *frames_dev, int32_t k0, int32_t K, int32_t use_graph,
                          ppf_filter_estimate_t *est_host);
 
