@@ -207,7 +207,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     n = args.n
     K, Wm = args.steps, args.warmup
-    extra = 0 if args.no_schemes else 6 * (args.scheme_steps + 2)
+    extra = 0 if args.no_schemes else 9 * (args.scheme_steps + 2)
     k_total = Wm + K + extra + (args.e2e_steps if not args.no_e2e else 0) + 2
     mv, params = make_workload(k_total, seed=0)
     model = ppf.Model(**params, seed=rank, filter_id=rank)
@@ -289,10 +289,11 @@ def run_ours(args):
     if not args.no_schemes:
         sch = {}
         k = kdone + 1
-        # every row starts from balanced groups except LGS, which unbalances them
-        # itself (it runs last so that no other row inherits its layout)
-        for name, alpha in [("rpa_gs", 0.0), ("rpa_sgs", 0.0), ("rna", 0.1), ("rna", 0.5), ("systematic", 0.0),
-                            ("rpa_lgs", 0.0)]:
+        # every row starts from balanced groups except the LGS rows, which
+        # unbalance them themselves (they run last so that no other row
+        # inherits their layout)
+        for name, alpha in [("rpa_gs", 0.0), ("rpa_sgs", 0.0), ("rpa2_gs", 0.0), ("rpa2_sgs", 0.0), ("rna", 0.1),
+                            ("rna", 0.5), ("systematic", 0.0), ("rpa_lgs", 0.0), ("rpa2_lgs", 0.0)]:
             sid = ppf.SCHEMES[name]
             for _ in range(2):
                 pf.step(frames[k - 1], k)
@@ -447,7 +448,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--scheme", default="systematic", choices=sorted(["systematic", "rpa_gs", "rpa_sgs",
-                                                                      "rpa_lgs", "rna"]))
+                                                                      "rpa_lgs", "rna", "rpa2_gs", "rpa2_sgs",
+                                                                      "rpa2_lgs"]))
     ap.add_argument("--alpha", type=float, default=0.1)
     ap.add_argument("--scheme-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=30)

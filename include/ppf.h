@@ -41,7 +41,14 @@ typedef enum {
     PPF_RPA_GS = 1,     /* proportional allocation + Greedy Scheduler (Alg. 2)  */
     PPF_RPA_SGS = 2,    /* proportional allocation + Sorted Greedy (Alg. 3)     */
     PPF_RPA_LGS = 3,    /* proportional allocation + Largest Gradient (Alg. 4)  */
-    PPF_RNA = 4         /* non-proportional allocation + ring migration (Sec. 3)*/
+    PPF_RNA = 4,        /* non-proportional allocation + ring migration (Sec. 3)*/
+    /* Two-stage proportional allocation (Sec. 3 RPA, in the stratified form
+     * of Bolic et al.): group g receives the same number N_g of offspring as
+     * with one global draw (so the same schedules and routing), but draws
+     * them inside the group with its own systematic offset. */
+    PPF_RPA2_GS = 5,
+    PPF_RPA2_SGS = 6,
+    PPF_RPA2_LGS = 7
 } ppf_scheme;
 
 typedef enum { PPF_F32 = 0, PPF_BF16 = 1, PPF_F16 = 2 } ppf_dtype;

@@ -25,6 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 SYSTEMATIC, RPA_GS, RPA_SGS, RPA_LGS, RNA = 0, 1, 2, 3, 4
+RPA2_GS, RPA2_SGS, RPA2_LGS = 5, 6, 7  # two-stage proportional allocation
 PURPOSE_INIT, PURPOSE_PROP, PURPOSE_RESAMPLE, PURPOSE_GROUP_RESAMPLE = 0, 1, 2, 3
 OK, EDEGENERATE = 0, 5
 

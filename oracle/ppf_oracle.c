@@ -474,6 +474,12 @@ void orc_balanced_offsets(int64_t N, int32_t G, int64_t *off)
 /*                       one global offset, so the ancestors do not depend on */
 /*                       G); group g keeps its first offspring, its surplus   */
 /*                       (the last ones) is routed to receivers per schedule. */
+/*   ORC_RPA2_GS/SGS/LGS two-stage proportional allocation (Bolic et al.):    */
+/*                       stage 1 gives group g the N_g global tickets of its  */
+/*                       cumulative range, as RPA does; stage 2 draws those   */
+/*                       N_g offspring inside the group by its own systematic */
+/*                       draw (offset from Philox(seed; g, k, filter, GROUP)) */
+/*                       over the group's fixed-point weights; routing as RPA.*/
 /*   ORC_RNA             each group resamples its own slots from its own      */
 /*                       weights with its own offset; the offspring carry the */
 /*                       group weight log(W_g / n_g); then the last           */
@@ -609,6 +615,8 @@ int orc_resample(const orc_model *m, int scheme, double alpha, int64_t N, int32_
     }
 
     /* RPA: offspring per group = tickets inside the group's cumulative range */
+    const int two_stage = (scheme >= ORC_RPA2_GS && scheme <= ORC_RPA2_LGS);
+    const int sched = two_stage ? scheme - (ORC_RPA2_GS - ORC_RPA_GS) : scheme;
     int64_t *T = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G + 1));
     int64_t *cnt_g = (int64_t *)malloc(sizeof(int64_t) * (size_t)G);
     int64_t *tgt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G + 1));
@@ -620,6 +628,20 @@ int orc_resample(const orc_model *m, int scheme, double alpha, int64_t N, int32_
         T[g + 1] = orc_tickets_below(C, N, u, Q);
         cnt_g[g] = T[g + 1] - T[g];
     }
+    if (two_stage) {
+        /* stage 2: group g's tickets T[g] .. T[g+1]-1 come from its own draw */
+        for (int32_t g = 0; g < G && rc == ORC_OK; ++g) {
+            if (cnt_g[g] == 0)
+                continue;
+            const int64_t lo = goff_in[g], sz = goff_in[g + 1] - lo;
+            uint64_t Qg = 0;
+            for (int64_t i = 0; i < sz; ++i)
+                Qg += q[lo + i];
+            const uint64_t ug = orc_ticket_offset(m->seed, m->filter_id, (uint32_t)frame,
+                                                  ORC_PURPOSE_GROUP_RESAMPLE, (uint32_t)g, Qg);
+            rc = orc_systematic(sz, q + lo, cnt_g[g], ug, lo, sys + T[g], NULL);
+        }
+    }
     orc_balanced_offsets(N, G, tgt);
     int64_t *target = (int64_t *)malloc(sizeof(int64_t) * (size_t)G);
     for (int32_t g = 0; g < G; ++g)
@@ -627,7 +649,7 @@ int orc_resample(const orc_model *m, int scheme, double alpha, int64_t N, int32_
     int32_t *lsrc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * G + 1));
     int32_t *ldst = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * G + 1));
     int64_t *lcnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * G + 1));
-    int64_t L = orc_schedule(scheme, G, cnt_g, target, lsrc, ldst, lcnt);
+    int64_t L = orc_schedule(sched, G, cnt_g, target, lsrc, ldst, lcnt);
     int64_t *sent = (int64_t *)calloc((size_t)G, sizeof(int64_t));
     int64_t *recv = (int64_t *)calloc((size_t)G, sizeof(int64_t));
     int64_t moved = 0;

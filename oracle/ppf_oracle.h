@@ -7,7 +7,8 @@
 #include <stdint.h>
 
 enum { ORC_OK = 0, ORC_EDEGENERATE = 5, ORC_EINTERNAL = 7 };
-enum { ORC_SYSTEMATIC = 0, ORC_RPA_GS = 1, ORC_RPA_SGS = 2, ORC_RPA_LGS = 3, ORC_RNA = 4 };
+enum { ORC_SYSTEMATIC = 0, ORC_RPA_GS = 1, ORC_RPA_SGS = 2, ORC_RPA_LGS = 3, ORC_RNA = 4,
+       ORC_RPA2_GS = 5, ORC_RPA2_SGS = 6, ORC_RPA2_LGS = 7 };
 enum { ORC_PURPOSE_INIT = 0, ORC_PURPOSE_PROP = 1, ORC_PURPOSE_RESAMPLE = 2,
        ORC_PURPOSE_GROUP_RESAMPLE = 3 };
 

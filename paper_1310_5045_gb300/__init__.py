@@ -15,6 +15,9 @@ from ._binding import (  # noqa: F401
     RNA,
     RPA_GS,
     RPA_LGS,
+    RPA2_GS,
+    RPA2_LGS,
+    RPA2_SGS,
     RPA_SGS,
     SCHEMES,
     SYSTEMATIC,

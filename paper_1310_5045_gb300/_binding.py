@@ -15,9 +15,11 @@ import threading
 from . import _build
 
 SYSTEMATIC, RPA_GS, RPA_SGS, RPA_LGS, RNA = 0, 1, 2, 3, 4
+RPA2_GS, RPA2_SGS, RPA2_LGS = 5, 6, 7  # two-stage proportional allocation
 F32, BF16, F16 = 0, 1, 2
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEGENERATE, ESTATE = range(7)
-SCHEMES = {"systematic": SYSTEMATIC, "rpa_gs": RPA_GS, "rpa_sgs": RPA_SGS, "rpa_lgs": RPA_LGS, "rna": RNA}
+SCHEMES = {"systematic": SYSTEMATIC, "rpa_gs": RPA_GS, "rpa_sgs": RPA_SGS, "rpa_lgs": RPA_LGS, "rna": RNA,
+           "rpa2_gs": RPA2_GS, "rpa2_sgs": RPA2_SGS, "rpa2_lgs": RPA2_LGS}
 
 EXPORTS = ["ppf_create", "ppf_destroy", "ppf_step", "ppf_step_host", "ppf_resample", "ppf_resample_if",
            "ppf_estimate",

@@ -265,11 +265,13 @@ ppf_status ppf_resample_if(ppf_ctx *c, ppf_scheme scheme, float alpha, double es
         return PPF_EINVAL;
     if (ess_threshold != ess_threshold)  // NaN
         return PPF_EINVAL;
-    if (scheme < PPF_SYSTEMATIC || scheme > PPF_RNA)
+    if (scheme < PPF_SYSTEMATIC || scheme > PPF_RPA2_LGS)
         return PPF_EINVAL;
     if (scheme == PPF_RNA && !(alpha >= 0.0f && alpha <= 1.0f))
         return PPF_EINVAL;
-    if (scheme >= PPF_RPA_GS && scheme <= PPF_RPA_LGS && c->G > MAX_SCHED_GROUPS) {
+    const bool routed = (scheme >= PPF_RPA_GS && scheme <= PPF_RPA_LGS) ||
+                        (scheme >= PPF_RPA2_GS && scheme <= PPF_RPA2_LGS);
+    if (routed && c->G > MAX_SCHED_GROUPS) {
         set_err(c, "RPA schedules support at most %d groups", MAX_SCHED_GROUPS);
         return PPF_EINVAL;
     }

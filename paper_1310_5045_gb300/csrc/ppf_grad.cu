@@ -250,8 +250,14 @@ __global__ void __launch_bounds__(256) grad_step_kernel(GradArgs a)
     const bool ident = a.first || *a.degenerate;
     GAcc acc;
     acc.init();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t p = ident ? i : (int64_t)__ldg(a.anc + i);
+    // the ancestor of the next slot is loaded one iteration ahead
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t pn = (i0 < N) ? (ident ? i0 : (int64_t)__ldg(a.anc + i0)) : 0;
+    for (int64_t i = i0; i < N; i += stride) {
+        int64_t p = pn;
+        if (i + stride < N)
+            pn = ident ? i + stride : (int64_t)__ldg(a.anc + i + stride);
         if ((uint64_t)p >= (uint64_t)N)
             p = i;
         const float x = __ldg(a.src + p), y = __ldg(a.src + N + p);

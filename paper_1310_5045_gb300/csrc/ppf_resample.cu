@@ -246,6 +246,67 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     ticket_parents_staged(C, n, Ct[t], tg, i_lo, i_hi, stage, [&](int64_t j, int i) { out[j] = (int32_t)(lo + i); });
 }
 
+// ------------------------------------------------ two-stage RPA, stage 2
+// One block per group: the group's N_g = Tg[g+1] - Tg[g] offspring (stage 1:
+// the global tickets of its cumulative range) drawn again inside the group by
+// its own systematic draw over the same fixed-point weights, offset from
+// Philox(seed; g, frame, filter, GROUP).  They are written, in ticket order,
+// where the global draw would have put them (ticket slots Tg[g] ..), so the
+// RPA schedule and routing copy apply unchanged.
+__global__ void __launch_bounds__(TILE_THREADS) group_fill_kernel(
+    const float *__restrict__ lw, int64_t N, const int64_t *__restrict__ goff, const int64_t *__restrict__ Tg,
+    const DevSummary *__restrict__ sum, double ess_thr, uint64_t seed, uint32_t fid, uint32_t frame,
+    int32_t *__restrict__ out)
+{
+    if (kept_by_ess(sum, ess_thr) || sum->degenerate)
+        return;  // kept by the N_eff test, or no usable weight (the schedule keeps the layout)
+    extern __shared__ uint64_t fill_smem[];  // FILL_SMEM_BYTES
+    uint64_t *C = fill_smem;
+    uint16_t *stage = reinterpret_cast<uint16_t *>(fill_smem + TILE_SMEM_U64);
+    __shared__ uint64_t red[33];
+    __shared__ uint64_t us, qNs;
+    __shared__ uint32_t qRs;
+    __shared__ Divisor dvs;
+    const int32_t g = blockIdx.x;
+    const int64_t lo = goff[g], sz = goff[g + 1] - lo;
+    const int64_t nt = Tg[g + 1] - Tg[g];
+    if (sz <= 0 || nt <= 0)
+        return;
+    const float M = sum->M;
+    const int s = scale_bits(N);
+    // the group's total fixed-point weight
+    uint64_t qs = 0;
+    for (int64_t i = threadIdx.x; i < sz; i += blockDim.x)
+        qs += quantise(__ldg(lw + lo + i), M, s);
+    uint64_t Qg;
+    block_excl_scan_u64(qs, red, &Qg);
+    if (threadIdx.x == 0) {
+        us = ticket_offset(seed, fid, frame, PURPOSE_GROUP, (uint32_t)g, Qg);
+        dvs = make_divisor((uint32_t)nt);
+        qNs = Qg / (uint64_t)nt;
+        qRs = (uint32_t)(Qg % (uint64_t)nt);
+    }
+    __syncthreads();
+    const uint64_t u = us;
+    const TicketGrid tg = ticket_grid(Qg, u, qNs, qRs, dvs);
+    int32_t *__restrict__ dst = out + Tg[g];
+    // chunks of TILE particles; the local tickets of chunk [c0, c0 + n) are
+    // [T(carry), T(carry + total)) with T the count below of the nt tickets
+    uint64_t carry = 0;
+    for (int64_t c0 = 0; c0 < sz; c0 += TILE) {
+        const int n = (int)(sz - c0 < TILE ? sz - c0 : TILE);
+        uint64_t q[TILE_ITEMS];
+        tile_weights(lw, lo + c0, n, M, s, C, q);
+        const uint64_t tot = tile_scan(q, C, red);
+        const int64_t t_lo = tickets_below(carry, nt, u, Qg);
+        const int64_t t_hi = tickets_below(carry + tot, nt, u, Qg);
+        ticket_parents_staged(C, n, carry, tg, t_lo, t_hi, stage,
+                              [&](int64_t j, int i) { dst[j] = (int32_t)(lo + c0 + i); });
+        carry += tot;
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------ RPA schedule
 // One block.  Senders / receivers from the offspring counts o_g = T_{g+1} -
 // T_g and the balanced targets n_g; SGS and LGS sort both lists by amount,
@@ -826,6 +887,9 @@ cudaError_t resample_kernel_attributes()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(rna_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILL_SMEM_BYTES);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(group_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FILL_SMEM_BYTES);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(schedule_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(uint64_t) * MAX_SCHED_GROUPS));
     return e;
@@ -844,10 +908,17 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
                                                 c->sc.item_tile, c->sum, ess_thr,
                                                 c->m.seed, c->m.filter_id, (uint32_t)c->last_frame,
                                                 c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg);
-    const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
     int32_t *out = rpa ? c->anc_sys : c->anc;
-    fill_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
-        lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, out);
+    const bool two_stage = (scheme >= PPF_RPA2_GS && scheme <= PPF_RPA2_LGS);
+    if (two_stage) {  // stage 2: every group draws its own offspring
+        group_fill_kernel<<<c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
+            lw, c->N, c->goff, c->sc.Tg, c->sum, ess_thr, c->m.seed, c->m.filter_id, (uint32_t)c->last_frame, out);
+    } else {
+        const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
+        fill_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
+            lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile,
+            out);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !rpa) {
         prof_mark(c, PH_RESAMPLE, 1);
@@ -856,7 +927,7 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     SchedArgs A;
     A.N = c->N;
     A.G = c->G;
-    A.scheme = scheme;
+    A.scheme = two_stage ? scheme - (PPF_RPA2_GS - PPF_RPA_GS) : scheme;  // the schedule
     A.goff = c->goff;
     A.goff_new = c->goff_new;
     A.Tg = c->sc.Tg;

@@ -4,7 +4,8 @@ times.  Propagation and likelihood are checked on sampled slots that the
 oracle computes one by one; normalisation, estimate and log-evidence by the
 oracle's FP64 summary over all particles (same log-weight inputs, exact bound
 as in gpu_common); the ancestors and group offsets bit-exactly for systematic,
-RPA-LGS and RNA resampling (the oracle resamples all 38 M weights)."""
+RPA-LGS, RNA and two-stage RPA-GS resampling (the oracle resamples all 38 M
+weights)."""
 import math
 
 import numpy as np
@@ -95,4 +96,6 @@ def test_full_size_frames(setup):
     one_frame(ppf, pf, gm, om, mv, frames, 1, orc.SYSTEMATIC)
     one_frame(ppf, pf, gm, om, mv, frames, 2, orc.RPA_LGS)
     est = one_frame(ppf, pf, gm, om, mv, frames, 3, orc.RNA, alpha=0.1)
+    assert math.isfinite(est.log_evidence)
+    est = one_frame(ppf, pf, gm, om, mv, frames, 4, orc.RPA2_GS)
     assert math.isfinite(est.log_evidence)

@@ -46,7 +46,8 @@ def test_init_matches_oracle(ppf):
     pf.close()
 
 
-@pytest.mark.parametrize("scheme", [orc.SYSTEMATIC, orc.RPA_GS, orc.RPA_SGS, orc.RPA_LGS, orc.RNA])
+@pytest.mark.parametrize("scheme", [orc.SYSTEMATIC, orc.RPA_GS, orc.RPA_SGS, orc.RPA_LGS, orc.RNA,
+                                    orc.RPA2_GS, orc.RPA2_SGS, orc.RPA2_LGS])
 @pytest.mark.parametrize("N,gs", [(16384, 4096), (10000, 777)])
 def test_lockstep_frames(ppf, movie, scheme, N, gs):
     from gpu_common import lockstep, paired_models
@@ -69,6 +70,26 @@ def test_ess_gated_resampling(ppf, scheme):
     lockstep(pf, gm, om, mv.frames, gpu_frames(mv), scheme, K=8, alpha=0.25, log=log, ess_threshold=4000.0)
     kept = [e[2] for e in log if e[0] == "kept"]
     assert any(kept) and not all(kept), kept
+    pf.close()
+
+
+@pytest.mark.parametrize("scheme", [orc.RPA_GS, orc.RPA_LGS, orc.RPA2_SGS])
+def test_rpa_at_the_group_limit(ppf, movie, scheme):
+    """The RPA schedules at their largest group count, G = 16384 groups of 40
+    particles (one block sorts and merges every sender and receiver), and one
+    group more is rejected."""
+    from gpu_common import lockstep, paired_models
+    gm, om = paired_models(ppf, seed=9)
+    pf = ppf.ParticleFilter(gm, 16384 * 40, group_size=40)
+    assert len(pf.groups()) == 16385
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), scheme, K=2)
+    pf.close()
+    pf = ppf.ParticleFilter(gm, 16385 * 40, group_size=40)
+    pf.step(gpu_frames(movie)[0], 1)
+    with pytest.raises(ppf.PPFError) as e:
+        pf.resample(scheme)
+    assert e.value.status == ppf.EINVAL
+    pf.resample(ppf.SYSTEMATIC)  # the other schemes have no group limit
     pf.close()
 
 

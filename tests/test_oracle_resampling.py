@@ -247,3 +247,61 @@ def test_global_degenerate_keeps_particles(orc):
     lw = np.full(N, np.nan, dtype=np.float32)
     rc, anc, lwr, gout, _ = orc.resample(m, orc.SYSTEMATIC, N, 1, orc.balanced_offsets(N, 2), lw)
     assert rc == orc.EDEGENERATE and np.array_equal(anc, np.arange(N))
+
+
+def test_systematic_enumeration_other_ticket_counts(orc):
+    """Systematic draws of n tickets over weights of a different length (the
+    second stage of two-stage RPA): for every offset u in [0, Q) the parents
+    equal direct ticket counting, and summed over u particle i receives
+    exactly n q_i tickets (unbiasedness, in integers)."""
+    rng = np.random.default_rng(12)
+    for n_in, nt in [(6, 4), (5, 9), (7, 1), (3, 3)]:
+        q = rng.integers(0, 150, size=n_in).astype(np.uint64)
+        q[rng.integers(0, n_in)] += 1
+        Q = int(q.sum())
+        C = np.cumsum(q.astype(np.int64))
+        total = np.zeros(n_in, dtype=np.int64)
+        for u in range(Q):
+            rc, anc, off = orc.systematic(q, u, n_tickets=nt)
+            assert rc == 0
+            for j in range(nt):
+                pos = u + j * Q
+                assert anc[j] == next(i for i in range(n_in) if nt * int(C[i]) > pos)
+            total += off
+        assert np.array_equal(total, nt * q.astype(np.int64))
+
+
+@pytest.mark.parametrize("scheme", ["GS", "SGS", "LGS"])
+def test_two_stage_rpa(orc, scheme):
+    """Two-stage proportional allocation: stage 1 gives every group the same
+    number of offspring as one-stage RPA (so the same layout and routing);
+    stage 2 draws them inside the group, each particle getting the floor or
+    the ceiling of N_g q_i / Q_g; with one group it is the group's own
+    systematic draw."""
+    m = orc.Model(seed=5)
+    N = 3000
+    lw = weights(N, 2)
+    q = orc.quantise(lw).astype(np.int64)
+    one, two = getattr(orc, "RPA_" + scheme), getattr(orc, "RPA2_" + scheme)
+    for G in [1, 7, 64]:
+        goff = orc.balanced_offsets(N, G)
+        rc1, anc1, _, gout1, st1 = orc.resample(m, one, N, 4, goff, lw)
+        rc2, anc2, lwr2, gout2, st2 = orc.resample(m, two, N, 4, goff, lw)
+        assert rc1 == 0 and rc2 == 0
+        assert np.array_equal(gout1, gout2) and np.array_equal(st1, st2) and np.all(lwr2 == 0.0)
+        src1 = np.searchsorted(goff, anc1, side="right") - 1
+        src2 = np.searchsorted(goff, anc2, side="right") - 1
+        Ng = np.bincount(src1, minlength=G)
+        assert np.array_equal(Ng, np.bincount(src2, minlength=G))
+        off = np.bincount(anc2, minlength=N)
+        for g in range(G):
+            lo, hi = goff[g], goff[g + 1]
+            Qg = int(q[lo:hi].sum())
+            if Ng[g] == 0:
+                continue
+            exact = Ng[g] * q[lo:hi] / Qg
+            assert np.all(off[lo:hi] >= np.floor(exact) - 1e-9) and np.all(off[lo:hi] <= np.ceil(exact) + 1e-9)
+        if G == 1:
+            u = orc.ticket_offset(5, 0, 4, orc.PURPOSE_GROUP_RESAMPLE, 0, int(q.sum()))
+            rc, want, _ = orc.systematic(q.astype(np.uint64), u)
+            assert np.array_equal(anc2, want)
