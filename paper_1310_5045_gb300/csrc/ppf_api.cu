@@ -144,7 +144,10 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
     c->T = (int32_t)((n + TILE - 1) / TILE);
     c->stream = (cudaStream_t)stream;
     c->pad = 2 * m->patch_radius;
-    c->Wp = m->width + 2 * c->pad;
+    // row pitch: the padded width plus one zero column, rounded up to even
+    // (the frame is held twice, the second copy shifted left by one column,
+    // so that the patch sum can read aligned pixel pairs)
+    c->Wp = (m->width + 2 * c->pad + 2) & ~1;
     c->Hp = m->height + 2 * c->pad;
     c->frame_bytes = (size_t)m->width * m->height * dtype_size(m->frame_dtype);
     c->mode = MODE_CARRY;
@@ -167,7 +170,7 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
         chk(dalloc(&c->lwp, N), "lwp");
         chk(dalloc(&c->goff, G + 1), "goff");
         chk(dalloc(&c->goff_new, G + 1), "goff_new");
-        chk(dalloc(&c->Zp, (size_t)c->Wp * c->Hp), "Zp");
+        chk(dalloc(&c->Zp, 2 * (size_t)c->Wp * c->Hp), "Zp");
         chk(dalloc((char **)&c->frame_buf, c->frame_bytes), "frame_buf");
         c->n_part = c->num_sms > 0 ? ppf::step_grid(c) : 1;
         chk(dalloc(&c->part, c->n_part), "partials");

@@ -111,17 +111,26 @@ struct PatchGeom {
     const float *Kc;   // exp(-(2k+1) inv2s2), k = 0..R-1
 };
 
+// The anchor c = floor(x + 1/2), the PSF samples of the patch columns and
+// rows (zero outside the image) and C = sum gx^2 sum gy^2.  Returns false when
+// no patch sum is needed, with the log-likelihood in *l: -inf for a
+// non-finite particle, 0 for a patch entirely outside the image.
 template <int R>
-__device__ __forceinline__ float patch_loglik(const PatchGeom &a, float x, float y, float I0)
+__device__ __forceinline__ bool patch_setup(const PatchGeom &a, float x, float y, float I0, int &cx, int &cy,
+                                            float gx[2 * R + 1], float gy[2 * R + 1], float &C, float *l)
 {
-    if (!isfinite(x) || !isfinite(y) || !isfinite(I0))
-        return -INFINITY;
+    if (!isfinite(x) || !isfinite(y) || !isfinite(I0)) {
+        *l = -INFINITY;
+        return false;
+    }
     const float cxf = floorf(x + 0.5f), cyf = floorf(y + 0.5f);
-    if (cxf < -(float)R || cxf > (float)(a.W - 1 + R) || cyf < -(float)R || cyf > (float)(a.H - 1 + R))
-        return 0.0f;
-    const int cx = (int)cxf, cy = (int)cyf;
+    if (cxf < -(float)R || cxf > (float)(a.W - 1 + R) || cyf < -(float)R || cyf > (float)(a.H - 1 + R)) {
+        *l = 0.0f;
+        return false;
+    }
+    cx = (int)cxf;
+    cy = (int)cyf;
     constexpr int P = 2 * R + 1;
-    float gx[P], gy[P];
     gauss_samples<R>(cxf - x, a.inv2s2, a.Kc, gx);
     gauss_samples<R>(cyf - y, a.inv2s2, a.Kc, gy);
     if (cx < R || cx > a.W - 1 - R || cy < R || cy > a.H - 1 - R) {
@@ -138,6 +147,18 @@ __device__ __forceinline__ float patch_loglik(const PatchGeom &a, float x, float
         sxx = fmaf(gx[i], gx[i], sxx);
         syy = fmaf(gy[i], gy[i], syy);
     }
+    C = sxx * syy;
+    return true;
+}
+
+template <int R>
+__device__ __forceinline__ float patch_loglik(const PatchGeom &a, float x, float y, float I0)
+{
+    constexpr int P = 2 * R + 1;
+    int cx, cy;
+    float gx[P], gy[P], C, l;
+    if (!patch_setup<R>(a, x, y, I0, cx, cy, gx, gy, C, &l))
+        return l;
     const float *row = a.Zp + (int64_t)(cy - R + a.pad) * a.Wp + (cx - R + a.pad);
     float B = 0.0f;
 #pragma unroll
@@ -149,7 +170,45 @@ __device__ __forceinline__ float patch_loglik(const PatchGeom &a, float x, float
         B = fmaf(gy[j], rj, B);
         row += a.Wp;
     }
-    const float C = sxx * syy;
+    return I0 * fmaf(-0.5f * I0, C, B) * a.inv_sxi2;
+}
+
+// The same sum read two pixels at a time.  a.Zp is the padded frame with an
+// even row pitch a.Wp and Z1 the same frame shifted left by one column, so a
+// row segment starting at an even padded column is read from Z0 and one
+// starting at an odd column from Z1, always as aligned float2.  The products
+// are added in the same order as in patch_loglik, so both give identical
+// results.  The pitch must exceed the padded width by at least one column
+// (the last pair may read one column past the patch, which both planes hold
+// as zero).
+template <int R>
+__device__ __forceinline__ float patch_loglik_pairs(const PatchGeom &a, const float *__restrict__ Z1, float x, float y,
+                                                    float I0)
+{
+    const float *__restrict__ Z0 = a.Zp;
+    const int Wp2 = a.Wp;
+    constexpr int P = 2 * R + 1;
+    int cx, cy;
+    float gx[P], gy[P], C, l;
+    if (!patch_setup<R>(a, x, y, I0, cx, cy, gx, gy, C, &l))
+        return l;
+    const int col = cx - R + a.pad;
+    const float *base = (col & 1) ? Z1 + (col - 1) : Z0 + col;
+    const float2 *row = reinterpret_cast<const float2 *>(base + (int64_t)(cy - R + a.pad) * Wp2);
+    float B = 0.0f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        float rj = 0.0f;
+#pragma unroll
+        for (int k = 0; k < (P + 1) / 2; ++k) {
+            const float2 z = __ldg(row + k);
+            rj = fmaf(gx[2 * k], z.x, rj);
+            if (2 * k + 1 < P)
+                rj = fmaf(gx[2 * k + 1], z.y, rj);
+        }
+        B = fmaf(gy[j], rj, B);
+        row += Wp2 / 2;
+    }
     return I0 * fmaf(-0.5f * I0, C, B) * a.inv_sxi2;
 }
 

@@ -47,20 +47,23 @@ template <typename T>
 __global__ void prepare_frame_kernel(const T *__restrict__ Z, float *__restrict__ Zp, int W, int H, int Wp,
                                      int Hp, int pad, float bg)
 {
+    // plane 0: Z - bg with a zero border of `pad` (row pitch Wp); plane 1:
+    // the same shifted left by one column
     const int n = Wp * Hp;
+    auto px_at = [&](int py, int px) -> float {
+        return (px >= 0 && px < W && py >= 0 && py < H) ? to_f32<T>(Z[(int64_t)py * W + px]) - bg : 0.0f;
+    };
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         const int py = idx / Wp - pad, px = idx % Wp - pad;
-        float v = 0.0f;
-        if (px >= 0 && px < W && py >= 0 && py < H)
-            v = to_f32<T>(Z[(int64_t)py * W + px]) - bg;
-        Zp[idx] = v;
+        Zp[idx] = px_at(py, px);
+        Zp[n + idx] = px_at(py, px + 1);
     }
 }
 
 // ------------------------------------------------------------ the SIS step
 struct StepArgs {
     int64_t N;
-    int W, H, Wp, pad;
+    int W, H, Wp, Hp, pad;
     float inv2s2;      // 1 / (2 sigma_PSF^2)
     float Kc[MAX_RADIUS];  // exp(-(2k+1) / (2 sigma_PSF^2)), k = 0..R-1
     float inv_sxi2;    // 1 / sigma_xi^2
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
         v[2] = fmaf(a.sv, e2, vx);
         v[3] = fmaf(a.sv, e3, vy);
         v[4] = fmaf(a.sI, e4, I0);
-        const float l = patch_loglik<R>(geom, v[0], v[1], v[4]);
+        const float l = patch_loglik_pairs<R>(geom, a.Zp + (size_t)a.Wp * a.Hp, v[0], v[1], v[4]);
         const float lw = lwp + l;
 #pragma unroll
         for (int c = 0; c < 5; ++c)
@@ -312,6 +315,7 @@ cudaError_t launch_step(ppf_ctx *c, int32_t k)
     a.W = c->m.width;
     a.H = c->m.height;
     a.Wp = c->Wp;
+    a.Hp = c->Hp;
     a.pad = c->pad;
     a.inv2s2 = 1.0f / (2.0f * c->m.psf_sigma * c->m.psf_sigma);
     for (int k = 0; k < MAX_RADIUS; ++k)
