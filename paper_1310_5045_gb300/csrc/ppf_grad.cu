@@ -22,7 +22,7 @@ namespace ppf {
 
 struct GradArgs {
     int64_t N;
-    int W, H, Wp, pad;
+    int W, H, Wp, Hp, pad;
     float sigma, inv2s2, inv_sxi2, A, sm, sv;
     float Kc[MAX_RADIUS];
     uint64_t seed;
@@ -34,7 +34,7 @@ struct GradArgs {
     float *__restrict__ tdst;
     const int32_t *__restrict__ anc;
     const int32_t *__restrict__ degenerate;  // last resample kept every particle
-    const float *__restrict__ Zp;
+    const float *__restrict__ Zp;    // prepared frame: plane 0, then plane 1 shifted left by one column
     int32_t *__restrict__ anchors;   // optional 2 x N export (cx, cy)
     GradPartial *__restrict__ part;
     unsigned int *done;
@@ -111,25 +111,41 @@ __device__ __forceinline__ void grad_patch(const GradArgs &a, float x, float y, 
         Gx += gx[i];
         Gy += gy[i];
     }
-    const float *row = a.Zp + (int64_t)(cy - R + a.pad) * a.Wp + (cx - R + a.pad);
+    // per-column weights gx, gx dx, gx dx^2; the row sums read pixel pairs
+    // from the two column-shifted frame planes (aligned float2)
+    float w0[P], w1[P], w2[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        const float dx = fx + (float)(i - R);
+        w0[i] = gx[i];
+        w1[i] = gx[i] * dx;
+        w2[i] = w1[i] * dx;
+    }
+    const int col = cx - R + a.pad;
+    const float *base = (col & 1) ? a.Zp + (int64_t)a.Wp * a.Hp + (col - 1) : a.Zp + col;
+    const float2 *row = reinterpret_cast<const float2 *>(base + (int64_t)(cy - R + a.pad) * a.Wp);
     float B = 0, By1 = 0, Bx1 = 0, Bs = 0;
 #pragma unroll
     for (int j = 0; j < P; ++j) {
         float r0 = 0, r1 = 0, r2 = 0;
 #pragma unroll
-        for (int i = 0; i < P; ++i) {
-            const float dx = fx + (float)(i - R);
-            const float gz = gx[i] * __ldg(row + i);
-            r0 += gz;
-            r1 = fmaf(gz, dx, r1);
-            r2 = fmaf(gz * dx, dx, r2);
+        for (int k = 0; k < (P + 1) / 2; ++k) {
+            const float2 z = __ldg(row + k);
+            r0 = fmaf(w0[2 * k], z.x, r0);
+            r1 = fmaf(w1[2 * k], z.x, r1);
+            r2 = fmaf(w2[2 * k], z.x, r2);
+            if (2 * k + 1 < P) {
+                r0 = fmaf(w0[2 * k + 1], z.y, r0);
+                r1 = fmaf(w1[2 * k + 1], z.y, r1);
+                r2 = fmaf(w2[2 * k + 1], z.y, r2);
+            }
         }
         const float dy = fy + (float)(j - R);
         B = fmaf(gy[j], r0, B);
         By1 = fmaf(gy[j] * dy, r0, By1);
         Bx1 = fmaf(gy[j], r1, Bx1);
         Bs = fmaf(gy[j], fmaf(dy * dy, r0, r2), Bs);
-        row += a.Wp;
+        row += a.Wp / 2;
     }
     const float C = Sx0 * Sy0;
     const float k2 = I0 * a.inv_sxi2 * a.inv2s2 * 2.0f;  // I0 / (sxi^2 s^2)
@@ -341,6 +357,7 @@ cudaError_t launch_grad_step(ppf_ctx *c, int32_t k, bool first, int32_t *anchors
     a.W = c->m.width;
     a.H = c->m.height;
     a.Wp = c->Wp;
+    a.Hp = c->Hp;
     a.pad = c->pad;
     a.sigma = c->m.psf_sigma;
     a.inv2s2 = 1.0f / (2.0f * c->m.psf_sigma * c->m.psf_sigma);
