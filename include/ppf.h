@@ -121,9 +121,13 @@ void ppf_destroy(ppf_ctx *ctx);
  * (pure SIS).  Errors: PPF_EINVAL (NULL frame, k < 1), PPF_ECUDA. */
 ppf_status ppf_step(ppf_ctx *ctx, const void *frame_dev, int32_t k);
 
-/* ppf_step for a frame in host memory: the frame is copied into a
- * library-owned device buffer on the context's stream first (pinned memory
- * makes that copy asynchronous). */
+/* ppf_step for a frame in host memory (H x W of model.frame_dtype).  The
+ * frame is copied into one of two library-owned device buffers on a second,
+ * library-owned stream, so that the copy of one frame overlaps the kernels of
+ * the previous one; the step waits for its copy.  With page-locked memory the
+ * call returns before the copy has run and frame_host must stay valid until
+ * the context's stream has run the step; with pageable memory the copy is
+ * synchronous.  Not for stream capture (the copy stream is not captured). */
 ppf_status ppf_step_host(ppf_ctx *ctx, const void *frame_host, int32_t k);
 
 /* The resampling step of Alg. 1 on the weights of the last step, using the
@@ -155,6 +159,16 @@ ppf_status ppf_resample_if(ppf_ctx *ctx, ppf_scheme scheme, float exchange_ratio
  * schedule (the values are still filled in; the flags are then cleared), and
  * PPF_ESTATE before the first step. */
 ppf_status ppf_estimate(ppf_ctx *ctx, ppf_estimate_t *out);
+
+/* ppf_estimate without waiting: enqueues, on the context's stream, a copy of
+ * the same fields into out_host and returns.  out_host must be host memory
+ * the device can write (page-locked or registered) and must stay valid until
+ * the stream has run the copy; read it after synchronising the stream.  The
+ * device flags are reported in status_flags but not cleared (ppf_estimate
+ * clears them).  This lets a caller read every frame's result while the
+ * next frames are already queued.
+ * Errors: PPF_EINVAL (NULL), PPF_ESTATE before the first step, PPF_ECUDA. */
+ppf_status ppf_estimate_async(ppf_ctx *ctx, ppf_estimate_t *out_host);
 
 /* Copies the current particles (those of the last step, or the initial ones)
  * into caller-owned device buffers, each optional (NULL = skip):

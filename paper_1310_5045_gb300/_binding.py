@@ -22,7 +22,7 @@ SCHEMES = {"systematic": SYSTEMATIC, "rpa_gs": RPA_GS, "rpa_sgs": RPA_SGS, "rpa_
            "rpa2_gs": RPA2_GS, "rpa2_sgs": RPA2_SGS, "rpa2_lgs": RPA2_LGS}
 
 EXPORTS = ["ppf_create", "ppf_destroy", "ppf_step", "ppf_step_host", "ppf_resample", "ppf_resample_if",
-           "ppf_estimate",
+           "ppf_estimate", "ppf_estimate_async",
            "ppf_get_particles", "ppf_set_particles", "ppf_get_groups", "ppf_status_string",
            "ppf_last_error", "ppf_profile_enable", "ppf_profile_read", "ppf_systematic_resample_noalloc",
            "ppf_loglik_grad", "ppf_batch_create", "ppf_batch_destroy", "ppf_batch_step", "ppf_batch_resample",
@@ -108,6 +108,19 @@ class Estimate:
     min_group: int
     status: int = OK
 
+    @staticmethod
+    def nbytes() -> int:
+        """Size of the buffer ParticleFilter.estimate_async writes."""
+        return C.sizeof(_Estimate)
+
+    @staticmethod
+    def from_buffer(buf) -> "Estimate":
+        """Decode a buffer written by ParticleFilter.estimate_async (after the
+        stream has run the copy)."""
+        e = _Estimate.from_buffer_copy(bytes(buf.numpy().tobytes()) if hasattr(buf, "numpy") else bytes(buf))
+        return Estimate(tuple(e.mean), e.log_evidence, e.ess, e.max_log_weight, e.frame, e.status_flags,
+                        e.links, e.moved, e.max_group, e.min_group, OK)
+
 
 _lib = None
 _lock = threading.Lock()
@@ -138,6 +151,7 @@ def load(build_if_missing: bool = True):
             "ppf_resample": (C.c_int, [ctxp, C.c_int, C.c_float]),
             "ppf_resample_if": (C.c_int, [ctxp, C.c_int, C.c_float, C.c_double]),
             "ppf_estimate": (C.c_int, [ctxp, P(_Estimate)]),
+            "ppf_estimate_async": (C.c_int, [ctxp, vp]),
             "ppf_get_particles": (C.c_int, [ctxp, vp, vp, vp]),
             "ppf_set_particles": (C.c_int, [ctxp, vp, vp, vp]),
             "ppf_get_groups": (C.c_int, [ctxp, P(C.c_int32), vp]),
@@ -272,6 +286,16 @@ class ParticleFilter:
             self._check(st, "ppf_estimate")
         return Estimate(tuple(e.mean), e.log_evidence, e.ess, e.max_log_weight, e.frame, e.status_flags,
                         e.links, e.moved, e.max_group, e.min_group, st)
+
+    def estimate_async(self, out=None):
+        """Enqueue a copy of the estimate into `out` (a page-locked uint8
+        tensor of the estimate's size, made when None) and return it without
+        waiting; decode with Estimate.from_buffer once the stream has run."""
+        torch = self._torch
+        if out is None:
+            out = torch.empty(C.sizeof(_Estimate), dtype=torch.uint8, pin_memory=True)
+        self._check(self.L.ppf_estimate_async(self._ctx, C.c_void_p(out.data_ptr())), "ppf_estimate_async")
+        return out
 
     def get_particles(self, state=True, anc=False, lw_prev=False):
         torch = self._torch

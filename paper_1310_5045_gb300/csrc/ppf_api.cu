@@ -59,7 +59,7 @@ void free_all(ppf_ctx *c)
 {
     void *ptrs[] = {c->tang[0], c->tang[1], c->gpart,
                     c->state[0], c->state[1], c->anc, c->anc_sys, c->lwp, c->goff, c->goff_new, c->Zp,
-                    c->frame_buf, c->part, c->sum, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sc.Cbl,
+                    c->frame_buf[0], c->frame_buf[1], c->part, c->sum, c->est_dev, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sc.Cbl,
                     c->sc.Tg, c->sc.skey, c->sc.sval, c->sc.seg_tick, c->sc.seg_dst, c->sc.seg_len,
                     c->sc.seg_chunk};
     for (void *p : ptrs)
@@ -171,10 +171,12 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
         chk(dalloc(&c->goff, G + 1), "goff");
         chk(dalloc(&c->goff_new, G + 1), "goff_new");
         chk(dalloc(&c->Zp, 2 * (size_t)c->Wp * c->Hp), "Zp");
-        chk(dalloc((char **)&c->frame_buf, c->frame_bytes), "frame_buf");
+        chk(dalloc((char **)&c->frame_buf[0], c->frame_bytes), "frame_buf");
+        chk(dalloc((char **)&c->frame_buf[1], c->frame_bytes), "frame_buf");
         c->n_part = c->num_sms > 0 ? ppf::step_grid(c) : 1;
         chk(dalloc(&c->part, c->n_part), "partials");
         chk(dalloc(&c->sum, 1), "summary");
+        chk(dalloc(&c->est_dev, 1), "estimate staging");
         chk(dalloc(&c->sc.Qt, T), "Qt");
         chk(dalloc(&c->sc.Ct, T + 1), "Ct");
         chk(dalloc(&c->sc.Tt, T + 1), "Tt");
@@ -225,6 +227,14 @@ void ppf_destroy(ppf_ctx *c)
     if (!c)
         return;
     cudaStreamSynchronize(c->stream);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        for (int b = 0; b < 2; ++b) {
+            cudaEventDestroy(c->fb_copied[b]);
+            cudaEventDestroy(c->fb_free[b]);
+        }
+        cudaStreamDestroy(c->copy_stream);
+    }
     free_all(c);
     delete c;
 }
@@ -248,13 +258,32 @@ ppf_status ppf_step(ppf_ctx *c, const void *frame_dev, int32_t k)
     return PPF_OK;
 }
 
+// The frame is copied on a second stream into one of two device buffers, so
+// the copy of frame k+1 overlaps the kernels of frame k: the step waits for
+// its copy (event), and a buffer is refilled only after the step that read it.
 ppf_status ppf_step_host(ppf_ctx *c, const void *frame_host, int32_t k)
 {
     if (!c || !frame_host || k < 1)
         return PPF_EINVAL;
-    CK(cudaMemcpyAsync(c->frame_buf, frame_host, c->frame_bytes, cudaMemcpyHostToDevice, c->stream));
+    if (!c->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            CK(cudaEventCreateWithFlags(&c->fb_copied[b], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&c->fb_free[b], cudaEventDisableTiming));
+        }
+    }
+    const int b = c->fb_next;
+    if (c->fb_used[b])
+        CK(cudaStreamWaitEvent(c->copy_stream, c->fb_free[b], 0));
+    CK(cudaMemcpyAsync(c->frame_buf[b], frame_host, c->frame_bytes, cudaMemcpyHostToDevice, c->copy_stream));
+    CK(cudaEventRecord(c->fb_copied[b], c->copy_stream));
+    CK(cudaStreamWaitEvent(c->stream, c->fb_copied[b], 0));
     c->h2d_bytes += (int64_t)c->frame_bytes;
-    return ppf_step(c, c->frame_buf, k);
+    const ppf_status st = ppf_step(c, c->frame_buf[b], k);
+    CK(cudaEventRecord(c->fb_free[b], c->stream));
+    c->fb_used[b] = true;
+    c->fb_next = b ^ 1;
+    return st;
 }
 
 ppf_status ppf_resample(ppf_ctx *c, ppf_scheme scheme, float alpha)
@@ -335,6 +364,18 @@ ppf_status ppf_estimate(ppf_ctx *c, ppf_estimate_t *out)
             return PPF_ETIMEOUT;
     }
     return PPF_OK;  // FLAG_KEPT (N_eff test) is information, not an error
+}
+
+ppf_status ppf_estimate_async(ppf_ctx *c, ppf_estimate_t *out)
+{
+    if (!c || !out)
+        return PPF_EINVAL;
+    if (!c->stepped)
+        return PPF_ESTATE;
+    CK(ppf::launch_format_estimate(c));
+    CK(cudaMemcpyAsync(out, c->est_dev, sizeof(ppf_estimate_t), cudaMemcpyDeviceToHost, c->stream));
+    c->d2h_bytes += (int64_t)sizeof(ppf_estimate_t);
+    return PPF_OK;
 }
 
 ppf_status ppf_get_particles(ppf_ctx *c, float *state_dev, int32_t *anc_dev, float *lwp_dev)

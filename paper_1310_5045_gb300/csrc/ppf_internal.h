@@ -93,7 +93,11 @@ struct ppf_ctx {
     int64_t *goff, *goff_new;     // group offsets [G+1]
     float *Zp;                    // padded frame minus background
     int32_t Wp, Hp, pad;
-    void *frame_buf;              // device copy for ppf_step_host
+    void *frame_buf[2];           // device copies for ppf_step_host (double-buffered)
+    int fb_next;                  // buffer the next ppf_step_host fills
+    bool fb_used[2];
+    cudaStream_t copy_stream;     // host-to-device frame copies, overlapping the previous frame
+    cudaEvent_t fb_copied[2], fb_free[2];
     size_t frame_bytes;
     ppf::Partial *part;
     int n_part;
@@ -102,6 +106,7 @@ struct ppf_ctx {
     ppf::GradPartial *gpart;
     ppf::DevSummary *sum;
     ppf::DevSummary *sum_host;    // pinned mirror for ppf_estimate
+    ppf_estimate_t *est_dev;      // device staging of ppf_estimate_async
     ppf::Scratch sc;
     int mode;                     // StepMode of the next step
     bool stepped;                 // at least one step since create/set
@@ -131,5 +136,6 @@ cudaError_t launch_resample_rna(ppf_ctx *c, float alpha, double ess_thr);
 cudaError_t launch_identity(ppf_ctx *c, int32_t *dst);
 cudaError_t launch_pending(ppf_ctx *c, int32_t *anc_out, float *lwp_out);
 cudaError_t launch_fill_f32(ppf_ctx *c, float *dst, float v);
+cudaError_t launch_format_estimate(ppf_ctx *c);
 int step_grid(ppf_ctx *c);
 }  // namespace ppf

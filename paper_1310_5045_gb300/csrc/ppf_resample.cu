@@ -977,6 +977,31 @@ cudaError_t launch_identity(ppf_ctx *c, int32_t *dst)
     return cudaGetLastError();
 }
 
+// the ppf_estimate_t fields of the device summary (for ppf_estimate_async)
+__global__ void format_estimate_kernel(const DevSummary *__restrict__ sum, ppf_estimate_t *__restrict__ out)
+{
+    ppf_estimate_t e;
+    for (int i = 0; i < 5; ++i)
+        e.mean[i] = sum->mean[i];
+    e.log_evidence = sum->log_evidence;
+    e.ess = sum->ess;
+    e.max_log_weight = sum->max_lw;
+    e.frame = sum->frame;
+    e.status_flags = sum->flags;
+    e.links = sum->links;
+    e.moved = sum->moved;
+    e.max_group = sum->max_group;
+    e.min_group = sum->min_group;
+    *out = e;
+}
+
+cudaError_t launch_format_estimate(ppf_ctx *c)
+{
+    format_estimate_kernel<<<1, 1, 0, c->stream>>>(c->sum, c->est_dev);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill_f32(ppf_ctx *c, float *dst, float v)
 {
     const int grid = (int)((c->N + 255) / 256 < 8192 ? (c->N + 255) / 256 : 8192);

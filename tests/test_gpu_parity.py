@@ -172,6 +172,58 @@ def test_degenerate_weights_keep_particles(ppf, movie):
     pf.close()
 
 
+def test_step_host_matches_device_frames(ppf, movie):
+    """Host frames (page-locked, double-buffered copies overlapping the
+    previous frame; then one pageable frame) give bit-identical particles to
+    device frames."""
+    import torch
+    from gpu_common import paired_models
+    gm, _ = paired_models(ppf, seed=6)
+    fr = gpu_frames(movie)
+    host = torch.from_numpy(movie.frames).pin_memory()
+    a = ppf.ParticleFilter(gm, 20000, group_size=4096)
+    b = ppf.ParticleFilter(gm, 20000, group_size=4096)
+    for k in range(1, 6):
+        a.step_host(host[k - 1] if k < 5 else torch.from_numpy(movie.frames[k - 1].copy()), k)
+        a.resample(ppf.SYSTEMATIC)
+        b.step(fr[k - 1], k)
+        b.resample(ppf.SYSTEMATIC)
+    sa, aa, _ = a.get_particles(state=True, anc=True)
+    sb, ab, _ = b.get_particles(state=True, anc=True)
+    assert torch.equal(sa, sb) and torch.equal(aa, ab)
+    a.close()
+    b.close()
+
+
+def test_estimate_async_matches_estimate(ppf, movie):
+    """Queued estimate copies (one per frame, read after the last frame) equal
+    the synchronous estimates of the same frames."""
+    import torch
+    from gpu_common import paired_models
+    gm, _ = paired_models(ppf, seed=2)
+    fr = gpu_frames(movie)
+    a = ppf.ParticleFilter(gm, 5000, group_size=1000)
+    b = ppf.ParticleFilter(gm, 5000, group_size=1000)
+    slots = torch.empty((4, ppf.Estimate.nbytes()), dtype=torch.uint8).pin_memory()
+    want = []
+    for k in range(1, 5):
+        a.step(fr[k - 1], k)
+        a.resample(ppf.RPA_SGS)
+        a.estimate_async(slots[k - 1])
+        b.step(fr[k - 1], k)
+        b.resample(ppf.RPA_SGS)
+        want.append(b.estimate())
+    a.stream.synchronize()
+    for k in range(4):
+        got = ppf.Estimate.from_buffer(slots[k])
+        w = want[k]
+        assert got.frame == w.frame == k + 1
+        assert got.mean == w.mean and got.ess == w.ess and got.log_evidence == w.log_evidence
+        assert (got.links, got.moved, got.max_group, got.min_group) == (w.links, w.moved, w.max_group, w.min_group)
+    a.close()
+    b.close()
+
+
 def test_state_errors(ppf):
     from gpu_common import paired_models
     gm, _ = paired_models(ppf)
