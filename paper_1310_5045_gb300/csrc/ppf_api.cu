@@ -144,10 +144,10 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
     c->T = (int32_t)((n + TILE - 1) / TILE);
     c->stream = (cudaStream_t)stream;
     c->pad = 2 * m->patch_radius;
-    // row pitch: the padded width plus one zero column, rounded up to even
-    // (the frame is held twice, the second copy shifted left by one column,
-    // so that the patch sum can read aligned pixel pairs)
-    c->Wp = (m->width + 2 * c->pad + 2) & ~1;
+    // row pitch (in pixel pairs): the padded width plus one zero column (the
+    // frame is held as pairs (Z(col), Z(col + 1)), so that the patch sum reads
+    // aligned pixel pairs)
+    c->Wp = m->width + 2 * c->pad + 1;
     c->Hp = m->height + 2 * c->pad;
     c->frame_bytes = (size_t)m->width * m->height * dtype_size(m->frame_dtype);
     c->mode = MODE_CARRY;

@@ -34,7 +34,7 @@ struct GradArgs {
     float *__restrict__ tdst;
     const int32_t *__restrict__ anc;
     const int32_t *__restrict__ degenerate;  // last resample kept every particle
-    const float *__restrict__ Zp;    // prepared frame: plane 0, then plane 1 shifted left by one column
+    const float *__restrict__ Zp;    // prepared frame as pixel pairs (float2, row pitch Wp)
     int32_t *__restrict__ anchors;   // optional 2 x N export (cx, cy)
     GradPartial *__restrict__ part;
     unsigned int *done;
@@ -111,8 +111,8 @@ __device__ __forceinline__ void grad_patch(const GradArgs &a, float x, float y, 
         Gx += gx[i];
         Gy += gy[i];
     }
-    // per-column weights gx, gx dx, gx dx^2; the row sums read pixel pairs
-    // from the two column-shifted frame planes (aligned float2)
+    // per-column weights gx, gx dx, gx dx^2; the row sums read the frame as
+    // pixel pairs (one aligned float2 per two columns)
     float w0[P], w1[P], w2[P];
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -121,16 +121,15 @@ __device__ __forceinline__ void grad_patch(const GradArgs &a, float x, float y, 
         w1[i] = gx[i] * dx;
         w2[i] = w1[i] * dx;
     }
-    const int col = cx - R + a.pad;
-    const float *base = (col & 1) ? a.Zp + (int64_t)a.Wp * a.Hp + (col - 1) : a.Zp + col;
-    const float2 *row = reinterpret_cast<const float2 *>(base + (int64_t)(cy - R + a.pad) * a.Wp);
+    const float2 *row = reinterpret_cast<const float2 *>(a.Zp) + (int64_t)(cy - R + a.pad) * a.Wp +
+                        (cx - R + a.pad);
     float B = 0, By1 = 0, Bx1 = 0, Bs = 0;
 #pragma unroll
     for (int j = 0; j < P; ++j) {
         float r0 = 0, r1 = 0, r2 = 0;
 #pragma unroll
         for (int k = 0; k < (P + 1) / 2; ++k) {
-            const float2 z = __ldg(row + k);
+            const float2 z = __ldg(row + 2 * k);
             r0 = fmaf(w0[2 * k], z.x, r0);
             r1 = fmaf(w1[2 * k], z.x, r1);
             r2 = fmaf(w2[2 * k], z.x, r2);
@@ -145,7 +144,7 @@ __device__ __forceinline__ void grad_patch(const GradArgs &a, float x, float y, 
         By1 = fmaf(gy[j] * dy, r0, By1);
         Bx1 = fmaf(gy[j], r1, Bx1);
         Bs = fmaf(gy[j], fmaf(dy * dy, r0, r2), Bs);
-        row += a.Wp / 2;
+        row += a.Wp;
     }
     const float C = Sx0 * Sy0;
     const float k2 = I0 * a.inv_sxi2 * a.inv2s2 * 2.0f;  // I0 / (sxi^2 s^2)

@@ -173,41 +173,37 @@ __device__ __forceinline__ float patch_loglik(const PatchGeom &a, float x, float
     return I0 * fmaf(-0.5f * I0, C, B) * a.inv_sxi2;
 }
 
-// The same sum read two pixels at a time.  a.Zp is the padded frame with an
-// even row pitch a.Wp and Z1 the same frame shifted left by one column, so a
-// row segment starting at an even padded column is read from Z0 and one
-// starting at an odd column from Z1, always as aligned float2.  The products
-// are added in the same order as in patch_loglik, so both give identical
-// results.  The pitch must exceed the padded width by at least one column
-// (the last pair may read one column past the patch, which both planes hold
-// as zero).
+// The same sum read two pixels at a time.  Here a.Zp holds the prepared
+// frame interleaved as pixel pairs: element (row, col) of the float2 array
+// (row pitch a.Wp) is (Z(row, col), Z(row, col + 1)), so the pair starting at
+// any column is one aligned float2 load, and the lanes of a warp whose
+// patches start at neighbouring columns read neighbouring words.  The
+// products are added in the same order as in patch_loglik, so both give
+// identical results.  The pitch exceeds the padded width by at least one
+// column (the last pair may read one column past the patch, which is zero).
 template <int R>
-__device__ __forceinline__ float patch_loglik_pairs(const PatchGeom &a, const float *__restrict__ Z1, float x, float y,
-                                                    float I0)
+__device__ __forceinline__ float patch_loglik_pairs(const PatchGeom &a, float x, float y, float I0)
 {
-    const float *__restrict__ Z0 = a.Zp;
-    const int Wp2 = a.Wp;
     constexpr int P = 2 * R + 1;
     int cx, cy;
     float gx[P], gy[P], C, l;
     if (!patch_setup<R>(a, x, y, I0, cx, cy, gx, gy, C, &l))
         return l;
-    const int col = cx - R + a.pad;
-    const float *base = (col & 1) ? Z1 + (col - 1) : Z0 + col;
-    const float2 *row = reinterpret_cast<const float2 *>(base + (int64_t)(cy - R + a.pad) * Wp2);
+    const float2 *row = reinterpret_cast<const float2 *>(a.Zp) + (int64_t)(cy - R + a.pad) * a.Wp +
+                        (cx - R + a.pad);
     float B = 0.0f;
 #pragma unroll
     for (int j = 0; j < P; ++j) {
         float rj = 0.0f;
 #pragma unroll
         for (int k = 0; k < (P + 1) / 2; ++k) {
-            const float2 z = __ldg(row + k);
+            const float2 z = __ldg(row + 2 * k);
             rj = fmaf(gx[2 * k], z.x, rj);
             if (2 * k + 1 < P)
                 rj = fmaf(gx[2 * k + 1], z.y, rj);
         }
         B = fmaf(gy[j], rj, B);
-        row += Wp2 / 2;
+        row += a.Wp;
     }
     return I0 * fmaf(-0.5f * I0, C, B) * a.inv_sxi2;
 }

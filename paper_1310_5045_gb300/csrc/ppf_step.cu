@@ -47,16 +47,16 @@ template <typename T>
 __global__ void prepare_frame_kernel(const T *__restrict__ Z, float *__restrict__ Zp, int W, int H, int Wp,
                                      int Hp, int pad, float bg)
 {
-    // plane 0: Z - bg with a zero border of `pad` (row pitch Wp); plane 1:
-    // the same shifted left by one column
+    // pixel pairs: element (row, col) = (Zb(row, col), Zb(row, col + 1)) with
+    // Zb = Z - bg inside the image and 0 in the border of `pad` (pitch Wp)
     const int n = Wp * Hp;
     auto px_at = [&](int py, int px) -> float {
         return (px >= 0 && px < W && py >= 0 && py < H) ? to_f32<T>(Z[(int64_t)py * W + px]) - bg : 0.0f;
     };
+    float2 *__restrict__ out = reinterpret_cast<float2 *>(Zp);
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         const int py = idx / Wp - pad, px = idx % Wp - pad;
-        Zp[idx] = px_at(py, px);
-        Zp[n + idx] = px_at(py, px + 1);
+        out[idx] = make_float2(px_at(py, px), px_at(py, px + 1));
     }
 }
 
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
         v[2] = fmaf(a.sv, e2, vx);
         v[3] = fmaf(a.sv, e3, vy);
         v[4] = fmaf(a.sI, e4, I0);
-        const float l = patch_loglik_pairs<R>(geom, a.Zp + (size_t)a.Wp * a.Hp, v[0], v[1], v[4]);
+        const float l = patch_loglik_pairs<R>(geom, v[0], v[1], v[4]);
         const float lw = lwp + l;
 #pragma unroll
         for (int c = 0; c < 5; ++c)
