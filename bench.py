@@ -39,7 +39,7 @@ STEP_BYTES = 48
 # measured DRAM bytes per particle of the same kernel (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum, 10th launch at N = 16M, profiles/step_kernel_spot512_n16m.md),
 # scaled to a launch by N; set to None whenever step_kernel changes
-STEP_TRAFFIC_PER_PARTICLE = (351.81e6 + 340.74e6) / 16e6
+STEP_TRAFFIC_PER_PARTICLE = (351.87e6 + 341.22e6) / 16e6
 # algorithmic FP32 flops per particle of the likelihood + propagation (an FMA
 # counts 2): bilinear form 2P^2, row combination 2P, sums of squares 4P, final
 # combination 6, propagation 10, with P = 2r + 1
