@@ -55,23 +55,6 @@ __device__ __forceinline__ uint64_t tile_scan(const uint64_t q[TILE_ITEMS], uint
     return total;
 }
 
-// floor(v / d), v mod d for v < 2^52, d < 2^32: float estimate, exact fix-up
-__device__ __forceinline__ uint64_t div_small(uint64_t v, uint32_t d, float rd, uint32_t *rem)
-{
-    uint64_t q = (uint64_t)((float)v * rd);
-    int64_t r = (int64_t)v - (int64_t)(q * d);
-    while (r < 0) {
-        --q;
-        r += d;
-    }
-    while (r >= (int64_t)d) {
-        ++q;
-        r -= d;
-    }
-    *rem = (uint32_t)r;
-    return q;
-}
-
 // floor(x / d) for a fixed divisor d >= 1 and any x < 2^64, from the
 // precomputed m = floor((2^64 - 1) / d): the product estimate floor(x m / 2^64)
 // lies within 2 below the quotient and never above it.
@@ -134,65 +117,74 @@ __device__ __forceinline__ TicketGrid ticket_grid(uint64_t Q, uint64_t u, uint64
 // its piece, advancing either the particle or the ticket at every step.  Every
 // thread does the same number of steps whatever the weights.
 // emit(j, i) receives every (ticket, parent), a thread's tickets in
-// increasing order.  Called by every thread of the block; contains barriers.
+// increasing order.  L <= STAGE_TICKETS (so the ticket offsets within the run
+// and the merge positions fit 32 bits).  Called by every thread of the block;
+// contains barriers.
 template <typename Emit>
 __device__ __forceinline__ void ticket_parents(const uint64_t *C, int n, uint64_t c0, const TicketGrid &tg,
-                                               int64_t j_lo, int64_t j_hi, Emit emit)
+                                               int64_t j_lo, int L, Emit emit)
 {
     __shared__ uint64_t s_thr;
     __shared__ uint32_t s_rem;
     const uint32_t nt = tg.nt.d;
     const uint64_t qN = tg.qN;
     const uint32_t qR = tg.qR;
-    // threshold and remainder of ticket j (j < nt < 2^31): u + j qR < 2^63 + 2^62
-    auto thr_of = [&](int64_t j, uint32_t *rem) -> uint64_t {
-        return (uint64_t)j * qN + div_by(tg.u + (uint64_t)j * qR, tg.nt, rem);
-    };
     __syncthreads();
     if (threadIdx.x == 0) {
+        // threshold and remainder of ticket j_lo (j_lo < nt < 2^31, so
+        // u + j_lo qR < 2^63 + 2^62)
         uint32_t r0;
-        s_thr = thr_of(j_lo, &r0);
+        s_thr = (uint64_t)j_lo * qN + div_by(tg.u + (uint64_t)j_lo * qR, tg.nt, &r0);
         s_rem = r0;
     }
     __syncthreads();
-    const int64_t L = j_hi - j_lo;
-    const int64_t D = (int64_t)n + L;
-    const int64_t K = (D + blockDim.x - 1) / blockDim.x;
-    const int64_t d0 = (int64_t)threadIdx.x * K;
+    const int D = n + L;
+    const int K = (D + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int d0 = (int)threadIdx.x * K;
     if (L <= 0 || d0 >= D)
         return;
-    const uint64_t thr0 = s_thr;
+    // the run's first ticket has thr >= c0 (it is not below the run)
+    const uint64_t lt0 = s_thr - c0;
     const uint32_t rem0 = s_rem;
-    const float rnt = 1.0f / (float)nt;
-    // thr_{j_lo + b} - c0 and rem_{j_lo + b}
-    auto lt_at = [&](int64_t b, uint32_t *rem) -> uint64_t {
-        uint64_t t;
-        if (b < (1 << 21))  // quotient < 2^21: the float estimate is off by at most 1
-            t = thr0 + (uint64_t)b * qN + div_small((uint64_t)rem0 + (uint64_t)b * qR, nt, rnt, rem);
-        else
-            t = thr_of(j_lo + b, rem);
-        return t - c0;
+    const float frem0 = (float)rem0, fqR = (float)qR, rnt = 1.0f / (float)nt;
+    // thr_{j_lo + b} - c0 and rem_{j_lo + b}: with v = rem0 + b qR the step
+    // past lt0 is b qN + floor(v / nt); the quotient is at most b + 1 <= 2^14,
+    // so its float estimate is off by at most one
+    auto lt_at = [&](int b, uint32_t *rem) -> uint64_t {
+        const int64_t v = (int64_t)rem0 + (int64_t)b * qR;
+        int64_t q = (int64_t)(fmaf((float)b, fqR, frem0) * rnt);
+        int64_t r = v - q * (int64_t)nt;
+        while (r < 0) {
+            --q;
+            r += nt;
+        }
+        while (r >= (int64_t)nt) {
+            ++q;
+            r -= nt;
+        }
+        *rem = (uint32_t)r;
+        return lt0 + (uint64_t)b * qN + (uint64_t)q;
     };
     // particles among the first d0 merged elements: the first a in
     // [max(0, d0 - L), min(d0, n)] with C[a] > lt(d0 - a - 1)
-    int64_t lo = d0 > L ? d0 - L : 0, hi = d0 < n ? d0 : n;
+    int lo = d0 > L ? d0 - L : 0, hi = d0 < n ? d0 : n;
     while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
+        const int mid = (lo + hi) >> 1;
         uint32_t rm;
-        if (C[padc((int)mid)] <= lt_at(d0 - mid - 1, &rm))
+        if (C[padc(mid)] <= lt_at(d0 - mid - 1, &rm))
             lo = mid + 1;
         else
             hi = mid;
     }
-    int i = (int)lo;
-    int64_t b = d0 - lo;
+    int i = lo;
+    int b = d0 - lo;
     if (b >= L)
         return;
     uint32_t r;
     uint64_t lt = lt_at(b, &r);
-    const int64_t steps = (D - d0 < K) ? D - d0 : K;
+    const int steps = (D - d0 < K) ? D - d0 : K;
     // every ticket has lt < C[n-1], so i stays below n while tickets remain
-    for (int64_t s = 0; s < steps; ++s) {
+    for (int s = 0; s < steps; ++s) {
         if (C[padc(i)] <= lt) {
             ++i;
         } else {
@@ -223,7 +215,7 @@ __device__ __forceinline__ void ticket_parents_staged(const uint64_t *C, int n, 
 {
     for (int64_t c = j_lo; c < j_hi; c += STAGE_TICKETS) {
         const int64_t ce = (j_hi - c < STAGE_TICKETS) ? j_hi : c + STAGE_TICKETS;
-        ticket_parents(C, n, c0, tg, c, ce, [&](int64_t j, int i) { stage[j - c] = (uint16_t)i; });
+        ticket_parents(C, n, c0, tg, c, (int)(ce - c), [&](int64_t j, int i) { stage[j - c] = (uint16_t)i; });
         __syncthreads();
         const int m = (int)(ce - c);
         for (int k = threadIdx.x; k < m; k += blockDim.x)
