@@ -8,8 +8,8 @@
  * implement the same published definitions independently.
  *
  * What it follows, step by step (Alg. 1, Sec. 2):
- *   init        Alg. 1 initialisation: w = 1/N, x_0 drawn "uniformly at
- *               random" (Sec. 7.3).
+ *   init        Alg. 1 initialisation: w = 1/N, x_0 drawn from a uniform
+ *               prior over the image (Sec. 7.3).
  *   propagate   Alg. 1 SIS draw with the bootstrap proposal pi = p(x_k|x_{k-1}),
  *               the near-constant-velocity model of Sec. 7.1.
  *   weight      Alg. 1 weight update, likelihood eq. 4 with the appearance
@@ -29,8 +29,8 @@
  *       vy' = vy + sv*e4, I0' = I0 + sI*e5, one frame per step.
  *   - patch S_x: a fixed (2r+1)x(2r+1) box centred on c = floor(x + 1/2);
  *     pixels outside the image are left out of the sum.  Pixels outside S_x
- *     are modelled as background, so the factor that eq. 4's "proportional
- *     to" leaves out is the particle-independent whole-frame background term:
+ *     are modelled as background, so the factor that eq. 4's proportionality
+ *     leaves out is the particle-independent whole-frame background term:
  *       l = -sum_{S_x} [(Z - I)^2 - (Z - I_bg)^2] / (2 sigma_xi^2).
  *     (For particles sharing an anchor this equals the literal form up to a
  *     constant; across anchors it keeps particles that leave the image from
