@@ -78,7 +78,7 @@ struct ppf_batch {
     float *state[2];
     int cur;
     int32_t *anc;
-    float *Zp;                         // F x Hp x Wp
+    float *Zp;                         // F x Hp x Wp pixel pairs (float2): (Z(col), Z(col + 1))
     // work units
     int32_t unit, block, bps;          // tuned launch shape
     int32_t U;
@@ -178,7 +178,8 @@ template <typename T>
 __global__ void batch_prepare_kernel(const BatchCursor *__restrict__ cur, float *__restrict__ Zp, int32_t F, int W,
                                      int H, int Wp, int Hp, int pad, const FilterParams *__restrict__ fp)
 {
-    // one warp per padded row (F * Hp rows), lanes across its columns
+    // one warp per padded row (F * Hp rows), lanes across its columns; each
+    // element is the pixel pair (Z(col), Z(col + 1)) minus the background
     const T *Z = reinterpret_cast<const T *>(cur->frames + cur->frame_bytes * cur->t);
     const int lane = threadIdx.x & 31;
     const int32_t rows = F * Hp;
@@ -187,12 +188,13 @@ __global__ void batch_prepare_kernel(const BatchCursor *__restrict__ cur, float 
         const int32_t f = row / Hp;
         const int py = row - f * Hp - pad;
         const float bg = fp[f].bg;
-        float *__restrict__ out = Zp + (int64_t)row * Wp;
+        float2 *__restrict__ out = reinterpret_cast<float2 *>(Zp) + (int64_t)row * Wp;
         const bool in_row = py >= 0 && py < H;
         const T *zrow = Z + ((int64_t)f * H + (in_row ? py : 0)) * W;
         for (int c = lane; c < Wp; c += 32) {
             const int px = c - pad;
-            out[c] = (in_row && px >= 0 && px < W) ? tof<T>(zrow[px]) - bg : 0.0f;
+            out[c] = make_float2((in_row && px >= 0 && px < W) ? tof<T>(zrow[px]) - bg : 0.0f,
+                                 (in_row && px + 1 >= 0 && px + 1 < W) ? tof<T>(zrow[px + 1]) - bg : 0.0f);
         }
     }
 }
@@ -243,7 +245,7 @@ __global__ void batch_step_kernel(BatchStepArgs a)
         if (lane < R)
             kcs[wib][lane] = P->Kc[lane];
         __syncwarp();
-        const PatchGeom geom{a.Zp + (int64_t)f * a.Wp * a.Hp, a.W, a.H, a.Wp, a.pad, P->inv2s2, P->inv_sxi2,
+        const PatchGeom geom{a.Zp + (int64_t)f * 2 * a.Wp * a.Hp, a.W, a.H, a.Wp, a.pad, P->inv2s2, P->inv_sxi2,
                              kcs[wib]};
         // after the prior draw, or when the last resample kept this filter's
         // particles, every slot continues its own particle with its weight
@@ -718,7 +720,7 @@ ppf_status ppf_batch_create(const ppf_model *models, const int64_t *n, int32_t F
     b->H = m0.height;
     b->r = m0.patch_radius;
     b->pad = 2 * b->r;
-    b->Wp = b->W + 2 * b->pad;
+    b->Wp = b->W + 2 * b->pad + 1;  // pixel pairs per row: one zero column past the padded frame
     b->Hp = b->H + 2 * b->pad;
     b->dtype = m0.frame_dtype;
     b->frame_bytes = (size_t)b->W * b->H * (b->dtype == PPF_F32 ? 4 : 2);
@@ -767,7 +769,7 @@ ppf_status ppf_batch_create(const ppf_model *models, const int64_t *n, int32_t F
     float *dv0A = nullptr;
     if (dmalloc(&b->fp, F) != cudaSuccess || dmalloc(&b->state[0], 6 * Ntot) != cudaSuccess ||
         dmalloc(&b->state[1], 6 * Ntot) != cudaSuccess || dmalloc(&b->anc, Ntot) != cudaSuccess ||
-        dmalloc(&b->Zp, (size_t)F * b->Wp * b->Hp) != cudaSuccess || dmalloc(&b->fu_off, F + 1) != cudaSuccess ||
+        dmalloc(&b->Zp, 2 * (size_t)F * b->Wp * b->Hp) != cudaSuccess || dmalloc(&b->fu_off, F + 1) != cudaSuccess ||
         dmalloc(&b->fsum, F) != cudaSuccess || dmalloc(&b->flags, 1) != cudaSuccess ||
         dmalloc(&b->fkeep, F) != cudaSuccess ||
         dmalloc(&b->cursor, 1) != cudaSuccess ||

@@ -104,7 +104,7 @@ __device__ __forceinline__ void gauss_samples(float f, float a, const float *Kc,
 // C = sum gx_i^2 sum gy_j^2.  Samples of columns / rows outside the image are
 // zeroed (only for patches that cross the border); Zp is zero there as well.
 struct PatchGeom {
-    const float *Zp;   // padded frame minus background
+    const float *Zp;   // padded frame minus background, as pixel pairs (see patch_loglik)
     int W, H, Wp, pad;
     float inv2s2;      // 1 / (2 sigma_PSF^2)
     float inv_sxi2;    // 1 / sigma_xi^2
@@ -151,38 +151,15 @@ __device__ __forceinline__ bool patch_setup(const PatchGeom &a, float x, float y
     return true;
 }
 
+// The patch sum B = sum_j gy_j sum_i gx_i Zb(i, j), read two pixels at a
+// time: a.Zp holds the prepared frame as pixel pairs, element (row, col) of
+// the float2 array (row pitch a.Wp) being (Zb(row, col), Zb(row, col + 1)).
+// The pair starting at any column is then one aligned float2 load, and lanes
+// whose patches start at neighbouring columns read neighbouring words.  The
+// pitch exceeds the padded width by at least one column (the last pair may
+// read one column past the patch, which is zero).
 template <int R>
 __device__ __forceinline__ float patch_loglik(const PatchGeom &a, float x, float y, float I0)
-{
-    constexpr int P = 2 * R + 1;
-    int cx, cy;
-    float gx[P], gy[P], C, l;
-    if (!patch_setup<R>(a, x, y, I0, cx, cy, gx, gy, C, &l))
-        return l;
-    const float *row = a.Zp + (int64_t)(cy - R + a.pad) * a.Wp + (cx - R + a.pad);
-    float B = 0.0f;
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-        float rj = 0.0f;
-#pragma unroll
-        for (int i = 0; i < P; ++i)
-            rj = fmaf(gx[i], __ldg(row + i), rj);
-        B = fmaf(gy[j], rj, B);
-        row += a.Wp;
-    }
-    return I0 * fmaf(-0.5f * I0, C, B) * a.inv_sxi2;
-}
-
-// The same sum read two pixels at a time.  Here a.Zp holds the prepared
-// frame interleaved as pixel pairs: element (row, col) of the float2 array
-// (row pitch a.Wp) is (Z(row, col), Z(row, col + 1)), so the pair starting at
-// any column is one aligned float2 load, and the lanes of a warp whose
-// patches start at neighbouring columns read neighbouring words.  The
-// products are added in the same order as in patch_loglik, so both give
-// identical results.  The pitch exceeds the padded width by at least one
-// column (the last pair may read one column past the patch, which is zero).
-template <int R>
-__device__ __forceinline__ float patch_loglik_pairs(const PatchGeom &a, float x, float y, float I0)
 {
     constexpr int P = 2 * R + 1;
     int cx, cy;

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
         v[2] = fmaf(a.sv, e2, vx);
         v[3] = fmaf(a.sv, e3, vy);
         v[4] = fmaf(a.sI, e4, I0);
-        const float l = patch_loglik_pairs<R>(geom, v[0], v[1], v[4]);
+        const float l = patch_loglik<R>(geom, v[0], v[1], v[4]);
         const float lw = lwp + l;
 #pragma unroll
         for (int c = 0; c < 5; ++c)
