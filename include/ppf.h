@@ -194,6 +194,11 @@ ppf_status ppf_set_particles(ppf_ctx *ctx, const float *state_dev, const int32_t
  * host buffer; synchronises).  offsets may be NULL to query G only. */
 ppf_status ppf_get_groups(ppf_ctx *ctx, int32_t *n_groups, int64_t *offsets_host);
 
+/* Replaces the group layout (restart hook, with ppf_set_particles): G + 1
+ * host int64 offsets, offsets[0] = 0, offsets[G] = N, non-decreasing (LGS
+ * leaves groups unequal).  Synchronises.  Errors: PPF_EINVAL, PPF_ECUDA. */
+ppf_status ppf_set_groups(ppf_ctx *ctx, const int64_t *offsets_host);
+
 /* Gradient of the log marginal likelihood estimate (the sum over frames of
  * the per-frame log-evidence of Alg. 1) with respect to
  * theta = (sigma_PSF, A, I_bg, sigma_m).  It runs K frames from a fresh prior

@@ -23,7 +23,7 @@ SCHEMES = {"systematic": SYSTEMATIC, "rpa_gs": RPA_GS, "rpa_sgs": RPA_SGS, "rpa_
 
 EXPORTS = ["ppf_create", "ppf_destroy", "ppf_step", "ppf_step_host", "ppf_resample", "ppf_resample_if",
            "ppf_estimate", "ppf_estimate_async",
-           "ppf_get_particles", "ppf_set_particles", "ppf_get_groups", "ppf_status_string",
+           "ppf_get_particles", "ppf_set_particles", "ppf_get_groups", "ppf_set_groups", "ppf_status_string",
            "ppf_last_error", "ppf_profile_enable", "ppf_profile_read", "ppf_systematic_resample_noalloc",
            "ppf_loglik_grad", "ppf_batch_create", "ppf_batch_destroy", "ppf_batch_step", "ppf_batch_resample",
            "ppf_batch_run", "ppf_batch_estimates", "ppf_batch_get_particles", "ppf_batch_autotune",
@@ -155,6 +155,7 @@ def load(build_if_missing: bool = True):
             "ppf_get_particles": (C.c_int, [ctxp, vp, vp, vp]),
             "ppf_set_particles": (C.c_int, [ctxp, vp, vp, vp]),
             "ppf_get_groups": (C.c_int, [ctxp, P(C.c_int32), vp]),
+            "ppf_set_groups": (C.c_int, [ctxp, vp]),
             "ppf_status_string": (C.c_char_p, [C.c_int]),
             "ppf_last_error": (C.c_char_p, [ctxp]),
             "ppf_profile_enable": (C.c_int, [ctxp, C.c_int, C.c_int32]),
@@ -328,6 +329,12 @@ class ParticleFilter:
         off = np.zeros(g.value + 1, dtype=np.int64)
         self._check(self.L.ppf_get_groups(self._ctx, C.byref(g), C.c_void_p(off.ctypes.data)), "ppf_get_groups")
         return off
+
+    def set_groups(self, offsets):
+        """Replace the group layout (G + 1 offsets, as returned by groups())."""
+        import numpy as np
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        self._check(self.L.ppf_set_groups(self._ctx, C.c_void_p(off.ctypes.data)), "ppf_set_groups")
 
     def profile_enable(self, enable: bool = True, capacity: int = 4096):
         self._check(self.L.ppf_profile_enable(self._ctx, 1 if enable else 0, int(capacity)), "ppf_profile_enable")

@@ -241,6 +241,7 @@ void ppf_destroy(ppf_ctx *c)
 
 ppf_status ppf_step(ppf_ctx *c, const void *frame_dev, int32_t k)
 {
+    const ppf::NvtxRange nvtx_range("ppf_step");
     if (!c || !frame_dev || k < 1)
         return PPF_EINVAL;
     if (fault("launch")) {
@@ -263,6 +264,7 @@ ppf_status ppf_step(ppf_ctx *c, const void *frame_dev, int32_t k)
 // its copy (event), and a buffer is refilled only after the step that read it.
 ppf_status ppf_step_host(ppf_ctx *c, const void *frame_host, int32_t k)
 {
+    const ppf::NvtxRange nvtx_range("ppf_step_host");
     if (!c || !frame_host || k < 1)
         return PPF_EINVAL;
     if (!c->copy_stream) {
@@ -293,6 +295,7 @@ ppf_status ppf_resample(ppf_ctx *c, ppf_scheme scheme, float alpha)
 
 ppf_status ppf_resample_if(ppf_ctx *c, ppf_scheme scheme, float alpha, double ess_threshold)
 {
+    const ppf::NvtxRange nvtx_range("ppf_resample");
     if (!c)
         return PPF_EINVAL;
     if (ess_threshold != ess_threshold)  // NaN
@@ -328,6 +331,7 @@ ppf_status ppf_resample_if(ppf_ctx *c, ppf_scheme scheme, float alpha, double es
 
 ppf_status ppf_estimate(ppf_ctx *c, ppf_estimate_t *out)
 {
+    const ppf::NvtxRange nvtx_range("ppf_estimate");
     if (!c || !out)
         return PPF_EINVAL;
     if (!c->stepped)
@@ -427,6 +431,20 @@ ppf_status ppf_get_groups(ppf_ctx *c, int32_t *n_groups, int64_t *offsets_host)
     return PPF_OK;
 }
 
+ppf_status ppf_set_groups(ppf_ctx *c, const int64_t *offsets_host)
+{
+    if (!c || !offsets_host)
+        return PPF_EINVAL;
+    if (offsets_host[0] != 0 || offsets_host[c->G] != c->N)
+        return PPF_EINVAL;
+    for (int32_t g = 0; g < c->G; ++g)
+        if (offsets_host[g + 1] < offsets_host[g])
+            return PPF_EINVAL;
+    CK(cudaMemcpyAsync(c->goff, offsets_host, sizeof(int64_t) * (c->G + 1), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));  // offsets_host may be released on return
+    return PPF_OK;
+}
+
 ppf_status ppf_profile_enable(ppf_ctx *c, int enable, int32_t capacity)
 {
     if (!c || (enable && capacity < 1))
@@ -489,6 +507,7 @@ ppf_status ppf_profile_read(ppf_ctx *c, ppf_profile_t *out)
 ppf_status ppf_loglik_grad(ppf_ctx *c, const void *frames_dev, int32_t K, const float *theta, double *loglik,
                            double *grad, int32_t *anc_dev, int32_t *anchors_dev)
 {
+    const ppf::NvtxRange nvtx_range("ppf_loglik_grad");
     if (!c || !frames_dev || K < 1 || !loglik || !grad)
         return PPF_EINVAL;
     if (theta && !(theta[0] > 0.0f && theta[3] >= 0.0f))

@@ -810,6 +810,7 @@ void ppf_batch_destroy(ppf_batch *b)
 
 ppf_status ppf_batch_step(ppf_batch *b, const void *frames_dev, int32_t k)
 {
+    const ppf::NvtxRange nvtx_range("ppf_batch_step");
     if (!b || !frames_dev || k < 1)
         return PPF_EINVAL;
     if (b->weighted)
@@ -826,6 +827,7 @@ ppf_status ppf_batch_step(ppf_batch *b, const void *frames_dev, int32_t k)
 
 ppf_status ppf_batch_resample(ppf_batch *b, int32_t k)
 {
+    const ppf::NvtxRange nvtx_range("ppf_batch_resample");
     if (!b)
         return PPF_EINVAL;
     if (!b->weighted)
@@ -840,6 +842,7 @@ ppf_status ppf_batch_resample(ppf_batch *b, int32_t k)
 ppf_status ppf_batch_run(ppf_batch *b, const void *frames_dev, int32_t k0, int32_t K, int32_t use_graph,
                          ppf_filter_estimate_t *est_host)
 {
+    const ppf::NvtxRange nvtx_range("ppf_batch_run");
     if (!b || !frames_dev || k0 < 1 || K < 1)
         return PPF_EINVAL;
     if (b->weighted)

@@ -6,7 +6,17 @@
 
 #include "ppf.h"  // include/ppf.h (the build passes -I include)
 
+#include <nvtx3/nvToolsExt.h>  // header-only; ranges cost nothing without an attached profiler
+
 namespace ppf {
+
+// A named NVTX range around one ABI call (visible in profiler timelines).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int TILE = 4096;          // particles per resampling tile (256 threads x 16)
 constexpr int TILE_THREADS = 256;

@@ -195,6 +195,38 @@ def test_step_host_matches_device_frames(ppf, movie):
     b.close()
 
 
+def test_checkpoint_and_resume(ppf, movie):
+    """A run snapshotted after LGS left the groups unequal (particles, pending
+    ancestors and starting weights, group layout) resumes in a new context
+    bit for bit: LGS, then RNA, then systematic frames."""
+    import torch
+    from gpu_common import paired_models
+    gm, _ = paired_models(ppf, seed=8)
+    fr = gpu_frames(movie)
+    a = ppf.ParticleFilter(gm, 30000, group_size=1000)
+    for k in (1, 2):
+        a.step(fr[k - 1], k)
+        a.resample(ppf.RPA_LGS)
+    st, anc, lwp = a.get_particles(state=True, anc=True, lw_prev=True)
+    goff = a.groups()
+    assert len(set(np.diff(goff).tolist())) > 1  # LGS left the groups unequal
+    b = ppf.ParticleFilter(gm, 30000, group_size=1000)
+    b.set_particles(st, anc, lwp)
+    b.set_groups(goff)
+    for k, sch in ((3, ppf.RPA_LGS), (4, ppf.RNA), (5, ppf.SYSTEMATIC)):
+        for f in (a, b):
+            f.step(fr[k - 1], k)
+            f.resample(sch, 0.3)
+        sa, aa, la = a.get_particles(state=True, anc=True, lw_prev=True)
+        sb, ab, lb = b.get_particles(state=True, anc=True, lw_prev=True)
+        assert torch.equal(sa, sb) and torch.equal(aa, ab) and torch.equal(la, lb), k
+        assert np.array_equal(a.groups(), b.groups())
+    with pytest.raises(ppf.PPFError):
+        b.set_groups(np.zeros(len(goff), dtype=np.int64))  # does not end at N
+    a.close()
+    b.close()
+
+
 def test_estimate_async_matches_estimate(ppf, movie):
     """Queued estimate copies (one per frame, read after the last frame) equal
     the synchronous estimates of the same frames."""
