@@ -150,6 +150,28 @@ def test_particles_outside_image(ppf, movie):
     pf.close()
 
 
+@pytest.mark.parametrize("r", [1, 3, 6])
+def test_odd_frame_sizes_and_borders(ppf, r):
+    """Odd frame widths and heights (the pixel-pair rows then have odd
+    lengths) with particles all over and around the image."""
+    import torch
+    from gpu_common import lockstep, paired_models
+    W, H = 97, 61
+    mv = synth.make_movie(W=W, H=H, K=3, sigma=1.3, amplitude=40.0, background=10.0, seed=4)
+    gm, om = paired_models(ppf, width=W, height=H, patch_radius=r, seed=12, psf_sigma=1.3, amplitude=40.0)
+    N = 6000
+    rng = np.random.default_rng(r)
+    st = np.zeros((6, N), dtype=np.float32)
+    st[0] = rng.uniform(-2 * r - 3, W + 2 * r + 3, N)
+    st[1] = rng.uniform(-2 * r - 3, H + 2 * r + 3, N)
+    st[2:4] = rng.normal(0.0, 0.5, (2, N))
+    st[4] = rng.uniform(10, 70, N)
+    pf = ppf.ParticleFilter(gm, N, group_size=1000)
+    pf.set_particles(torch.from_numpy(st))
+    lockstep(pf, gm, om, mv.frames, gpu_frames(mv), orc.RPA_SGS, K=3)
+    pf.close()
+
+
 def test_degenerate_weights_keep_particles(ppf, movie):
     import torch
     from gpu_common import paired_models
