@@ -314,6 +314,28 @@ def run_ours(args):
         line["schemes"] = sch
         kdone = k - 1
 
+    # pcSIR (Sec. 6): the same workload with the piecewise constant likelihood
+    # (one lookup per particle in the per-frame map of cell-centre patch sums)
+    if not args.no_pcsir:
+        ppc = ppf.ParticleFilter(ppf.Model(**params, seed=rank, filter_id=rank, likelihood=1), n,
+                                 group_size=GROUP, stream=stream)
+        for k in range(1, Wm + 1):
+            ppc.step(frames[k - 1], k)
+            ppc.resample(scheme, args.alpha)
+        torch.cuda.synchronize()
+        ppc.profile_enable(True, capacity=K + 8)
+        tpc = timed_frames(ppc, frames, Wm + 1, K, scheme, args.alpha, stream)
+        prc = ppc.profile_read()
+        epc = ppc.estimate()
+        line["pcsir"] = {"workload": "the same frames and N with the piecewise constant likelihood (pcSIR)",
+                         "value": n * K / (tpc / 1e3), "ms_per_step": tpc / K,
+                         "step_ms": prc["step_ms"] / max(1, prc["timed_steps"]),
+                         "prepare_ms": prc["prepare_ms"] / max(1, prc["timed_steps"]),
+                         "resample_ms": prc["resample_ms"] / max(1, prc["timed_steps"]),
+                         "last_mean_xy": list(epc.mean[:2]), "truth_xy": mv.truth[Wm + K - 1][:2].tolist()}
+        ppc.close()
+        del ppc
+
     # batched filters: 4096 filters, N_f log-uniform in [256, 65536], 64^2 frames
     if not args.no_batch:
         import synth
@@ -467,6 +489,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-pcsir", action="store_true")
     ap.add_argument("--batch-filters", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true", help="batched stage: keep the default launch shape")

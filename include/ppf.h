@@ -70,7 +70,13 @@ typedef struct {
     float v0_max;             /* prior velocity range: v ~ U[-v0, v0]            */
     uint64_t seed;            /* Philox key                                      */
     uint32_t filter_id;       /* Philox counter word 2 (independent filters)     */
-    uint32_t reserved;
+    uint32_t likelihood;      /* 0: eq. 4 at the particle's position;
+                                 1: pcSIR (Sec. 6), the likelihood held constant
+                                    on every pixel cell at its value for the
+                                    cell centre c = floor((x, y) + 1/2): one
+                                    lookup per particle in a per-frame map of
+                                    the patch sums of every anchor.  Not for
+                                    ppf_loglik_grad or batches.                 */
 } ppf_model;
 
 /* Per-frame results (Alg. 1 normalisation / N_eff; MMSE estimate of Sec. 2). */

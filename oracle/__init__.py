@@ -48,7 +48,7 @@ def build(force: bool = False) -> str:
 
 class _Model(C.Structure):
     _fields_ = [
-        ("width", C.c_int32), ("height", C.c_int32), ("patch_radius", C.c_int32), ("pad_", C.c_int32),
+        ("width", C.c_int32), ("height", C.c_int32), ("patch_radius", C.c_int32), ("likelihood", C.c_int32),
         ("psf_sigma", C.c_double), ("amplitude", C.c_double), ("background", C.c_double),
         ("sigma_xi", C.c_double), ("sigma_m", C.c_double), ("sigma_v", C.c_double),
         ("sigma_I", C.c_double), ("v0_max", C.c_double),
@@ -72,9 +72,10 @@ class Model:
     v0_max: float = 1.0
     seed: int = 0
     filter_id: int = 0
+    likelihood: int = 0  # 0: eq. 4 at the particle; 1: piecewise constant over pixel cells (pcSIR)
 
     def c(self) -> _Model:
-        return _Model(self.width, self.height, self.patch_radius, 0,
+        return _Model(self.width, self.height, self.patch_radius, self.likelihood,
                       self.psf_sigma, self.amplitude, self.background, self.sigma_xi,
                       self.sigma_m, self.sigma_v, self.sigma_I, self.v0_max,
                       self.seed & 0xFFFFFFFFFFFFFFFF, self.filter_id, 0)

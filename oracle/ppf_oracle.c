@@ -222,6 +222,13 @@ double orc_loglik(const orc_model *m, const double *frame, double x, double y, d
 {
     if (!isfinite(x) || !isfinite(y) || !isfinite(I0))
         return -INFINITY;
+    if (m->likelihood == 1) {
+        /* pcSIR (Sec. 6): the likelihood is held constant on every pixel
+         * cell [c - 1/2, c + 1/2)^2, at its value for the particle moved to
+         * the cell centre c = floor((x, y) + 1/2) */
+        x = floor(x + 0.5);
+        y = floor(y + 0.5);
+    }
     const int r = m->patch_radius;
     const double cxd = floor(x + 0.5), cyd = floor(y + 0.5);
     /* anchors far outside the image see no pixel: empty sum */

@@ -13,7 +13,8 @@ enum { ORC_PURPOSE_INIT = 0, ORC_PURPOSE_PROP = 1, ORC_PURPOSE_RESAMPLE = 2,
        ORC_PURPOSE_GROUP_RESAMPLE = 3 };
 
 typedef struct {
-    int32_t width, height, patch_radius, pad_;
+    int32_t width, height, patch_radius;
+    int32_t likelihood; /* 0: eq. 4 at the particle; 1: piecewise constant over pixel cells (pcSIR) */
     double psf_sigma, amplitude, background, sigma_xi;
     double sigma_m, sigma_v, sigma_I, v0_max;
     uint64_t seed;

@@ -41,7 +41,7 @@ class _Model(C.Structure):
         ("width", C.c_int32), ("height", C.c_int32), ("patch_radius", C.c_int32), ("frame_dtype", C.c_int32),
         ("psf_sigma", C.c_float), ("amplitude", C.c_float), ("background", C.c_float), ("sigma_xi", C.c_float),
         ("sigma_m", C.c_float), ("sigma_v", C.c_float), ("sigma_I", C.c_float), ("v0_max", C.c_float),
-        ("seed", C.c_uint64), ("filter_id", C.c_uint32), ("reserved", C.c_uint32),
+        ("seed", C.c_uint64), ("filter_id", C.c_uint32), ("likelihood", C.c_uint32),
     ]
 
 
@@ -87,11 +87,13 @@ class Model:
     seed: int = 0
     filter_id: int = 0
     frame_dtype: int = F32
+    likelihood: int = 0  # 0: eq. 4 at the particle; 1: piecewise constant over pixel cells (pcSIR)
 
     def c(self) -> _Model:
         return _Model(self.width, self.height, self.patch_radius, self.frame_dtype, self.psf_sigma,
                       self.amplitude, self.background, self.sigma_xi, self.sigma_m, self.sigma_v,
-                      self.sigma_I, self.v0_max, self.seed & 0xFFFFFFFFFFFFFFFF, self.filter_id, 0)
+                      self.sigma_I, self.v0_max, self.seed & 0xFFFFFFFFFFFFFFFF, self.filter_id,
+                      self.likelihood)
 
 
 @dataclasses.dataclass

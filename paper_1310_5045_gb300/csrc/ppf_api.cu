@@ -59,7 +59,7 @@ void free_all(ppf_ctx *c)
 {
     void *ptrs[] = {c->tang[0], c->tang[1], c->gpart,
                     c->state[0], c->state[1], c->anc, c->anc_sys, c->lwp, c->goff, c->goff_new, c->Zp,
-                    c->frame_buf[0], c->frame_buf[1], c->part, c->sum, c->est_dev, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sc.Cbl,
+                    c->frame_buf[0], c->frame_buf[1], c->lmap, c->part, c->sum, c->est_dev, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sc.Cbl,
                     c->sc.Tg, c->sc.skey, c->sc.sval, c->sc.seg_tick, c->sc.seg_dst, c->sc.seg_len,
                     c->sc.seg_chunk};
     for (void *p : ptrs)
@@ -129,6 +129,8 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
         return PPF_EINVAL;
     if (m->frame_dtype != PPF_F32 && m->frame_dtype != PPF_BF16 && m->frame_dtype != PPF_F16)
         return PPF_EINVAL;
+    if (m->likelihood > 1)
+        return PPF_EINVAL;
     if ((int64_t)(m->width + 4 * m->patch_radius) * (m->height + 4 * m->patch_radius) > (1LL << 31))
         return PPF_EINVAL;
     if (fault("alloc"))
@@ -171,6 +173,9 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
         chk(dalloc(&c->goff, G + 1), "goff");
         chk(dalloc(&c->goff_new, G + 1), "goff_new");
         chk(dalloc(&c->Zp, 2 * (size_t)c->Wp * c->Hp), "Zp");
+        if (m->likelihood == 1)
+            chk(dalloc(&c->lmap, (size_t)(m->width + 2 * m->patch_radius) * (m->height + 2 * m->patch_radius)),
+                "cell map");
         chk(dalloc((char **)&c->frame_buf[0], c->frame_bytes), "frame_buf");
         chk(dalloc((char **)&c->frame_buf[1], c->frame_bytes), "frame_buf");
         c->n_part = c->num_sms > 0 ? ppf::step_grid(c) : 1;
@@ -508,6 +513,10 @@ ppf_status ppf_loglik_grad(ppf_ctx *c, const void *frames_dev, int32_t K, const 
                            double *grad, int32_t *anc_dev, int32_t *anchors_dev)
 {
     const ppf::NvtxRange nvtx_range("ppf_loglik_grad");
+    if (c && c->m.likelihood != 0) {
+        set_err(c, "ppf_loglik_grad needs the eq. 4 likelihood (model.likelihood = 0)");
+        return PPF_EINVAL;
+    }
     if (!c || !frames_dev || K < 1 || !loglik || !grad)
         return PPF_EINVAL;
     if (theta && !(theta[0] > 0.0f && theta[3] >= 0.0f))

@@ -698,7 +698,7 @@ ppf_status ppf_batch_create(const ppf_model *models, const int64_t *n, int32_t F
     for (int32_t f = 0; f < F; ++f) {
         const ppf_model &m = models[f];
         if (m.width != m0.width || m.height != m0.height || m.patch_radius != m0.patch_radius ||
-            m.frame_dtype != m0.frame_dtype)
+            m.frame_dtype != m0.frame_dtype || m.likelihood != 0)  // batches use eq. 4 at the particle
             return PPF_EINVAL;
         if (!(m.psf_sigma > 0.0f) || !(m.sigma_xi > 0.0f) || !(m.sigma_m >= 0.0f) || !(m.sigma_v >= 0.0f) ||
             !(m.sigma_I >= 0.0f) || !(m.v0_max >= 0.0f))

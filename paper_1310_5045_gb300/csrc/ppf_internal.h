@@ -102,6 +102,7 @@ struct ppf_ctx {
     float *lwp;                   // per-slot starting log-weights (MODE_EXPLICIT)
     int64_t *goff, *goff_new;     // group offsets [G+1]
     float *Zp;                    // padded frame minus background
+    float2 *lmap;                 // pcSIR: (B, C) patch sums of every anchor (W + 2r) x (H + 2r)
     int32_t Wp, Hp, pad;
     void *frame_buf[2];           // device copies for ppf_step_host (double-buffered)
     int fb_next;                  // buffer the next ppf_step_host fills
@@ -147,5 +148,6 @@ cudaError_t launch_identity(ppf_ctx *c, int32_t *dst);
 cudaError_t launch_pending(ppf_ctx *c, int32_t *anc_out, float *lwp_out);
 cudaError_t launch_fill_f32(ppf_ctx *c, float *dst, float v);
 cudaError_t launch_format_estimate(ppf_ctx *c);
+cudaError_t launch_cell_map(ppf_ctx *c);
 int step_grid(ppf_ctx *c);
 }  // namespace ppf

@@ -159,13 +159,10 @@ __device__ __forceinline__ bool patch_setup(const PatchGeom &a, float x, float y
 // pitch exceeds the padded width by at least one column (the last pair may
 // read one column past the patch, which is zero).
 template <int R>
-__device__ __forceinline__ float patch_loglik(const PatchGeom &a, float x, float y, float I0)
+__device__ __forceinline__ float patch_sum(const PatchGeom &a, int cx, int cy, const float gx[2 * R + 1],
+                                           const float gy[2 * R + 1])
 {
     constexpr int P = 2 * R + 1;
-    int cx, cy;
-    float gx[P], gy[P], C, l;
-    if (!patch_setup<R>(a, x, y, I0, cx, cy, gx, gy, C, &l))
-        return l;
     const float2 *row = reinterpret_cast<const float2 *>(a.Zp) + (int64_t)(cy - R + a.pad) * a.Wp +
                         (cx - R + a.pad);
     float B = 0.0f;
@@ -182,7 +179,36 @@ __device__ __forceinline__ float patch_loglik(const PatchGeom &a, float x, float
         B = fmaf(gy[j], rj, B);
         row += a.Wp;
     }
+    return B;
+}
+
+template <int R>
+__device__ __forceinline__ float patch_loglik(const PatchGeom &a, float x, float y, float I0)
+{
+    constexpr int P = 2 * R + 1;
+    int cx, cy;
+    float gx[P], gy[P], C, l;
+    if (!patch_setup<R>(a, x, y, I0, cx, cy, gx, gy, C, &l))
+        return l;
+    const float B = patch_sum<R>(a, cx, cy, gx, gy);
     return I0 * fmaf(-0.5f * I0, C, B) * a.inv_sxi2;
+}
+
+// pcSIR (Sec. 6): the likelihood held constant on every pixel cell, at its
+// value for the cell centre c = floor((x, y) + 1/2).  lmap holds (B, C) of the
+// patch sum at every anchor c (row pitch W + 2R, c shifted by R), so a
+// particle costs one lookup: l = I0 (B - I0 C / 2) / sigma_xi^2.
+template <int R>
+__device__ __forceinline__ float cell_loglik(const PatchGeom &a, const float2 *__restrict__ lmap, float x, float y,
+                                             float I0)
+{
+    if (!isfinite(x) || !isfinite(y) || !isfinite(I0))
+        return -INFINITY;
+    const float cxf = floorf(x + 0.5f), cyf = floorf(y + 0.5f);
+    if (cxf < -(float)R || cxf > (float)(a.W - 1 + R) || cyf < -(float)R || cyf > (float)(a.H - 1 + R))
+        return 0.0f;
+    const float2 bc = __ldg(lmap + (int64_t)((int)cyf + R) * (a.W + 2 * R) + ((int)cxf + R));
+    return I0 * fmaf(-0.5f * I0, bc.y, bc.x) * a.inv_sxi2;
 }
 
 }  // namespace ppf

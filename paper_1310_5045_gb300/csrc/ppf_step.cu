@@ -78,6 +78,7 @@ struct StepArgs {
     int32_t *flags;
     int mode;
     const float *__restrict__ Zp;
+    const float2 *__restrict__ lmap;  // pcSIR cell map, or nullptr (eq. 4 at the particle)
     Partial *__restrict__ part;
     unsigned int *done;    // blocks finished (reset by the last one)
     DevSummary *sum;
@@ -148,7 +149,8 @@ __device__ void finalize_block(const Partial *part, int n, DevSummary *sum, int3
     }
 }
 
-template <int R>
+// PC: pcSIR (cell map lookup) instead of the patch sum at the particle
+template <int R, bool PC>
 __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
 {
     int mode = a.mode;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
         v[2] = fmaf(a.sv, e2, vx);
         v[3] = fmaf(a.sv, e3, vy);
         v[4] = fmaf(a.sI, e4, I0);
-        const float l = patch_loglik<R>(geom, v[0], v[1], v[4]);
+        const float l = PC ? cell_loglik<R>(geom, a.lmap, v[0], v[1], v[4]) : patch_loglik<R>(geom, v[0], v[1], v[4]);
         const float lw = lwp + l;
 #pragma unroll
         for (int c = 0; c < 5; ++c)
@@ -261,12 +263,66 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
 int step_grid(ppf_ctx *c)
 {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<5>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<5, false>, 256, 0);
     if (per_sm < 1)
         per_sm = 1;
     int64_t need = (c->N + 255) / 256;
     int64_t g = (int64_t)c->num_sms * per_sm;
     return (int)(need < g ? need : g);
+}
+
+// pcSIR cell map: (B, C) of the patch sum at every anchor c in
+// [-R, W-1+R] x [-R, H-1+R], PSF samples at the cell centre (offset 0); the
+// same arithmetic as patch_loglik for a particle at the centre
+struct KcArr {
+    float v[MAX_RADIUS];
+};
+
+template <int R>
+__global__ void cell_map_kernel(PatchGeom geom, KcArr kc, float2 *__restrict__ lmap)
+{
+    constexpr int P = 2 * R + 1;
+    geom.Kc = kc.v;
+    const int lw = geom.W + 2 * R, lh = geom.H + 2 * R;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < lw * lh; idx += gridDim.x * blockDim.x) {
+        const int cx = idx % lw - R, cy = idx / lw - R;
+        int ax, ay;
+        float gx[P], gy[P], C, l;
+        const bool inside = patch_setup<R>(geom, (float)cx, (float)cy, 1.0f, ax, ay, gx, gy, C, &l);
+        lmap[idx] = inside ? make_float2(patch_sum<R>(geom, ax, ay, gx, gy), C) : make_float2(0.0f, 0.0f);
+    }
+}
+
+template <int R>
+static void launch_cell_map_r(const PatchGeom &g, const KcArr &kc, float2 *lmap, int n, cudaStream_t s)
+{
+    const int grid = (n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048;
+    cell_map_kernel<R><<<grid, 256, 0, s>>>(g, kc, lmap);
+}
+
+cudaError_t launch_cell_map(ppf_ctx *c)
+{
+    const int R = c->m.patch_radius;
+    PatchGeom g{c->Zp, c->m.width, c->m.height, c->Wp, c->pad, 0.0f, 0.0f, nullptr};
+    g.inv2s2 = 1.0f / (2.0f * c->m.psf_sigma * c->m.psf_sigma);
+    g.inv_sxi2 = 1.0f / (c->m.sigma_xi * c->m.sigma_xi);
+    KcArr kc;
+    for (int k = 0; k < MAX_RADIUS; ++k)
+        kc.v[k] = (float)exp(-(2.0 * k + 1.0) * (double)g.inv2s2);
+    const int n = (c->m.width + 2 * R) * (c->m.height + 2 * R);
+    switch (R) {
+    case 0: launch_cell_map_r<0>(g, kc, c->lmap, n, c->stream); break;
+    case 1: launch_cell_map_r<1>(g, kc, c->lmap, n, c->stream); break;
+    case 2: launch_cell_map_r<2>(g, kc, c->lmap, n, c->stream); break;
+    case 3: launch_cell_map_r<3>(g, kc, c->lmap, n, c->stream); break;
+    case 4: launch_cell_map_r<4>(g, kc, c->lmap, n, c->stream); break;
+    case 5: launch_cell_map_r<5>(g, kc, c->lmap, n, c->stream); break;
+    case 6: launch_cell_map_r<6>(g, kc, c->lmap, n, c->stream); break;
+    case 7: launch_cell_map_r<7>(g, kc, c->lmap, n, c->stream); break;
+    default: launch_cell_map_r<8>(g, kc, c->lmap, n, c->stream); break;
+    }
+    c->launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init(ppf_ctx *c)
@@ -298,14 +354,20 @@ cudaError_t launch_prepare_frame(ppf_ctx *c, const void *frame)
         prepare_frame_kernel<float><<<grid, 256, 0, c->stream>>>(
             (const float *)frame, c->Zp, c->m.width, c->m.height, c->Wp, c->Hp, c->pad, bg);
     }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && c->lmap)
+        e = launch_cell_map(c);  // pcSIR: the patch sums of every anchor of this frame
     prof_mark(c, PH_PREPARE, 1);
-    return cudaGetLastError();
+    return e;
 }
 
 template <int R>
 static void launch_step_r(const StepArgs &a, int grid, cudaStream_t s)
 {
-    step_kernel<R><<<grid, 256, 0, s>>>(a);
+    if (a.lmap)
+        step_kernel<R, true><<<grid, 256, 0, s>>>(a);
+    else
+        step_kernel<R, false><<<grid, 256, 0, s>>>(a);
 }
 
 cudaError_t launch_step(ppf_ctx *c, int32_t k)
@@ -335,6 +397,7 @@ cudaError_t launch_step(ppf_ctx *c, int32_t k)
     a.flags = &c->sum->flags;
     a.mode = c->mode;
     a.Zp = c->Zp;
+    a.lmap = c->lmap;
     a.part = c->part;
     a.done = &c->sum->blocks_done;
     a.sum = c->sum;

@@ -93,6 +93,33 @@ def test_rpa_at_the_group_limit(ppf, movie, scheme):
     pf.close()
 
 
+@pytest.mark.parametrize("scheme", [orc.SYSTEMATIC, orc.RNA])
+@pytest.mark.parametrize("r", [2, 4, 8])
+def test_piecewise_constant_likelihood(ppf, movie, scheme, r):
+    """pcSIR: every particle's likelihood is looked up in the per-frame map of
+    cell-centre patch sums; lockstep against the oracle's pcSIR reading."""
+    from gpu_common import lockstep, paired_models
+    gm, om = paired_models(ppf, seed=13, patch_radius=r, likelihood=1)
+    pf = ppf.ParticleFilter(gm, 12000, group_size=3000)
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), scheme, K=4, alpha=0.2)
+    pf.close()
+
+
+def test_piecewise_constant_likelihood_is_rejected_where_unsupported(ppf, movie):
+    from gpu_common import paired_models
+    gm, _ = paired_models(ppf, seed=13, likelihood=1)
+    pf = ppf.ParticleFilter(gm, 1000, group_size=1000)
+    with pytest.raises(ppf.PPFError) as e:
+        pf.loglik_grad(gpu_frames(movie)[:2])
+    assert e.value.status == ppf.EINVAL
+    pf.close()
+    with pytest.raises(ppf.PPFError):
+        ppf.BatchFilter([gm, gm], [100, 100])
+    bad = paired_models(ppf, seed=13, likelihood=2)[0]
+    with pytest.raises(ppf.PPFError):
+        ppf.ParticleFilter(bad, 100, group_size=100)
+
+
 @pytest.mark.parametrize("r", [0, 1, 5, 8])
 def test_patch_radius_and_ragged_tile(ppf, movie, r):
     from gpu_common import lockstep, paired_models
