@@ -46,8 +46,10 @@
  *     precision), s = 63 - ceil(log2 n); ticket offset u = floor(r64 * Q / 2^64).
  *
  * parity pins: every function here is checked by the CPU test-suite against a
- * closed form, a library routine, an invariant or brute force; nothing here is
- * "parity unpinned".
+ * closed form, a library routine, an invariant or brute force.  One reading
+ * is parity unpinned: that the piecewise constant likelihood below
+ * (likelihood = 1) is the pcSIR of the cited pcSIR paper, which is not
+ * available; the function itself is pinned (constant cells, centre value).
  */
 #include <math.h>
 #include <stdint.h>
