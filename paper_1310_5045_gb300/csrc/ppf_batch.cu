@@ -278,7 +278,7 @@ __global__ void batch_step_kernel(BatchStepArgs a)
             v[2] = fmaf(sv, e2, vx);
             v[3] = fmaf(sv, e3, vy);
             v[4] = fmaf(sIn, e4, I0);
-            const float lw = lwp + patch_loglik<R>(geom, v[0], v[1], v[4]);
+            const float lw = lwp + patch_loglik<R, false>(geom, v[0], v[1], v[4]);
 #pragma unroll
             for (int c = 0; c < 5; ++c)
                 dst[(size_t)c * N + i] = v[c];

@@ -112,7 +112,10 @@ __device__ __forceinline__ void grad_patch(const GradArgs &a, float x, float y, 
         Gy += gy[i];
     }
     // per-column weights gx, gx dx, gx dx^2; the row sums read the frame as
-    // pixel pairs (one aligned float2 per two columns)
+    // pixel pairs (one aligned float2 per two columns) and run as packed
+    // two-lane FMAs over the full column pairs, the odd last column on the
+    // even lane
+    constexpr int Q = P / 2;
     float w0[P], w1[P], w2[P];
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -126,19 +129,18 @@ __device__ __forceinline__ void grad_patch(const GradArgs &a, float x, float y, 
     float B = 0, By1 = 0, Bx1 = 0, Bs = 0;
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-        float r0 = 0, r1 = 0, r2 = 0;
+        float2 p0 = make_float2(0.0f, 0.0f), p1 = p0, p2 = p0;
 #pragma unroll
-        for (int k = 0; k < (P + 1) / 2; ++k) {
+        for (int k = 0; k < Q; ++k) {
             const float2 z = __ldg(row + 2 * k);
-            r0 = fmaf(w0[2 * k], z.x, r0);
-            r1 = fmaf(w1[2 * k], z.x, r1);
-            r2 = fmaf(w2[2 * k], z.x, r2);
-            if (2 * k + 1 < P) {
-                r0 = fmaf(w0[2 * k + 1], z.y, r0);
-                r1 = fmaf(w1[2 * k + 1], z.y, r1);
-                r2 = fmaf(w2[2 * k + 1], z.y, r2);
-            }
+            p0 = __ffma2_rn(make_float2(w0[2 * k], w0[2 * k + 1]), z, p0);
+            p1 = __ffma2_rn(make_float2(w1[2 * k], w1[2 * k + 1]), z, p1);
+            p2 = __ffma2_rn(make_float2(w2[2 * k], w2[2 * k + 1]), z, p2);
         }
+        const float zl = __ldg(row + 2 * Q).x;
+        const float r0 = fmaf(w0[P - 1], zl, p0.x) + p0.y;
+        const float r1 = fmaf(w1[P - 1], zl, p1.x) + p1.y;
+        const float r2 = fmaf(w2[P - 1], zl, p2.x) + p2.y;
         const float dy = fy + (float)(j - R);
         B = fmaf(gy[j], r0, B);
         By1 = fmaf(gy[j] * dy, r0, By1);

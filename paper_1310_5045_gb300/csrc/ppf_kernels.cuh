@@ -155,34 +155,59 @@ __device__ __forceinline__ bool patch_setup(const PatchGeom &a, float x, float y
 // time: a.Zp holds the prepared frame as pixel pairs, element (row, col) of
 // the float2 array (row pitch a.Wp) being (Zb(row, col), Zb(row, col + 1)).
 // The pair starting at any column is then one aligned float2 load, and lanes
-// whose patches start at neighbouring columns read neighbouring words.  The
-// pitch exceeds the padded width by at least one column (the last pair may
-// read one column past the patch, which is zero).
-template <int R>
+// whose patches start at neighbouring columns read neighbouring words.
+//
+// PACKED: each row is summed with packed two-lane FMAs over the P / 2 full
+// column pairs, r_j = sum_k (gx_2k, gx_2k+1) * (Zb(2k, j), Zb(2k + 1, j)), with
+// the odd last column added to the even lane; the rows then accumulate as
+// pairs, b += (gy_j, gy_j) * r_j, and B = b.x + b.y.  Each lane rounds as a
+// scalar fmaf; only the order of the additions differs from the scalar form
+// (one fmaf per pixel, row by row), which the batched step keeps: its
+// warp-per-unit kernel ran slower with the packed form.
+template <int R, bool PACKED>
 __device__ __forceinline__ float patch_sum(const PatchGeom &a, int cx, int cy, const float gx[2 * R + 1],
                                            const float gy[2 * R + 1])
 {
     constexpr int P = 2 * R + 1;
+    constexpr int Q = P / 2;  // full column pairs; column P - 1 is the odd one out
     const float2 *row = reinterpret_cast<const float2 *>(a.Zp) + (int64_t)(cy - R + a.pad) * a.Wp +
                         (cx - R + a.pad);
-    float B = 0.0f;
+    if constexpr (PACKED) {
+        float2 b = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
-        float rj = 0.0f;
+        for (int j = 0; j < P; ++j) {
+            float2 r = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int k = 0; k < (P + 1) / 2; ++k) {
-            const float2 z = __ldg(row + 2 * k);
-            rj = fmaf(gx[2 * k], z.x, rj);
-            if (2 * k + 1 < P)
-                rj = fmaf(gx[2 * k + 1], z.y, rj);
+            for (int k = 0; k < Q; ++k) {
+                const float2 z = __ldg(row + 2 * k);
+                r = (k == 0) ? __fmul2_rn(make_float2(gx[0], gx[1]), z)
+                             : __ffma2_rn(make_float2(gx[2 * k], gx[2 * k + 1]), z, r);
+            }
+            r.x = fmaf(gx[P - 1], __ldg(row + 2 * Q).x, r.x);
+            b = (j == 0) ? __fmul2_rn(make_float2(gy[0], gy[0]), r) : __ffma2_rn(make_float2(gy[j], gy[j]), r, b);
+            row += a.Wp;
         }
-        B = fmaf(gy[j], rj, B);
-        row += a.Wp;
+        return b.x + b.y;
+    } else {
+        float B = 0.0f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            float rj = 0.0f;
+#pragma unroll
+            for (int k = 0; k <= Q; ++k) {
+                const float2 z = __ldg(row + 2 * k);
+                rj = fmaf(gx[2 * k], z.x, rj);
+                if (2 * k + 1 < P)
+                    rj = fmaf(gx[2 * k + 1], z.y, rj);
+            }
+            B = fmaf(gy[j], rj, B);
+            row += a.Wp;
+        }
+        return B;
     }
-    return B;
 }
 
-template <int R>
+template <int R, bool PACKED = true>
 __device__ __forceinline__ float patch_loglik(const PatchGeom &a, float x, float y, float I0)
 {
     constexpr int P = 2 * R + 1;
@@ -190,7 +215,7 @@ __device__ __forceinline__ float patch_loglik(const PatchGeom &a, float x, float
     float gx[P], gy[P], C, l;
     if (!patch_setup<R>(a, x, y, I0, cx, cy, gx, gy, C, &l))
         return l;
-    const float B = patch_sum<R>(a, cx, cy, gx, gy);
+    const float B = patch_sum<R, PACKED>(a, cx, cy, gx, gy);
     return I0 * fmaf(-0.5f * I0, C, B) * a.inv_sxi2;
 }
 

@@ -289,7 +289,7 @@ __global__ void cell_map_kernel(PatchGeom geom, KcArr kc, float2 *__restrict__ l
         int ax, ay;
         float gx[P], gy[P], C, l;
         const bool inside = patch_setup<R>(geom, (float)cx, (float)cy, 1.0f, ax, ay, gx, gy, C, &l);
-        lmap[idx] = inside ? make_float2(patch_sum<R>(geom, ax, ay, gx, gy), C) : make_float2(0.0f, 0.0f);
+        lmap[idx] = inside ? make_float2(patch_sum<R, true>(geom, ax, ay, gx, gy), C) : make_float2(0.0f, 0.0f);
     }
 }
 
