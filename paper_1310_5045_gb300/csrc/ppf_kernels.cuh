@@ -157,13 +157,13 @@ __device__ __forceinline__ bool patch_setup(const PatchGeom &a, float x, float y
 // The pair starting at any column is then one aligned float2 load, and lanes
 // whose patches start at neighbouring columns read neighbouring words.
 //
-// PACKED: each row is summed with packed two-lane FMAs over the P / 2 full
-// column pairs, r_j = sum_k (gx_2k, gx_2k+1) * (Zb(2k, j), Zb(2k + 1, j)), with
-// the odd last column added to the even lane; the rows then accumulate as
-// pairs, b += (gy_j, gy_j) * r_j, and B = b.x + b.y.  Each lane rounds as a
-// scalar fmaf; only the order of the additions differs from the scalar form
-// (one fmaf per pixel, row by row), which the batched step keeps: its
-// warp-per-unit kernel ran slower with the packed form.
+// The even and the odd columns are summed apart: for every row,
+// r_j = (sum_k gx_2k Zb(2k, j) + gx_P-1 Zb(P-1, j), sum_k gx_2k+1 Zb(2k+1, j)),
+// k over the P / 2 full column pairs; then b = sum_j gy_j r_j lane by lane and
+// B = b.x + b.y.  PACKED computes the two lanes with packed two-lane FMAs
+// over the pixel pairs; the scalar form (kept by the batched step, whose
+// warp-per-unit kernel ran slower with packed FMAs) performs the same
+// roundings in the same order, so both give the same bits.
 template <int R, bool PACKED>
 __device__ __forceinline__ float patch_sum(const PatchGeom &a, int cx, int cy, const float gx[2 * R + 1],
                                            const float gy[2 * R + 1])
@@ -172,39 +172,31 @@ __device__ __forceinline__ float patch_sum(const PatchGeom &a, int cx, int cy, c
     constexpr int Q = P / 2;  // full column pairs; column P - 1 is the odd one out
     const float2 *row = reinterpret_cast<const float2 *>(a.Zp) + (int64_t)(cy - R + a.pad) * a.Wp +
                         (cx - R + a.pad);
-    if constexpr (PACKED) {
-        float2 b = make_float2(0.0f, 0.0f);
+    float2 b = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-            float2 r = make_float2(0.0f, 0.0f);
+    for (int j = 0; j < P; ++j) {
+        float2 r = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                const float2 z = __ldg(row + 2 * k);
+        for (int k = 0; k < Q; ++k) {
+            const float2 z = __ldg(row + 2 * k);
+            if constexpr (PACKED) {
                 r = (k == 0) ? __fmul2_rn(make_float2(gx[0], gx[1]), z)
                              : __ffma2_rn(make_float2(gx[2 * k], gx[2 * k + 1]), z, r);
+            } else {
+                r.x = (k == 0) ? __fmul_rn(gx[0], z.x) : __fmaf_rn(gx[2 * k], z.x, r.x);
+                r.y = (k == 0) ? __fmul_rn(gx[1], z.y) : __fmaf_rn(gx[2 * k + 1], z.y, r.y);
             }
-            r.x = fmaf(gx[P - 1], __ldg(row + 2 * Q).x, r.x);
+        }
+        r.x = __fmaf_rn(gx[P - 1], __ldg(row + 2 * Q).x, r.x);
+        if constexpr (PACKED) {
             b = (j == 0) ? __fmul2_rn(make_float2(gy[0], gy[0]), r) : __ffma2_rn(make_float2(gy[j], gy[j]), r, b);
-            row += a.Wp;
+        } else {
+            b.x = (j == 0) ? __fmul_rn(gy[0], r.x) : __fmaf_rn(gy[j], r.x, b.x);
+            b.y = (j == 0) ? __fmul_rn(gy[0], r.y) : __fmaf_rn(gy[j], r.y, b.y);
         }
-        return b.x + b.y;
-    } else {
-        float B = 0.0f;
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-            float rj = 0.0f;
-#pragma unroll
-            for (int k = 0; k <= Q; ++k) {
-                const float2 z = __ldg(row + 2 * k);
-                rj = fmaf(gx[2 * k], z.x, rj);
-                if (2 * k + 1 < P)
-                    rj = fmaf(gx[2 * k + 1], z.y, rj);
-            }
-            B = fmaf(gy[j], rj, B);
-            row += a.Wp;
-        }
-        return B;
+        row += a.Wp;
     }
+    return __fadd_rn(b.x, b.y);
 }
 
 template <int R, bool PACKED = true>
