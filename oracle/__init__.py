@@ -26,7 +26,8 @@ _lib = None
 
 SYSTEMATIC, RPA_GS, RPA_SGS, RPA_LGS, RNA = 0, 1, 2, 3, 4
 RPA2_GS, RPA2_SGS, RPA2_LGS = 5, 6, 7  # two-stage proportional allocation
-PURPOSE_INIT, PURPOSE_PROP, PURPOSE_RESAMPLE, PURPOSE_GROUP_RESAMPLE = 0, 1, 2, 3
+ARNA = 8  # adaptive RNA (exchange ratio from the involved groups, ring redrawn when lost)
+PURPOSE_INIT, PURPOSE_PROP, PURPOSE_RESAMPLE, PURPOSE_GROUP_RESAMPLE, PURPOSE_RING = 0, 1, 2, 3, 4
 OK, EDEGENERATE = 0, 5
 
 
@@ -116,6 +117,9 @@ def lib():
                 "orc_balanced_offsets": (None, [C.c_int64, C.c_int32, i64p]),
                 "orc_resample": (C.c_int, [mp, C.c_int, C.c_double, C.c_int64, C.c_int32, C.c_int32,
                                            i64p, fp, dp, i32p, dp, i64p, i64p]),
+                "orc_arna_ring": (None, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int32, i32p]),
+                "orc_resample_arna": (C.c_int, [mp, C.c_double, C.c_int64, C.c_int32, C.c_int32, i64p, fp, dp,
+                                                C.c_int32, i32p, i32p, dp, i64p, i64p]),
                 "orc_run": (C.c_int, [mp, C.c_int64, C.c_int32, C.c_int, C.c_double, C.c_double, C.c_int32,
                                       dp, dp, dp]),
                 "orc_loglik_partials": (None, [mp, dp, C.c_double, C.c_double, C.c_double, C.c_int32,
@@ -299,6 +303,34 @@ def resample(m: Model, scheme: int, N: int, frame: int, goff: np.ndarray, lw: np
                             _p(lwf, C.c_float), _p(lws, C.c_double), _p(anc, C.c_int32),
                             _p(lwr, C.c_double), _p(go, C.c_int64), _p(stats, C.c_int64))
     return rc, anc, lwr, go, stats
+
+
+def arna_ring(seed: int, filter_id: int, frame: int, G: int) -> np.ndarray:
+    """The ring order ARNA draws when the object is lost: the groups in
+    increasing order of the first Philox word of (seed; g, frame, filter,
+    RING), ties by group index."""
+    ring = np.zeros(G, dtype=np.int32)
+    lib().orc_arna_ring(seed, filter_id, frame, G, _p(ring, C.c_int32))
+    return ring
+
+
+def resample_arna(m: Model, N: int, frame: int, goff: np.ndarray, lw: np.ndarray, lost: bool,
+                  ring: np.ndarray, lw_sum: np.ndarray | None = None, alpha: float = 0.5):
+    """ARNA resampling of one frame.  Returns (rc, anc, lw_reset, goff_out,
+    stats[links, moved, max, min, involved], ring_out)."""
+    g = np.ascontiguousarray(goff, dtype=np.int64)
+    G = g.shape[0] - 1
+    lwf = np.ascontiguousarray(lw, dtype=np.float32)
+    lws = np.ascontiguousarray(lwf.astype(np.float64) if lw_sum is None else lw_sum, dtype=np.float64)
+    rg = np.array(ring, dtype=np.int32)
+    anc = np.zeros(N, dtype=np.int32)
+    lwr = np.zeros(N)
+    go = np.zeros(G + 1, dtype=np.int64)
+    stats = np.zeros(5, dtype=np.int64)
+    rc = lib().orc_resample_arna(C.byref(m.c()), alpha, N, frame, G, _p(g, C.c_int64), _p(lwf, C.c_float),
+                                 _p(lws, C.c_double), 1 if lost else 0, _p(rg, C.c_int32), _p(anc, C.c_int32),
+                                 _p(lwr, C.c_double), _p(go, C.c_int64), _p(stats, C.c_int64))
+    return rc, anc, lwr, go, stats, rg
 
 
 def run(m: Model, N: int, frames: np.ndarray, group_size: int = 4096, scheme: int = SYSTEMATIC,

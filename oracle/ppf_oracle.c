@@ -498,6 +498,89 @@ void orc_balanced_offsets(int64_t N, int32_t G, int64_t *off)
 /* lw_sum: per-particle log-weights used for the RNA group weights (FP64).   */
 /* stats: links, moved, max group size, min group size.                      */
 /* ------------------------------------------------------------------------ */
+/* RNA local resampling and ring exchange (Sec. 3): every group resamples its
+ * own slots from its own fixed-point weights with its own offset, the
+ * offspring carry the group weight log(W_g / n_g) (FP64), and the last mig
+ * offspring of group g go to the last mig slots of group succ[g]. */
+static int rna_exchange(const orc_model *m, int64_t N, int32_t frame, int32_t G, const int64_t *goff_in,
+                        const float *lw, const double *lw_sum, int64_t mig, const int32_t *succ,
+                        int32_t *anc, double *lw_reset)
+{
+    int rc = ORC_OK;
+    int64_t maxsz = 0;
+    for (int32_t g = 0; g < G; ++g)
+        if (goff_in[g + 1] - goff_in[g] > maxsz)
+            maxsz = goff_in[g + 1] - goff_in[g];
+    /* group log-weights log W_g = log sum_g e^lw - log sum e^lw, in FP64 */
+    double Mall = -INFINITY;
+    for (int64_t i = 0; i < N; ++i)
+        if (lw_sum[i] > Mall) Mall = lw_sum[i];
+    double tot = 0.0;
+    for (int64_t i = 0; i < N; ++i)
+        tot += exp(lw_sum[i] - Mall);
+    const double log_tot = Mall + log(tot);
+    int32_t *local = (int32_t *)malloc(sizeof(int32_t) * (size_t)(maxsz > 0 ? maxsz : 1));
+    uint64_t *q = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(maxsz > 0 ? maxsz : 1));
+    for (int32_t g = 0; g < G; ++g) {
+        int64_t lo = goff_in[g], sz = goff_in[g + 1] - lo;
+        if (sz == 0)
+            continue;
+        float Mg = -INFINITY;
+        double Mgd = -INFINITY;
+        for (int64_t i = 0; i < sz; ++i) {
+            if (lw[lo + i] > Mg) Mg = lw[lo + i];
+            if (lw_sum[lo + i] > Mgd) Mgd = lw_sum[lo + i];
+        }
+        int s = orc_scale_bits(sz);
+        uint64_t Q = 0;
+        for (int64_t i = 0; i < sz; ++i) {
+            q[i] = orc_quantise(lw[lo + i], Mg, s);
+            Q += q[i];
+        }
+        double lwg;
+        if (Q == 0) {
+            /* every weight of the group is zero: it keeps its slots */
+            for (int64_t i = 0; i < sz; ++i)
+                local[i] = (int32_t)(lo + i);
+            lwg = -INFINITY;
+        } else {
+            uint64_t u = orc_ticket_offset(m->seed, m->filter_id, (uint32_t)frame,
+                                           ORC_PURPOSE_GROUP_RESAMPLE, (uint32_t)g, Q);
+            int r2 = orc_systematic(sz, q, sz, u, lo, local, NULL);
+            if (r2 != ORC_OK) { rc = r2; break; }
+            double sg = 0.0;
+            for (int64_t i = 0; i < sz; ++i)
+                sg += exp(lw_sum[lo + i] - Mgd);
+            lwg = (Mgd + log(sg)) - log_tot - log((double)sz);
+        }
+        int32_t gn = succ[g];
+        int64_t gn_lo = goff_in[gn], gn_sz = goff_in[gn + 1] - gn_lo;
+        for (int64_t s2 = 0; s2 < sz; ++s2) {
+            int64_t slot;
+            if (s2 < sz - mig)
+                slot = lo + s2;
+            else
+                slot = gn_lo + gn_sz - mig + (s2 - (sz - mig));
+            anc[slot] = local[s2];
+            lw_reset[slot] = lwg;
+        }
+    }
+    free(local);
+    free(q);
+    return rc;
+}
+
+static void group_extents(int32_t G, const int64_t *goff, int64_t *mx, int64_t *mn)
+{
+    *mx = 0;
+    *mn = INT64_MAX;
+    for (int32_t g = 0; g < G; ++g) {
+        int64_t sz = goff[g + 1] - goff[g];
+        if (sz > *mx) *mx = sz;
+        if (sz < *mn) *mn = sz;
+    }
+}
+
 int orc_resample(const orc_model *m, int scheme, double alpha, int64_t N, int32_t frame,
                  int32_t G, const int64_t *goff_in, const float *lw, const double *lw_sum,
                  int32_t *anc, double *lw_reset, int64_t *goff_out, int64_t stats[4])
@@ -505,69 +588,14 @@ int orc_resample(const orc_model *m, int scheme, double alpha, int64_t N, int32_
     int rc = ORC_OK;
     stats[0] = stats[1] = 0;
     if (scheme == ORC_RNA) {
-        int64_t minsz = INT64_MAX, maxsz = 0;
-        for (int32_t g = 0; g < G; ++g) {
-            int64_t sz = goff_in[g + 1] - goff_in[g];
-            if (sz < minsz) minsz = sz;
-            if (sz > maxsz) maxsz = sz;
-        }
+        int64_t minsz, maxsz;
+        group_extents(G, goff_in, &maxsz, &minsz);
         int64_t mig = (int64_t)floor(alpha * (double)minsz);
-        /* group log-weights log W_g = log sum_g e^lw - log sum e^lw, in FP64 */
-        double Mall = -INFINITY;
-        for (int64_t i = 0; i < N; ++i)
-            if (lw_sum[i] > Mall) Mall = lw_sum[i];
-        double tot = 0.0;
-        for (int64_t i = 0; i < N; ++i)
-            tot += exp(lw_sum[i] - Mall);
-        const double log_tot = Mall + log(tot);
-        int32_t *local = (int32_t *)malloc(sizeof(int32_t) * (size_t)(maxsz > 0 ? maxsz : 1));
-        uint64_t *q = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(maxsz > 0 ? maxsz : 1));
-        for (int32_t g = 0; g < G; ++g) {
-            int64_t lo = goff_in[g], sz = goff_in[g + 1] - lo;
-            if (sz == 0)
-                continue;
-            float Mg = -INFINITY;
-            double Mgd = -INFINITY;
-            for (int64_t i = 0; i < sz; ++i) {
-                if (lw[lo + i] > Mg) Mg = lw[lo + i];
-                if (lw_sum[lo + i] > Mgd) Mgd = lw_sum[lo + i];
-            }
-            int s = orc_scale_bits(sz);
-            uint64_t Q = 0;
-            for (int64_t i = 0; i < sz; ++i) {
-                q[i] = orc_quantise(lw[lo + i], Mg, s);
-                Q += q[i];
-            }
-            double lwg;
-            if (Q == 0) {
-                /* every weight of the group is zero: it keeps its slots */
-                for (int64_t i = 0; i < sz; ++i)
-                    local[i] = (int32_t)(lo + i);
-                lwg = -INFINITY;
-            } else {
-                uint64_t u = orc_ticket_offset(m->seed, m->filter_id, (uint32_t)frame,
-                                               ORC_PURPOSE_GROUP_RESAMPLE, (uint32_t)g, Q);
-                int r2 = orc_systematic(sz, q, sz, u, lo, local, NULL);
-                if (r2 != ORC_OK) { rc = r2; break; }
-                double sg = 0.0;
-                for (int64_t i = 0; i < sz; ++i)
-                    sg += exp(lw_sum[lo + i] - Mgd);
-                lwg = (Mgd + log(sg)) - log_tot - log((double)sz);
-            }
-            int32_t gn = (g + 1) % G;
-            int64_t gn_lo = goff_in[gn], gn_sz = goff_in[gn + 1] - gn_lo;
-            for (int64_t s2 = 0; s2 < sz; ++s2) {
-                int64_t slot;
-                if (s2 < sz - mig)
-                    slot = lo + s2;
-                else
-                    slot = gn_lo + gn_sz - mig + (s2 - (sz - mig));
-                anc[slot] = local[s2];
-                lw_reset[slot] = lwg;
-            }
-        }
-        free(local);
-        free(q);
+        int32_t *succ = (int32_t *)calloc((size_t)(G > 0 ? G : 1), sizeof(int32_t));
+        for (int32_t g = 0; g < G; ++g)
+            succ[g] = (g + 1) % G;
+        rc = rna_exchange(m, N, frame, G, goff_in, lw, lw_sum, mig, succ, anc, lw_reset);
+        free(succ);
         for (int32_t g = 0; g <= G; ++g)
             goff_out[g] = goff_in[g];
         stats[0] = (G > 1 && mig > 0) ? G : 0; /* ring links that carry particles */
@@ -707,6 +735,97 @@ int orc_resample(const orc_model *m, int scheme, double alpha, int64_t N, int32_
 }
 
 /* ------------------------------------------------------------------------ */
+/* ARNA (Sec. 7): RNA whose exchange ratio follows the number of groups      */
+/* involved in tracking and whose ring order is redrawn when the object is   */
+/* lost.  The paper describes ARNA in words only; this is the reading taken: */
+/*   involved   group g is involved when proportional allocation (the global */
+/*              systematic tickets of RPA over its cumulative range) gives   */
+/*              it at least its own size: o_g >= n_g (exact integers; none   */
+/*              when no weight is usable).                                   */
+/*   ratio      alpha_k = alpha (1 - |I| / G), alpha the caller's maximum;    */
+/*              mig = floor(alpha (G - |I|) min_g n_g / G), evaluated in     */
+/*              FP64 in that order.                                          */
+/*   ring       a permutation of the groups kept between frames; group       */
+/*              ring[p] sends its last mig offspring to ring[(p+1) mod G].    */
+/*   lost       decided by the caller (the frame's log-evidence below zero:  */
+/*              the cloud explains the frame no better than the background). */
+/*              Then the ring is redrawn before the exchange: the groups in  */
+/*              increasing order of the first Philox word of (seed; g,      */
+/*              frame, filter, RING), ties by group index.                   */
+/* stats: links, moved, max group size, min group size, involved groups.    */
+/* ------------------------------------------------------------------------ */
+typedef struct { uint32_t key; int32_t group; } orc_ring_key;
+
+static int ring_key_asc(const void *a, const void *b)
+{
+    const orc_ring_key *x = (const orc_ring_key *)a, *y = (const orc_ring_key *)b;
+    if (x->key != y->key)
+        return x->key < y->key ? -1 : 1;
+    return x->group < y->group ? -1 : (x->group > y->group);
+}
+
+void orc_arna_ring(uint64_t seed, uint32_t filter, uint32_t frame, int32_t G, int32_t *ring)
+{
+    orc_ring_key *k = (orc_ring_key *)malloc(sizeof(orc_ring_key) * (size_t)(G > 0 ? G : 1));
+    for (int32_t g = 0; g < G; ++g) {
+        uint32_t r[4];
+        draw(seed, (uint32_t)g, frame, filter, ORC_PURPOSE_RING, 0, r);
+        k[g].key = r[0];
+        k[g].group = g;
+    }
+    qsort(k, (size_t)G, sizeof(orc_ring_key), ring_key_asc);
+    for (int32_t p = 0; p < G; ++p)
+        ring[p] = k[p].group;
+    free(k);
+}
+
+int orc_resample_arna(const orc_model *m, double alpha, int64_t N, int32_t frame, int32_t G,
+                      const int64_t *goff_in, const float *lw, const double *lw_sum, int32_t lost,
+                      int32_t *ring, int32_t *anc, double *lw_reset, int64_t *goff_out, int64_t stats[5])
+{
+    /* offspring of every group under proportional allocation */
+    float M = -INFINITY;
+    for (int64_t i = 0; i < N; ++i)
+        if (lw[i] > M) M = lw[i];
+    const int s = orc_scale_bits(N);
+    uint64_t Q = 0;
+    for (int64_t i = 0; i < N; ++i)
+        Q += orc_quantise(lw[i], M, s);
+    int32_t involved = 0;
+    if (Q > 0) {
+        const uint64_t u = orc_ticket_offset(m->seed, m->filter_id, (uint32_t)frame, ORC_PURPOSE_RESAMPLE, 0u, Q);
+        uint64_t C = 0;
+        int64_t below = 0;
+        for (int32_t g = 0; g < G; ++g) {
+            for (int64_t i = goff_in[g]; i < goff_in[g + 1]; ++i)
+                C += orc_quantise(lw[i], M, s);
+            const int64_t t = orc_tickets_below(C, N, u, Q);
+            if (t - below >= goff_in[g + 1] - goff_in[g])
+                ++involved;
+            below = t;
+        }
+    }
+    int64_t minsz, maxsz;
+    group_extents(G, goff_in, &maxsz, &minsz);
+    const int64_t mig = (int64_t)floor(alpha * (double)(G - involved) * (double)minsz / (double)G);
+    if (lost)
+        orc_arna_ring(m->seed, m->filter_id, (uint32_t)frame, G, ring);
+    int32_t *succ = (int32_t *)calloc((size_t)(G > 0 ? G : 1), sizeof(int32_t));
+    for (int32_t p = 0; p < G; ++p)
+        succ[ring[p]] = ring[(p + 1) % G];
+    const int rc = rna_exchange(m, N, frame, G, goff_in, lw, lw_sum, mig, succ, anc, lw_reset);
+    free(succ);
+    for (int32_t g = 0; g <= G; ++g)
+        goff_out[g] = goff_in[g];
+    stats[0] = (G > 1 && mig > 0) ? G : 0;
+    stats[1] = G > 1 ? mig * G : 0;
+    stats[2] = maxsz;
+    stats[3] = minsz;
+    stats[4] = involved;
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* A whole SIR run (Alg. 1): init, then for each frame propagate, weight,    */
 /* summarise, resample (when N_eff < ess_threshold; +inf: every frame).     */
 /* frames: K x H x W doubles.  est: K x 8 (mean[5],                          */
@@ -723,6 +842,9 @@ int orc_run(const orc_model *m, int64_t N, int32_t group_size, int scheme, doubl
     int32_t *anc = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
     int64_t *goff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G + 1));
     int64_t *goff2 = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G + 1));
+    int32_t *ring = (int32_t *)malloc(sizeof(int32_t) * (size_t)G);  /* ARNA ring order, identity at start */
+    for (int32_t g = 0; g < G; ++g)
+        ring[g] = g;
     int rc = ORC_OK;
     orc_init(m, N, cur);
     orc_balanced_offsets(N, G, goff);
@@ -745,8 +867,15 @@ int orc_run(const orc_model *m, int64_t N, int32_t group_size, int scheme, doubl
         } else {
             for (int64_t i = 0; i < N; ++i)
                 lwf[i] = (float)nxt[5 * N + i];
-            int64_t stats[4];
-            rc = orc_resample(m, scheme, alpha, N, k + 1, G, goff, lwf, nxt + 5 * N, anc, lw_prev, goff2, stats);
+            int64_t stats[5];
+            if (scheme == ORC_ARNA) {
+                const int32_t lost = !(est[8 * (int64_t)k + 5] >= 0.0);
+                rc = orc_resample_arna(m, alpha, N, k + 1, G, goff, lwf, nxt + 5 * N, lost, ring, anc, lw_prev,
+                                       goff2, stats);
+            } else {
+                rc = orc_resample(m, scheme, alpha, N, k + 1, G, goff, lwf, nxt + 5 * N, anc, lw_prev, goff2,
+                                  stats);
+            }
             if (rc != ORC_OK)
                 break;
             memcpy(goff, goff2, sizeof(int64_t) * (size_t)(G + 1));
@@ -755,7 +884,7 @@ int orc_run(const orc_model *m, int64_t N, int32_t group_size, int scheme, doubl
     }
     if (st_out)
         memcpy(st_out, cur, sizeof(double) * (size_t)(6 * N));
-    free(cur); free(nxt); free(lw_prev); free(lwf); free(anc); free(goff); free(goff2);
+    free(cur); free(nxt); free(lw_prev); free(lwf); free(anc); free(goff); free(goff2); free(ring);
     return rc;
 }
 

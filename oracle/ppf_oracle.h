@@ -8,9 +8,9 @@
 
 enum { ORC_OK = 0, ORC_EDEGENERATE = 5, ORC_EINTERNAL = 7 };
 enum { ORC_SYSTEMATIC = 0, ORC_RPA_GS = 1, ORC_RPA_SGS = 2, ORC_RPA_LGS = 3, ORC_RNA = 4,
-       ORC_RPA2_GS = 5, ORC_RPA2_SGS = 6, ORC_RPA2_LGS = 7 };
+       ORC_RPA2_GS = 5, ORC_RPA2_SGS = 6, ORC_RPA2_LGS = 7, ORC_ARNA = 8 };
 enum { ORC_PURPOSE_INIT = 0, ORC_PURPOSE_PROP = 1, ORC_PURPOSE_RESAMPLE = 2,
-       ORC_PURPOSE_GROUP_RESAMPLE = 3 };
+       ORC_PURPOSE_GROUP_RESAMPLE = 3, ORC_PURPOSE_RING = 4 };
 
 typedef struct {
     int32_t width, height, patch_radius;
@@ -50,6 +50,10 @@ void orc_balanced_offsets(int64_t N, int32_t G, int64_t *off);
 int orc_resample(const orc_model *m, int scheme, double alpha, int64_t N, int32_t frame,
                  int32_t G, const int64_t *goff_in, const float *lw, const double *lw_sum,
                  int32_t *anc, double *lw_reset, int64_t *goff_out, int64_t stats[4]);
+void orc_arna_ring(uint64_t seed, uint32_t filter, uint32_t frame, int32_t G, int32_t *ring);
+int orc_resample_arna(const orc_model *m, double alpha, int64_t N, int32_t frame, int32_t G,
+                      const int64_t *goff_in, const float *lw, const double *lw_sum, int32_t lost,
+                      int32_t *ring, int32_t *anc, double *lw_reset, int64_t *goff_out, int64_t stats[5]);
 int orc_run(const orc_model *m, int64_t N, int32_t group_size, int scheme, double alpha,
             double ess_threshold, int32_t K, const double *frames, double *est, double *st_out);
 void orc_loglik_partials(const orc_model *m, const double *frame, double x, double y, double I0, int32_t ax,
