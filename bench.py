@@ -48,6 +48,12 @@ STEP_FLOPS = 2 * 11 * 11 + 2 * 11 + 4 * 11 + 6 + 10
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+# the scheme rows, in the order they run in one context: every row starts
+# from balanced groups except the LGS rows, which unbalance them themselves
+SCHEME_ROWS = [("rpa_gs", 0.0), ("rpa_sgs", 0.0), ("rpa2_gs", 0.0), ("rpa2_sgs", 0.0), ("rna", 0.1), ("rna", 0.5),
+               ("arna", 0.5), ("systematic", 0.0), ("rpa_lgs", 0.0), ("rpa2_lgs", 0.0)]
+
+
 def workload_desc(n, scheme):
     return {
         "workload": f"spot512: {W}x{H} float32 Poisson frames, one Gaussian-PSF spot, N={n:,} particles, "
@@ -135,14 +141,25 @@ def run_reference(args):
     st = orc.init(m, n)
     anc = np.arange(n, dtype=np.int32)
     lw_prev = np.zeros(n)
-    goff = orc.balanced_offsets(n, (n + GROUP - 1) // GROUP)
+    G = (n + GROUP - 1) // GROUP
+    goff = orc.balanced_offsets(n, G)
+    ring = np.arange(G, dtype=np.int32)
+    scheme = {"systematic": orc.SYSTEMATIC, "rpa_gs": orc.RPA_GS, "rpa_sgs": orc.RPA_SGS, "rpa_lgs": orc.RPA_LGS,
+              "rna": orc.RNA, "rpa2_gs": orc.RPA2_GS, "rpa2_sgs": orc.RPA2_SGS, "rpa2_lgs": orc.RPA2_LGS,
+              "arna": orc.ARNA}[args.scheme]
+    alpha = float(np.float32(args.alpha))
     times = []
     for k in range(1, args.warmup + args.steps + 1):
         t0 = time.perf_counter()
         nxt = orc.propagate(m, k, st, anc, lw_prev)
         nxt = orc.weight(m, mv.frames[k - 1], nxt)
-        orc.summary(nxt, lw_prev)
-        rc, anc, lw_prev, goff, _ = orc.resample(m, orc.SYSTEMATIC, n, k, goff, nxt[5].astype(np.float32), nxt[5])
+        so = orc.summary(nxt, lw_prev)
+        lwf = nxt[5].astype(np.float32)
+        if scheme == orc.ARNA:
+            rc, anc, lw_prev, goff, _, ring = orc.resample_arna(m, n, k, goff, lwf, so["log_evidence"] < 0.0, ring,
+                                                                lw_sum=nxt[5], alpha=alpha)
+        else:
+            rc, anc, lw_prev, goff, _ = orc.resample(m, scheme, n, k, goff, lwf, nxt[5], alpha=alpha)
         st = nxt
         if k > args.warmup:
             times.append(time.perf_counter() - t0)
@@ -152,7 +169,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_desc(N_FULL, "systematic"),
+            "data": "synthetic", "config": workload_desc(N_FULL, args.scheme),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -207,7 +224,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     n = args.n
     K, Wm = args.steps, args.warmup
-    extra = 0 if args.no_schemes else 9 * (args.scheme_steps + 2)
+    extra = 0 if args.no_schemes else len(SCHEME_ROWS) * (args.scheme_steps + 2)
     k_total = Wm + K + extra + (args.e2e_steps if not args.no_e2e else 0) + 2
     mv, params = make_workload(k_total, seed=0)
     model = ppf.Model(**params, seed=rank, filter_id=rank)
@@ -298,8 +315,7 @@ def run_ours(args):
         # every row starts from balanced groups except the LGS rows, which
         # unbalance them themselves (they run last so that no other row
         # inherits their layout)
-        for name, alpha in [("rpa_gs", 0.0), ("rpa_sgs", 0.0), ("rpa2_gs", 0.0), ("rpa2_sgs", 0.0), ("rna", 0.1),
-                            ("rna", 0.5), ("systematic", 0.0), ("rpa_lgs", 0.0), ("rpa2_lgs", 0.0)]:
+        for name, alpha in SCHEME_ROWS:
             sid = ppf.SCHEMES[name]
             for _ in range(2):
                 pf.step(frames[k - 1], k)
@@ -477,7 +493,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--scheme", default="systematic", choices=sorted(["systematic", "rpa_gs", "rpa_sgs",
                                                                       "rpa_lgs", "rna", "rpa2_gs", "rpa2_sgs",
-                                                                      "rpa2_lgs"]))
+                                                                      "rpa2_lgs", "arna"]))
     ap.add_argument("--alpha", type=float, default=0.1)
     ap.add_argument("--scheme-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=100)

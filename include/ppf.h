@@ -49,7 +49,17 @@ typedef enum {
      * them inside the group with its own systematic offset. */
     PPF_RPA2_GS = 5,
     PPF_RPA2_SGS = 6,
-    PPF_RPA2_LGS = 7
+    PPF_RPA2_LGS = 7,
+    /* Adaptive RNA (Sec. 7, described there in words only; the reading
+     * taken): RNA whose exchange ratio is exchange_ratio * (1 - |I| / G),
+     * I the groups that proportional allocation (the global systematic
+     * tickets of RPA) would give at least their own size, and whose ring is
+     * a permutation of the groups kept between calls.  When the step's
+     * log-evidence is negative (the object counts as lost) the ring is first
+     * redrawn: the groups in increasing order of the first Philox word of
+     * (seed; g, frame, filter, 4), ties by group index.  At most 16384
+     * groups. */
+    PPF_ARNA = 8
 } ppf_scheme;
 
 typedef enum { PPF_F32 = 0, PPF_BF16 = 1, PPF_F16 = 2 } ppf_dtype;
@@ -90,7 +100,8 @@ typedef struct {
                                  2 inconsistent routing (copy skipped),
                                  3 caller ancestor out of range (identity used),
                                  4 resampling skipped by the N_eff test
-                                   (ppf_resample_if)                            */
+                                   (ppf_resample_if),
+                                 5 ARNA redrew its ring (object lost)           */
     int64_t links;            /* routing links of the last resample (Sec. 4-5)   */
     int64_t moved;            /* particles moved between groups by that resample */
     int64_t max_group;        /* largest / smallest group after it               */
@@ -139,8 +150,9 @@ ppf_status ppf_step_host(ppf_ctx *ctx, const void *frame_host, int32_t k);
 
 /* The resampling step of Alg. 1 on the weights of the last step, using the
  * scheme's allocation (Sec. 3) and, for RPA, the scheme's routing schedule
- * (Sec. 4).  exchange_ratio: RNA only, the fraction alpha of the smallest
- * group that migrates to the next group of the ring (0 <= alpha <= 1).
+ * (Sec. 4).  exchange_ratio: RNA, the fraction alpha of the smallest group
+ * that migrates to the next group of the ring; ARNA, the largest such
+ * fraction (0 <= alpha <= 1; ignored by the other schemes).
  * Systematic and RPA reset the weights to equal; RNA gives every offspring
  * its group's weight / group size.  LGS may leave the groups unequal.
  * Errors: PPF_ESTATE (no step since the last resample), PPF_EINVAL, PPF_ECUDA.
@@ -204,6 +216,14 @@ ppf_status ppf_get_groups(ppf_ctx *ctx, int32_t *n_groups, int64_t *offsets_host
  * host int64 offsets, offsets[0] = 0, offsets[G] = N, non-decreasing (LGS
  * leaves groups unequal).  Synchronises.  Errors: PPF_EINVAL, PPF_ECUDA. */
 ppf_status ppf_set_groups(ppf_ctx *ctx, const int64_t *offsets_host);
+
+/* The ARNA ring order: G int32 group indices, ring[p] sending its migrants
+ * to ring[(p + 1) mod G] (identity when the context is created and after
+ * ppf_set_groups).  ppf_get_ring copies it to a host buffer (synchronises);
+ * ppf_set_ring replaces it (restart hook) and returns PPF_EINVAL unless the
+ * values are a permutation of 0..G-1.  Errors: PPF_EINVAL, PPF_ECUDA. */
+ppf_status ppf_get_ring(ppf_ctx *ctx, int32_t *ring_host);
+ppf_status ppf_set_ring(ppf_ctx *ctx, const int32_t *ring_host);
 
 /* Gradient of the log marginal likelihood estimate (the sum over frames of
  * the per-frame log-evidence of Alg. 1) with respect to

@@ -1,9 +1,10 @@
 """GB300-native SIR particle filter for single-spot tracking (PPF, Demirel et
 al.): propagation, patch likelihood, normalisation, estimate and the
-systematic / RPA (GS, SGS, LGS) / RNA resampling steps as hand-written CUDA
+systematic / RPA (GS, SGS, LGS, one- and two-stage) / RNA / ARNA resampling steps as hand-written CUDA
 kernels for sm_103a behind the C ABI of ``include/ppf.h``."""
 
 from ._binding import (  # noqa: F401
+    ARNA,
     BF16,
     EDEGENERATE,
     EINVAL,

@@ -16,14 +16,16 @@ from . import _build
 
 SYSTEMATIC, RPA_GS, RPA_SGS, RPA_LGS, RNA = 0, 1, 2, 3, 4
 RPA2_GS, RPA2_SGS, RPA2_LGS = 5, 6, 7  # two-stage proportional allocation
+ARNA = 8  # adaptive RNA: exchange ratio from the involved groups, ring redrawn when the object is lost
 F32, BF16, F16 = 0, 1, 2
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEGENERATE, ESTATE = range(7)
 SCHEMES = {"systematic": SYSTEMATIC, "rpa_gs": RPA_GS, "rpa_sgs": RPA_SGS, "rpa_lgs": RPA_LGS, "rna": RNA,
-           "rpa2_gs": RPA2_GS, "rpa2_sgs": RPA2_SGS, "rpa2_lgs": RPA2_LGS}
+           "rpa2_gs": RPA2_GS, "rpa2_sgs": RPA2_SGS, "rpa2_lgs": RPA2_LGS, "arna": ARNA}
 
 EXPORTS = ["ppf_create", "ppf_destroy", "ppf_step", "ppf_step_host", "ppf_resample", "ppf_resample_if",
            "ppf_estimate", "ppf_estimate_async",
-           "ppf_get_particles", "ppf_set_particles", "ppf_get_groups", "ppf_set_groups", "ppf_status_string",
+           "ppf_get_particles", "ppf_set_particles", "ppf_get_groups", "ppf_set_groups", "ppf_get_ring",
+           "ppf_set_ring", "ppf_status_string",
            "ppf_last_error", "ppf_profile_enable", "ppf_profile_read", "ppf_systematic_resample_noalloc",
            "ppf_loglik_grad", "ppf_batch_create", "ppf_batch_destroy", "ppf_batch_step", "ppf_batch_resample",
            "ppf_batch_run", "ppf_batch_estimates", "ppf_batch_get_particles", "ppf_batch_autotune",
@@ -158,6 +160,8 @@ def load(build_if_missing: bool = True):
             "ppf_set_particles": (C.c_int, [ctxp, vp, vp, vp]),
             "ppf_get_groups": (C.c_int, [ctxp, P(C.c_int32), vp]),
             "ppf_set_groups": (C.c_int, [ctxp, vp]),
+            "ppf_get_ring": (C.c_int, [ctxp, vp]),
+            "ppf_set_ring": (C.c_int, [ctxp, vp]),
             "ppf_status_string": (C.c_char_p, [C.c_int]),
             "ppf_last_error": (C.c_char_p, [ctxp]),
             "ppf_profile_enable": (C.c_int, [ctxp, C.c_int, C.c_int32]),
@@ -337,6 +341,19 @@ class ParticleFilter:
         import numpy as np
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         self._check(self.L.ppf_set_groups(self._ctx, C.c_void_p(off.ctypes.data)), "ppf_set_groups")
+
+    def ring(self):
+        """ARNA's ring order: ring[p] sends its migrants to ring[(p + 1) % G]."""
+        import numpy as np
+        r = np.zeros(len(self.groups()) - 1, dtype=np.int32)
+        self._check(self.L.ppf_get_ring(self._ctx, C.c_void_p(r.ctypes.data)), "ppf_get_ring")
+        return r
+
+    def set_ring(self, ring):
+        """Replace ARNA's ring order (a permutation of the G group indices)."""
+        import numpy as np
+        r = np.ascontiguousarray(ring, dtype=np.int32)
+        self._check(self.L.ppf_set_ring(self._ctx, C.c_void_p(r.ctypes.data)), "ppf_set_ring")
 
     def profile_enable(self, enable: bool = True, capacity: int = 4096):
         self._check(self.L.ppf_profile_enable(self._ctx, 1 if enable else 0, int(capacity)), "ppf_profile_enable")

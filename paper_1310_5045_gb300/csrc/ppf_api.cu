@@ -58,7 +58,7 @@ cudaError_t dalloc(T **p, size_t count)
 void free_all(ppf_ctx *c)
 {
     void *ptrs[] = {c->tang[0], c->tang[1], c->gpart,
-                    c->state[0], c->state[1], c->anc, c->anc_sys, c->lwp, c->goff, c->goff_new, c->Zp,
+                    c->state[0], c->state[1], c->anc, c->anc_sys, c->lwp, c->goff, c->goff_new, c->ring, c->succ, c->Zp,
                     c->frame_buf[0], c->frame_buf[1], c->lmap, c->part, c->sum, c->est_dev, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sc.Cbl,
                     c->sc.Tg, c->sc.skey, c->sc.sval, c->sc.seg_tick, c->sc.seg_dst, c->sc.seg_len,
                     c->sc.seg_chunk};
@@ -72,6 +72,21 @@ void free_all(ppf_ctx *c)
             cudaEventDestroy(c->prof_ev[i]);
         free(c->prof_ev);
     }
+}
+
+// the ARNA ring in group order (host copy, synchronous)
+cudaError_t identity_ring(ppf_ctx *c)
+{
+    int32_t *h = (int32_t *)malloc(sizeof(int32_t) * (size_t)c->G);
+    if (!h)
+        return cudaErrorMemoryAllocation;
+    for (int32_t g = 0; g < c->G; ++g)
+        h[g] = g;
+    cudaError_t e = cudaMemcpyAsync(c->ring, h, sizeof(int32_t) * (size_t)c->G, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    free(h);
+    return e;
 }
 
 size_t dtype_size(int32_t dt)
@@ -172,6 +187,8 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
         chk(dalloc(&c->lwp, N), "lwp");
         chk(dalloc(&c->goff, G + 1), "goff");
         chk(dalloc(&c->goff_new, G + 1), "goff_new");
+        chk(dalloc(&c->ring, G), "ring");
+        chk(dalloc(&c->succ, G), "ring successors");
         chk(dalloc(&c->Zp, 2 * (size_t)c->Wp * c->Hp), "Zp");
         if (m->likelihood == 1)
             chk(dalloc(&c->lmap, (size_t)(m->width + 2 * m->patch_radius) * (m->height + 2 * m->patch_radius)),
@@ -212,6 +229,8 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
             free(h);
         }
     }
+    if (st == PPF_OK)
+        chk(identity_ring(c), "ring");
     if (st == PPF_OK)
         chk(ppf::resample_kernel_attributes(), "kernel attributes");
     if (st == PPF_OK)
@@ -305,20 +324,21 @@ ppf_status ppf_resample_if(ppf_ctx *c, ppf_scheme scheme, float alpha, double es
         return PPF_EINVAL;
     if (ess_threshold != ess_threshold)  // NaN
         return PPF_EINVAL;
-    if (scheme < PPF_SYSTEMATIC || scheme > PPF_RPA2_LGS)
+    if (scheme < PPF_SYSTEMATIC || scheme > PPF_ARNA)
         return PPF_EINVAL;
-    if (scheme == PPF_RNA && !(alpha >= 0.0f && alpha <= 1.0f))
+    if ((scheme == PPF_RNA || scheme == PPF_ARNA) && !(alpha >= 0.0f && alpha <= 1.0f))
         return PPF_EINVAL;
-    const bool routed = (scheme >= PPF_RPA_GS && scheme <= PPF_RPA_LGS) ||
-                        (scheme >= PPF_RPA2_GS && scheme <= PPF_RPA2_LGS);
-    if (routed && c->G > MAX_SCHED_GROUPS) {
-        set_err(c, "RPA schedules support at most %d groups", MAX_SCHED_GROUPS);
+    const bool sorted_groups = (scheme >= PPF_RPA_GS && scheme <= PPF_RPA_LGS) ||
+                               (scheme >= PPF_RPA2_GS && scheme <= PPF_RPA2_LGS) || scheme == PPF_ARNA;
+    if (sorted_groups && c->G > MAX_SCHED_GROUPS) {
+        set_err(c, "RPA schedules and the ARNA ring support at most %d groups", MAX_SCHED_GROUPS);
         return PPF_EINVAL;
     }
     if (!c->weighted)
         return PPF_ESTATE;
-    if (scheme == PPF_RNA) {
-        CK(ppf::launch_resample_rna(c, alpha, ess_threshold));
+    if (scheme == PPF_RNA || scheme == PPF_ARNA) {
+        CK(scheme == PPF_RNA ? ppf::launch_resample_rna(c, alpha, ess_threshold)
+                             : ppf::launch_resample_arna(c, alpha, ess_threshold));
         c->mode = MODE_EXPLICIT;
     } else {
         CK(ppf::launch_resample_global(c, (int)scheme, ess_threshold));
@@ -372,7 +392,7 @@ ppf_status ppf_estimate(ppf_ctx *c, ppf_estimate_t *out)
         if (s.flags & FLAG_TIMEOUT)
             return PPF_ETIMEOUT;
     }
-    return PPF_OK;  // FLAG_KEPT (N_eff test) is information, not an error
+    return PPF_OK;  // FLAG_KEPT (N_eff test) and FLAG_RING (ARNA redraw) are information, not errors
 }
 
 ppf_status ppf_estimate_async(ppf_ctx *c, ppf_estimate_t *out)
@@ -447,6 +467,38 @@ ppf_status ppf_set_groups(ppf_ctx *c, const int64_t *offsets_host)
             return PPF_EINVAL;
     CK(cudaMemcpyAsync(c->goff, offsets_host, sizeof(int64_t) * (c->G + 1), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));  // offsets_host may be released on return
+    CK(identity_ring(c));
+    return PPF_OK;
+}
+
+ppf_status ppf_get_ring(ppf_ctx *c, int32_t *ring_host)
+{
+    if (!c || !ring_host)
+        return PPF_EINVAL;
+    CK(cudaMemcpyAsync(ring_host, c->ring, sizeof(int32_t) * (size_t)c->G, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PPF_OK;
+}
+
+ppf_status ppf_set_ring(ppf_ctx *c, const int32_t *ring_host)
+{
+    if (!c || !ring_host)
+        return PPF_EINVAL;
+    unsigned char *seen = (unsigned char *)calloc((size_t)c->G, 1);
+    if (!seen)
+        return PPF_ENOMEM;
+    bool ok = true;
+    for (int32_t p = 0; p < c->G && ok; ++p) {
+        const int32_t g = ring_host[p];
+        ok = g >= 0 && g < c->G && !seen[g];
+        if (ok)
+            seen[g] = 1;
+    }
+    free(seen);
+    if (!ok)
+        return PPF_EINVAL;
+    CK(cudaMemcpyAsync(c->ring, ring_host, sizeof(int32_t) * (size_t)c->G, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return PPF_OK;
 }
 

@@ -20,7 +20,7 @@ namespace ppf {
 
 typedef unsigned __int128 u128;
 
-enum : uint32_t { PURPOSE_INIT = 0, PURPOSE_PROP = 1, PURPOSE_RESAMPLE = 2, PURPOSE_GROUP = 3 };
+enum : uint32_t { PURPOSE_INIT = 0, PURPOSE_PROP = 1, PURPOSE_RESAMPLE = 2, PURPOSE_GROUP = 3, PURPOSE_RING = 4 };
 
 // One Philox4x32-10 block: ten rounds of two 32x32->64 multiplications of
 // counter words 0 and 2, the high halves xor-ed with the other counter words

@@ -33,7 +33,10 @@ enum StepMode : int {
     MODE_EXPLICIT = 2   // resampled: per-slot lw_prev buffer (RNA, restarts)
 };
 
-enum : int { FLAG_DEGENERATE = 1, FLAG_TIMEOUT = 2, FLAG_INTERNAL = 4, FLAG_BAD_ANCESTOR = 8, FLAG_KEPT = 16 };
+enum : int {
+    FLAG_DEGENERATE = 1, FLAG_TIMEOUT = 2, FLAG_INTERNAL = 4, FLAG_BAD_ANCESTOR = 8, FLAG_KEPT = 16,
+    FLAG_RING = 32  // ARNA redrew its ring
+};
 
 // per-block weight statistics of one step (online log-sum-exp partials)
 struct Partial {
@@ -64,6 +67,7 @@ struct DevSummary {
     int32_t n_items;           // fill work items of the last resample
     int32_t n_chunks;          // routing-copy work items of the last RPA resample
     int64_t mig;               // RNA: slots migrating to the next group
+    int32_t involved;          // ARNA: groups that proportional allocation gives at least their size
     uint32_t blocks_done;      // step kernel: blocks that published partials
     double grad_L;             // ppf_loglik_grad: running sum of log-evidences
     double grad_g[4];          // and of their derivatives
@@ -101,6 +105,7 @@ struct ppf_ctx {
     int32_t *anc_sys;             // systematic ancestors before RPA routing
     float *lwp;                   // per-slot starting log-weights (MODE_EXPLICIT)
     int64_t *goff, *goff_new;     // group offsets [G+1]
+    int32_t *ring, *succ;         // ARNA ring order [G] and each group's successor on it [G]
     float *Zp;                    // padded frame minus background
     float2 *lmap;                 // pcSIR: (B, C) patch sums of every anchor (W + 2r) x (H + 2r)
     int32_t Wp, Hp, pad;
@@ -144,6 +149,7 @@ cudaError_t launch_grad_step(ppf_ctx *c, int32_t k, bool first, int32_t *anchors
 cudaError_t resample_kernel_attributes();
 cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr);
 cudaError_t launch_resample_rna(ppf_ctx *c, float alpha, double ess_thr);
+cudaError_t launch_resample_arna(ppf_ctx *c, float alpha, double ess_thr);
 cudaError_t launch_identity(ppf_ctx *c, int32_t *dst);
 cudaError_t launch_pending(ppf_ctx *c, int32_t *anc_out, float *lwp_out);
 cudaError_t launch_fill_f32(ppf_ctx *c, float *dst, float v);

@@ -708,10 +708,12 @@ __global__ void __launch_bounds__(256) route_copy_kernel(const int32_t *__restri
 // One block per group: group max, fixed-point weights, local total and group
 // weight (FP64 against the global total of the step), local systematic
 // tickets, then every offspring is written to its slot -- the last `mig`
-// slots of the group go to the tail of the next group of the ring.
+// slots of the group go to the tail of the next group of the ring (group
+// g + 1 mod G, or succ[g] for ARNA's ring).
 __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
-    const float *__restrict__ lw, int64_t N, int32_t G, const int64_t *__restrict__ goff, DevSummary *sum,
-    double ess_thr, uint64_t seed, uint32_t fid, uint32_t frame, int32_t *__restrict__ anc, float *__restrict__ lwp)
+    const float *__restrict__ lw, int64_t N, int32_t G, const int64_t *__restrict__ goff,
+    const int32_t *__restrict__ succ, DevSummary *sum, double ess_thr, uint64_t seed, uint32_t fid, uint32_t frame,
+    int32_t *__restrict__ anc, float *__restrict__ lwp)
 {
     if (kept_by_ess(sum, ess_thr))
         return;
@@ -729,7 +731,7 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
     const int64_t lo = goff[g], sz = goff[g + 1] - lo;
     if (sz <= 0)
         return;
-    const int32_t gn = (g + 1) % G;
+    const int32_t gn = succ ? succ[g] : (g + 1) % G;
     const int64_t gn_lo = goff[gn], gn_sz = goff[gn + 1] - gn_lo;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // pass 1: group maximum
@@ -851,6 +853,89 @@ __global__ void __launch_bounds__(1024) rna_prep_kernel(const int64_t *__restric
     }
 }
 
+// ------------------------------------------------------------------ ARNA
+// One block, after the RPA tile passes have counted the tickets below every
+// group start (Tg): the involved groups (proportional allocation gives them
+// at least their own size), the adaptive number of migrants
+// mig = floor(alpha (G - |I|) min_g n_g / G) (FP64, in that order), and the
+// ring -- redrawn when the step's log-evidence is negative (the object
+// counts as lost): the groups in increasing order of the first Philox word of
+// (seed; g, frame, filter, RING), ties by index (a bitonic sort of
+// word << 32 | g).  Then every group's successor on the ring.
+// Dynamic shared memory: MAX_SCHED_GROUPS u64 (G <= MAX_SCHED_GROUPS).
+__global__ void __launch_bounds__(1024) arna_prep_kernel(const int64_t *__restrict__ goff, int32_t G, float alpha,
+                                                         DevSummary *sum, double ess_thr,
+                                                         const int64_t *__restrict__ Tg, int32_t *__restrict__ ring,
+                                                         int32_t *__restrict__ succ, uint64_t seed, uint32_t fid,
+                                                         uint32_t frame)
+{
+    extern __shared__ uint64_t sm[];
+    __shared__ long long smx[32], smn[32];
+    __shared__ int sinv[32];
+    __shared__ bool s_lost;
+    const bool kept = kept_by_ess(sum, ess_thr);  // N_eff test: no resampling, no exchange, ring kept
+    const bool usable = !kept && sum->Q != 0ull;  // Tg holds the tickets only when some weight is usable
+    long long mx = 0, mn = INT64_MAX;
+    int inv = 0;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        const long long sz = goff[g + 1] - goff[g];
+        mx = sz > mx ? sz : mx;
+        mn = sz < mn ? sz : mn;
+        if (usable && Tg[g + 1] - Tg[g] >= sz)
+            ++inv;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long a = __shfl_xor_sync(0xffffffffu, mx, o);
+        const long long b = __shfl_xor_sync(0xffffffffu, mn, o);
+        mx = a > mx ? a : mx;
+        mn = b < mn ? b : mn;
+        inv += __shfl_xor_sync(0xffffffffu, inv, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        smx[threadIdx.x >> 5] = mx;
+        smn[threadIdx.x >> 5] = mn;
+        sinv[threadIdx.x >> 5] = inv;
+    }
+    if (threadIdx.x == 0)
+        s_lost = !kept && !(sum->log_evidence >= 0.0);
+    __syncthreads();
+    if (s_lost) {
+        for (int g = threadIdx.x; g < G; g += blockDim.x) {
+            const uint4 r = draw(seed, (uint32_t)g, frame, fid, PURPOSE_RING, 0);
+            sm[g] = ((uint64_t)r.x << 32) | (uint32_t)g;
+        }
+        __syncthreads();
+        block_sort_u64(sm, G, sm);
+        for (int p = threadIdx.x; p < G; p += blockDim.x)
+            ring[p] = (int32_t)(uint32_t)sm[p];
+        __syncthreads();
+    }
+    for (int p = threadIdx.x; p < G; p += blockDim.x)
+        succ[ring[p]] = ring[(p + 1) % G];
+    if (threadIdx.x == 0) {
+        long long a = 0, b = INT64_MAX;
+        int in = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a = smx[w] > a ? smx[w] : a;
+            b = smn[w] < b ? smn[w] : b;
+            in += sinv[w];
+        }
+        const int64_t mig =
+            kept ? 0 : (int64_t)floor((double)alpha * (double)(G - in) * (double)b / (double)G);
+        sum->mig = mig;
+        sum->involved = in;
+        sum->max_group = a;
+        sum->min_group = b;
+        sum->links = (G > 1 && mig > 0) ? G : 0;
+        sum->moved = (G > 1) ? mig * G : 0;
+        sum->degenerate = kept ? 1 : 0;
+        if (kept)
+            sum->flags |= FLAG_KEPT;
+        if (s_lost)
+            sum->flags |= FLAG_RING;
+    }
+}
+
 // ancestors / starting log-weights the next step will use
 __global__ void pending_kernel(int64_t N, int mode, const int32_t *__restrict__ anc, const float *__restrict__ lwp,
                                const float *__restrict__ lw_cur, const int32_t *__restrict__ degenerate,
@@ -891,6 +976,9 @@ cudaError_t resample_kernel_attributes()
                                  (int)FILL_SMEM_BYTES);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(schedule_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(uint64_t) * MAX_SCHED_GROUPS));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(arna_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(uint64_t) * MAX_SCHED_GROUPS));
     return e;
 }
@@ -953,10 +1041,34 @@ cudaError_t launch_resample_rna(ppf_ctx *c, float alpha, double ess_thr)
     const float *lw = c->state[c->cur] + 5 * c->N;
     prof_mark(c, PH_RESAMPLE, 0);
     rna_prep_kernel<<<1, 1024, 0, c->stream>>>(c->goff, c->G, alpha, c->sum, ess_thr);
-    rna_kernel<<<c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(lw, c->N, c->G, c->goff, c->sum, ess_thr, c->m.seed,
-                                                     c->m.filter_id, (uint32_t)c->last_frame, c->anc, c->lwp);
+    rna_kernel<<<c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(lw, c->N, c->G, c->goff, nullptr, c->sum, ess_thr,
+                                                                   c->m.seed, c->m.filter_id,
+                                                                   (uint32_t)c->last_frame, c->anc, c->lwp);
     prof_mark(c, PH_RESAMPLE, 1);
     c->launches += 2;
+    return cudaGetLastError();
+}
+
+// ARNA: the RPA tile passes count each group's proportional offspring, one
+// block settles the exchange and the ring, then RNA's per-group kernel.
+cudaError_t launch_resample_arna(ppf_ctx *c, float alpha, double ess_thr)
+{
+    const float *lw = c->state[c->cur] + 5 * c->N;
+    const int T = c->T;
+    prof_mark(c, PH_RESAMPLE, 0);
+    tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff, c->G,
+                                                          c->sc.Cbl);
+    tile_scan_kernel<<<1, 1024, 0, c->stream>>>(c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, nullptr,
+                                                c->sum, ess_thr, c->m.seed, c->m.filter_id,
+                                                (uint32_t)c->last_frame, c->goff, c->G, 1, c->sc.Cbl, c->sc.Tg);
+    arna_prep_kernel<<<1, 1024, sizeof(uint64_t) * MAX_SCHED_GROUPS, c->stream>>>(
+        c->goff, c->G, alpha, c->sum, ess_thr, c->sc.Tg, c->ring, c->succ, c->m.seed, c->m.filter_id,
+        (uint32_t)c->last_frame);
+    rna_kernel<<<c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(lw, c->N, c->G, c->goff, c->succ, c->sum, ess_thr,
+                                                                   c->m.seed, c->m.filter_id,
+                                                                   (uint32_t)c->last_frame, c->anc, c->lwp);
+    prof_mark(c, PH_RESAMPLE, 1);
+    c->launches += 4;
     return cudaGetLastError();
 }
 

@@ -119,6 +119,7 @@ def lockstep(pf, gm, om, frames_np, frames_gpu, scheme, K, alpha=0.1, check_resa
         if scheme is None:
             continue
         # S6-S8: resampling from the same float32 log-weights
+        ring0 = pf.ring() if scheme == orc.ARNA else None
         pf.resample(scheme, alpha, ess_threshold)
         _, anc1, lwp1 = pf.get_particles(state=False, anc=True, lw_prev=True)
         goff1 = pf.groups()
@@ -140,8 +141,22 @@ def lockstep(pf, gm, om, frames_np, frames_gpu, scheme, K, alpha=0.1, check_resa
             assert np.array_equal(goff1, goff0)
             assert (est2.links, est2.moved) == (0, 0)
             continue
-        rc, anc_ref, lwr_ref, goff_ref, stats = orc.resample(om, scheme, N, k, goff0, lwf,
-                                                             lwf.astype(np.float64), alpha)
+        if scheme == orc.ARNA:
+            # the object counts as lost when the log-evidence is negative;
+            # away from zero both sides must agree, and the oracle follows the
+            # decision the GPU took
+            lost = bool(est2.status_flags & 32)
+            le = so["log_evidence"]
+            if abs(le) > 1e-6 * max(1.0, abs(le)):
+                assert lost == (le < 0.0), (k, le, lost)
+            if log is not None:
+                log.append(("lost", k, lost))
+            rc, anc_ref, lwr_ref, goff_ref, stats, ring_ref = orc.resample_arna(
+                om, N, k, goff0, lwf, lost, ring0, lw_sum=lwf.astype(np.float64), alpha=f32(alpha))
+            assert np.array_equal(pf.ring(), ring_ref), f"frame {k}: ring differs"
+        else:
+            rc, anc_ref, lwr_ref, goff_ref, stats = orc.resample(om, scheme, N, k, goff0, lwf,
+                                                                 lwf.astype(np.float64), alpha)
         assert rc == 0
         a1 = anc1.cpu().numpy()
         assert np.array_equal(a1, anc_ref), f"frame {k}: {np.sum(a1 != anc_ref)} ancestors differ"

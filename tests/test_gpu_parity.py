@@ -1,5 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
 same seeded inputs (tolerances derived in tests/gpu_common.py)."""
+import dataclasses
 import math
 
 import numpy as np
@@ -274,6 +275,45 @@ def test_checkpoint_and_resume(ppf, movie):
         b.set_groups(np.zeros(len(goff), dtype=np.int64))  # does not end at N
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("N,gs", [(16384, 1024), (10000, 777)])
+def test_arna_lockstep_with_a_lost_object(ppf, N, gs):
+    """ARNA frame by frame against the oracle on a movie whose spot vanishes
+    for two frames: the exchange ratio follows the involved groups, the ring
+    is redrawn on the frames the object is lost (negative log-evidence) and
+    kept otherwise; ancestors, weights, ring and counts bit-exact."""
+    from gpu_common import lockstep, paired_models
+    mv = synth.make_movie(W=128, H=128, K=8, sigma=1.5, amplitude=50.0, background=10.0, seed=4)
+    blank = synth.make_movie(W=128, H=128, K=8, sigma=1.5, amplitude=0.0, background=10.0, seed=5)
+    frames = mv.frames.copy()
+    frames[3:5] = blank.frames[3:5]
+    gm, om = paired_models(ppf, seed=6)
+    pf = ppf.ParticleFilter(gm, N, group_size=gs)
+    log = []
+    lockstep(pf, gm, om, frames, gpu_frames(dataclasses.replace(mv, frames=frames)), orc.ARNA, K=8, alpha=0.5,
+             log=log)
+    lost = [e[2] for e in log if isinstance(e, tuple) and e[0] == "lost"]
+    assert any(lost) and not all(lost)
+    pf.close()
+
+
+def test_arna_ring_accessors(ppf, movie):
+    from gpu_common import paired_models
+    gm, _ = paired_models(ppf, seed=1)
+    pf = ppf.ParticleFilter(gm, 8000, group_size=1000)
+    assert np.array_equal(pf.ring(), np.arange(8))
+    pf.set_ring([3, 1, 2, 0, 7, 6, 5, 4])
+    assert np.array_equal(pf.ring(), [3, 1, 2, 0, 7, 6, 5, 4])
+    for bad in ([0, 1, 2, 3, 4, 5, 6, 6], [0, 1, 2, 3, 4, 5, 6, 8], [-1, 1, 2, 3, 4, 5, 6, 7]):
+        with pytest.raises(ppf.PPFError):
+            pf.set_ring(bad)
+    assert np.array_equal(pf.ring(), [3, 1, 2, 0, 7, 6, 5, 4])
+    pf.set_groups(pf.groups())  # a new layout starts from the identity ring
+    assert np.array_equal(pf.ring(), np.arange(8))
+    with pytest.raises(ppf.PPFError):
+        pf.resample(ppf.ARNA, 1.5)   # ratio outside [0, 1]
+    pf.close()
 
 
 def test_estimate_async_matches_estimate(ppf, movie):
