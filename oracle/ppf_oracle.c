@@ -20,8 +20,10 @@
  *   systematic  systematic resampling on 64-bit fixed-point weights.
  *   schedule    Sec. 4: Greedy (Alg. 2), Sorted Greedy (Alg. 3) and Largest
  *               Gradient (Alg. 4) schedulers for RPA particle routing.
- *   resample    Sec. 3: RPA (proportional allocation) and RNA (local
- *               resampling + ring migration).
+ *   resample    Sec. 3: RPA (proportional allocation, one- and two-stage)
+ *               and RNA (local resampling + ring migration); Sec. 7's ARNA
+ *               (adaptive exchange ratio, ring redrawn when the object is
+ *               lost).
  *
  * Readings of points the paper leaves open (kept identical on the CUDA side):
  *   - dynamics (Sec. 7.1 names the model, gives no equations):
@@ -46,10 +48,14 @@
  *     precision), s = 63 - ceil(log2 n); ticket offset u = floor(r64 * Q / 2^64).
  *
  * parity pins: every function here is checked by the CPU test-suite against a
- * closed form, a library routine, an invariant or brute force.  One reading
- * is parity unpinned: that the piecewise constant likelihood below
- * (likelihood = 1) is the pcSIR of the cited pcSIR paper, which is not
- * available; the function itself is pinned (constant cells, centre value).
+ * closed form, a library routine, an invariant or brute force.  Two readings
+ * are parity unpinned, as the papers that define them are not available:
+ * that the piecewise constant likelihood below (likelihood = 1) is the cited
+ * pcSIR, and that orc_resample_arna's rules (involved groups, ratio, loss
+ * test, ring order) are the cited ARNA.  The functions themselves are pinned
+ * (constant cells and centre value; ring order against Philox, the exchange
+ * against RNA's local draws and the involved count against the systematic
+ * draw).
  */
 #include <math.h>
 #include <stdint.h>
