@@ -4,8 +4,8 @@ times.  Propagation and likelihood are checked on sampled slots that the
 oracle computes one by one; normalisation, estimate and log-evidence by the
 oracle's FP64 summary over all particles (same log-weight inputs, exact bound
 as in gpu_common); the ancestors and group offsets bit-exactly for systematic,
-RPA-LGS, RNA and two-stage RPA-GS resampling (the oracle resamples all 38 M
-weights)."""
+RPA-LGS, RNA, two-stage RPA-GS and ARNA resampling (the oracle resamples all
+38 M weights)."""
 import math
 
 import numpy as np
@@ -29,7 +29,7 @@ def setup():
         pytest.skip("needs ~8 GB of free device memory")
     import paper_1310_5045_gb300 as ppf
     from gpu_common import paired_models
-    mv, p = synth.preset("spot512_k50", seed=0, K=4)
+    mv, p = synth.preset("spot512_k50", seed=0, K=5)
     gm, om = paired_models(ppf, width=512, height=512, patch_radius=5, psf_sigma=float(p["sigma"]),
                            amplitude=float(p["amplitude"]), seed=0)
     frames = torch.from_numpy(mv.frames).cuda()
@@ -75,18 +75,27 @@ def one_frame(ppf, pf, gm, om, mv, frames, k, scheme, alpha=0.1, n_sample=20000)
     # S6-S8 bit-exact from the same float32 log-weights
     lwf = st1[5].cpu().numpy()
     del full
+    ring0 = pf.ring() if scheme == orc.ARNA else None
     pf.resample(scheme, alpha)
     _, anc1, lwp1 = pf.get_particles(state=False, anc=True, lw_prev=True)
-    rc, anc_ref, lwr_ref, goff_ref, stats = orc.resample(om, scheme, N_FULL, k, goff0, lwf,
-                                                         lwf.astype(np.float64), alpha)
+    e2 = pf.estimate()
+    if scheme == orc.ARNA:
+        lost = bool(e2.status_flags & 32)
+        assert lost == (so["log_evidence"] < 0.0)
+        rc, anc_ref, lwr_ref, goff_ref, stats, ring_ref = orc.resample_arna(
+            om, N_FULL, k, goff0, lwf, lost, ring0, lw_sum=lwf.astype(np.float64), alpha=float(np.float32(alpha)))
+        assert np.array_equal(pf.ring(), ring_ref)
+        stats = stats[:4]
+    else:
+        rc, anc_ref, lwr_ref, goff_ref, stats = orc.resample(om, scheme, N_FULL, k, goff0, lwf,
+                                                             lwf.astype(np.float64), alpha)
     assert rc == 0
     a1 = anc1.cpu().numpy()
     assert np.array_equal(a1, anc_ref), int(np.sum(a1 != anc_ref))
     assert np.array_equal(pf.groups(), goff_ref)
-    if scheme == orc.RNA:
+    if scheme in (orc.RNA, orc.ARNA):
         l1 = lwp1.double().cpu().numpy()
         assert np.all(np.abs(l1 - lwr_ref) <= 1e-5 * np.maximum(1.0, np.abs(lwr_ref)))
-    e2 = pf.estimate()
     assert (e2.links, e2.moved, e2.max_group, e2.min_group) == tuple(int(v) for v in stats)
     return est
 
@@ -98,4 +107,6 @@ def test_full_size_frames(setup):
     est = one_frame(ppf, pf, gm, om, mv, frames, 3, orc.RNA, alpha=0.1)
     assert math.isfinite(est.log_evidence)
     est = one_frame(ppf, pf, gm, om, mv, frames, 4, orc.RPA2_GS)
+    assert math.isfinite(est.log_evidence)
+    est = one_frame(ppf, pf, gm, om, mv, frames, 5, orc.ARNA, alpha=0.5)
     assert math.isfinite(est.log_evidence)
