@@ -37,9 +37,9 @@ R = 5
 # resample: ancestor 4 + gathered parent x, y, vx, vy, I0 20 + written state 24
 STEP_BYTES = 48
 # measured DRAM bytes per particle of the same kernel (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum, 10th launch at N = 16M, profiles/step_kernel_spot512_n16m.md),
+# dram__bytes_write.sum, 10th launch at N = 16M, the step kernel's summary under profiles/),
 # scaled to a launch by N; set to None whenever step_kernel changes
-STEP_TRAFFIC_PER_PARTICLE = (351.87e6 + 341.22e6) / 16e6
+STEP_TRAFFIC_PER_PARTICLE = (351.33e6 + 341.29e6) / 16e6
 # algorithmic FP32 flops per particle of the likelihood + propagation (an FMA
 # counts 2): bilinear form 2P^2, row combination 2P, sums of squares 4P, final
 # combination 6, propagation 10, with P = 2r + 1
