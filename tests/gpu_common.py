@@ -140,6 +140,8 @@ def lockstep(pf, gm, om, frames_np, frames_gpu, scheme, K, alpha=0.1, check_resa
             assert np.array_equal(lwp1.cpu().numpy(), lwf)
             assert np.array_equal(goff1, goff0)
             assert (est2.links, est2.moved) == (0, 0)
+            if ring0 is not None:
+                assert np.array_equal(pf.ring(), ring0)  # ARNA keeps its ring on a kept step
             continue
         if scheme == orc.ARNA:
             # the object counts as lost when the log-evidence is negative;

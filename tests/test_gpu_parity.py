@@ -58,7 +58,7 @@ def test_lockstep_frames(ppf, movie, scheme, N, gs):
     pf.close()
 
 
-@pytest.mark.parametrize("scheme", [orc.SYSTEMATIC, orc.RPA_SGS, orc.RNA])
+@pytest.mark.parametrize("scheme", [orc.SYSTEMATIC, orc.RPA_SGS, orc.RNA, orc.RPA2_GS, orc.ARNA])
 def test_ess_gated_resampling(ppf, scheme):
     """Alg. 1's N_eff test on the device: with sigma_xi^2 = 2000 and a
     threshold of 4000 (N = 16384) the oracle keeps the particles at frames
@@ -247,8 +247,8 @@ def test_step_host_matches_device_frames(ppf, movie):
 
 def test_checkpoint_and_resume(ppf, movie):
     """A run snapshotted after LGS left the groups unequal (particles, pending
-    ancestors and starting weights, group layout) resumes in a new context
-    bit for bit: LGS, then RNA, then systematic frames."""
+    ancestors and starting weights, group layout, ARNA ring) resumes in a new
+    context bit for bit: LGS, RNA, ARNA, then systematic frames."""
     import torch
     from gpu_common import paired_models
     gm, _ = paired_models(ppf, seed=8)
@@ -260,10 +260,13 @@ def test_checkpoint_and_resume(ppf, movie):
     st, anc, lwp = a.get_particles(state=True, anc=True, lw_prev=True)
     goff = a.groups()
     assert len(set(np.diff(goff).tolist())) > 1  # LGS left the groups unequal
+    a.set_ring(np.random.default_rng(0).permutation(30))  # an ARNA ring other than the identity
+    ring = a.ring()
     b = ppf.ParticleFilter(gm, 30000, group_size=1000)
     b.set_particles(st, anc, lwp)
     b.set_groups(goff)
-    for k, sch in ((3, ppf.RPA_LGS), (4, ppf.RNA), (5, ppf.SYSTEMATIC)):
+    b.set_ring(ring)
+    for k, sch in ((3, ppf.RPA_LGS), (4, ppf.RNA), (5, ppf.ARNA), (6, ppf.SYSTEMATIC)):
         for f in (a, b):
             f.step(fr[k - 1], k)
             f.resample(sch, 0.3)
@@ -271,6 +274,7 @@ def test_checkpoint_and_resume(ppf, movie):
         sb, ab, lb = b.get_particles(state=True, anc=True, lw_prev=True)
         assert torch.equal(sa, sb) and torch.equal(aa, ab) and torch.equal(la, lb), k
         assert np.array_equal(a.groups(), b.groups())
+        assert np.array_equal(a.ring(), b.ring())
     with pytest.raises(ppf.PPFError):
         b.set_groups(np.zeros(len(goff), dtype=np.int64))  # does not end at N
     a.close()
