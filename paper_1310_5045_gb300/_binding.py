@@ -130,21 +130,28 @@ _lib = None
 _lock = threading.Lock()
 
 
+def _debug() -> bool:
+    return os.environ.get("PPF_DEBUG", "") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    """libppf.so, or libppf_debug.so (device-side index checks) when PPF_DEBUG=1."""
+    return _build.LIB_DEBUG if _debug() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Load libppf.so (building it in-tree first if needed)."""
+    """Load the library (building it in-tree first if needed)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
+        path = lib_path()
         if build_if_missing:
-            _build.build()
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError(f"libppf.so not built ({_build.LIB}); run paper_1310_5045_gb300._build.build()")
-        L = C.CDLL(_build.LIB)
+            _build.build(debug=_debug())
+        if not os.path.exists(path):
+            raise RuntimeError(f"{os.path.basename(path)} not built ({path}); run "
+                               "paper_1310_5045_gb300._build.build()")
+        L = C.CDLL(path)
         P = C.POINTER
         vp, ctxp = C.c_void_p, C.c_void_p
         sig = {

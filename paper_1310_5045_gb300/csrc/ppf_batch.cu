@@ -101,7 +101,7 @@ struct ppf_batch {
     ppf::FilterSummary *fsum_host;     // pinned [F]
     ppf::FilterSummary *fsum_run;      // device [K x F] of the last graph run
     int64_t fsum_run_cap;
-    int32_t *flags;                    // device: any degenerate filter
+    int32_t *flags;                    // device: FLAG_DEGENERATE (a degenerate filter), FLAG_INTERNAL (a debug check)
     ppf::BatchCursor *cursor;          // device
     cudaStream_t gstream;              // stream the cached graph runs on
     cudaGraphExec_t gexec;             // cached one-frame iteration
@@ -213,6 +213,7 @@ struct BatchStepArgs {
     const int32_t *__restrict__ fkeep;
     const float *__restrict__ Zp;
     Partial *__restrict__ part;
+    int32_t *flags;             // FLAG_INTERNAL from a failed debug check
 };
 
 // Persistent SIS step over all work units of all filters.  A unit is a run
@@ -246,7 +247,7 @@ __global__ void batch_step_kernel(BatchStepArgs a)
             kcs[wib][lane] = P->Kc[lane];
         __syncwarp();
         const PatchGeom geom{a.Zp + (int64_t)f * 2 * a.Wp * a.Hp, a.W, a.H, a.Wp, a.pad, P->inv2s2, P->inv_sxi2,
-                             kcs[wib]};
+                             kcs[wib], a.Hp, a.flags};
         // after the prior draw, or when the last resample kept this filter's
         // particles, every slot continues its own particle with its weight
         const bool carry = first || a.fkeep[f] != 0;
@@ -442,7 +443,8 @@ __global__ void __launch_bounds__(TILE_THREADS) batch_fill(const float *st0, con
                                                            const int32_t *__restrict__ ft_off,
                                                            const uint64_t *__restrict__ tC,
                                                            const int64_t *__restrict__ tT,
-                                                           const uint64_t *__restrict__ fQu, int32_t *__restrict__ anc)
+                                                           const uint64_t *__restrict__ fQu, int32_t *__restrict__ anc,
+                                                           int32_t *flags)
 {
     extern __shared__ uint64_t fill_smem[];  // FILL_SMEM_BYTES
     uint64_t *C = fill_smem;
@@ -467,7 +469,11 @@ __global__ void __launch_bounds__(TILE_THREADS) batch_fill(const float *st0, con
     tile_scan(q, C, red);
     const TicketGrid tg = ticket_grid(Q, u, fQu[4 * f + 2], (uint32_t)fQu[4 * f + 3], P.ndiv);
     ticket_parents_staged(C, n, tC[t], tg, j_lo, j_hi, stage,
-                          [&](int64_t j, int i) { anc[P.off + j] = (int32_t)(lo + i); });
+                          [&](int64_t j, int i) {
+                              if (PPF_DCHECK(j >= 0 && j < P.n && P.off + j < Ntot && i >= 0 && i < n, flags,
+                                             FLAG_INTERNAL))
+                                  anc[P.off + j] = (int32_t)(lo + i);
+                          });
 }
 
 // ------------------------------------------------------------------ host side
@@ -567,6 +573,7 @@ cudaError_t launch_batch_step(ppf_batch *b, bool commit)
     a.anc = b->anc;
     a.fkeep = b->fkeep;
     a.Zp = b->Zp;
+    a.flags = b->flags;
     a.part = b->upart;
     int grid = b->num_sms * b->bps;
     if (grid > b->U)
@@ -629,7 +636,7 @@ cudaError_t launch_batch_resample(ppf_batch *b)
                                                                       b->flags);
     batch_fill<<<b->T, TILE_THREADS, FILL_SMEM_BYTES, b->stream>>>(b->state[0], b->state[1], b->Ntot, b->fp, b->fsum, b->cursor,
                                                      b->tile_f, b->tile_lo, b->tile_n, b->ft_off, b->tC, b->tT, b->fQu,
-                                                     b->anc);
+                                                     b->anc, b->flags);
     b->launches += 3;
     return cudaGetLastError();
 }
@@ -917,6 +924,10 @@ ppf_status ppf_batch_estimates(ppf_batch *b, ppf_filter_estimate_t *out_host)
     BCK(cudaMemcpy(&fl, b->flags, sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (fl) {
         BCK(cudaMemset(b->flags, 0, sizeof(int32_t)));
+        if (fl & FLAG_INTERNAL) {
+            snprintf(b->err, sizeof(b->err), "device flags 0x%x: an index check of the debug build failed", fl);
+            return PPF_EINVAL;
+        }
         return PPF_EDEGENERATE;
     }
     return PPF_OK;

@@ -20,6 +20,24 @@ namespace ppf {
 
 typedef unsigned __int128 u128;
 
+// Debug builds (-DPPF_DEBUG) check the index of every scattered store of the
+// resampling kernels and the window of every patch read before the access:
+// a failed check ors `bit` into *flags (the internal-error flag, which
+// ppf_estimate reports as PPF_EINVAL) and skips the access, so a broken
+// invariant shows up as an error status instead of a memory fault.  Release
+// builds compile the checks away.
+#ifdef PPF_DEBUG
+__device__ __forceinline__ bool debug_check(bool ok, const int32_t *flags, int32_t bit)
+{
+    if (!ok && flags)
+        atomicOr(const_cast<int32_t *>(flags), bit);
+    return ok;
+}
+#define PPF_DCHECK(cond, flags, bit) ::ppf::debug_check((cond), (flags), (bit))
+#else
+#define PPF_DCHECK(cond, flags, bit) true
+#endif
+
 enum : uint32_t { PURPOSE_INIT = 0, PURPOSE_PROP = 1, PURPOSE_RESAMPLE = 2, PURPOSE_GROUP = 3, PURPOSE_RING = 4 };
 
 // One Philox4x32-10 block: ten rounds of two 32x32->64 multiplications of

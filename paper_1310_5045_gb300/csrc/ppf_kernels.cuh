@@ -6,6 +6,7 @@
 #include <cmath>
 
 #include "ppf_device.cuh"
+#include "ppf_internal.h"
 
 namespace ppf {
 
@@ -109,6 +110,8 @@ struct PatchGeom {
     float inv2s2;      // 1 / (2 sigma_PSF^2)
     float inv_sxi2;    // 1 / sigma_xi^2
     const float *Kc;   // exp(-(2k+1) inv2s2), k = 0..R-1
+    int Hp = 0;                      // padded frame height (the debug build's window check)
+    const int32_t *flags = nullptr;  // debug build: where a failed window check is reported
 };
 
 // The anchor c = floor(x + 1/2), the PSF samples of the patch columns and
@@ -170,6 +173,12 @@ __device__ __forceinline__ float patch_sum(const PatchGeom &a, int cx, int cy, c
 {
     constexpr int P = 2 * R + 1;
     constexpr int Q = P / 2;  // full column pairs; column P - 1 is the odd one out
+    // the window: P rows from cy - R, pairs from column cx - R up to 2Q + 1
+    // columns on (inside the padded frame by the anchor's range)
+    if (a.flags && !PPF_DCHECK(cy - R + a.pad >= 0 && cy + R + a.pad < a.Hp && cx - R + a.pad >= 0 &&
+                                   cx - R + a.pad + 2 * Q < a.Wp,
+                               a.flags, FLAG_INTERNAL))
+        return 0.0f;
     const float2 *row = reinterpret_cast<const float2 *>(a.Zp) + (int64_t)(cy - R + a.pad) * a.Wp +
                         (cx - R + a.pad);
     float2 b = make_float2(0.0f, 0.0f);

@@ -243,7 +243,10 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     const int64_t i_lo = Tt[t] + (int64_t)(b - item_off[t]) * ITEM_TICKETS;
     const int64_t i_hi = (Tt[t + 1] < i_lo + ITEM_TICKETS) ? Tt[t + 1] : i_lo + ITEM_TICKETS;
     const TicketGrid tg = ticket_grid(sum->Q, sum->u, sum->qN, sum->qR, ndiv);
-    ticket_parents_staged(C, n, Ct[t], tg, i_lo, i_hi, stage, [&](int64_t j, int i) { out[j] = (int32_t)(lo + i); });
+    ticket_parents_staged(C, n, Ct[t], tg, i_lo, i_hi, stage, [&](int64_t j, int i) {
+        if (PPF_DCHECK(j >= 0 && j < N && i >= 0 && i < n, &sum->flags, FLAG_INTERNAL))
+            out[j] = (int32_t)(lo + i);
+    });
 }
 
 // ------------------------------------------------ two-stage RPA, stage 2
@@ -301,7 +304,11 @@ __global__ void __launch_bounds__(TILE_THREADS) group_fill_kernel(
         const int64_t t_lo = tickets_below(carry, nt, u, Qg);
         const int64_t t_hi = tickets_below(carry + tot, nt, u, Qg);
         ticket_parents_staged(C, n, carry, tg, t_lo, t_hi, stage,
-                              [&](int64_t j, int i) { dst[j] = (int32_t)(lo + c0 + i); });
+                              [&](int64_t j, int i) {
+                                  if (PPF_DCHECK(j >= 0 && j < nt && Tg[g] + j < N && i >= 0 && i < n,
+                                                 &sum->flags, FLAG_INTERNAL))
+                                      dst[j] = (int32_t)(lo + c0 + i);
+                              });
         carry += tot;
         __syncthreads();
     }
@@ -787,6 +794,8 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
     if (Q == 0ull) {  // no usable weight in the group: it keeps its slots
         for (int64_t s2 = threadIdx.x; s2 < sz; s2 += blockDim.x) {
             const int64_t d = dest(s2);
+            if (!PPF_DCHECK(d >= 0 && d < N, &sum->flags, FLAG_INTERNAL))
+                continue;
             anc[d] = (int32_t)(lo + s2);
             lwp[d] = lwg;
         }
@@ -805,6 +814,8 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
         const int64_t t_hi = tickets_below(carry + tot, sz, u, Q);
         ticket_parents_staged(C, n, carry, tg, t_lo, t_hi, stage, [&](int64_t j, int i) {
             const int64_t d = dest(j);
+            if (!PPF_DCHECK(d >= 0 && d < N && i >= 0 && i < n, &sum->flags, FLAG_INTERNAL))
+                return;
             anc[d] = (int32_t)(lo + c0 + i);
             lwp[d] = lwg;
         });

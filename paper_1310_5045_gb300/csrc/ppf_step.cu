@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
     int mode = a.mode;
     if (mode != MODE_CARRY && *a.degenerate)
         mode = MODE_CARRY;  // the last resample kept every particle
-    const PatchGeom geom{a.Zp, a.W, a.H, a.Wp, a.pad, a.inv2s2, a.inv_sxi2, a.Kc};
+    const PatchGeom geom{a.Zp, a.W, a.H, a.Wp, a.pad, a.inv2s2, a.inv_sxi2, a.Kc, a.Hp, a.flags};
     // N < 2^31: 32-bit slot indices into per-component planes
     const int32_t N = (int32_t)a.N;
     const float *__restrict__ sx = a.src, *__restrict__ sy = a.src + a.N, *__restrict__ svx = a.src + 2 * a.N;
@@ -303,7 +303,7 @@ static void launch_cell_map_r(const PatchGeom &g, const KcArr &kc, float2 *lmap,
 cudaError_t launch_cell_map(ppf_ctx *c)
 {
     const int R = c->m.patch_radius;
-    PatchGeom g{c->Zp, c->m.width, c->m.height, c->Wp, c->pad, 0.0f, 0.0f, nullptr};
+    PatchGeom g{c->Zp, c->m.width, c->m.height, c->Wp, c->pad, 0.0f, 0.0f, nullptr, c->Hp, &c->sum->flags};
     g.inv2s2 = 1.0f / (2.0f * c->m.psf_sigma * c->m.psf_sigma);
     g.inv_sxi2 = 1.0f / (c->m.sigma_xi * c->m.sigma_xi);
     KcArr kc;
