@@ -468,12 +468,8 @@ __global__ void __launch_bounds__(TILE_THREADS) batch_fill(const float *st0, con
     tile_weights(lw, lo, n, fs[f].M, scale_bits(P.n), C, q);
     tile_scan(q, C, red);
     const TicketGrid tg = ticket_grid(Q, u, fQu[4 * f + 2], (uint32_t)fQu[4 * f + 3], P.ndiv);
-    ticket_parents_staged(C, n, tC[t], tg, j_lo, j_hi, stage,
-                          [&](int64_t j, int i) {
-                              if (PPF_DCHECK(j >= 0 && j < P.n && P.off + j < Ntot && i >= 0 && i < n, flags,
-                                             FLAG_INTERNAL))
-                                  anc[P.off + j] = (int32_t)(lo + i);
-                          });
+    ticket_parents_contig(C, n, tC[t], tg, j_lo, j_hi, stage, anc + P.off, (int32_t)lo,
+                          (P.n < Ntot - P.off) ? P.n : Ntot - P.off, flags);
 }
 
 // ------------------------------------------------------------------ host side

@@ -25,6 +25,7 @@ constexpr int ITEM_TICKETS = 8192;  // tickets per fill work item
 constexpr int COPY_CHUNK = 2048;    // slots per routing-copy work item
 constexpr int MAX_RADIUS = 8;
 constexpr int MAX_SCHED_GROUPS = 16384;
+constexpr int SCAN_SMEM_TILES = 16384;  // tile scan in shared memory up to this many tiles (N <= 67 M)
 
 // How the next step forms a slot's starting log-weight.
 enum StepMode : int {

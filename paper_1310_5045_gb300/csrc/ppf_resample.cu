@@ -93,14 +93,18 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_totals_kernel(
 // One block: exclusive tile prefix, total Q, ticket offset u, tickets below
 // each tile start, fill work items (and the tile of each item when item_tile
 // is given); for RPA the tickets below each group start.
-// Every array is walked in rounds of blockDim consecutive entries (coalesced),
-// each round closed by a block scan.
+// When the T + 1 tile values fit the dynamic shared memory (T <= smem_tiles),
+// they are loaded there with coalesced reads, and each of the two prefix sums
+// gives every thread one contiguous segment: a local sum, one block scan,
+// then the segment's prefixes.  Otherwise every array is walked in rounds of
+// blockDim consecutive entries, each round closed by a block scan.
 __global__ void __launch_bounds__(1024) tile_scan_kernel(
     int64_t N, int32_t T, const uint64_t *__restrict__ Qt, uint64_t *__restrict__ Ct, int64_t *__restrict__ Tt,
     int32_t *__restrict__ item_off, int32_t *__restrict__ item_tile, DevSummary *sum, double ess_thr, uint64_t seed,
     uint32_t fid, uint32_t frame, const int64_t *__restrict__ goff, int32_t G, int rpa,
-    const uint64_t *__restrict__ Cbl, int64_t *__restrict__ Tg)
+    const uint64_t *__restrict__ Cbl, int64_t *__restrict__ Tg, int32_t smem_tiles)
 {
+    extern __shared__ uint64_t sT[];  // (smem_tiles + 1) tile values
     __shared__ uint64_t red[33];
     __shared__ uint64_t su;
     if (kept_by_ess(sum, ess_thr)) {  // N_eff test: keep the particles and the layout
@@ -113,15 +117,36 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
         }
         return;
     }
+    const bool in_smem = T <= smem_tiles;
+    const int seg = (T + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int s0 = min(T, (int)threadIdx.x * seg), s1 = min(T, s0 + seg);
     uint64_t total = 0;
-    for (int base = 0; base < T; base += blockDim.x) {
-        const int t = base + threadIdx.x;
-        const uint64_t v = (t < T) ? Qt[t] : 0ull;
-        uint64_t tot;
-        const uint64_t ex = block_excl_scan_u64(v, red, &tot);
-        if (t < T)
-            Ct[t] = total + ex;
-        total += tot;
+    if (in_smem) {
+        for (int t = threadIdx.x; t < T; t += blockDim.x)
+            sT[t] = __ldg(Qt + t);
+        __syncthreads();
+        uint64_t loc = 0;
+        for (int t = s0; t < s1; ++t)
+            loc += sT[t];
+        uint64_t run = block_excl_scan_u64(loc, red, &total);
+        for (int t = s0; t < s1; ++t) {
+            const uint64_t v = sT[t];
+            sT[t] = run;  // exclusive tile prefix
+            run += v;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < T; t += blockDim.x)
+            Ct[t] = sT[t];
+    } else {
+        for (int base = 0; base < T; base += blockDim.x) {
+            const int t = base + threadIdx.x;
+            const uint64_t v = (t < T) ? Qt[t] : 0ull;
+            uint64_t tot;
+            const uint64_t ex = block_excl_scan_u64(v, red, &tot);
+            if (t < T)
+                Ct[t] = total + ex;
+            total += tot;
+        }
     }
     if (threadIdx.x == 0) {
         Ct[T] = total;
@@ -142,23 +167,46 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
             sum->n_items = 0;
         return;
     }
-    for (int t = threadIdx.x; t <= T; t += blockDim.x)
-        Tt[t] = (t == T) ? N : tickets_below(Ct[t], N, u, Q);
+    for (int t = threadIdx.x; t <= T; t += blockDim.x) {
+        const int64_t v = (t == T) ? N : tickets_below(in_smem ? sT[t] : Ct[t], N, u, Q);
+        Tt[t] = v;
+        if (in_smem)
+            sT[t] = (uint64_t)v;  // each thread rewrites only the entries it read
+    }
     __syncthreads();
     // fill work items: ceil(tickets / ITEM_TICKETS) per tile
     uint64_t items_total = 0;
-    for (int base = 0; base < T; base += blockDim.x) {
-        const int t = base + threadIdx.x;
-        const uint64_t cnt = (t < T) ? (uint64_t)((Tt[t + 1] - Tt[t] + ITEM_TICKETS - 1) / ITEM_TICKETS) : 0ull;
-        uint64_t tot;
-        const uint64_t ex = block_excl_scan_u64(cnt, red, &tot);
-        if (t < T) {
-            item_off[t] = (int32_t)(items_total + ex);
+    if (in_smem) {
+        auto items_of = [&](int t) -> int32_t {
+            return (int32_t)(((int64_t)sT[t + 1] - (int64_t)sT[t] + ITEM_TICKETS - 1) / ITEM_TICKETS);
+        };
+        uint64_t loc = 0;
+        for (int t = s0; t < s1; ++t)
+            loc += (uint64_t)items_of(t);
+        int32_t off = (int32_t)block_excl_scan_u64(loc, red, &items_total);
+        for (int t = s0; t < s1; ++t) {
+            const int32_t cnt = items_of(t);
+            item_off[t] = off;
             if (item_tile)
-                for (uint64_t k = 0; k < cnt; ++k)
-                    item_tile[items_total + ex + k] = t;
+                for (int32_t k = 0; k < cnt; ++k)
+                    item_tile[off + k] = t;
+            off += cnt;
         }
-        items_total += tot;
+    } else {
+        for (int base = 0; base < T; base += blockDim.x) {
+            const int t = base + threadIdx.x;
+            const uint64_t cnt =
+                (t < T) ? (uint64_t)((Tt[t + 1] - Tt[t] + ITEM_TICKETS - 1) / ITEM_TICKETS) : 0ull;
+            uint64_t tot;
+            const uint64_t ex = block_excl_scan_u64(cnt, red, &tot);
+            if (t < T) {
+                item_off[t] = (int32_t)(items_total + ex);
+                if (item_tile)
+                    for (uint64_t k = 0; k < cnt; ++k)
+                        item_tile[items_total + ex + k] = t;
+            }
+            items_total += tot;
+        }
     }
     if (threadIdx.x == 0) {
         item_off[T] = (int32_t)items_total;
@@ -243,10 +291,7 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     const int64_t i_lo = Tt[t] + (int64_t)(b - item_off[t]) * ITEM_TICKETS;
     const int64_t i_hi = (Tt[t + 1] < i_lo + ITEM_TICKETS) ? Tt[t + 1] : i_lo + ITEM_TICKETS;
     const TicketGrid tg = ticket_grid(sum->Q, sum->u, sum->qN, sum->qR, ndiv);
-    ticket_parents_staged(C, n, Ct[t], tg, i_lo, i_hi, stage, [&](int64_t j, int i) {
-        if (PPF_DCHECK(j >= 0 && j < N && i >= 0 && i < n, &sum->flags, FLAG_INTERNAL))
-            out[j] = (int32_t)(lo + i);
-    });
+    ticket_parents_contig(C, n, Ct[t], tg, i_lo, i_hi, stage, out, (int32_t)lo, N, &sum->flags);
 }
 
 // ------------------------------------------------ two-stage RPA, stage 2
@@ -303,12 +348,8 @@ __global__ void __launch_bounds__(TILE_THREADS) group_fill_kernel(
         const uint64_t tot = tile_scan(q, C, red);
         const int64_t t_lo = tickets_below(carry, nt, u, Qg);
         const int64_t t_hi = tickets_below(carry + tot, nt, u, Qg);
-        ticket_parents_staged(C, n, carry, tg, t_lo, t_hi, stage,
-                              [&](int64_t j, int i) {
-                                  if (PPF_DCHECK(j >= 0 && j < nt && Tg[g] + j < N && i >= 0 && i < n,
-                                                 &sum->flags, FLAG_INTERNAL))
-                                      dst[j] = (int32_t)(lo + c0 + i);
-                              });
+        ticket_parents_contig(C, n, carry, tg, t_lo, t_hi, stage, dst, (int32_t)(lo + c0),
+                              (nt < N - Tg[g]) ? nt : N - Tg[g], &sum->flags);
         carry += tot;
         __syncthreads();
     }
@@ -991,6 +1032,9 @@ cudaError_t resample_kernel_attributes()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(arna_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(uint64_t) * MAX_SCHED_GROUPS));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(uint64_t) * (SCAN_SMEM_TILES + 1)));
     return e;
 }
 
@@ -1003,10 +1047,10 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     c->launches += rpa ? 5 : 3;
     tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt,
                                                           rpa ? c->goff : nullptr, c->G, c->sc.Cbl);
-    tile_scan_kernel<<<1, 1024, 0, c->stream>>>(c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off,
-                                                c->sc.item_tile, c->sum, ess_thr,
-                                                c->m.seed, c->m.filter_id, (uint32_t)c->last_frame,
-                                                c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg);
+    const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
+    tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
+        c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sum, ess_thr, c->m.seed,
+        c->m.filter_id, (uint32_t)c->last_frame, c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg, st_tiles);
     int32_t *out = rpa ? c->anc_sys : c->anc;
     const bool two_stage = (scheme >= PPF_RPA2_GS && scheme <= PPF_RPA2_LGS);
     if (two_stage) {  // stage 2: every group draws its own offspring
@@ -1069,9 +1113,10 @@ cudaError_t launch_resample_arna(ppf_ctx *c, float alpha, double ess_thr)
     prof_mark(c, PH_RESAMPLE, 0);
     tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff, c->G,
                                                           c->sc.Cbl);
-    tile_scan_kernel<<<1, 1024, 0, c->stream>>>(c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, nullptr,
-                                                c->sum, ess_thr, c->m.seed, c->m.filter_id,
-                                                (uint32_t)c->last_frame, c->goff, c->G, 1, c->sc.Cbl, c->sc.Tg);
+    const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
+    tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
+        c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, nullptr, c->sum, ess_thr, c->m.seed, c->m.filter_id,
+        (uint32_t)c->last_frame, c->goff, c->G, 1, c->sc.Cbl, c->sc.Tg, st_tiles);
     arna_prep_kernel<<<1, 1024, sizeof(uint64_t) * MAX_SCHED_GROUPS, c->stream>>>(
         c->goff, c->G, alpha, c->sum, ess_thr, c->sc.Tg, c->ring, c->succ, c->m.seed, c->m.filter_id,
         (uint32_t)c->last_frame);

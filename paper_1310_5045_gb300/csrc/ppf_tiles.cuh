@@ -183,21 +183,23 @@ __device__ __forceinline__ void ticket_parents(const uint64_t *C, int n, uint64_
     uint32_t r;
     uint64_t lt = lt_at(b, &r);
     const int steps = (D - d0 < K) ? D - d0 : K;
-    // every ticket has lt < C[n-1], so i stays below n while tickets remain
+    // every ticket has lt < C[n-1], so i stays below n while tickets remain.
+    // Each step either advances the particle or emits the ticket and moves to
+    // the next threshold; both updates are formed and selected, so the lanes
+    // of a warp do not diverge (r + qR < 2 nt < 2^32).
     for (int s = 0; s < steps; ++s) {
-        if (C[padc(i)] <= lt) {
-            ++i;
-        } else {
+        const bool adv = C[padc(i)] <= lt;
+        if (!adv)
             emit(j_lo + b, i);
-            if (++b >= L)
-                break;
-            lt += qN;
-            r += qR;
-            if (r >= nt) {
-                r -= nt;
-                ++lt;
-            }
-        }
+        const uint32_t rn = r + qR;
+        const bool cy = rn >= nt;
+        const uint64_t ltn = lt + qN + (cy ? 1u : 0u);
+        i += adv ? 1 : 0;
+        b += adv ? 0 : 1;
+        lt = adv ? lt : ltn;
+        r = adv ? r : (cy ? rn - nt : rn);
+        if (b >= L)
+            break;
     }
 }
 
@@ -220,6 +222,46 @@ __device__ __forceinline__ void ticket_parents_staged(const uint64_t *C, int n, 
         const int m = (int)(ce - c);
         for (int k = threadIdx.x; k < m; k += blockDim.x)
             store(c + k, (int)stage[k]);
+        __syncthreads();
+    }
+}
+
+// ticket_parents_staged for the common contiguous output out[j] = base + i:
+// the staged chunk is written as 16-byte int4 stores (after up to three
+// single stores that reach 16-byte alignment), four tickets per thread and
+// iteration.  The debug build checks every ticket's slot against [0, j_max)
+// and its parent against [0, n).
+__device__ __forceinline__ void ticket_parents_contig(const uint64_t *C, int n, uint64_t c0, const TicketGrid &tg,
+                                                      int64_t j_lo, int64_t j_hi, uint16_t *stage,
+                                                      int32_t *__restrict__ out, int32_t base, int64_t j_max,
+                                                      const int32_t *flags)
+{
+    for (int64_t c = j_lo; c < j_hi; c += STAGE_TICKETS) {
+        const int64_t ce = (j_hi - c < STAGE_TICKETS) ? j_hi : c + STAGE_TICKETS;
+        const int m = (int)(ce - c);
+        ticket_parents(C, n, c0, tg, c, m, [&](int64_t j, int i) { stage[j - c] = (uint16_t)i; });
+        __syncthreads();
+        if (!PPF_DCHECK(c >= 0 && ce <= j_max, flags, FLAG_INTERNAL)) {
+            __syncthreads();
+            continue;
+        }
+        int32_t *o = out + c;
+        const int head = (int)((4u - ((uint32_t)(reinterpret_cast<uintptr_t>(o) >> 2) & 3u)) & 3u);
+        const int h = head < m ? head : m;
+        const int m4 = (m - h) >> 2;
+        const int t0 = h + 4 * m4;
+        const int k = threadIdx.x;
+        if (k < h && PPF_DCHECK(stage[k] < n, flags, FLAG_INTERNAL))
+            o[k] = base + stage[k];
+        int4 *o4 = reinterpret_cast<int4 *>(o + h);
+        for (int q = k; q < m4; q += blockDim.x) {
+            const int e = h + 4 * q;
+            const int32_t p0 = stage[e], p1 = stage[e + 1], p2 = stage[e + 2], p3 = stage[e + 3];
+            if (PPF_DCHECK(p0 < n && p1 < n && p2 < n && p3 < n, flags, FLAG_INTERNAL))
+                o4[q] = make_int4(base + p0, base + p1, base + p2, base + p3);
+        }
+        if (k < m - t0 && PPF_DCHECK(stage[t0 + k] < n, flags, FLAG_INTERNAL))
+            o[t0 + k] = base + stage[t0 + k];
         __syncthreads();
     }
 }
