@@ -383,8 +383,11 @@ __global__ void __launch_bounds__(TILE_THREADS) batch_tile_totals(const float *s
     }
     uint64_t acc = 0;
 #pragma unroll
-    for (int k = 0; k < TILE_ITEMS; ++k)
-        acc += quantise(v[k], Mf, s);
+    for (int k = 0; k < TILE_ITEMS; k += 2) {
+        uint64_t a, b;
+        quantise2(v[k], v[k + 1], Mf, s, a, b);
+        acc += a + b;
+    }
     uint64_t total;
     block_excl_scan_u64(acc, red, &total);
     if (threadIdx.x == 0)

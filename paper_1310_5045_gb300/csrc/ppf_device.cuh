@@ -130,13 +130,9 @@ __device__ __forceinline__ float exp2_frac(float f)
     return p;
 }
 
-__device__ __forceinline__ uint64_t quantise(float lw, float M, int s)
+// The integer part of the quantiser: q = floor(p 2^(s + kf)) for t > -64.
+__device__ __forceinline__ uint64_t quantise_tail(float t, float kf, float p, int s)
 {
-    const float d = __fsub_rn(lw, M);
-    const float t = __fmul_rn(d, 0x1.715476p+0f);
-    const float kf = fmaxf(floorf(t), -64.0f);  // the clamp only affects results that are 0 anyway
-    const float f = __fsub_rn(t, kf);
-    const float p = exp2_frac(f);
     const int e = s + (int)kf;
     // p lies in [1, 2]: P = p 2^23 is its mantissa with the implicit bit,
     // doubled when p = 2.  q = floor(P 2^(e - 23)) without branches:
@@ -147,6 +143,47 @@ __device__ __forceinline__ uint64_t quantise(float lw, float M, int s)
     const int sh = 62 - e;
     const uint64_t q = (sh < 0) ? (X << 1) : (X >> (sh < 63 ? sh : 63));
     return (t > -64.0f && e >= -1) ? q : 0ull;  // t <= -64 or NaN: zero weight
+}
+
+__device__ __forceinline__ uint64_t quantise(float lw, float M, int s)
+{
+    const float d = __fsub_rn(lw, M);
+    const float t = __fmul_rn(d, 0x1.715476p+0f);
+    const float kf = fmaxf(floorf(t), -64.0f);  // the clamp only affects results that are 0 anyway
+    const float f = __fsub_rn(t, kf);
+    return quantise_tail(t, kf, exp2_frac(f), s);
+}
+
+// exp2_frac of two values at once: the same Horner steps as packed two-lane
+// FMAs, each lane rounding as the scalar form.
+__device__ __forceinline__ float2 exp2_frac2(float2 f)
+{
+    auto c = [](float v) { return make_float2(v, v); };
+    float2 p = c(0x1.b5253ep-24f);
+    p = __ffma2_rn(p, f, c(0x1.62c022p-20f));
+    p = __ffma2_rn(p, f, c(0x1.ffcbfcp-17f));
+    p = __ffma2_rn(p, f, c(0x1.430912p-13f));
+    p = __ffma2_rn(p, f, c(0x1.5d87fep-10f));
+    p = __ffma2_rn(p, f, c(0x1.3b2ab6p-7f));
+    p = __ffma2_rn(p, f, c(0x1.c6b08ep-5f));
+    p = __ffma2_rn(p, f, c(0x1.ebfbep-3f));
+    p = __ffma2_rn(p, f, c(0x1.62e43p-1f));
+    p = __ffma2_rn(p, f, c(1.0f));
+    return p;
+}
+
+// quantise of two weights: the float32 steps as packed two-lane operations
+// (a - M as a + (-M), exact in IEEE arithmetic), so both results equal the
+// scalar quantise bit for bit.
+__device__ __forceinline__ void quantise2(float a, float b, float M, int s, uint64_t &qa, uint64_t &qb)
+{
+    const float2 d = __fadd2_rn(make_float2(a, b), make_float2(-M, -M));
+    const float2 t = __fmul2_rn(d, make_float2(0x1.715476p+0f, 0x1.715476p+0f));
+    const float2 kf = make_float2(fmaxf(floorf(t.x), -64.0f), fmaxf(floorf(t.y), -64.0f));
+    const float2 f = __fadd2_rn(t, make_float2(-kf.x, -kf.y));
+    const float2 p = exp2_frac2(f);
+    qa = quantise_tail(t.x, kf.x, p.x, s);
+    qb = quantise_tail(t.y, kf.y, p.y, s);
 }
 
 // Number of systematic tickets below cumulative weight c:

@@ -52,7 +52,10 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_totals_kernel(
         if (n == TILE && ((reinterpret_cast<uintptr_t>(lw + lo) & 15) == 0)) {
             for (int e = threadIdx.x; e < TILE / 4; e += blockDim.x) {
                 const float4 v = __ldg(v4 + e);
-                acc += quantise(v.x, M, s) + quantise(v.y, M, s) + quantise(v.z, M, s) + quantise(v.w, M, s);
+                uint64_t a, b, c, d;
+                quantise2(v.x, v.y, M, s, a, b);
+                quantise2(v.z, v.w, M, s, c, d);
+                acc += a + b + c + d;
             }
         } else {
             for (int e = threadIdx.x; e < n; e += blockDim.x)

@@ -30,8 +30,8 @@ __device__ __forceinline__ void tile_weights(const float *__restrict__ lw, int64
     __syncthreads();
     const int base = threadIdx.x * TILE_ITEMS;
 #pragma unroll
-    for (int k = 0; k < TILE_ITEMS; ++k)
-        q[k] = quantise(f[padf(base + k)], M, s);
+    for (int k = 0; k < TILE_ITEMS; k += 2)
+        quantise2(f[padf(base + k)], f[padf(base + k + 1)], M, s, q[k], q[k + 1]);
     __syncthreads();
 }
 
