@@ -25,9 +25,9 @@
 namespace ppf {
 
 // kernels of ppf_resample.cu used unchanged
-__global__ void __launch_bounds__(TILE_THREADS) tile_totals_kernel(const float *__restrict__ lw, int64_t N, const DevSummary *__restrict__ sum,
-                                   double ess_thr, uint64_t *__restrict__ Qt, const int64_t *__restrict__ goff,
-                                   int32_t G, uint64_t *__restrict__ Cbl);
+__global__ void __launch_bounds__(TILE_THREADS, 8) tile_totals_kernel(const float *__restrict__ lw, int64_t N,
+                                                                      const DevSummary *__restrict__ sum,
+                                                                      double ess_thr, uint64_t *__restrict__ Qt);
 __global__ void __launch_bounds__(1024) tile_scan_kernel(int64_t N, int32_t T, const uint64_t *__restrict__ Qt, uint64_t *__restrict__ Ct,
                                  int64_t *__restrict__ Tt, int32_t *__restrict__ item_off,
                                  int32_t *__restrict__ item_tile, DevSummary *sum, double ess_thr, uint64_t seed,
@@ -170,7 +170,7 @@ extern "C" ppf_status ppf_systematic_resample_noalloc(const float *lw_dev, int64
     const int gmax = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
     noalloc_max_kernel<<<gmax, 256, 0, st>>>(lw_dev, n, s);
     // (every call resamples: the N_eff threshold is +inf)
-    tile_totals_kernel<<<T, TILE_THREADS, 0, st>>>(lw_dev, n, sum, INFINITY, Qt, nullptr, 0, nullptr);
+    tile_totals_kernel<<<T, TILE_THREADS, 0, st>>>(lw_dev, n, sum, INFINITY, Qt);
     // (no item-to-tile map: the fill blocks find their tile by binary search)
     // (T <= 4096 tiles: the scan's tile values, 32 KB, fit the default shared memory)
     tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (T + 1), st>>>(n, T, Qt, Ct, Tt, item_off, nullptr, sum, INFINITY,

@@ -31,9 +31,48 @@ __device__ __forceinline__ bool kept_by_ess(const DevSummary *sum, double ess_th
 }
 
 // ---------------------------------------------------------------- R1 tiles
-// Tile totals Q_t (coalesced loads and a block sum); for RPA also the local
-// prefix at every group start that falls inside the tile (needs the scan).
-__global__ void __launch_bounds__(TILE_THREADS) tile_totals_kernel(
+// Tile totals Q_t: every thread loads its four float4 (coalesced, all in
+// flight together), then quantises them two at a time; one block sum.  No
+// shared buffer, so more blocks fit an SM.
+__global__ void __launch_bounds__(TILE_THREADS, 8) tile_totals_kernel(const float *__restrict__ lw, int64_t N,
+                                                                      const DevSummary *__restrict__ sum,
+                                                                      double ess_thr, uint64_t *__restrict__ Qt)
+{
+    if (kept_by_ess(sum, ess_thr))
+        return;
+    __shared__ uint64_t red[33];
+    const int64_t lo = (int64_t)blockIdx.x * TILE;
+    const int n = (int)(N - lo < TILE ? N - lo : TILE);
+    const float M = sum->M;
+    const int s = scale_bits(N);
+    uint64_t acc = 0;
+    if (n == TILE && ((reinterpret_cast<uintptr_t>(lw + lo) & 15) == 0) && blockDim.x == TILE_THREADS) {
+        constexpr int V = TILE / 4 / TILE_THREADS;
+        const float4 *v4 = reinterpret_cast<const float4 *>(lw + lo) + threadIdx.x;
+        float4 v[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            v[k] = __ldg(v4 + k * TILE_THREADS);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            uint64_t a, b, c, d;
+            quantise2(v[k].x, v[k].y, M, s, a, b);
+            quantise2(v[k].z, v[k].w, M, s, c, d);
+            acc += a + b + c + d;
+        }
+    } else {
+        for (int e = threadIdx.x; e < n; e += blockDim.x)
+            acc += quantise(__ldg(lw + lo + e), M, s);
+    }
+    uint64_t total;
+    block_excl_scan_u64(acc, red, &total);
+    if (threadIdx.x == 0)
+        Qt[blockIdx.x] = total;
+}
+
+// Tile totals for RPA and ARNA: the tile's scan in shared memory gives, for
+// every group start inside the tile, the local prefix before it.
+__global__ void __launch_bounds__(TILE_THREADS) tile_group_totals_kernel(
     const float *__restrict__ lw, int64_t N, const DevSummary *__restrict__ sum, double ess_thr,
     uint64_t *__restrict__ Qt, const int64_t *__restrict__ goff, int32_t G, uint64_t *__restrict__ Cbl)
 {
@@ -44,31 +83,8 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_totals_kernel(
     __shared__ int32_t gfirst;
     const int64_t lo = (int64_t)blockIdx.x * TILE;
     const int n = (int)(N - lo < TILE ? N - lo : TILE);
-    const float M = sum->M;
-    const int s = scale_bits(N);
-    if (goff == nullptr) {
-        uint64_t acc = 0;
-        const float4 *v4 = reinterpret_cast<const float4 *>(lw + lo);
-        if (n == TILE && ((reinterpret_cast<uintptr_t>(lw + lo) & 15) == 0)) {
-            for (int e = threadIdx.x; e < TILE / 4; e += blockDim.x) {
-                const float4 v = __ldg(v4 + e);
-                uint64_t a, b, c, d;
-                quantise2(v.x, v.y, M, s, a, b);
-                quantise2(v.z, v.w, M, s, c, d);
-                acc += a + b + c + d;
-            }
-        } else {
-            for (int e = threadIdx.x; e < n; e += blockDim.x)
-                acc += quantise(__ldg(lw + lo + e), M, s);
-        }
-        uint64_t total;
-        block_excl_scan_u64(acc, red, &total);
-        if (threadIdx.x == 0)
-            Qt[blockIdx.x] = total;
-        return;
-    }
     uint64_t q[TILE_ITEMS];
-    tile_weights(lw, lo, n, M, s, buf, q);
+    tile_weights(lw, lo, n, sum->M, scale_bits(N), buf, q);
     const uint64_t total = tile_scan(q, buf, red);
     if (threadIdx.x == 0) {
         Qt[blockIdx.x] = total;
@@ -761,7 +777,7 @@ __global__ void __launch_bounds__(256) route_copy_kernel(const int32_t *__restri
 // tickets, then every offspring is written to its slot -- the last `mig`
 // slots of the group go to the tail of the next group of the ring (group
 // g + 1 mod G, or succ[g] for ARNA's ring).
-__global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
+__global__ void __launch_bounds__(TILE_THREADS, 4) rna_kernel(
     const float *__restrict__ lw, int64_t N, int32_t G, const int64_t *__restrict__ goff,
     const int32_t *__restrict__ succ, DevSummary *sum, double ess_thr, uint64_t seed, uint32_t fid, uint32_t frame,
     int32_t *__restrict__ anc, float *__restrict__ lwp)
@@ -801,11 +817,18 @@ __global__ void __launch_bounds__(TILE_THREADS) rna_kernel(
     // pass 2: total fixed-point weight and sum of e^(lw - Mg)
     uint64_t qs = 0;
     float es = 0.0f;
-    for (int64_t i = threadIdx.x; i < sz; i += blockDim.x) {
+    for (int64_t i = threadIdx.x; i < sz; i += 2 * (int64_t)blockDim.x) {
+        // two strided elements at a time (the sum of e^(lw - Mg) keeps its order)
+        const int64_t i2 = i + blockDim.x;
         const float v = __ldg(lw + lo + i);
-        qs += quantise(v, Mg, s);
+        const float w = (i2 < sz) ? __ldg(lw + lo + i2) : -INFINITY;
+        uint64_t a, b;
+        quantise2(v, w, Mg, s, a, b);
+        qs += a + b;
         if (v > -INFINITY)
             es += __expf(v - Mg);
+        if (w > -INFINITY)
+            es += __expf(w - Mg);
     }
     uint64_t Qg;
     block_excl_scan_u64(qs, red, &Qg);
@@ -1048,8 +1071,11 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     const int T = c->T;
     prof_mark(c, PH_RESAMPLE, 0);
     c->launches += rpa ? 5 : 3;
-    tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt,
-                                                          rpa ? c->goff : nullptr, c->G, c->sc.Cbl);
+    if (rpa)
+        tile_group_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff,
+                                                                    c->G, c->sc.Cbl);
+    else
+        tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt);
     const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
     tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
         c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sum, ess_thr, c->m.seed,
@@ -1114,8 +1140,8 @@ cudaError_t launch_resample_arna(ppf_ctx *c, float alpha, double ess_thr)
     const float *lw = c->state[c->cur] + 5 * c->N;
     const int T = c->T;
     prof_mark(c, PH_RESAMPLE, 0);
-    tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff, c->G,
-                                                          c->sc.Cbl);
+    tile_group_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff, c->G,
+                                                                c->sc.Cbl);
     const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
     tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
         c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, nullptr, c->sum, ess_thr, c->m.seed, c->m.filter_id,
