@@ -284,7 +284,11 @@ __global__ void batch_step_kernel(BatchStepArgs a)
             for (int c = 0; c < 5; ++c)
                 dst[(size_t)c * N + i] = v[c];
             dst[5 * (size_t)N + i] = lw;
-            acc.add(lw, lwp, v);
+            acc.add_cur(lw, v);
+            if (carry)
+                acc.add_prev(lwp);
+            else
+                acc.add_prev_zero();
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)

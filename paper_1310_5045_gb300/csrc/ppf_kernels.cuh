@@ -23,6 +23,11 @@ struct Acc {
     }
     __device__ __forceinline__ void add(float lw, float lwp, const float v[5])
     {
+        add_cur(lw, v);
+        add_prev(lwp);
+    }
+    __device__ __forceinline__ void add_cur(float lw, const float v[5])
+    {
         if (lw > m) {
             const float sc = __expf(m - lw);
             s0 *= sc;
@@ -40,12 +45,22 @@ struct Acc {
             for (int c = 0; c < 5; ++c)
                 s[c] = fmaf(e, v[c], s[c]);
         }
+    }
+    __device__ __forceinline__ void add_prev(float lwp)
+    {
         if (lwp > mp) {
             sp *= __expf(mp - lwp);
             mp = lwp;
         }
         if (lwp > -INFINITY)
             sp += __expf(lwp - mp);
+    }
+    // add_prev(0) after a resample to equal weights: the same bits without
+    // the exponentials (mp = 0, sp counts the particles)
+    __device__ __forceinline__ void add_prev_zero()
+    {
+        mp = 0.0f;
+        sp += 1.0f;
     }
     __device__ __forceinline__ void merge(const Acc &o)
     {

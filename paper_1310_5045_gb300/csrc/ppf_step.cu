@@ -210,7 +210,11 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
         for (int c = 0; c < 5; ++c)
             dplane[c][i] = v[c];
         dplane[5][i] = lw;
-        acc.add(lw, lwp, v);
+        acc.add_cur(lw, v);
+        if (mode == MODE_UNIFORM)
+            acc.add_prev_zero();
+        else
+            acc.add_prev(lwp);
     }
     // block reduction of the partial statistics
 #pragma unroll
