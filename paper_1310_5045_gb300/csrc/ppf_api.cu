@@ -74,6 +74,24 @@ void free_all(ppf_ctx *c)
     }
 }
 
+// the largest and smallest group of a layout into the device summary (the
+// systematic resample keeps the layout and leaves them as they are)
+cudaError_t store_group_extents(ppf_ctx *c, const int64_t *off)
+{
+    int64_t mx = 0, mn = INT64_MAX;
+    for (int32_t g = 0; g < c->G; ++g) {
+        const int64_t sz = off[g + 1] - off[g];
+        mx = sz > mx ? sz : mx;
+        mn = sz < mn ? sz : mn;
+    }
+    const int64_t ext[2] = {mx, mn};
+    static_assert(offsetof(DevSummary, min_group) == offsetof(DevSummary, max_group) + sizeof(int64_t),
+                  "max_group and min_group are adjacent");
+    cudaError_t e = cudaMemcpyAsync((char *)c->sum + offsetof(DevSummary, max_group), ext, sizeof(ext),
+                                    cudaMemcpyHostToDevice, c->stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(c->stream) : e;
+}
+
 // the ARNA ring in group order (host copy, synchronous)
 cudaError_t identity_ring(ppf_ctx *c)
 {
@@ -226,6 +244,8 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
             for (int64_t g = 0; g < G; ++g)
                 h[g + 1] = h[g] + base + (g < extra ? 1 : 0);
             chk(cudaMemcpy(c->goff, h, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice), "goff");
+            if (st == PPF_OK)
+                chk(store_group_extents(c, h), "group extents");
             free(h);
         }
     }
@@ -467,6 +487,7 @@ ppf_status ppf_set_groups(ppf_ctx *c, const int64_t *offsets_host)
             return PPF_EINVAL;
     CK(cudaMemcpyAsync(c->goff, offsets_host, sizeof(int64_t) * (c->G + 1), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));  // offsets_host may be released on return
+    CK(store_group_extents(c, offsets_host));
     CK(identity_ring(c));
     return PPF_OK;
 }

@@ -436,8 +436,14 @@ __global__ void batch_tile_scan(const FilterParams *__restrict__ fp, const Filte
         if (Q == 0ull)
             atomicOr(flags, FLAG_DEGENERATE);
     }
+    if (Q == 0ull) {
+        for (int32_t t = t0 + lane; t < t1; t += 32)
+            tT[t] = 0;
+        return;
+    }
+    const TicketGrid tg = ticket_grid(Q, u, Q / (uint64_t)P.n, (uint32_t)(Q % (uint64_t)P.n), P.ndiv);
     for (int32_t t = t0 + lane; t < t1; t += 32)
-        tT[t] = (Q == 0ull) ? 0 : tickets_below(tC[t], P.n, u, Q);
+        tT[t] = tickets_below_grid(tC[t], tg);
 }
 
 __global__ void __launch_bounds__(TILE_THREADS) batch_fill(const float *st0, const float *st1, int64_t Ntot,

@@ -186,7 +186,8 @@ __device__ __forceinline__ void quantise2(float a, float b, float M, int s, uint
     qb = quantise_tail(t.y, kf.y, p.y, s);
 }
 
-// Number of systematic tickets below cumulative weight c:
+// Number of systematic tickets below cumulative weight c (the per-group
+// draws of RNA and two-stage RPA; the global draw uses tickets_below_grid):
 // #{j in [0, n) : u + j Q < n c} = clamp(ceil((n c - u) / Q), 0, n).
 // Exact integer result: the quotient (at most n < 2^31) is estimated twice
 // with a float reciprocal of Q (the second time on the remainder) and then

@@ -121,11 +121,12 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
     int64_t N, int32_t T, const uint64_t *__restrict__ Qt, uint64_t *__restrict__ Ct, int64_t *__restrict__ Tt,
     int32_t *__restrict__ item_off, int32_t *__restrict__ item_tile, DevSummary *sum, double ess_thr, uint64_t seed,
     uint32_t fid, uint32_t frame, const int64_t *__restrict__ goff, int32_t G, int rpa,
-    const uint64_t *__restrict__ Cbl, int64_t *__restrict__ Tg, int32_t smem_tiles)
+    const uint64_t *__restrict__ Cbl, int64_t *__restrict__ Tg, int32_t smem_tiles, Divisor ndiv)
 {
     extern __shared__ uint64_t sT[];  // (smem_tiles + 1) tile values
     __shared__ uint64_t red[33];
-    __shared__ uint64_t su;
+    __shared__ uint64_t su, s_qN;
+    __shared__ uint32_t s_qR;
     if (kept_by_ess(sum, ess_thr)) {  // N_eff test: keep the particles and the layout
         if (threadIdx.x == 0) {
             sum->degenerate = 1;
@@ -174,20 +175,23 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
         if (deg)
             sum->flags |= FLAG_DEGENERATE;
         sum->Q = total;
-        sum->qN = total / (uint64_t)N;
-        sum->qR = (uint32_t)(total % (uint64_t)N);
+        s_qN = total / (uint64_t)N;
+        s_qR = (uint32_t)(total % (uint64_t)N);
+        sum->qN = s_qN;
+        sum->qR = s_qR;
         su = deg ? 0ull : ticket_offset(seed, fid, frame, PURPOSE_RESAMPLE, 0u, total);
         sum->u = su;
     }
     __syncthreads();
     const uint64_t Q = total, u = su;
+    const TicketGrid tg = ticket_grid(Q, u, s_qN, s_qR, ndiv);
     if (Q == 0ull) {
         if (threadIdx.x == 0)
             sum->n_items = 0;
         return;
     }
     for (int t = threadIdx.x; t <= T; t += blockDim.x) {
-        const int64_t v = (t == T) ? N : tickets_below(in_smem ? sT[t] : Ct[t], N, u, Q);
+        const int64_t v = (t == T) ? N : tickets_below_grid(in_smem ? sT[t] : Ct[t], tg);
         Tt[t] = v;
         if (in_smem)
             sT[t] = (uint64_t)v;  // each thread rewrites only the entries it read
@@ -235,36 +239,12 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
         for (int g = threadIdx.x; g <= G; g += blockDim.x) {
             const int64_t pos = goff[g];
             const uint64_t c = (pos >= N) ? Q : Ct[pos / TILE] + Cbl[g];
-            Tg[g] = (pos >= N) ? N : tickets_below(c, N, u, Q);
+            Tg[g] = (pos >= N) ? N : tickets_below_grid(c, tg);
         }
     } else {
-        // systematic keeps the group layout: report its extent, no routing
-        __shared__ long long smx[32], smn[32];
-        long long mx = 0, mn = INT64_MAX;
-        for (int g = threadIdx.x; g < G; g += blockDim.x) {
-            const long long sz = goff[g + 1] - goff[g];
-            mx = sz > mx ? sz : mx;
-            mn = sz < mn ? sz : mn;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const long long a = __shfl_xor_sync(0xffffffffu, mx, o);
-            const long long b = __shfl_xor_sync(0xffffffffu, mn, o);
-            mx = a > mx ? a : mx;
-            mn = b < mn ? b : mn;
-        }
-        if ((threadIdx.x & 31) == 0) {
-            smx[threadIdx.x >> 5] = mx;
-            smn[threadIdx.x >> 5] = mn;
-        }
-        __syncthreads();
+        // systematic keeps the group layout (the summary already holds its
+        // extent, set whenever the layout changes); no routing
         if (threadIdx.x == 0) {
-            long long a = 0, b = INT64_MAX;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                a = smx[w] > a ? smx[w] : a;
-                b = smn[w] < b ? smn[w] : b;
-            }
-            sum->max_group = a;
-            sum->min_group = b;
             sum->links = 0;
             sum->moved = 0;
         }
@@ -1079,7 +1059,8 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
     tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
         c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sum, ess_thr, c->m.seed,
-        c->m.filter_id, (uint32_t)c->last_frame, c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg, st_tiles);
+        c->m.filter_id, (uint32_t)c->last_frame, c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg, st_tiles,
+        make_divisor((uint32_t)c->N));
     int32_t *out = rpa ? c->anc_sys : c->anc;
     const bool two_stage = (scheme >= PPF_RPA2_GS && scheme <= PPF_RPA2_LGS);
     if (two_stage) {  // stage 2: every group draws its own offspring
@@ -1145,7 +1126,7 @@ cudaError_t launch_resample_arna(ppf_ctx *c, float alpha, double ess_thr)
     const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
     tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
         c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, nullptr, c->sum, ess_thr, c->m.seed, c->m.filter_id,
-        (uint32_t)c->last_frame, c->goff, c->G, 1, c->sc.Cbl, c->sc.Tg, st_tiles);
+        (uint32_t)c->last_frame, c->goff, c->G, 1, c->sc.Cbl, c->sc.Tg, st_tiles, make_divisor((uint32_t)c->N));
     arna_prep_kernel<<<1, 1024, sizeof(uint64_t) * MAX_SCHED_GROUPS, c->stream>>>(
         c->goff, c->G, alpha, c->sum, ess_thr, c->sc.Tg, c->ring, c->succ, c->m.seed, c->m.filter_id,
         (uint32_t)c->last_frame);

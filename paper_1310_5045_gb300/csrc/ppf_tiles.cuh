@@ -102,6 +102,37 @@ __device__ __forceinline__ TicketGrid ticket_grid(uint64_t Q, uint64_t u, uint64
     return g;
 }
 
+// The threshold of ticket j, thr_j = floor((u + jQ)/nt) = j qN + floor((u + j qR)/nt):
+// exact in 64-bit arithmetic (j < nt < 2^31 and u < Q <= 2^63, so
+// u + j qR < 2^64).
+__device__ __forceinline__ uint64_t ticket_threshold(int64_t j, const TicketGrid &tg)
+{
+    uint32_t r;
+    return (uint64_t)j * tg.qN + div_by(tg.u + (uint64_t)j * tg.qR, tg.nt, &r);
+}
+
+// Number of tickets below cumulative weight c, #{j in [0, nt) : u + jQ < nt c}
+// = #{j : thr_j < c} (thr_j < c iff (u + jQ)/nt < c for integer c): a float
+// estimate c nt / Q, corrected once by the float estimate of the distance
+// from c to the estimate's exact threshold, then moved to the exact boundary
+// by comparing thresholds (they do not decrease with j).  No 128-bit or FP64
+// arithmetic.
+__device__ __forceinline__ int64_t tickets_below_grid(uint64_t c, const TicketGrid &tg)
+{
+    const int64_t n = tg.nt.d;
+    const float rstep = (float)n / (float)tg.Q;
+    int64_t j = (int64_t)((float)c * rstep);
+    j = j < 0 ? 0 : (j > n - 1 ? n - 1 : j);
+    const int64_t d = (int64_t)(c - ticket_threshold(j, tg));
+    j += (int64_t)floorf((float)d * rstep);
+    j = j < 0 ? 0 : (j > n ? n : j);
+    while (j > 0 && ticket_threshold(j - 1, tg) >= c)
+        --j;
+    while (j < n && ticket_threshold(j, tg) < c)
+        ++j;
+    return j;
+}
+
 // Parents of the tickets [j_lo, j_hi) of one run of particles with inclusive
 // cumulative weights C[0..n) (local; the run starts at cumulative weight c0,
 // n <= TILE).  Ticket j sits at (u + jQ)/nt; its parent is the first i with
