@@ -58,6 +58,40 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
+// The ten round keys of one Philox key (the key advanced by the Weyl
+// increments), computed once on the host so that a kernel reads them from its
+// parameters instead of recomputing them for every block it draws.
+struct PhiloxKeys {
+    uint32_t k[10][2];
+};
+
+__host__ __device__ inline PhiloxKeys philox_keys(uint64_t seed)
+{
+    PhiloxKeys r;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        r.k[round][0] = k0;
+        r.k[round][1] = k1;
+    }
+    return r;
+}
+
+// philox() with precomputed round keys (the same block)
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const PhiloxKeys &rk)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk.k[round][0], lo1, hi0 ^ c.w ^ rk.k[round][1], lo0);
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t index, uint32_t frame, uint32_t filter,
                                       uint32_t purpose, uint32_t block)
 {

@@ -26,6 +26,7 @@ struct GradArgs {
     float sigma, inv2s2, inv_sxi2, A, sm, sv;
     float Kc[MAX_RADIUS];
     uint64_t seed;
+    PhiloxKeys rk;     // round keys of seed
     uint32_t fid, frame;
     int first;                       // first frame: identity ancestry, zero tangents
     const float *__restrict__ src;   // 6 x N
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(256) grad_step_kernel(GradArgs a)
         const float vx = __ldg(a.src + 2 * N + p), vy = __ldg(a.src + 3 * N + p);
         const float tx = a.first ? 0.0f : __ldg(a.tsrc + p), ty = a.first ? 0.0f : __ldg(a.tsrc + N + p);
         uint32_t f[6];
-        prop_fields(draw(a.seed, (uint32_t)i, a.frame, a.fid, PURPOSE_PROP, 0), f);
+        prop_fields(philox_rk(make_uint4((uint32_t)i, a.frame, a.fid, PURPOSE_PROP << 8), a.rk), f);
         float e0, e1, e2, e3;
         box_muller(u21(f[0]), u21(f[1]), e0, e1);
         box_muller(u21(f[2]), u21(f[3]), e2, e3);
@@ -369,6 +370,7 @@ cudaError_t launch_grad_step(ppf_ctx *c, int32_t k, bool first, int32_t *anchors
     a.sm = c->m.sigma_m;
     a.sv = c->m.sigma_v;
     a.seed = c->m.seed;
+    a.rk = philox_keys(c->m.seed);
     a.fid = c->m.filter_id;
     a.frame = (uint32_t)k;
     a.first = first ? 1 : 0;

@@ -69,6 +69,7 @@ struct StepArgs {
     float inv_sxi2;    // 1 / sigma_xi^2
     float sm, sv, sI;
     uint64_t seed;
+    PhiloxKeys rk;     // round keys of seed
     uint32_t fid, frame;
     const float *__restrict__ src;
     float *__restrict__ dst;
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
         else
             lwp = __ldg(a.lwp + i);
         uint32_t f[6];
-        prop_fields(draw(a.seed, (uint32_t)i, a.frame, a.fid, PURPOSE_PROP, 0), f);
+        prop_fields(philox_rk(make_uint4((uint32_t)i, a.frame, a.fid, PURPOSE_PROP << 8), a.rk), f);
         float e0, e1, e2, e3, e4, e5;
         box_muller(u21(f[0]), u21(f[1]), e0, e1);
         box_muller(u21(f[2]), u21(f[3]), e2, e3);
@@ -391,6 +392,7 @@ cudaError_t launch_step(ppf_ctx *c, int32_t k)
     a.sv = c->m.sigma_v;
     a.sI = c->m.sigma_I;
     a.seed = c->m.seed;
+    a.rk = philox_keys(c->m.seed);
     a.fid = c->m.filter_id;
     a.frame = (uint32_t)k;
     a.src = c->state[c->cur];
