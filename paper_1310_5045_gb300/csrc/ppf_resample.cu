@@ -632,11 +632,19 @@ __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
         // now PS[i], PR[j] are exclusive starts; piece starts are the union of
         // both start sets (0 is in both).  Merge them (PS first on ties).
         int64_t *MG = A.val + 4 * G;  // at most nS + nR <= G entries
+        // the binary searches below run on shared copies of the two prefix
+        // arrays (nS + nR <= G <= MAX_SCHED_GROUPS entries; the sort is done)
+        int64_t *sPS = reinterpret_cast<int64_t *>(sm), *sPR = sPS + nS;
         __syncthreads();
         for (int i = threadIdx.x; i < nS; i += blockDim.x)
-            MG[i + lower_bound_i64(PR, nR, PS[i])] = PS[i];
+            sPS[i] = PS[i];
         for (int j = threadIdx.x; j < nR; j += blockDim.x)
-            MG[j + upper_bound_i64(PS, nS, PR[j])] = PR[j];
+            sPR[j] = PR[j];
+        __syncthreads();
+        for (int i = threadIdx.x; i < nS; i += blockDim.x)
+            MG[i + lower_bound_i64(sPR, nR, sPS[i])] = sPS[i];
+        for (int j = threadIdx.x; j < nR; j += blockDim.x)
+            MG[j + upper_bound_i64(sPS, nS, sPR[j])] = sPR[j];
         __syncthreads();
         const int nm = nS + nR;
         // distinct starts -> links; store compacted into seg arrays after G
@@ -655,16 +663,16 @@ __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
                 const int i = i0 + k;
                 if (i < nm && (i == 0 || MG[i] != MG[i - 1])) {
                     const int64_t a = MG[i];
-                    const int si = upper_bound_i64(PS, nS, a) - 1;  // sender piece contains a
-                    const int rj = upper_bound_i64(PR, nR, a) - 1;
-                    const int64_t se = PS[si] + amount(Skey[si]);
-                    const int64_t re = PR[rj] + amount(Rkey[rj]);
+                    const int si = upper_bound_i64(sPS, nS, a) - 1;  // sender piece contains a
+                    const int rj = upper_bound_i64(sPR, nR, a) - 1;
+                    const int64_t se = sPS[si] + amount(Skey[si]);
+                    const int64_t re = sPR[rj] + amount(Rkey[rj]);
                     const int64_t e = se < re ? se : re;
                     const int32_t s = group(Skey[si]), r = group(Rkey[rj]);
                     const int64_t keep_s = (A.Tg[s + 1] - A.Tg[s]) - sent[s];
                     const int64_t keep_r = A.Tg[r + 1] - A.Tg[r];
-                    seg_tick[G + pos] = A.Tg[s] + keep_s + (a - PS[si]);
-                    seg_dst[G + pos] = off[r] + keep_r + (a - PR[rj]);
+                    seg_tick[G + pos] = A.Tg[s] + keep_s + (a - sPS[si]);
+                    seg_dst[G + pos] = off[r] + keep_r + (a - sPR[rj]);
                     seg_len[G + pos] = e - a;
                     ++pos;
                 }
