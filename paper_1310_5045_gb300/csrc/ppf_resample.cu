@@ -88,7 +88,20 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_group_totals_kernel(
     const uint64_t total = tile_scan(q, buf, red);
     if (threadIdx.x == 0) {
         Qt[blockIdx.x] = total;
-        int32_t a = 0, b = G + 1;  // first g with goff[g] >= lo
+        // first g with goff[g] >= lo.  For a balanced layout the guess
+        // lo G / N or its successor is the answer (two loads); otherwise the
+        // guess halves the bracket of the bisection.
+        const int32_t g = (int32_t)(lo * (int64_t)G / N);
+        int32_t a = 0, b = G + 1;
+        if (goff[g] >= lo) {
+            b = g;
+            if (g == 0 || goff[g - 1] < lo)
+                a = g;
+        } else {
+            a = g + 1;
+            if (goff[g + 1] >= lo)
+                b = g + 1;
+        }
         while (a < b) {
             const int32_t mid = (a + b) >> 1;
             if (goff[mid] < lo)
