@@ -6,10 +6,12 @@ kernels for sm_103a behind the C ABI of ``include/ppf.h``."""
 from ._binding import (  # noqa: F401
     ARNA,
     BF16,
+    ECUDA,
     EDEGENERATE,
     EINVAL,
     ENOMEM,
     ESTATE,
+    ETIMEOUT,
     F16,
     F32,
     OK,

@@ -26,7 +26,8 @@ void set_err(ppf_ctx *c, const char *fmt, ...)
 
 // Host-side fault injection: PPF_FAULT=alloc makes ppf_create fail as if the
 // device allocation failed, PPF_FAULT=launch makes ppf_step fail as if the
-// launch failed.  No GPU fault is ever produced.
+// launch failed, PPF_FAULT=timeout makes ppf_estimate report the timeout flag
+// as if a bounded device wait had given up.  No GPU fault is ever produced.
 bool fault(const char *what)
 {
     const char *f = getenv("PPF_FAULT");
@@ -385,31 +386,36 @@ ppf_status ppf_estimate(ppf_ctx *c, ppf_estimate_t *out)
     c->d2h_bytes += (int64_t)sizeof(DevSummary);
     CK(cudaStreamSynchronize(c->stream));
     const DevSummary &s = *c->sum_host;
+    const int32_t flags = s.flags | (fault("timeout") ? FLAG_TIMEOUT : 0);
     for (int i = 0; i < 5; ++i)
         out->mean[i] = s.mean[i];
     out->log_evidence = s.log_evidence;
     out->ess = s.ess;
     out->max_log_weight = s.max_lw;
     out->frame = s.frame;
-    out->status_flags = s.flags;
+    out->status_flags = flags;
     out->links = s.links;
     out->moved = s.moved;
     out->max_group = s.max_group;
     out->min_group = s.min_group;
-    if (s.flags) {
-        const int32_t zero = 0;
-        CK(cudaMemcpyAsync((char *)c->sum + offsetof(DevSummary, flags), &zero, sizeof(zero),
-                           cudaMemcpyHostToDevice, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        if (s.flags & (FLAG_INTERNAL | FLAG_BAD_ANCESTOR)) {
-            set_err(c, "device flags 0x%x: %s", s.flags,
-                    (s.flags & FLAG_BAD_ANCESTOR) ? "ancestor index out of range (treated as identity)"
-                                                  : "inconsistent routing schedule (copy skipped)");
+    if (flags) {
+        if (s.flags) {
+            const int32_t zero = 0;
+            CK(cudaMemcpyAsync((char *)c->sum + offsetof(DevSummary, flags), &zero, sizeof(zero),
+                               cudaMemcpyHostToDevice, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        if (flags & (FLAG_INTERNAL | FLAG_BAD_ANCESTOR)) {
+            set_err(c, "device flags 0x%x: %s", flags,
+                    (flags & FLAG_BAD_ANCESTOR)
+                        ? "ancestor index out of range (treated as identity)"
+                        : "internal consistency check failed (routing schedule, or an index check of the "
+                          "debug build); the access was skipped");
             return PPF_EINVAL;
         }
-        if (s.flags & FLAG_DEGENERATE)
+        if (flags & FLAG_DEGENERATE)
             return PPF_EDEGENERATE;
-        if (s.flags & FLAG_TIMEOUT)
+        if (flags & FLAG_TIMEOUT)
             return PPF_ETIMEOUT;
     }
     return PPF_OK;  // FLAG_KEPT (N_eff test) and FLAG_RING (ARNA redraw) are information, not errors

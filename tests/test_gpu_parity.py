@@ -320,6 +320,35 @@ def test_arna_ring_accessors(ppf, movie):
     pf.close()
 
 
+def test_injected_host_faults_leave_the_context_usable(ppf, movie, monkeypatch):
+    """Host-side fault injection (no GPU fault): a failed launch is reported
+    as PPF_ECUDA with its message, a bounded-wait timeout as PPF_ETIMEOUT from
+    ppf_estimate; without the fault the same context steps and estimates."""
+    from gpu_common import paired_models
+    gm, _ = paired_models(ppf, seed=2)
+    fr = gpu_frames(movie)
+    pf = ppf.ParticleFilter(gm, 4096, group_size=1024)
+    monkeypatch.setenv("PPF_FAULT", "launch")
+    with pytest.raises(ppf.PPFError) as err:
+        pf.step(fr[0], 1)
+    assert err.value.status == ppf.ECUDA and "injected launch failure" in str(err.value)
+    monkeypatch.delenv("PPF_FAULT")
+    pf.step(fr[0], 1)
+    monkeypatch.setenv("PPF_FAULT", "timeout")
+    e = pf.estimate()
+    assert e.status == ppf.ETIMEOUT
+    assert e.status_flags & 2
+    with pytest.raises(ppf.PPFError):
+        pf.estimate(raise_on_flags=True)
+    monkeypatch.delenv("PPF_FAULT")
+    e = pf.estimate()
+    assert e.status == 0 and e.status_flags == 0 and math.isfinite(e.log_evidence)
+    pf.resample(ppf.SYSTEMATIC)
+    pf.step(fr[1], 2)
+    assert pf.estimate().status == 0
+    pf.close()
+
+
 def test_estimate_async_matches_estimate(ppf, movie):
     """Queued estimate copies (one per frame, read after the last frame) equal
     the synchronous estimates of the same frames."""
