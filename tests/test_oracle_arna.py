@@ -146,3 +146,23 @@ def test_run_follows_the_ring_state(orc):
     assert rc == 0 and np.all(np.isfinite(est))
     err = np.hypot(est[-1, 0] - mv.truth[-1][0], est[-1, 1] - mv.truth[-1][1])
     assert err < 1.0
+
+
+def test_unequal_groups(orc):
+    """An LGS-like layout of unequal groups: the involved test compares each
+    group's proportional offspring with its own size, the migrant count uses
+    the smallest group, and the exchange follows a permuted ring."""
+    m = orc.Model(seed=9)
+    N, frame = 2000, 6
+    sizes = np.array([500, 120, 380, 260, 740])
+    goff = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    G = len(sizes)
+    lw = weights(N, 5, spread=3.0)
+    ring = np.array([3, 0, 4, 1, 2], dtype=np.int32)
+    rc, anc, lwr, gout, st, ring_out = orc.resample_arna(m, N, frame, goff, lw, False, ring, alpha=0.5)
+    assert rc == 0 and np.array_equal(gout, goff) and np.array_equal(ring_out, ring)
+    inv = involved_groups(orc, m, N, frame, goff, lw)
+    mig = int(math.floor(0.5 * (G - inv) * 120 / G))
+    assert st[4] == inv and st[2] == 740 and st[3] == 120 and st[1] == mig * G
+    want_anc, want_lwr = expected_exchange(orc, m, N, frame, goff, lw, mig, ring)
+    assert np.array_equal(anc, want_anc) and np.array_equal(lwr, want_lwr)
