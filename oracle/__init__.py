@@ -42,7 +42,11 @@ def build(force: bool = False) -> str:
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
            "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP over particles where the toolchain has it; the results do not
+    # depend on it (per-particle loops only, reductions summed serially)
+    p = subprocess.run(cmd[:-1] + ["-fopenmp", "-lm"], capture_output=True, text=True)
+    if p.returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -93,6 +97,7 @@ def lib():
                                               P(C.c_uint64), P(C.c_double), P(C.c_float))
             mp = P(_Model)
             sig = {
+                "orc_set_threads": (C.c_int, [C.c_int]),
                 "orc_philox": (None, [u32p, u32p, u32p]),
                 "orc_u01": (C.c_double, [C.c_uint32]),
                 "orc_u21": (C.c_double, [C.c_uint32]),
@@ -141,6 +146,12 @@ def _p(a: np.ndarray, ct):
 # ----------------------------------------------------------------------------
 # thin wrappers (arrays in / arrays out); all arithmetic is in ppf_oracle.c
 # ----------------------------------------------------------------------------
+def set_threads(n: int = 0) -> int:
+    """Threads of the per-particle loops (0: leave as is); returns the count
+    in use (1 without OpenMP).  Results do not depend on it."""
+    return int(lib().orc_set_threads(int(n)))
+
+
 def philox(ctr, key) -> np.ndarray:
     c = np.ascontiguousarray(ctr, dtype=np.uint32)
     k = np.ascontiguousarray(key, dtype=np.uint32)

@@ -61,8 +61,27 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include "ppf_oracle.h"
+
+/* Threads: the per-particle loops (init, propagation, likelihood, the
+ * exponentials of the summary) may run in parallel over particles; each
+ * particle's arithmetic is unchanged and every reduction is summed serially
+ * in particle order, so results do not depend on the thread count. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon et al., SC'11: "Parallel random numbers: as easy as  */
@@ -153,6 +172,7 @@ void orc_normals5(uint64_t seed, uint32_t slot, uint32_t frame, uint32_t filter,
 void orc_init(const orc_model *m, int64_t N, double *st)
 {
     double *x = st, *y = st + N, *vx = st + 2 * N, *vy = st + 3 * N, *I0 = st + 4 * N, *lw = st + 5 * N;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) {
         uint32_t a[4], b[4];
         draw(m->seed, (uint32_t)i, 0u, m->filter_id, ORC_PURPOSE_INIT, 0, a);
@@ -176,6 +196,7 @@ void orc_propagate(const orc_model *m, int64_t N, int32_t frame, const double *p
 {
     const double *px = par, *py = par + N, *pvx = par + 2 * N, *pvy = par + 3 * N, *pI = par + 4 * N;
     double *x = st, *y = st + N, *vx = st + 2 * N, *vy = st + 3 * N, *I0 = st + 4 * N, *lw = st + 5 * N;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) {
         int64_t a = anc[i];
         double e[5];
@@ -194,6 +215,7 @@ void orc_propagate(const orc_model *m, int64_t N, int32_t frame, const double *p
 void orc_propagate_slots(const orc_model *m, int64_t n, int32_t frame, const int64_t *slots,
                          const double *parents5, double *out5)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n; ++k) {
         double e[5];
         orc_normals5(m->seed, (uint32_t)slots[k], (uint32_t)frame, m->filter_id, e);
@@ -211,6 +233,7 @@ void orc_propagate_slots(const orc_model *m, int64_t n, int32_t frame, const int
 void orc_loglik_many(const orc_model *m, const double *frame, int64_t n, const double *x, const double *y,
                      const double *I0, double *l)
 {
+#pragma omp parallel for schedule(dynamic, 4096)
     for (int64_t k = 0; k < n; ++k)
         l[k] = orc_loglik(m, frame, x[k], y[k], I0[k]);
 }
@@ -266,6 +289,7 @@ void orc_weight(const orc_model *m, int64_t N, const double *frame, double *st)
 {
     const double *x = st, *y = st + N, *I0 = st + 4 * N;
     double *lw = st + 5 * N;
+#pragma omp parallel for schedule(dynamic, 4096)
     for (int64_t i = 0; i < N; ++i)
         lw[i] += orc_loglik(m, frame, x[i], y[i], I0[i]);
 }
@@ -285,24 +309,33 @@ void orc_summary(int64_t N, const double *st, const double *lw_prev, double out[
         if (lw[i] > M) M = lw[i];
         if (lw_prev[i] > Mp) Mp = lw_prev[i];
     }
+    /* the exponentials in parallel, the sums serially in particle order */
+    double *e = (double *)malloc(sizeof(double) * (size_t)(2 * (N > 0 ? N : 1)));
+    double *ep = e + N;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        e[i] = lw[i] > -INFINITY ? exp(lw[i] - M) : 0.0;
+        ep[i] = lw_prev[i] > -INFINITY ? exp(lw_prev[i] - Mp) : 0.0;
+    }
     double total = 0.0, totalp = 0.0;
     for (int64_t i = 0; i < N; ++i) {
         if (lw[i] > -INFINITY)
-            total += exp(lw[i] - M);
+            total += e[i];
         if (lw_prev[i] > -INFINITY)
-            totalp += exp(lw_prev[i] - Mp);
+            totalp += ep[i];
     }
     double mean[5] = {0, 0, 0, 0, 0}, sumsq = 0.0;
     for (int64_t i = 0; i < N; ++i) {
         if (!(lw[i] > -INFINITY))
             continue;
-        double w = exp(lw[i] - M) / total;
+        double w = e[i] / total;
         if (w == 0.0)
             continue;
         for (int c = 0; c < 5; ++c)
             mean[c] += w * st[c * N + i];
         sumsq += w * w;
     }
+    free(e);
     for (int c = 0; c < 5; ++c)
         out[c] = mean[c];
     out[5] = (M + log(total)) - (Mp + log(totalp));

@@ -21,6 +21,7 @@ typedef struct {
     uint32_t filter_id, pad2_;
 } orc_model;
 
+int orc_set_threads(int n);
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_u01(uint32_t r);
 double orc_u21(uint32_t field);

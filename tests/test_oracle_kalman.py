@@ -9,11 +9,26 @@ Case 2 resamples only while the effective sample size is below N/2 (the
 N_eff test of Alg. 1), so the carried-weight path of the recursion is pinned
 as well.
 
-Monte Carlo error: 20 runs with independent random streams (the paper repeats
-each test 20 times, Sec. 7.3); the seed-mean of every posterior-mean component
-and of the log-evidence must lie within 4 standard errors of the closed form,
-the standard error taken from the spread across the 20 runs."""
+Monte Carlo error: 20 runs with independent random streams per case (the
+paper repeats each test 20 times, Sec. 7.3).  The Monte Carlo standard
+error (MCSE) of one run is the standard deviation of its estimate across the
+20 runs; that of the seed-mean is that over sqrt(20).  Over the three cases,
+at most 1 % of the checks may lie beyond 3 MCSE -- of one run, and of the
+seed-mean, pooled over the posterior means and log-evidences below -- and
+none beyond 4.5:
+  * the posterior mean (12 frames x 5 components) at N = 2^16;
+  * the log-evidence per frame at N = 2^18.  It is the log of an unbiased
+    estimate, so it is biased low by O(1/N); at N = 2^16 that bias reaches
+    4 MCSE of the seed-mean on frames where the observation falls in the
+    tail of the predictive density (N_eff down to 300 of 65536), and at
+    N = 2^18 it is below the Monte Carlo error.
+
+The per-run MCSE sqrt(Var_post / N_eff) is not used: it leaves out the
+variance that resampling accumulates along the particle paths (the
+velocities are observed only through the positions), and understates the
+run-to-run spread by factors of up to 17 here."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -62,10 +77,8 @@ def run_sir(orc, seed, zs, prior_m, prior_s, sm, sv, sI, sz, N, ess_threshold=ma
     return np.array(means), np.array(ev)
 
 
-@pytest.mark.parametrize("case", [0, 1, 2])
-def test_sir_matches_kalman(orc, case):
+def kalman_case(orc, case, N, K, R):
     rng = np.random.default_rng(100 + case)
-    N, K, R = 1 << 14, 12, 20
     sm, sv, sI, sz = 0.5, 0.15, 0.8, 0.7
     prior_m = np.array([40.0, 30.0, 0.5, -0.3, 25.0])
     prior_s = np.array([2.0, 1.5, 0.4, 0.3, 2.0])
@@ -85,9 +98,32 @@ def test_sir_matches_kalman(orc, case):
     runs = [run_sir(orc, 1000 * case + s, zs, prior_m, prior_s, sm, sv, sI, sz, N, thr) for s in range(R)]
     M = np.array([r[0] for r in runs])       # (R, K, 5)
     E = np.array([r[1] for r in runs])       # (R, K)
-    se = M.std(axis=0, ddof=1) / math.sqrt(R)
-    z = np.abs(M.mean(axis=0) - want) / se
-    assert z.max() < 4.0, np.round(z, 2)
-    se_ev = E.std(axis=0, ddof=1) / math.sqrt(R)
-    zev = np.abs(E.mean(axis=0) - want_ev) / se_ev
-    assert zev.max() < 4.0, np.round(zev, 2)
+    return mcse_z(M, want, R), mcse_z(E, want_ev, R)
+
+
+def mcse_z(X, want, R):
+    """|X - want| in MCSE of one run, and |mean X - want| in MCSE of the mean."""
+    sd = X.std(axis=0, ddof=1)
+    return (np.abs(X - want) / sd).ravel(), (np.abs(X.mean(axis=0) - want) / (sd / math.sqrt(R))).ravel()
+
+
+def check_z(z, what):
+    z = np.concatenate(z)
+    assert np.all(np.isfinite(z)), what
+    n3 = int((z > 3.0).sum())
+    assert n3 <= 0.01 * z.size and z.max() < 4.5, (what, n3, z.size, np.round(np.sort(z)[-4:], 2))
+
+
+def test_sir_matches_kalman(orc):
+    K, R = 12, 20
+    orc.set_threads(os.cpu_count() or 1)
+    zr, zm, er, em = [], [], [], []
+    for case in (0, 1, 2):
+        (a, b), _ = kalman_case(orc, case, 1 << 16, K, R)
+        zr.append(a)
+        zm.append(b)
+        _, (c, d) = kalman_case(orc, case, 1 << 18, K, R)
+        er.append(c)
+        em.append(d)
+    check_z(zr + er, "single runs")
+    check_z(zm + em, "seed-means")

@@ -1,42 +1,10 @@
 """Pins for the oracle's random streams: Philox4x32-10 against an independent
 library implementation (triton's, run by its CPU interpreter), the uniform
 map, and the Box-Muller normals against scipy's normal distribution."""
-import json
-import os
-import subprocess
-import sys
-import textwrap
-
 import numpy as np
 import pytest
 
-TRITON_SCRIPT = textwrap.dedent(
-    """
-    import os, sys, json
-    os.environ["TRITON_INTERPRET"] = "1"
-    import numpy as np, torch, triton, triton.language as tl
-
-    @triton.jit
-    def k(out_ptr, c0_ptr, c1_ptr, c2_ptr, c3_ptr, seed, n: tl.constexpr):
-        offs = tl.arange(0, n)
-        c0 = tl.load(c0_ptr + offs); c1 = tl.load(c1_ptr + offs)
-        c2 = tl.load(c2_ptr + offs); c3 = tl.load(c3_ptr + offs)
-        a, b, c, d = tl.philox(seed, c0, c1, c2, c3, 10)
-        tl.store(out_ptr + offs * 4 + 0, a); tl.store(out_ptr + offs * 4 + 1, b)
-        tl.store(out_ptr + offs * 4 + 2, c); tl.store(out_ptr + offs * 4 + 3, d)
-
-    cases = json.loads(sys.stdin.read())
-    res = []
-    for seed, ctrs in cases:
-        ctr = np.array(ctrs, dtype=np.uint32)
-        n = ctr.shape[0]
-        cs = [torch.from_numpy(ctr[:, i].copy()) for i in range(4)]
-        out = torch.zeros(4 * n, dtype=torch.uint32)
-        k[(1,)](out, *cs, seed, n)
-        res.append(out.numpy().reshape(n, 4).tolist())
-    print(json.dumps(res))
-    """
-)
+from philox_ref import triton_philox
 
 
 def test_philox_matches_triton_reference(orc):
@@ -50,12 +18,9 @@ def test_philox_matches_triton_reference(orc):
         ctrs[1] = [1, 0, 0, 0]
         cases.append([seed, ctrs.tolist()])
     cases.append([0, [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [7, 3, 1, 2 << 8 | 1], [1, 2, 3, 4]]])
-    env = dict(os.environ, TRITON_INTERPRET="1")
-    p = subprocess.run([sys.executable, "-c", TRITON_SCRIPT], input=json.dumps(cases),
-                       capture_output=True, text=True, env=env, timeout=600)
-    if p.returncode != 0:
-        pytest.skip("triton interpreter unavailable: " + p.stderr[-300:])
-    ref = json.loads(p.stdout.strip().splitlines()[-1])
+    ref, why = triton_philox(cases)
+    if ref is None:
+        pytest.skip(why)
     for (seed, ctrs), want in zip(cases, ref):
         key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
         for ctr, w in zip(ctrs, want):

@@ -98,11 +98,63 @@ def test_systematic_degenerate(orc):
     assert rc == orc.EDEGENERATE
 
 
-def test_ticket_offset_range(orc):
-    for Q in [1, 2, 12345, 2**63]:
-        for k in range(20):
-            u = orc.ticket_offset(9, 0, k, orc.PURPOSE_RESAMPLE, 0, Q)
-            assert 0 <= u < Q
+def _offset_words(orc, cases):
+    """Philox words of the ticket-offset counters: triton's when its CPU
+    interpreter runs, else the oracle's own (pinned against triton by
+    test_philox_matches_triton_reference)."""
+    from philox_ref import triton_philox
+    ref, _ = triton_philox(cases)
+    if ref is not None:
+        return ref
+    return [[orc.philox(c, [seed & 0xFFFFFFFF, seed >> 32]).tolist() for c in ctrs] for seed, ctrs in cases]
+
+
+def test_ticket_offset_is_high_word_of_r64_times_q(orc):
+    """R2: u = floor(r64 Q / 2^64) with r64 = w1 2^32 + w0, (w0, w1) the
+    first two words of Philox4x32-10 with key (seed_lo, seed_hi) and counter
+    (index, frame, filter, purpose << 8).  The product is formed here with
+    Python integers from independently computed Philox words, so swapped
+    words, a 32-bit r64 or the low half of the product all fail."""
+    rng = np.random.default_rng(77)
+    seeds = [9, 2**40 + 3, 0xDEADBEEFCAFEF00D]
+    cases = []
+    for seed in seeds:
+        ctrs = []
+        for j in range(8):
+            purpose = orc.PURPOSE_RESAMPLE if j % 2 == 0 else orc.PURPOSE_GROUP_RESAMPLE
+            index = 0 if purpose == orc.PURPOSE_RESAMPLE else int(rng.integers(0, 20000))
+            frame = int(rng.integers(1, 2**31))
+            filt = int(rng.integers(0, 5000)) if j >= 4 else 0
+            ctrs.append([index, frame, filt, purpose << 8])
+        cases.append([seed, ctrs])
+    words = _offset_words(orc, cases)
+    Qs = [1, 3, 2**40 + 7, 2**63, 2**64 - 1, int(rng.integers(1, 2**62))]
+    for (seed, ctrs), ws in zip(cases, words):
+        for (index, frame, filt, pw), w in zip(ctrs, ws):
+            r64 = (int(w[1]) << 32) | int(w[0])
+            for Q in Qs:
+                want = (r64 * Q) >> 64
+                got = orc.ticket_offset(seed, filt, frame, pw >> 8, index, Q)
+                assert got == want, (seed, index, frame, filt, pw >> 8, Q, got, want)
+                assert 0 <= got < Q
+
+
+def test_ticket_offset_is_uniform(orc):
+    """u / Q over 10^4 frames is uniform on [0, 1) (Kolmogorov-Smirnov at
+    large Q), and u is uniform on {0, 1, 2} at Q = 3 (chi-square)."""
+    stats = pytest.importorskip("scipy.stats")
+    K = 10_000
+    for Q in [2**63, 2**40 + 7]:
+        u = np.array([orc.ticket_offset(5, 0, k, orc.PURPOSE_RESAMPLE, 0, Q) for k in range(1, K + 1)],
+                     dtype=np.float64) / float(Q)
+        assert stats.kstest(u, "uniform").pvalue > 1e-4
+    g = np.array([orc.ticket_offset(5, 3, 17, orc.PURPOSE_GROUP_RESAMPLE, i, 2**50) for i in range(K)],
+                 dtype=np.float64) / 2.0**50
+    assert stats.kstest(g, "uniform").pvalue > 1e-4
+    c = np.bincount([orc.ticket_offset(11, 0, k, orc.PURPOSE_RESAMPLE, 0, 3) for k in range(1, K + 1)],
+                    minlength=3)
+    assert c.sum() == K and len(c) == 3
+    assert stats.chisquare(c).pvalue > 1e-4
 
 
 # ---------------------------------------------------------------- schedulers
