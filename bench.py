@@ -41,11 +41,18 @@ STEP_BYTES = 48
 # scaled to a launch by N; set to None whenever step_kernel changes
 STEP_TRAFFIC_PER_PARTICLE = (351.25e6 + 340.96e6) / 16e6
 # algorithmic FP32 flops per particle of the likelihood + propagation (an FMA
-# counts 2): bilinear form 2P^2, row combination 2P, sums of squares 4P, final
-# combination 6, propagation 10, with P = 2r + 1
+# counts 2), two counts:
+#  * the expanded form the kernel evaluates, l = I0 (B - I0 C / 2) / sigma_xi^2
+#    with B, C separable patch sums: bilinear form 2P^2, row combination 2P,
+#    sums of squares 4P, final combination 6, propagation 10, P = 2r + 1;
+#  * the per-pixel form: model FMA, residual, accumulating FMA = 5 flops per
+#    pixel over P^2 pixels (605 at r = 5)
 STEP_FLOPS = 2 * 11 * 11 + 2 * 11 + 4 * 11 + 6 + 10
-# FP32 peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (maximum SM clock)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+STEP_FLOPS_PER_PIXEL_FORM = 5 * 11 * 11
+# unit-count FP32 peak (152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz), used
+# only when the FMA-chain measurement cannot run
+FP32_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+TIMED_RUNS = 5
 
 
 # the scheme rows, in the order they run in one context: every row starts
@@ -54,14 +61,17 @@ SCHEME_ROWS = [("rpa_gs", 0.0), ("rpa_sgs", 0.0), ("rpa2_gs", 0.0), ("rpa2_sgs",
                ("arna", 0.5), ("systematic", 0.0), ("rpa_lgs", 0.0), ("rpa2_lgs", 0.0)]
 
 
-def workload_desc(n, scheme):
-    return {
+def workload_desc(n, scheme, target_n=None):
+    d = {
         "workload": f"spot512: {W}x{H} float32 Poisson frames, one Gaussian-PSF spot, N={n:,} particles, "
                     f"{2 * R + 1}x{2 * R + 1} patch, groups of {GROUP}, {scheme} resampling every frame",
         "N": n, "frame": f"{W}x{H}", "patch": 2 * R + 1, "group_size": GROUP, "scheme": scheme,
         "state": "6 x float32 SoA (x, y, vx, vy, I0, lw), double-buffered",
         "l2": "inputs larger than L2: 1.8 GB of particle state per frame (no flush needed)",
     }
+    if target_n is not None and target_n != n:
+        d["target_N"] = target_n
+    return d
 
 
 def make_workload(k_total, seed=0):
@@ -120,14 +130,57 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle legs
-def oracle_rate(params, frames, n, k, seed=0):
-    """The FP64 oracle as it stands (single thread) on n particles x k frames."""
+def cpu_model():
+    """The host CPU's model name (x86 'model name', else lscpu's 'Model name')."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_rate(params, frames, n, k, threads, seed=0):
+    """The FP64 oracle as it stands on n particles x k frames, with `threads`
+    OpenMP threads over particles (results do not depend on the count).
+    Returns (particle-steps/s, seconds, threads used)."""
     import oracle as orc
+    used = orc.set_threads(threads)
     m = orc.Model(**{**params, "seed": seed})
     t0 = time.perf_counter()
     rc, est, _ = orc.run(m, n, frames[:k], group_size=GROUP, scheme=orc.SYSTEMATIC)
     dt = time.perf_counter() - t0
-    return n * k / dt, dt
+    return n * k / dt, dt, used
+
+
+def cpu_baseline(params, frames, cn, ck):
+    """The oracle on the host cores: the spot512 workload (n particles x k
+    frames) on all cores, and the 128 x 128 workload in full (N = 16384,
+    20 frames, 9 x 9 patch) on one core and on all cores."""
+    import synth
+    allc = os.cpu_count() or 1
+    rate, dt, used = oracle_rate(params, frames, cn, ck, allc)
+    mv1 = synth.make_movie(W=128, H=128, K=20, sigma=1.5, amplitude=50.0, background=10.0, seed=0)
+    p1 = dict(width=128, height=128, patch_radius=4, psf_sigma=1.5, amplitude=50.0, background=10.0,
+              sigma_xi=math.sqrt(10.0), sigma_m=0.5, sigma_v=0.1, sigma_I=1.0, v0_max=1.0)
+    r1, d1, _ = oracle_rate(p1, mv1.frames, 16384, 20, 1)
+    rm, dm, um = oracle_rate(p1, mv1.frames, 16384, 20, allc)
+    return {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"FP64 C oracle, OpenMP over particles on {used} threads, {cn:,} particles x {ck} frames of "
+                      f"the same workload ({dt:.1f} s)",
+            "cpu_model": cpu_model(), "nproc": allc,
+            "spot128_full": {"workload": "128x128, 20 frames, N=16384, 9x9 patch, systematic",
+                             "single_thread": r1, "single_thread_s": d1, "all_cores": rm, "all_cores_s": dm,
+                             "threads": um}}
 
 
 def run_reference(args):
@@ -136,6 +189,7 @@ def run_reference(args):
         return 0
     import oracle as orc
     n = args.ref_n
+    used = orc.set_threads(os.cpu_count() or 1)
     mv, params = make_workload(args.warmup + args.steps + 1)
     m = orc.Model(**{**params, "seed": 0})
     st = orc.init(m, n)
@@ -165,12 +219,14 @@ def run_reference(args):
             times.append(time.perf_counter() - t0)
     total = sum(times)
     value = n * args.steps / total
-    sample = f"{n} particles of the same workload per step (one frame each), FP64, single thread"
+    sample = (f"{n:,} particles of the same workload per step (one frame each), FP64, OpenMP over particles on "
+              f"{used} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_desc(N_FULL, args.scheme),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": workload_desc(n, args.scheme, target_n=N_FULL),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -225,7 +281,7 @@ def run_ours(args):
     n = args.n
     K, Wm = args.steps, args.warmup
     extra = 0 if args.no_schemes else len(SCHEME_ROWS) * (args.scheme_steps + 2)
-    k_total = Wm + K + extra + (args.e2e_steps if not args.no_e2e else 0) + 2
+    k_total = Wm + TIMED_RUNS * K + extra + (args.e2e_steps if not args.no_e2e else 0) + 2
     mv, params = make_workload(k_total, seed=0)
     model = ppf.Model(**params, seed=rank, filter_id=rank)
     frames = torch.from_numpy(mv.frames).to(dev)
@@ -239,15 +295,26 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    pf.profile_enable(True, capacity=K + 8)
-    clocks = ClockSampler(torch.cuda.current_device())
-    t_ms = timed_frames(pf, frames, Wm + 1, K, scheme, args.alpha, stream)
-    torch.cuda.synchronize()
+    # TIMED_RUNS runs of exactly K frames each, on consecutive frames; each
+    # run is bracketed by a barrier and a synchronisation, its time is the
+    # slowest rank's, and the median run is reported
+    pf.profile_enable(True, capacity=TIMED_RUNS * K + 8)
+    clocks = ClockSampler(torch.cuda.current_device(), period_ms=50)
+    runs_ms = []
+    k0 = Wm + 1
+    for _ in range(TIMED_RUNS):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t = timed_frames(pf, frames, k0, K, scheme, args.alpha, stream)
+        torch.cuda.synchronize()
+        runs_ms.append(max_over_ranks(t, dist, dev))
+        k0 += K
     clk = clocks.stop()
-    t_ms = max_over_ranks(t_ms, dist, dev)
+    t_ms = statistics.median(runs_ms)
     prof = pf.profile_read()
     est = pf.estimate()
-    kdone = Wm + K
+    kdone = k0 - 1
     value = job_rate(n, K, world, t_ms)
 
     step_ms = prof["step_ms"] / max(1, prof["timed_steps"])
@@ -266,13 +333,34 @@ def run_ours(args):
                 "traffic_source": "ncu dram bytes at N=16M scaled by N (profiles/step_kernel_spot512_n16m.md)",
                 "phase_ms_per_step": {kk: prof[kk] / max(1, prof["timed_steps"]) for kk in
                                       ("prepare_ms", "step_ms", "finalize_ms", "resample_ms")}}
+    # FP32 peak: FMA chains on every SM (scalar and packed two-lane), timed
+    # with CUDA events, the SM clock sampled meanwhile
+    fp32 = {}
+    try:
+        pclk = ClockSampler(torch.cuda.current_device(), period_ms=50)
+        for name, packed in (("ffma", False), ("ffma2", True)):
+            tf, ms = ppf.fp32_peak(packed=packed, repeats=5)
+            fp32[name] = {"tflops": tf, "ms_per_launch": ms}
+        fp32["clocks"] = pclk.stop()
+        fp32_peak = max(fp32["ffma"]["tflops"], fp32["ffma2"]["tflops"])
+        peak_src = ("measured: FMA chains on every SM, best of the scalar and packed two-lane forms, CUDA events "
+                    "(ppf_fp32_peak)")
+    except Exception as e:  # noqa: BLE001 - the derived figure is reported with its source
+        fp32_peak = FP32_PEAK_DERIVED_TFLOPS
+        peak_src = f"derived (152 SMs x 128 lanes x 2 x 2.07 GHz); measurement failed: {e}"
     tflops = STEP_FLOPS * n / (step_ms / 1e3) / 1e12
-    roofline_alu = {"bound": "alu", "kernel": "step_kernel<5>", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS, "flops_per_particle": STEP_FLOPS,
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    tflops_px = STEP_FLOPS_PER_PIXEL_FORM * n / (step_ms / 1e3) / 1e12
+    roofline_alu = {"bound": "alu", "kernel": "step_kernel<5>", "achieved": tflops, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": tflops / fp32_peak, "flops_per_particle": STEP_FLOPS,
+                    "per_pixel_form": {"flops_per_particle": STEP_FLOPS_PER_PIXEL_FORM, "achieved": tflops_px,
+                                       "frac": tflops_px / fp32_peak},
+                    "peak_source": peak_src, "fp32_measured": fp32,
+                    "peak_derived": FP32_PEAK_DERIVED_TFLOPS}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
-            "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": t_ms / K, "timing": f"median of {TIMED_RUNS} runs of {K} frames (CUDA events)",
+            "runs_ms_per_step": [r / K for r in runs_ms],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded Poisson spot movie, random-init particles)",
             "config": workload_desc(n, args.scheme), "roofline": roofline, "roofline_alu": roofline_alu,
             "clocks": clk,
@@ -441,7 +529,8 @@ def run_ours(args):
                                          "(non-integer counts, so BF16/FP16 storage rounds them)",
                              "frames": args.precision_frames, **prec,
                              "note": "integer photon counts <= 256 are exact in BF16 (<= 2048 in FP16): on the "
-                                     "unscaled movie the reduced-precision paths reproduce FP32 bit for bit"}
+                                     "unscaled movie the reduced-precision paths reproduce FP32 bit for bit",
+                             "vs_fp64_oracle": "per frame, N=2^20 and 38M, five seeds: tests/test_gpu_precision.py"}
 
     # gradient of the log marginal likelihood: N = 2^20, 50 frames of 256^2
     if not args.no_grad:
@@ -473,11 +562,7 @@ def run_ours(args):
         gpf.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cn, ck = args.cpu_n, args.cpu_frames
-        rate, dt = oracle_rate(params, mv.frames, cn, ck)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"FP64 C oracle, single thread, {cn} particles x {ck} frames of the "
-                                          f"same workload ({dt:.1f} s)"}
+        line["cpu_baseline"] = cpu_baseline(params, mv.frames, args.cpu_n, args.cpu_frames)
     pf.close()
     if rank == 0:
         print(json.dumps(line))
@@ -489,7 +574,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_FULL)
@@ -499,9 +584,9 @@ def main():
     ap.add_argument("--alpha", type=float, default=0.1)
     ap.add_argument("--scheme-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=100)
-    ap.add_argument("--cpu-n", type=int, default=1 << 22)
-    ap.add_argument("--cpu-frames", type=int, default=3)
-    ap.add_argument("--ref-n", type=int, default=1 << 17)
+    ap.add_argument("--cpu-n", type=int, default=N_FULL)
+    ap.add_argument("--cpu-frames", type=int, default=2)
+    ap.add_argument("--ref-n", type=int, default=1 << 21)
     ap.add_argument("--no-schemes", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

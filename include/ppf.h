@@ -348,6 +348,20 @@ ppf_status ppf_profile_enable(ppf_ctx *ctx, int enable, int32_t capacity);
 /* Synchronises the stream and sums the recorded event pairs. */
 ppf_status ppf_profile_read(ppf_ctx *ctx, ppf_profile_t *out);
 
+/* Measurement hook, not part of the method: the FP32 fused multiply-add
+ * throughput of the current device, the peak the likelihood's ALU roofline
+ * is taken against.  Every thread runs eight independent FMA chains
+ * (packed != 0: four chains of packed two-lane FMAs) over a grid of eight
+ * 256-thread blocks per SM; an FMA counts two flops.  One warm-up launch,
+ * then `repeats` timed launches (CUDA events on the legacy default stream);
+ * the fastest is reported.  Synchronous; allocates and frees a small output
+ * buffer.
+ *   tflops_out  host: the best rate in TFLOP/s.
+ *   ms_out      host, optional: that launch's duration.
+ * Errors: PPF_EINVAL (NULL tflops_out, repeats outside 1..100), PPF_ENOMEM,
+ * PPF_ECUDA. */
+ppf_status ppf_fp32_peak(int32_t packed, int32_t repeats, double *tflops_out, double *ms_out);
+
 /* Systematic resampling of n device log-weights with no device allocation.
  * (A library addition for callers that cannot allocate; the paper has no
  * counterpart.)  Some callers cannot call cudaMalloc: serving or real-time
@@ -365,8 +379,9 @@ ppf_status ppf_profile_read(ppf_ctx *ctx, ppf_profile_t *out);
  *   cuda_stream stream to enqueue on (NULL = legacy default stream).
  * The scratch array (about 113 KB) lives on every device that loads the
  * library until the process exits.  The first call on a device looks up its
- * address (once per device, with that device current); make that first call
- * before any stream capture.  Every call shares the array and it keeps the
+ * address (with that device current), and so does the first call after the
+ * device's context changed (a cudaDeviceReset); make those calls before any
+ * stream capture.  Every call shares the array and it keeps the
  * last call's contents (each call clears what must start at zero): calls
  * whose work overlaps on the GPU race and must be serialised by the caller.
  * Errors: PPF_EINVAL (NULL pointers, n out of range, frame < 0), PPF_ECUDA. */

@@ -1023,10 +1023,10 @@ int orc_grad_run(const orc_model *m0, int64_t N, int32_t K, const double *frames
             memcpy(anc_io + (int64_t)k * N, anc, sizeof(int32_t) * (size_t)N);
         orc_propagate(&m, N, k + 1, cur, anc, zero, nxt);
         const double *fr = frames + (int64_t)k * npix;
-        double M = -INFINITY;
+        int32_t *an = anchor_io + (int64_t)k * 2 * N;
+#pragma omp parallel for schedule(dynamic, 4096)
         for (int64_t i = 0; i < N; ++i) {
             int32_t ax = INT32_MIN, ay = INT32_MIN;
-            int32_t *an = anchor_io + (int64_t)k * 2 * N;
             if (replay) {
                 ax = an[i];
                 ay = an[N + i];
@@ -1037,15 +1037,21 @@ int orc_grad_run(const orc_model *m0, int64_t N, int32_t K, const double *frames
                 an[N + i] = (int32_t)floor(nxt[N + i] + 0.5);
             }
             nxt[5 * N + i] = part[6 * i];
+        }
+        double M = -INFINITY;
+        for (int64_t i = 0; i < N; ++i)
             if (part[6 * i] > M)
                 M = part[6 * i];
-        }
+        /* the exponentials in parallel, the sums serially in particle order */
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < N; ++i)
+            lam2[i] = exp(nxt[5 * N + i] - M);
         double tot = 0.0;
         for (int64_t i = 0; i < N; ++i)
-            tot += exp(nxt[5 * N + i] - M);
+            tot += lam2[i];
         L += M + log(tot) - log((double)N);
         for (int64_t i = 0; i < N; ++i) {
-            const double w = exp(nxt[5 * N + i] - M) / tot;
+            const double w = lam2[i] / tot;
             gd[0] += w * part[6 * i + 1];
             gd[1] += w * part[6 * i + 2];
             gd[2] += w * part[6 * i + 3];
@@ -1081,11 +1087,16 @@ int orc_grad_run(const orc_model *m0, int64_t N, int32_t K, const double *frames
                 mu2[a[c]] += mu[c];
             }
         }
+        /* the normals in parallel, the sum serially in particle order */
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < N; ++i) {
             double e[5];
             orc_normals5(m.seed, (uint32_t)i, (uint32_t)(k + 1), m.filter_id, e);
-            gsm += lam2[i] * e[0] + mu2[i] * e[1];  /* dx/dsigma_m = e1, dy/dsigma_m = e2 */
+            part[2 * i] = e[0];
+            part[2 * i + 1] = e[1];
         }
+        for (int64_t i = 0; i < N; ++i)
+            gsm += lam2[i] * part[2 * i] + mu2[i] * part[2 * i + 1];  /* dx/dsigma_m = e1, dy/dsigma_m = e2 */
         double *t = lam; lam = lam2; lam2 = t;
         t = mu; mu = mu2; mu2 = t;
     }

@@ -26,6 +26,7 @@ from ._binding import (  # noqa: F401
     SYSTEMATIC,
     BatchFilter,
     Estimate,
+    fp32_peak,
     Model,
     ParticleFilter,
     PPFError,

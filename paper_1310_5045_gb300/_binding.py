@@ -187,6 +187,7 @@ def load(build_if_missing: bool = True):
             "ppf_batch_autotune": (C.c_int, [vp, vp, C.c_int32, P(C.c_int32)]),
             "ppf_batch_set_ess_threshold": (C.c_int, [vp, C.c_double]),
             "ppf_batch_last_error": (C.c_char_p, [vp]),
+            "ppf_fp32_peak": (C.c_int, [C.c_int32, C.c_int32, P(C.c_double), P(C.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -213,6 +214,16 @@ def systematic_resample_noalloc(lw, seed: int, filter_id: int, frame: int, out=N
     if rc != OK:
         raise PPFError(rc, f"ppf_systematic_resample_noalloc: {status_string(rc)}")
     return out
+
+
+def fp32_peak(packed: bool = False, repeats: int = 5):
+    """``ppf_fp32_peak``: the measured FP32 FMA rate of the current device in
+    TFLOP/s (packed: two-lane FMAs) and the fastest launch's duration in ms."""
+    tf, ms = C.c_double(), C.c_double()
+    rc = load().ppf_fp32_peak(1 if packed else 0, int(repeats), C.byref(tf), C.byref(ms))
+    if rc != OK:
+        raise PPFError(rc, f"ppf_fp32_peak: {status_string(rc)}")
+    return tf.value, ms.value
 
 
 def status_string(s: int) -> str:

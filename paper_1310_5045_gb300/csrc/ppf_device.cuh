@@ -283,7 +283,8 @@ __device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v)
 }
 
 // exclusive scan over the block (blockDim.x a multiple of 32, <= 1024);
-// smem: 32 u64.  Returns the exclusive prefix; *total gets the block sum.
+// smem: 33 u64 (32 warp prefixes and the block total).  Returns the
+// exclusive prefix; *total gets the block sum.
 __device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t v, uint64_t *smem, uint64_t *total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;

@@ -18,6 +18,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "ppf_device.cuh"
 #include "ppf_internal.h"
 #include "ppf_tiles.cuh"
@@ -117,9 +119,41 @@ __global__ void noalloc_identity_if_degenerate(int32_t *__restrict__ anc, int64_
         anc[i] = (int32_t)i;
 }
 
-// device address of g_scratch, looked up once per device with that device current
+// The unique id of the calling thread's current CUDA context (cuCtxGetId,
+// reached through the runtime's driver entry points, so the library does
+// not link the driver library).  0 when it cannot be had.
+unsigned long long current_context_id()
+{
+    typedef CUresult (*GetCurrent)(CUcontext *);
+    typedef CUresult (*GetId)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f = nullptr, *g = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(f);
+            get_id = reinterpret_cast<GetId>(g);
+        }
+        looked_up = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of g_scratch, looked up with the device current: once per
+// device and CUDA context.  A reset device (cudaDeviceReset) gets a new
+// context, and with it a new lookup and the fill kernel's attribute set again.
 std::mutex g_mu;
 unsigned char *g_addr[128] = {};
+unsigned long long g_ctx[128] = {};
 
 unsigned char *scratch_address(int dev, cudaError_t *err)
 {
@@ -128,7 +162,10 @@ unsigned char *scratch_address(int dev, cudaError_t *err)
         *err = cudaErrorInvalidDevice;
         return nullptr;
     }
-    if (!g_addr[dev]) {
+    // (no context current yet on this thread: id 0, and the lookup below
+    // makes the device's primary context current)
+    const unsigned long long ctx = current_context_id();
+    if (!g_addr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
         void *p = nullptr;
         *err = cudaGetSymbolAddress(&p, g_scratch);
         if (*err != cudaSuccess)
@@ -138,6 +175,7 @@ unsigned char *scratch_address(int dev, cudaError_t *err)
         if (*err != cudaSuccess)
             return nullptr;
         g_addr[dev] = static_cast<unsigned char *>(p);
+        g_ctx[dev] = current_context_id();
     }
     *err = cudaSuccess;
     return g_addr[dev];

@@ -13,12 +13,18 @@ Readings used here (all data-side only):
     "SNR 2 (6 dB)" in Sec. 7.3), so I0 solves I0^2 = SNR^2 (I0 + I_bg).
   * Frames are float32 photon counts.  Reduced-precision copies are made by the
     caller (counts <= 256 are exact in bf16, <= 2048 in fp16).
+  * Streams: the seed's SeedSequence spawns one stream for the trajectory and
+    one for the Poisson noise (in a batch, one pair per filter), each drawn
+    frame after frame, so frame k is the same whatever the number of frames
+    generated.
 """
 
 from __future__ import annotations
 
+import concurrent.futures
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -107,16 +113,19 @@ def make_movie(
     seed: int = 0,
     noise: bool = True,
 ) -> Movie:
-    """One spot moving through K frames of W x H Poisson noise."""
-    rng = np.random.Generator(np.random.PCG64(seed))
+    """One spot moving through K frames of W x H Poisson noise.  Frame k
+    depends on the seed and k only, not on K."""
+    traj_ss, noise_ss = np.random.SeedSequence(seed).spawn(2)
+    rng = np.random.Generator(np.random.PCG64(traj_ss))
     lo = (start_frac[0] * W, start_frac[0] * H)
     hi = (start_frac[1] * W, start_frac[1] * H)
     margin = min(8.0, 0.1 * min(W, H))
     truth = _trajectory(rng, K, W, H, lo, hi, v0, sigma_m, sigma_v, amplitude, margin)
     frames = np.empty((K, H, W), dtype=np.float32)
+    nrng = np.random.Generator(np.random.PCG64(noise_ss))
     for k in range(K):
         mu = _render(W, H, truth[k, 0], truth[k, 1], amplitude, background, sigma)
-        frames[k] = rng.poisson(mu) if noise else mu
+        frames[k] = nrng.poisson(mu) if noise else mu
     return Movie(frames, truth, sigma, amplitude, background, sigma_m, sigma_v, seed)
 
 
@@ -145,8 +154,10 @@ def make_movie_batch(
     seed: int = 0,
 ) -> MovieBatch:
     """F independent single-spot movies with uneven particle counts
-    N_f = floor(exp(U[ln n_lo, ln n_hi]))."""
-    rng = np.random.Generator(np.random.PCG64(seed))
+    N_f = floor(exp(U[ln n_lo, ln n_hi])).  Filter f's frame k depends on the
+    seed, f and k only, not on K."""
+    par_ss, filt_ss = np.random.SeedSequence(seed).spawn(2)
+    rng = np.random.Generator(np.random.PCG64(par_ss))
     sig = rng.uniform(*sigma_range, size=F)
     snr = rng.uniform(*snr_range, size=F)
     amp = np.array([amplitude_for_snr(s, background) for s in snr])
@@ -157,14 +168,24 @@ def make_movie_batch(
     px = np.arange(W, dtype=np.float64)
     py = np.arange(H, dtype=np.float64)
     margin = min(8.0, 0.1 * min(W, H))
-    for f in range(F):
-        truth[f] = _trajectory(rng, K, W, H, (0.25 * W, 0.25 * H), (0.75 * W, 0.75 * H),
-                               1.0, sigma_m, sigma_v, amp[f], margin)
+    noise = []
+    for f, fss in enumerate(filt_ss.spawn(F)):
+        traj_ss, noise_ss = fss.spawn(2)
+        truth[f] = _trajectory(np.random.Generator(np.random.PCG64(traj_ss)), K, W, H, (0.25 * W, 0.25 * H),
+                               (0.75 * W, 0.75 * H), 1.0, sigma_m, sigma_v, amp[f], margin)
+        noise.append(noise_ss)
+
+    def draw(f):
         s2 = 2.0 * sig[f] * sig[f]
         gx = np.exp(-((px[None, :] - truth[f, :, 0:1]) ** 2) / s2)   # (K, W)
         gy = np.exp(-((py[None, :] - truth[f, :, 1:2]) ** 2) / s2)   # (K, H)
         mu = background + amp[f] * gy[:, :, None] * gx[:, None, :]
-        frames[:, f] = rng.poisson(mu)
+        # one call draws the frames in order, frame 0 first
+        frames[:, f] = np.random.Generator(np.random.PCG64(noise[f])).poisson(mu)
+
+    # every filter has its own stream, so the draws may run on several threads
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(draw, range(F)))
     return MovieBatch(frames, truth, sig, amp, background, n, seed)
 
 

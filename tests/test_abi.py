@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared():
     hdr = open(os.path.join(ROOT, "include", "ppf.h")).read()
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    return sorted(set(re.findall(r"\b(ppf_[a-z_]+)\s*\(", hdr)))
+    return sorted(set(re.findall(r"\b(ppf_[a-z0-9_]+)\s*\(", hdr)))
 
 
 @pytest.fixture(scope="module")

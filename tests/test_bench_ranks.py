@@ -82,4 +82,7 @@ def test_reference_arm_prints_one_json_line(monkeypatch, capsys, scheme):
     assert d["unit"] == "particle-steps/s" and d["higher_is_better"] is True and d["n_gpus"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["config"]["scheme"] == scheme and d["config"]["N"] == 38_000_000
+    # the config names the size the oracle was timed on, and the benchmark's size beside it
+    assert d["config"]["scheme"] == scheme and d["config"]["N"] == 4096
+    assert d["config"]["target_N"] == 38_000_000
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["cpu_model"]

@@ -195,3 +195,77 @@ def test_step_api_matches_run(ppf):
         a.resample(3)  # no step since the last resample
     a.close()
     b.close()
+
+
+def test_batch_full_size_sampled_filters(ppf):
+    """The batched workload in full, in the benchmark's launch configuration:
+    4096 filters, N_f log-uniform in [256, 65536] (about 49 M particles in
+    all), 64 x 64 frames, 11 x 11 patch, 30 frames, the launch shape
+    autotuned on the third frame.  Every frame, a sample of filters (the
+    largest, the smallest and ten drawn at random) is checked against the
+    oracle in lockstep: propagation, likelihood, estimate and log-evidence
+    within gpu_common's tolerances, ancestors bit-exact."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < 8 * 2**30:
+        pytest.skip("needs ~8 GB of free device memory")
+    from gpu_common import MEAN_RTOL, LOGEV_RTOL, f32, loglik_tol
+    F, K, Wd = 4096, 30, 64
+    mb = synth.make_movie_batch(F=F, W=Wd, H=Wd, K=K, n_range=(256, 65536), seed=0)
+    gms, oms = [], []
+    for f in range(F):
+        kw = dict(width=Wd, height=Wd, patch_radius=5, psf_sigma=f32(mb.sigma[f]), amplitude=f32(mb.amplitude[f]),
+                  background=10.0, sigma_xi=f32(math.sqrt(10.0)), sigma_m=0.5, sigma_v=0.1, sigma_I=1.0,
+                  v0_max=1.0, seed=0, filter_id=f)
+        gms.append(ppf.Model(**kw))
+        oms.append(orc.Model(**kw))
+    frames = torch.from_numpy(np.ascontiguousarray(mb.frames)).cuda()
+    ns = mb.n_particles
+    bf = ppf.BatchFilter(gms, ns)
+    off = bf.offsets
+    assert off[-1] == int(ns.sum()) > 40_000_000
+    rng = np.random.default_rng(5)
+    orc.set_threads(0)
+    for k in range(1, K + 1):
+        if k == 3:
+            bf.autotune(frames[2], 3)
+        pick = np.unique(np.concatenate([[int(np.argmax(ns)), int(np.argmin(ns))], rng.choice(F, 10, replace=False)]))
+        st0, anc0 = bf.get_particles(state=True, anc=(k > 1))
+        sl0 = {f: st0[:, off[f]:off[f + 1]].double().cpu().numpy() for f in pick}
+        a0 = {f: (anc0[off[f]:off[f + 1]].cpu().numpy() - off[f]) if anc0 is not None
+              else np.arange(off[f + 1] - off[f], dtype=np.int32) for f in pick}
+        del st0, anc0
+        bf.step(frames[k - 1], k)
+        est = bf.estimates()
+        st1, _ = bf.get_particles()
+        sl1 = {f: st1[:, off[f]:off[f + 1]].double().cpu().numpy() for f in pick}
+        lwf = {f: st1[5, off[f]:off[f + 1]].cpu().numpy() for f in pick}
+        del st1
+        bf.resample(k)
+        _, anc1 = bf.get_particles(state=False, anc=True)
+        a1 = {f: anc1[off[f]:off[f + 1]].cpu().numpy() - off[f] for f in pick}
+        del anc1
+        for f in pick:
+            n = off[f + 1] - off[f]
+            par, S, om = sl0[f], sl1[f], oms[f]
+            lp = np.zeros(n) if k > 1 else par[5][a0[f]]
+            ref = orc.propagate(om, k, par, a0[f], lp)
+            pp = par[:, a0[f]]
+            scale = np.abs(pp[:5]).copy()
+            scale[0] += np.abs(pp[2])
+            scale[1] += np.abs(pp[3])
+            sig = np.array([0.5, 0.5, f32(0.1), f32(0.1), 1.0])[:, None]
+            assert np.all(np.abs(S[:5] - ref[:5]) <= 2e-6 * (scale + 6 * sig + 1.0)), (k, f)
+            l_ref = orc.loglik_many(om, mb.frames[k - 1, f].astype(np.float64), S[0], S[1], S[4])
+            lw_ref = lp + l_ref
+            tol = loglik_tol(l_ref, S[4], 5, om.sigma_xi) + 4 * np.spacing(np.abs(lw_ref).astype(np.float32))
+            assert np.all(np.abs(S[5] - lw_ref) <= tol), (k, f)
+            so_st = S.copy()
+            so_st[5] = lw_ref
+            so = orc.summary(so_st, lp)
+            sc = np.array([Wd, Wd, 1.0, 1.0, om.amplitude])
+            assert np.all(np.abs(est[f]["mean"] - so["mean"]) <= MEAN_RTOL * np.maximum(np.abs(so["mean"]), sc)), (k, f)
+            assert abs(est[f]["log_evidence"] - so["log_evidence"]) <= LOGEV_RTOL * max(1.0, abs(so["log_evidence"]))
+            rc, want, _, _, _ = orc.resample(om, orc.SYSTEMATIC, n, k, np.array([0, n]), lwf[f])
+            assert rc == 0 and np.array_equal(a1[f], want), (k, f)
+    bf.close()

@@ -9,6 +9,7 @@ float32 per-particle derivatives and must be within 1e-3 relative of the
 central differences (the target), plus 1e-3 of the largest derivative scale
 for components near zero."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -77,3 +78,41 @@ def test_gradient_is_deterministic_and_autograd(ppf):
     # after the gradient run the context holds weighted particles: resampling may follow
     pf.resample(ppf.SYSTEMATIC)
     pf.close()
+
+
+def test_gradient_full_size(ppf):
+    """The gradient workload in full, in the benchmark's launch configuration:
+    N = 2^20 particles, 50 frames of 256 x 256, 9 x 9 patch, I0 = A, groups of
+    4096.  The GPU's L and gradient against the oracle's reverse mode on the
+    whole replayed stop-gradient path, and against central differences
+    (eps = 1e-3 of each parameter) of the replayed objective."""
+    import torch
+    from gpu_common import paired_models
+    free, _ = torch.cuda.mem_get_info()
+    if free < 4 * 2**30:
+        pytest.skip("needs ~4 GB of free device memory")
+    orc.set_threads(os.cpu_count() or 1)
+    gmv, gp = synth.preset("spot256_k50", seed=1)
+    N = gp["N"]
+    gm, om = paired_models(ppf, width=256, height=256, patch_radius=4, psf_sigma=1.5, amplitude=50.0,
+                           background=10.0, sigma_m=0.5, sigma_v=0.1, sigma_I=0.0, seed=0)
+    fr = torch.from_numpy(gmv.frames).cuda()
+    pf = ppf.ParticleFilter(gm, N, group_size=4096)
+    theta = np.array([1.5, 50.0, 10.0, 0.5], dtype=np.float32).astype(np.float64)
+    L, g, anc, anchors = pf.loglik_grad(fr, theta, return_path=True)
+    a = anc.cpu().numpy()
+    an = anchors.cpu().numpy()
+    del anc, anchors
+    pf.close()
+    rc, Lo, go, _, _ = orc.grad_run(om, N, gmv.frames, theta, a, an)
+    assert rc == 0
+    assert L == pytest.approx(Lo, rel=1e-5)
+    scale = np.max(np.abs(go))
+    assert np.all(np.abs(g - go) <= 1e-4 * np.abs(go) + 1e-5 * scale), (g, go)
+    for c in range(4):
+        h = 1e-3 * theta[c]
+        tp, tm = theta.copy(), theta.copy()
+        tp[c] += h
+        tm[c] -= h
+        fd = (orc.grad_run(om, N, gmv.frames, tp, a, an)[1] - orc.grad_run(om, N, gmv.frames, tm, a, an)[1]) / (2 * h)
+        assert abs(g[c] - fd) <= 1e-3 * abs(fd) + 1e-5 * scale, (c, g[c], fd)

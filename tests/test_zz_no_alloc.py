@@ -66,3 +66,52 @@ def test_noalloc_degenerate_weights_give_identity():
     # one particle 148x heavier than the rest: every ticket lands on a live particle
     a = out.cpu().numpy()
     assert np.all(a >= 1000) and np.all(np.diff(a) >= 0)
+
+
+RESET_SCRIPT = r"""
+import ctypes as C, sys
+import numpy as np
+L = C.CDLL(sys.argv[1])
+L.ppf_systematic_resample_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_uint64, C.c_uint32, C.c_int32,
+                                              C.c_void_p, C.c_void_p]
+n = 70001
+rng = np.random.default_rng(3)
+lw = (rng.standard_normal(n) * 3.0).astype(np.float32)
+
+def once():
+    # device buffers from the CUDA runtime the library is linked with
+    d_lw, d_anc = C.c_void_p(), C.c_void_p()
+    assert L.cudaMalloc(C.byref(d_lw), C.c_size_t(4 * n)) == 0
+    assert L.cudaMalloc(C.byref(d_anc), C.c_size_t(4 * n)) == 0
+    assert L.cudaMemcpy(d_lw, lw.ctypes.data_as(C.c_void_p), C.c_size_t(4 * n), 1) == 0
+    assert L.ppf_systematic_resample_noalloc(d_lw, n, 9, 1, 5, d_anc, None) == 0
+    out = np.zeros(n, dtype=np.int32)
+    assert L.cudaMemcpy(out.ctypes.data_as(C.c_void_p), d_anc, C.c_size_t(4 * n), 2) == 0
+    L.cudaFree(d_lw)
+    L.cudaFree(d_anc)
+    return out
+
+a = once()
+assert L.cudaDeviceReset() == 0   # ends this process's context only
+b = once()                        # a new context: the scratch address is looked up again
+assert np.array_equal(a, b) and np.all(np.diff(a) >= 0)
+print("ok")
+"""
+
+
+def test_noalloc_after_device_reset():
+    """After cudaDeviceReset the device has a new context; the entry point
+    must look its scratch array up again rather than use the old address.
+    Run in a child process that uses the CUDA runtime directly (no torch), so
+    the reset touches no other test's state."""
+    import os
+    import subprocess
+    import sys
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1310_5045_gb300 as ppf
+    ppf.load()
+    p = subprocess.run([sys.executable, "-c", RESET_SCRIPT, ppf.lib_path()], capture_output=True, text=True,
+                       timeout=300, env=dict(os.environ, CUDA_VISIBLE_DEVICES=os.environ.get("CUDA_VISIBLE_DEVICES", "0")))
+    assert p.returncode == 0 and p.stdout.strip().endswith("ok"), p.stdout[-500:] + p.stderr[-2000:]
