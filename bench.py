@@ -265,6 +265,57 @@ def timed_frames(pf, frames, k0, K, scheme, alpha, stream):
     return ev0.elapsed_time(ev1)
 
 
+def spread_ab(ppf, params, rank, n, stream, args):
+    """Frame 1 (the prior draw, spread over the whole frame) on each
+    likelihood path, and an ARNA run through a movie whose spot vanishes for
+    ten frames (direct path forced against the automatic choice)."""
+    import torch
+    import synth
+    out = {"workload": f"spot512 at N={n:,}: frame 1 from the prior; and 5 frames, the spot gone for 10, 5 more "
+                       "(ARNA, maximum alpha 0.5)"}
+    mv, _ = make_workload(20, seed=0)
+    blank = synth.make_movie(W=W, H=H, K=20, sigma=1.5, amplitude=0.0, background=10.0, seed=99)
+    frames = torch.from_numpy(mv.frames).cuda()
+    lost = mv.frames.copy()
+    lost[5:15] = blank.frames[5:15]
+    lost = torch.from_numpy(lost).cuda()
+    model = ppf.Model(**params, seed=rank, filter_id=rank)
+    first = {}
+    for name, path in (("direct", ppf.PATH_DIRECT), ("binned", ppf.PATH_BINNED), ("auto", ppf.PATH_AUTO)):
+        pf = ppf.ParticleFilter(model, n, group_size=GROUP, stream=stream)
+        pf.set_likelihood_path(path)
+        torch.cuda.synchronize()
+        pf.profile_enable(True, capacity=4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pf.step(frames[0], 1)
+        e1.record(stream)
+        e1.synchronize()
+        pr = pf.profile_read()
+        first[name] = {"ms": e0.elapsed_time(e1), "step_ms": pr["step_ms"], "binned": pf.last_step_binned()}
+        pf.close()
+    out["frame1"] = first
+    lostrun = {}
+    for name, path in (("direct", ppf.PATH_DIRECT), ("auto", ppf.PATH_AUTO)):
+        pf = ppf.ParticleFilter(model, n, group_size=GROUP, stream=stream)
+        pf.set_likelihood_path(path)
+        ms, binned = [], []
+        for k in range(1, 21):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pf.step(lost[k - 1], k)
+            e1.record(stream)
+            pf.resample(ppf.ARNA, 0.5)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            binned.append(pf.last_step_binned())
+        lostrun[name] = {"step_ms_per_frame": ms, "binned": binned}
+        pf.close()
+    out["lost_object_arna"] = lostrun
+    out["timing"] = "CUDA events around ppf_step (frame preparation and every kernel of the step)"
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_1310_5045_gb300 as ppf
@@ -417,6 +468,12 @@ def run_ours(args):
                         "links": e.links, "moved": e.moved, "max_group": e.max_group, "min_group": e.min_group}
         line["schemes"] = sch
         kdone = k - 1
+
+    # the spread regime (Sec. 6.3's input-space decomposition): the prior draw
+    # of frame 1 covers the whole frame, and a lost object leaves the weights
+    # flat; each likelihood path on them
+    if not args.no_spread:
+        line["spread"] = spread_ab(ppf, params, rank, n, stream, args)
 
     # pcSIR (Sec. 6): the same workload with the piecewise constant likelihood
     # (one lookup per particle in the per-frame map of cell-centre patch sums)
@@ -593,6 +650,7 @@ def main():
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-pcsir", action="store_true")
+    ap.add_argument("--no-spread", action="store_true")
     ap.add_argument("--batch-filters", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true", help="batched stage: keep the default launch shape")

@@ -123,7 +123,9 @@ typedef struct ppf_ctx ppf_ctx;
  *   cuda_stream cudaStream_t to enqueue on (NULL = legacy default stream).
  *   out         receives the context; untouched on error.
  * Errors: PPF_EINVAL (sizes, radius > 8, non-positive sigma_PSF / sigma_xi,
- * unknown dtype), PPF_ENOMEM, PPF_ECUDA. */
+ * unknown dtype), PPF_ENOMEM, PPF_ECUDA.  No context exists after an error,
+ * so there is no ppf_last_error text; with the environment variable
+ * PPF_VERBOSE set, the failing step is printed to stderr. */
 ppf_status ppf_create(const ppf_model *model, int64_t n, int32_t group_size,
                       void *cuda_stream, ppf_ctx **out);
 
@@ -347,6 +349,33 @@ ppf_status ppf_profile_enable(ppf_ctx *ctx, int enable, int32_t capacity);
 
 /* Synchronises the stream and sums the recorded event pairs. */
 ppf_status ppf_profile_read(ppf_ctx *ctx, ppf_profile_t *out);
+
+/* The likelihood path of the steps (Sec. 6.3, input-space decomposition).
+ * Both paths compute the same step and give the same results bit for bit;
+ * they differ in how the patch of eq. 4 is read:
+ *   PPF_PATH_DIRECT  one fused kernel; each particle reads its patch from the
+ *                    prepared frame through the L1 cache.  Fastest when the
+ *                    particles of neighbouring slots lie close together (after
+ *                    resampling from a concentrated posterior).
+ *   PPF_PATH_BINNED  the particles are binned by image tile (T x T patch
+ *                    anchors, T = 16 up to 512 x 512 frames), each tile's
+ *                    window (tile plus patch halo) is copied once into shared
+ *                    memory by the tensor-memory accelerator, and every patch
+ *                    is read from there.  Fastest when the particles are
+ *                    spread over the frame (the prior draw, a lost object).
+ *   PPF_PATH_AUTO    (the default) each step's path is chosen on the device
+ *                    from the previous step: binned when more than a quarter
+ *                    of its warps held particles whose patch anchors spanned
+ *                    more than 64 pixels.  The first step after ppf_create or
+ *                    ppf_set_particles is binned.
+ * Errors: PPF_EINVAL (path out of range; PPF_PATH_BINNED for a pcSIR context
+ * or a frame whose tiles would exceed 3072). */
+enum { PPF_PATH_AUTO = 0, PPF_PATH_DIRECT = 1, PPF_PATH_BINNED = 2 };
+ppf_status ppf_set_likelihood_path(ppf_ctx *ctx, int32_t path);
+
+/* Whether the last step took the binned path (1) or the direct one (0).
+ * Synchronises the context's stream. */
+ppf_status ppf_get_likelihood_path(ppf_ctx *ctx, int32_t *last_step_binned);
 
 /* Measurement hook, not part of the method: the FP32 fused multiply-add
  * throughput of the current device, the peak the likelihood's ALU roofline

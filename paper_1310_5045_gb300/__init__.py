@@ -15,6 +15,9 @@ from ._binding import (  # noqa: F401
     F16,
     F32,
     OK,
+    PATH_AUTO,
+    PATH_BINNED,
+    PATH_DIRECT,
     RNA,
     RPA_GS,
     RPA_LGS,

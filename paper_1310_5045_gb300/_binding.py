@@ -18,6 +18,7 @@ SYSTEMATIC, RPA_GS, RPA_SGS, RPA_LGS, RNA = 0, 1, 2, 3, 4
 RPA2_GS, RPA2_SGS, RPA2_LGS = 5, 6, 7  # two-stage proportional allocation
 ARNA = 8  # adaptive RNA: exchange ratio from the involved groups, ring redrawn when the object is lost
 F32, BF16, F16 = 0, 1, 2
+PATH_AUTO, PATH_DIRECT, PATH_BINNED = 0, 1, 2  # likelihood path (ppf_set_likelihood_path)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEGENERATE, ESTATE = range(7)
 SCHEMES = {"systematic": SYSTEMATIC, "rpa_gs": RPA_GS, "rpa_sgs": RPA_SGS, "rpa_lgs": RPA_LGS, "rna": RNA,
            "rpa2_gs": RPA2_GS, "rpa2_sgs": RPA2_SGS, "rpa2_lgs": RPA2_LGS, "arna": ARNA}
@@ -188,6 +189,8 @@ def load(build_if_missing: bool = True):
             "ppf_batch_set_ess_threshold": (C.c_int, [vp, C.c_double]),
             "ppf_batch_last_error": (C.c_char_p, [vp]),
             "ppf_fp32_peak": (C.c_int, [C.c_int32, C.c_int32, P(C.c_double), P(C.c_double)]),
+            "ppf_set_likelihood_path": (C.c_int, [ctxp, C.c_int32]),
+            "ppf_get_likelihood_path": (C.c_int, [ctxp, P(C.c_int32)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -372,6 +375,17 @@ class ParticleFilter:
         import numpy as np
         r = np.ascontiguousarray(ring, dtype=np.int32)
         self._check(self.L.ppf_set_ring(self._ctx, C.c_void_p(r.ctypes.data)), "ppf_set_ring")
+
+    def set_likelihood_path(self, path: int):
+        """``ppf_set_likelihood_path``: PATH_AUTO (chosen per step on the device),
+        PATH_DIRECT or PATH_BINNED; both paths give the same results."""
+        self._check(self.L.ppf_set_likelihood_path(self._ctx, int(path)), "ppf_set_likelihood_path")
+
+    def last_step_binned(self) -> bool:
+        """``ppf_get_likelihood_path``: whether the last step took the binned path."""
+        v = C.c_int32()
+        self._check(self.L.ppf_get_likelihood_path(self._ctx, C.byref(v)), "ppf_get_likelihood_path")
+        return bool(v.value)
 
     def profile_enable(self, enable: bool = True, capacity: int = 4096):
         self._check(self.L.ppf_profile_enable(self._ctx, 1 if enable else 0, int(capacity)), "ppf_profile_enable")

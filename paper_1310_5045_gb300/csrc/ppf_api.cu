@@ -62,7 +62,7 @@ void free_all(ppf_ctx *c)
                     c->state[0], c->state[1], c->anc, c->anc_sys, c->lwp, c->goff, c->goff_new, c->ring, c->succ, c->Zp,
                     c->frame_buf[0], c->frame_buf[1], c->lmap, c->part, c->sum, c->est_dev, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sc.Cbl,
                     c->sc.Tg, c->sc.skey, c->sc.sval, c->sc.seg_tick, c->sc.seg_dst, c->sc.seg_len,
-                    c->sc.seg_chunk};
+                    c->sc.seg_chunk, c->bin_key, c->bin_l, c->bin_tot, c->bin_item, c->bin_rec};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -182,8 +182,9 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
     c->pad = 2 * m->patch_radius;
     // row pitch (in pixel pairs): the padded width plus one zero column (the
     // frame is held as pairs (Z(col), Z(col + 1)), so that the patch sum reads
-    // aligned pixel pairs)
-    c->Wp = m->width + 2 * c->pad + 1;
+    // aligned pixel pairs), rounded up to even so that a row is a multiple of
+    // 16 bytes (the tensor copies of the binned path need it)
+    c->Wp = (m->width + 2 * c->pad + 2) & ~1;
     c->Hp = m->height + 2 * c->pad;
     c->frame_bytes = (size_t)m->width * m->height * dtype_size(m->frame_dtype);
     c->mode = MODE_CARRY;
@@ -254,11 +255,16 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
         chk(identity_ring(c), "ring");
     if (st == PPF_OK)
         chk(ppf::resample_kernel_attributes(), "kernel attributes");
+    c->bin_force = -1;
+    if (st == PPF_OK)
+        chk(ppf::bin_setup(c), "binned likelihood path");
     if (st == PPF_OK)
         chk(ppf::launch_init(c), "init_kernel");
     if (st == PPF_OK)
         chk(ppf::launch_identity(c, c->anc), "identity");
     if (st != PPF_OK) {
+        if (getenv("PPF_VERBOSE"))
+            fprintf(stderr, "ppf_create: %s\n", c->err);
         free_all(c);
         delete c;
         return st;
@@ -464,7 +470,33 @@ ppf_status ppf_set_particles(ppf_ctx *c, const float *state_dev, const int32_t *
     const int32_t zero = 0;
     CK(cudaMemcpyAsync((char *)c->sum + offsetof(DevSummary, degenerate), &zero, sizeof(zero),
                        cudaMemcpyHostToDevice, c->stream));
+    // particles of unknown spread: the next step bins them (and measures)
+    CK(ppf::bin_set_next(c, 1));
     c->weighted = false;
+    return PPF_OK;
+}
+
+ppf_status ppf_set_likelihood_path(ppf_ctx *c, int32_t path)
+{
+    if (!c || path < PPF_PATH_AUTO || path > PPF_PATH_BINNED)
+        return PPF_EINVAL;
+    if (path == PPF_PATH_BINNED && !c->bin_key) {
+        set_err(c, "the binned likelihood path is not available for this context (pcSIR, or a frame too large)");
+        return PPF_EINVAL;
+    }
+    c->bin_force = path == PPF_PATH_AUTO ? -1 : (path == PPF_PATH_BINNED ? 1 : 0);
+    return PPF_OK;
+}
+
+ppf_status ppf_get_likelihood_path(ppf_ctx *c, int32_t *last_step_binned)
+{
+    if (!c || !last_step_binned)
+        return PPF_EINVAL;
+    int32_t v = 0;
+    CK(cudaMemcpyAsync(&v, (char *)c->sum + offsetof(DevSummary, bin_this), sizeof(v), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *last_step_binned = c->bin_key ? v : 0;
     return PPF_OK;
 }
 

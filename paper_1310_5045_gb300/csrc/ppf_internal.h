@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (the tensor map is encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 #include "ppf.h"  // include/ppf.h (the build passes -I include)
@@ -26,6 +27,7 @@ constexpr int COPY_CHUNK = 2048;    // slots per routing-copy work item
 constexpr int MAX_RADIUS = 8;
 constexpr int MAX_SCHED_GROUPS = 16384;
 constexpr int SCAN_SMEM_TILES = 16384;  // tile scan in shared memory up to this many tiles (N <= 67 M)
+constexpr int BIN_MAX_BINS = 3073;      // binned likelihood: at most this many bins (tiles + 1)
 
 // How the next step forms a slot's starting log-weight.
 enum StepMode : int {
@@ -72,6 +74,13 @@ struct DevSummary {
     uint32_t blocks_done;      // step kernel: blocks that published partials
     double grad_L;             // ppf_loglik_grad: running sum of log-evidences
     double grad_g[4];          // and of their derivatives
+    // likelihood path: bin_this is the path of the current step (set by the
+    // frame preparation from bin_next or the caller's choice); bin_next is
+    // decided by the step's finaliser from the warps it saw spread
+    int32_t bin_this, bin_next;
+    uint32_t spread_warps, total_warps;
+    uint32_t bin_blocks_done;  // binned path: scan blocks that finished
+    int32_t n_bin_items;       // binned path: likelihood work items of this step
 };
 
 struct Scratch {
@@ -125,6 +134,16 @@ struct ppf_ctx {
     ppf::DevSummary *sum_host;    // pinned mirror for ppf_estimate
     ppf_estimate_t *est_dev;      // device staging of ppf_estimate_async
     ppf::Scratch sc;
+    // binned likelihood path (input-space decomposition): tiles of bin_T
+    // anchors, bin_nbins bins (the last for particles with no patch sum)
+    int32_t bin_T, bin_nx, bin_nbins, bin_grid, bin_items_max;  // bin_grid: blocks of the binned likelihood
+    int bin_force;                // -1: chosen per step on the device; 0: direct path; 1: binned path
+    uint32_t *bin_key;            // [N] bin of every slot, then the place of its record in bin order
+    uint32_t *bin_tot;            // [nbins + 1] bin sizes, then their exclusive prefix (the scatter's cursors)
+    int32_t *bin_item;            // [3 x items_max] work items: bin, first record, count
+    float4 *bin_rec;              // [N] records in bin order: (x, y, I0, -)
+    float *bin_l;                 // [N] l of every record, in bin order
+    CUtensorMap bin_tmap;         // the prepared frame as a 2D float tensor for the window copies (64-byte aligned type)
     int mode;                     // StepMode of the next step
     bool stepped;                 // at least one step since create/set
     bool weighted;                // a step happened since the last resample
@@ -157,4 +176,8 @@ cudaError_t launch_fill_f32(ppf_ctx *c, float *dst, float v);
 cudaError_t launch_format_estimate(ppf_ctx *c);
 cudaError_t launch_cell_map(ppf_ctx *c);
 int step_grid(ppf_ctx *c);
+// binned likelihood path (ppf_binned.cu)
+cudaError_t bin_setup(ppf_ctx *c);                      // tile geometry, buffers and tensor map (at create)
+cudaError_t launch_binned(ppf_ctx *c);                  // scan, scatter and likelihood (exit early when not chosen)
+cudaError_t bin_set_next(ppf_ctx *c, int binned);       // the path of the next step in auto mode
 }  // namespace ppf

@@ -182,27 +182,30 @@ __device__ __forceinline__ bool patch_setup(const PatchGeom &a, float x, float y
 // over the pixel pairs; the scalar form (kept by the batched step, whose
 // warp-per-unit kernel ran slower with packed FMAs) performs the same
 // roundings in the same order, so both give the same bits.
-template <int R, bool PACKED>
-__device__ __forceinline__ float patch_sum(const PatchGeom &a, int cx, int cy, const float gx[2 * R + 1],
-                                           const float gy[2 * R + 1])
+//
+// patch_rows takes the first pair of the window's first row and the row pitch
+// (in pairs); SMEM reads a window staged in shared memory with plain loads,
+// otherwise the prepared frame through the read-only path.  Both forms do the
+// same arithmetic, so a particle's likelihood has the same bits either way.
+template <int R, bool PACKED, bool SMEM = false>
+__device__ __forceinline__ float patch_rows(const float2 *row, int pitch, const float gx[2 * R + 1],
+                                            const float gy[2 * R + 1])
 {
     constexpr int P = 2 * R + 1;
     constexpr int Q = P / 2;  // full column pairs; column P - 1 is the odd one out
-    // the window: P rows from cy - R, pairs from column cx - R up to 2Q + 1
-    // columns on (inside the padded frame by the anchor's range)
-    if (a.flags && !PPF_DCHECK(cy - R + a.pad >= 0 && cy + R + a.pad < a.Hp && cx - R + a.pad >= 0 &&
-                                   cx - R + a.pad + 2 * Q < a.Wp,
-                               a.flags, FLAG_INTERNAL))
-        return 0.0f;
-    const float2 *row = reinterpret_cast<const float2 *>(a.Zp) + (int64_t)(cy - R + a.pad) * a.Wp +
-                        (cx - R + a.pad);
+    auto ld = [](const float2 *q) -> float2 {
+        if constexpr (SMEM)
+            return *q;
+        else
+            return __ldg(q);
+    };
     float2 b = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int j = 0; j < P; ++j) {
         float2 r = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-            const float2 z = __ldg(row + 2 * k);
+            const float2 z = ld(row + 2 * k);
             if constexpr (PACKED) {
                 r = (k == 0) ? __fmul2_rn(make_float2(gx[0], gx[1]), z)
                              : __ffma2_rn(make_float2(gx[2 * k], gx[2 * k + 1]), z, r);
@@ -211,16 +214,32 @@ __device__ __forceinline__ float patch_sum(const PatchGeom &a, int cx, int cy, c
                 r.y = (k == 0) ? __fmul_rn(gx[1], z.y) : __fmaf_rn(gx[2 * k + 1], z.y, r.y);
             }
         }
-        r.x = __fmaf_rn(gx[P - 1], __ldg(row + 2 * Q).x, r.x);
+        r.x = __fmaf_rn(gx[P - 1], ld(row + 2 * Q).x, r.x);
         if constexpr (PACKED) {
             b = (j == 0) ? __fmul2_rn(make_float2(gy[0], gy[0]), r) : __ffma2_rn(make_float2(gy[j], gy[j]), r, b);
         } else {
             b.x = (j == 0) ? __fmul_rn(gy[0], r.x) : __fmaf_rn(gy[j], r.x, b.x);
             b.y = (j == 0) ? __fmul_rn(gy[0], r.y) : __fmaf_rn(gy[j], r.y, b.y);
         }
-        row += a.Wp;
+        row += pitch;
     }
     return __fadd_rn(b.x, b.y);
+}
+
+template <int R, bool PACKED>
+__device__ __forceinline__ float patch_sum(const PatchGeom &a, int cx, int cy, const float gx[2 * R + 1],
+                                           const float gy[2 * R + 1])
+{
+    constexpr int Q = R;  // (2R + 1) / 2 full column pairs
+    // the window: 2R + 1 rows from cy - R, pairs from column cx - R up to
+    // 2Q + 1 columns on (inside the padded frame by the anchor's range)
+    if (a.flags && !PPF_DCHECK(cy - R + a.pad >= 0 && cy + R + a.pad < a.Hp && cx - R + a.pad >= 0 &&
+                                   cx - R + a.pad + 2 * Q < a.Wp,
+                               a.flags, FLAG_INTERNAL))
+        return 0.0f;
+    const float2 *row = reinterpret_cast<const float2 *>(a.Zp) + (int64_t)(cy - R + a.pad) * a.Wp +
+                        (cx - R + a.pad);
+    return patch_rows<R, PACKED, false>(row, a.Wp, gx, gy);
 }
 
 template <int R, bool PACKED = true>
@@ -250,6 +269,124 @@ __device__ __forceinline__ float cell_loglik(const PatchGeom &a, const float2 *_
         return 0.0f;
     const float2 bc = __ldg(lmap + (int64_t)((int)cyf + R) * (a.W + 2 * R) + ((int)cxf + R));
     return I0 * fmaf(-0.5f * I0, bc.y, bc.x) * a.inv_sxi2;
+}
+
+// ------------------------------------------------------------ the finaliser
+// Cross-block totals in FP64 (the paper's global sum for normalisation):
+// estimate, N_eff, log-evidence, from n per-block partials.  Run by the last
+// block of the kernel that produced them.  It also decides which likelihood
+// path the next step takes (the binned path when more than a quarter of the
+// warps of this step saw their particles spread wider than BIN_SPREAD_PX)
+// and clears the counters of that decision.
+__device__ __forceinline__ void finalize_block(const Partial *part, int n, DevSummary *sum, int32_t frame)
+{
+    __shared__ float smf[32];
+    __shared__ double smd[32][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float m = -INFINITY, mp = -INFINITY;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        m = fmaxf(m, __ldcg(&part[b].m));
+        mp = fmaxf(mp, __ldcg(&part[b].mp));
+    }
+    m = warp_max(m);
+    if (lane == 0)
+        smf[warp] = m;
+    __syncthreads();
+    float M = -INFINITY;
+    for (int w = 0; w < nw; ++w)
+        M = fmaxf(M, smf[w]);
+    __syncthreads();
+    mp = warp_max(mp);
+    if (lane == 0)
+        smf[warp] = mp;
+    __syncthreads();
+    float Mp = -INFINITY;
+    for (int w = 0; w < nw; ++w)
+        Mp = fmaxf(Mp, smf[w]);
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // s0, s[5], s2, sp
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        const float qm = __ldcg(&part[b].m), qmp = __ldcg(&part[b].mp);
+        if (qm > -INFINITY) {
+            const double f = (double)expf(qm - M);  // scale factor to 1 ulp; sums in FP64
+            acc[0] += __ldcg(&part[b].s0) * f;
+            for (int c = 0; c < 5; ++c)
+                acc[1 + c] += __ldcg(&part[b].s[c]) * f;
+            acc[6] += __ldcg(&part[b].s2) * f * f;
+        }
+        if (qmp > -INFINITY)
+            acc[7] += __ldcg(&part[b].sp) * (double)expf(qmp - Mp);
+    }
+    for (int c = 0; c < 8; ++c)
+        acc[c] = warp_sum_d(acc[c]);
+    if (lane == 0)
+        for (int c = 0; c < 8; ++c)
+            smd[warp][c] = acc[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < nw; ++w)
+            for (int c = 0; c < 8; ++c)
+                t[c] += smd[w][c];
+        for (int c = 0; c < 5; ++c)
+            sum->mean[c] = t[1 + c] / t[0];
+        sum->ess = t[0] * t[0] / t[6];
+        sum->log_total = (double)M + log(t[0]);
+        sum->log_evidence = sum->log_total - ((double)Mp + log(t[7]));
+        sum->max_lw = (double)M;
+        sum->M = M;
+        sum->frame = frame;
+        if (!(t[0] > 0.0))
+            sum->flags |= FLAG_DEGENERATE;
+        const uint32_t spread = sum->spread_warps, total = sum->total_warps;
+        sum->bin_next = (4ull * spread > (uint64_t)total) ? 1 : 0;
+        sum->spread_warps = 0u;
+        sum->total_warps = 0u;
+    }
+}
+
+// ------------------------------------------------------- input-space bins
+// The binned likelihood path (Sec. 6.3's input-space decomposition): the
+// particles are binned by the image tile that holds their patch anchor, and
+// each tile's window (the tile plus the patch halo) is staged in shared
+// memory once for all the particles of its bin.  Anchors u = cx + R in
+// [0, W + 2R) and v = cy + R in [0, H + 2R) (the range with a nonempty
+// patch) are tiled by T x T; the last bin holds the particles that need no
+// patch sum (non-finite, or no pixel of the patch inside the image).
+struct BinGeom {
+    int T, nx, nbins;  // tile edge, tiles per row, bins (tiles + 1)
+};
+
+template <int R>
+__device__ __forceinline__ uint32_t bin_of(const BinGeom &g, int W, int H, float x, float y, float I0)
+{
+    if (!isfinite(x) || !isfinite(y) || !isfinite(I0))
+        return (uint32_t)(g.nbins - 1);
+    const float cxf = floorf(x + 0.5f), cyf = floorf(y + 0.5f);
+    if (cxf < -(float)R || cxf > (float)(W - 1 + R) || cyf < -(float)R || cyf > (float)(H - 1 + R))
+        return (uint32_t)(g.nbins - 1);
+    const int u = (int)cxf + R, v = (int)cyf + R;
+    return (uint32_t)((v / g.T) * g.nx + u / g.T);
+}
+
+// warps whose particles' anchors span more than this many pixels in x or y
+// count as spread (their patch reads touch a separate cache line per lane)
+constexpr int BIN_SPREAD_PX = 64;
+
+// Per warp: the extent of the anchors of the active lanes; one count per
+// warp into the block's counters (its first active lane).  Called on a sample
+// of the iterations (every eighth): the decision needs a fraction, not a census.
+__device__ __forceinline__ void spread_tally(float x, float y, bool active, unsigned &n_spread, unsigned &n_total)
+{
+    const bool fin = active && isfinite(x) && isfinite(y) && fabsf(x) < 1e9f && fabsf(y) < 1e9f;
+    const int cx = fin ? (int)floorf(x + 0.5f) : 0, cy = fin ? (int)floorf(y + 0.5f) : 0;
+    const unsigned m = __activemask();
+    const int lox = __reduce_min_sync(m, fin ? cx : INT32_MAX), hix = __reduce_max_sync(m, fin ? cx : INT32_MIN);
+    const int loy = __reduce_min_sync(m, fin ? cy : INT32_MAX), hiy = __reduce_max_sync(m, fin ? cy : INT32_MIN);
+    if ((threadIdx.x & 31) == (__ffs(m) - 1)) {
+        n_total += 1u;
+        if (lox <= hix && ((int64_t)hix - lox > BIN_SPREAD_PX || (int64_t)hiy - loy > BIN_SPREAD_PX))
+            n_spread += 1u;
+    }
 }
 
 }  // namespace ppf

@@ -45,8 +45,16 @@ __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(
 
 template <typename T>
 __global__ void prepare_frame_kernel(const T *__restrict__ Z, float *__restrict__ Zp, int W, int H, int Wp,
-                                     int Hp, int pad, float bg)
+                                     int Hp, int pad, float bg, DevSummary *sum, int force,
+                                     uint32_t *__restrict__ bin_tot, int nbins)
 {
+    // the likelihood path of this step: the caller's choice, else the one the
+    // previous step's finaliser decided; and the binned path's counts cleared
+    if (blockIdx.x == 0 && threadIdx.x == 0 && sum)
+        sum->bin_this = force >= 0 ? force : sum->bin_next;
+    if (bin_tot)
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= nbins; t += gridDim.x * blockDim.x)
+            bin_tot[t] = 0u;
     // pixel pairs: element (row, col) = (Zb(row, col), Zb(row, col + 1)) with
     // Zb = Z - bg inside the image and 0 in the border of `pad` (pitch Wp)
     const int n = Wp * Hp;
@@ -83,99 +91,80 @@ struct StepArgs {
     Partial *__restrict__ part;
     unsigned int *done;    // blocks finished (reset by the last one)
     DevSummary *sum;
+    // binned path: the bin of every slot (then its place in bin order), the
+    // bin sizes, and every record's l in bin order
+    uint32_t *__restrict__ bin_key;
+    uint32_t *__restrict__ bin_tot;
+    const float *__restrict__ bin_l;
+    BinGeom bg;
 };
 
-// --------------------------------------------------------------- finalise
-// Cross-block totals in FP64 (the paper's global sum for normalisation):
-// estimate, N_eff, log-evidence.  Run by the last block of the step.
-__device__ void finalize_block(const Partial *part, int n, DevSummary *sum, int32_t frame)
+// PC: pcSIR (cell map lookup) instead of the patch sum at the particle
+// The propagation of slot i (Sec. 7.1 NCV dynamics, bootstrap proposal):
+// parent p, its state, the starting log-weight, the five propagated values.
+struct Propagated {
+    float v[5];
+    float lwp;
+};
+
+__device__ __forceinline__ Propagated propagate_slot(const StepArgs &a, int mode, uint32_t i, uint32_t p)
 {
-    __shared__ float smf[32];
-    __shared__ double smd[32][8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float m = -INFINITY, mp = -INFINITY;
-    for (int b = threadIdx.x; b < n; b += blockDim.x) {
-        m = fmaxf(m, __ldcg(&part[b].m));
-        mp = fmaxf(mp, __ldcg(&part[b].mp));
-    }
-    m = warp_max(m);
-    if (lane == 0)
-        smf[warp] = m;
-    __syncthreads();
-    float M = -INFINITY;
-    for (int w = 0; w < nw; ++w)
-        M = fmaxf(M, smf[w]);
-    __syncthreads();
-    mp = warp_max(mp);
-    if (lane == 0)
-        smf[warp] = mp;
-    __syncthreads();
-    float Mp = -INFINITY;
-    for (int w = 0; w < nw; ++w)
-        Mp = fmaxf(Mp, smf[w]);
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // s0, s[5], s2, sp
-    for (int b = threadIdx.x; b < n; b += blockDim.x) {
-        const float qm = __ldcg(&part[b].m), qmp = __ldcg(&part[b].mp);
-        if (qm > -INFINITY) {
-            const double f = (double)expf(qm - M);  // scale factor to 1 ulp; sums in FP64
-            acc[0] += __ldcg(&part[b].s0) * f;
-            for (int c = 0; c < 5; ++c)
-                acc[1 + c] += __ldcg(&part[b].s[c]) * f;
-            acc[6] += __ldcg(&part[b].s2) * f * f;
-        }
-        if (qmp > -INFINITY)
-            acc[7] += __ldcg(&part[b].sp) * (double)expf(qmp - Mp);
-    }
-    for (int c = 0; c < 8; ++c)
-        acc[c] = warp_sum_d(acc[c]);
-    if (lane == 0)
-        for (int c = 0; c < 8; ++c)
-            smd[warp][c] = acc[c];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int w = 0; w < nw; ++w)
-            for (int c = 0; c < 8; ++c)
-                t[c] += smd[w][c];
-        for (int c = 0; c < 5; ++c)
-            sum->mean[c] = t[1 + c] / t[0];
-        sum->ess = t[0] * t[0] / t[6];
-        sum->log_total = (double)M + log(t[0]);
-        sum->log_evidence = sum->log_total - ((double)Mp + log(t[7]));
-        sum->max_lw = (double)M;
-        sum->M = M;
-        sum->frame = frame;
-        if (!(t[0] > 0.0))
-            sum->flags |= FLAG_DEGENERATE;
+    const float *__restrict__ src = a.src;
+    const int64_t n = a.N;
+    const float x = __ldg(src + p), y = __ldg(src + n + p);
+    const float vx = __ldg(src + 2 * n + p), vy = __ldg(src + 3 * n + p);
+    const float I0 = __ldg(src + 4 * n + p);
+    Propagated r;
+    if (mode == MODE_CARRY)
+        r.lwp = __ldg(src + 5 * n + p);
+    else if (mode == MODE_UNIFORM)
+        r.lwp = 0.0f;
+    else
+        r.lwp = __ldg(a.lwp + i);
+    uint32_t f[6];
+    prop_fields(philox_rk(make_uint4(i, a.frame, a.fid, PURPOSE_PROP << 8), a.rk), f);
+    float e0, e1, e2, e3, e4, e5;
+    box_muller(u21(f[0]), u21(f[1]), e0, e1);
+    box_muller(u21(f[2]), u21(f[3]), e2, e3);
+    box_muller(u21(f[4]), u21(f[5]), e4, e5);
+    r.v[0] = fmaf(a.sm, e0, x + vx);
+    r.v[1] = fmaf(a.sm, e1, y + vy);
+    r.v[2] = fmaf(a.sv, e2, vx);
+    r.v[3] = fmaf(a.sv, e3, vy);
+    r.v[4] = fmaf(a.sI, e4, I0);
+    return r;
+}
+
+// the warps' spread counts of this block into the step's counters
+__device__ __forceinline__ void publish_spread(DevSummary *sum, unsigned ns, unsigned nt)
+{
+    ns = __reduce_add_sync(0xffffffffu, ns);
+    nt = __reduce_add_sync(0xffffffffu, nt);
+    if ((threadIdx.x & 31) == 0 && nt) {
+        atomicAdd(&sum->spread_warps, ns);
+        atomicAdd(&sum->total_warps, nt);
     }
 }
 
-// PC: pcSIR (cell map lookup) instead of the patch sum at the particle
-template <int R, bool PC>
-__global__ void __launch_bounds__(256) step_kernel(StepArgs a)
+// The binned path's first pass: propagate every slot, write its state (the
+// log-weight plane is filled by the sums of phase 1), its bin, and count the
+// bin sizes (a shared-memory histogram per block, added to the global one).
+// Particles of one bin may land in any order: the likelihood of each does not
+// depend on it, and the sums are taken in slot order.
+template <int R>
+__device__ __forceinline__ void bin_propagate(const StepArgs &a, int mode)
 {
-    int mode = a.mode;
-    if (mode != MODE_CARRY && *a.degenerate)
-        mode = MODE_CARRY;  // the last resample kept every particle
-    const PatchGeom geom{a.Zp, a.W, a.H, a.Wp, a.pad, a.inv2s2, a.inv_sxi2, a.Kc, a.Hp, a.flags};
-    // N < 2^31: 32-bit slot indices into per-component planes
+    __shared__ uint32_t shist[BIN_MAX_BINS];
+    const int nb = a.bg.nbins;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x)
+        shist[t] = 0u;
+    __syncthreads();
     const int32_t N = (int32_t)a.N;
-    const float *__restrict__ sx = a.src, *__restrict__ sy = a.src + a.N, *__restrict__ svx = a.src + 2 * a.N;
-    const float *__restrict__ svy = a.src + 3 * a.N, *__restrict__ sI = a.src + 4 * a.N;
-    const float *__restrict__ slw = a.src + 5 * a.N;
-    float *__restrict__ dplane[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c)
-        dplane[c] = a.dst + c * a.N;
-    Acc acc;
-    acc.init();
-    // unsigned: i + stride stays below 2^32 for any N < 2^31.  The ancestor of
-    // the next slot is loaded one iteration ahead, so the parent-state gather
-    // does not wait on a dependent load.
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned ns = 0, nt = 0, it = 0;
     uint32_t pn = (i0 < (uint32_t)N) ? ((mode == MODE_CARRY) ? i0 : (uint32_t)__ldg(a.anc + i0)) : 0u;
-    for (uint32_t i = i0; i < (uint32_t)N; i += stride) {
+    for (uint32_t i = i0; i < (uint32_t)N; i += stride, ++it) {
         uint32_t p = pn;
         if (i + stride < (uint32_t)N)
             pn = (mode == MODE_CARRY) ? i + stride : (uint32_t)__ldg(a.anc + i + stride);
@@ -183,39 +172,134 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
             atomicOr(a.flags, FLAG_BAD_ANCESTOR);
             p = i;
         }
-        const float x = __ldg(sx + p), y = __ldg(sy + p);
-        const float vx = __ldg(svx + p), vy = __ldg(svy + p);
-        const float I0 = __ldg(sI + p);
-        float lwp;
-        if (mode == MODE_CARRY)
-            lwp = __ldg(slw + p);
-        else if (mode == MODE_UNIFORM)
-            lwp = 0.0f;
-        else
-            lwp = __ldg(a.lwp + i);
-        uint32_t f[6];
-        prop_fields(philox_rk(make_uint4((uint32_t)i, a.frame, a.fid, PURPOSE_PROP << 8), a.rk), f);
-        float e0, e1, e2, e3, e4, e5;
-        box_muller(u21(f[0]), u21(f[1]), e0, e1);
-        box_muller(u21(f[2]), u21(f[3]), e2, e3);
-        box_muller(u21(f[4]), u21(f[5]), e4, e5);
-        float v[5];
-        v[0] = fmaf(a.sm, e0, x + vx);
-        v[1] = fmaf(a.sm, e1, y + vy);
-        v[2] = fmaf(a.sv, e2, vx);
-        v[3] = fmaf(a.sv, e3, vy);
-        v[4] = fmaf(a.sI, e4, I0);
-        const float l = PC ? cell_loglik<R>(geom, a.lmap, v[0], v[1], v[4]) : patch_loglik<R>(geom, v[0], v[1], v[4]);
-        const float lw = lwp + l;
+        const Propagated q = propagate_slot(a, mode, i, p);
 #pragma unroll
         for (int c = 0; c < 5; ++c)
-            dplane[c][i] = v[c];
-        dplane[5][i] = lw;
-        acc.add_cur(lw, v);
-        if (mode == MODE_UNIFORM)
-            acc.add_prev_zero();
-        else
-            acc.add_prev(lwp);
+            a.dst[c * a.N + i] = q.v[c];
+        const uint32_t key = bin_of<R>(a.bg, a.W, a.H, q.v[0], q.v[1], q.v[4]);
+        a.bin_key[i] = key;
+        atomicAdd(&shist[key], 1u);
+        if ((it & 7u) == 0u)
+            spread_tally(q.v[0], q.v[1], true, ns, nt);
+    }
+    publish_spread(a.sum, ns, nt);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nb; t += blockDim.x)
+        if (shist[t])
+            atomicAdd(a.bin_tot + t, shist[t]);
+}
+
+// PC: pcSIR (cell map lookup) instead of the patch sum at the particle.
+// Phase 0: with the binned path chosen for this step (bin_this), only
+// propagate and bin (bin_propagate); otherwise the whole direct step.
+// Phase 1 (launched after the binned likelihood; returns at once on the
+// direct path): the binned path's sums.  It visits the slots in the direct
+// path's order, reads each slot's state and its l, forms lw = lw_prev + l and
+// accumulates exactly as the direct path does, so both paths give the same
+// bits for every result of the step.
+template <int R, bool PC>
+__global__ void __launch_bounds__(256) step_kernel(StepArgs a, int phase)
+{
+    int mode = a.mode;
+    if (mode != MODE_CARRY && *a.degenerate)
+        mode = MODE_CARRY;  // the last resample kept every particle
+    const bool binned = !PC && a.bin_key && __ldcg(&a.sum->bin_this) != 0;
+    if (phase == 0 && binned) {
+        bin_propagate<R>(a, mode);
+        return;
+    }
+    if (phase == 1 && !binned)
+        return;
+    const PatchGeom geom{a.Zp, a.W, a.H, a.Wp, a.pad, a.inv2s2, a.inv_sxi2, a.Kc, a.Hp, a.flags};
+    // N < 2^31: 32-bit slot indices into per-component planes
+    const int32_t N = (int32_t)a.N;
+    float *__restrict__ dplane[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+        dplane[c] = a.dst + c * a.N;
+    Acc acc;
+    acc.init();
+    unsigned ns = 0, nt = 0;
+    // unsigned: i + stride stays below 2^32 for any N < 2^31.  The ancestor of
+    // the next slot is loaded one iteration ahead, so the parent-state gather
+    // does not wait on a dependent load.
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const float *__restrict__ sx = a.src, *__restrict__ sy = a.src + a.N, *__restrict__ svx = a.src + 2 * a.N;
+    const float *__restrict__ svy = a.src + 3 * a.N, *__restrict__ sI = a.src + 4 * a.N;
+    const float *__restrict__ slw = a.src + 5 * a.N;
+    if (phase == 1) {
+        // l of slot i sits in bin order at the place its key entry now holds
+        for (uint32_t i = i0; i < (uint32_t)N; i += stride) {
+            float v[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c)
+                v[c] = __ldcg(dplane[c] + i);
+            const float l = __ldcg(a.bin_l + __ldcg(a.bin_key + i));
+            float lwp;
+            if (mode == MODE_CARRY)
+                lwp = __ldg(slw + i);  // identity ancestry
+            else if (mode == MODE_UNIFORM)
+                lwp = 0.0f;
+            else
+                lwp = __ldg(a.lwp + i);
+            const float lw = lwp + l;
+            dplane[5][i] = lw;
+            acc.add_cur(lw, v);
+            if (mode == MODE_UNIFORM)
+                acc.add_prev_zero();
+            else
+                acc.add_prev(lwp);
+        }
+    } else {
+        uint32_t pn = (i0 < (uint32_t)N) ? ((mode == MODE_CARRY) ? i0 : (uint32_t)__ldg(a.anc + i0)) : 0u;
+        unsigned it = 0;
+        for (uint32_t i = i0; i < (uint32_t)N; i += stride, ++it) {
+            uint32_t p = pn;
+            if (i + stride < (uint32_t)N)
+                pn = (mode == MODE_CARRY) ? i + stride : (uint32_t)__ldg(a.anc + i + stride);
+            if (p >= (uint32_t)N) {  // caller-supplied ancestors are checked, never trusted
+                atomicOr(a.flags, FLAG_BAD_ANCESTOR);
+                p = i;
+            }
+            const float x = __ldg(sx + p), y = __ldg(sy + p);
+            const float vx = __ldg(svx + p), vy = __ldg(svy + p);
+            const float I0 = __ldg(sI + p);
+            float lwp;
+            if (mode == MODE_CARRY)
+                lwp = __ldg(slw + p);
+            else if (mode == MODE_UNIFORM)
+                lwp = 0.0f;
+            else
+                lwp = __ldg(a.lwp + i);
+            uint32_t f[6];
+            prop_fields(philox_rk(make_uint4((uint32_t)i, a.frame, a.fid, PURPOSE_PROP << 8), a.rk), f);
+            float e0, e1, e2, e3, e4, e5;
+            box_muller(u21(f[0]), u21(f[1]), e0, e1);
+            box_muller(u21(f[2]), u21(f[3]), e2, e3);
+            box_muller(u21(f[4]), u21(f[5]), e4, e5);
+            float v[5];
+            v[0] = fmaf(a.sm, e0, x + vx);
+            v[1] = fmaf(a.sm, e1, y + vy);
+            v[2] = fmaf(a.sv, e2, vx);
+            v[3] = fmaf(a.sv, e3, vy);
+            v[4] = fmaf(a.sI, e4, I0);
+            const float l = PC ? cell_loglik<R>(geom, a.lmap, v[0], v[1], v[4]) : patch_loglik<R>(geom, v[0], v[1], v[4]);
+            const float lw = lwp + l;
+#pragma unroll
+            for (int c = 0; c < 5; ++c)
+                dplane[c][i] = v[c];
+            dplane[5][i] = lw;
+            acc.add_cur(lw, v);
+            if (mode == MODE_UNIFORM)
+                acc.add_prev_zero();
+            else
+                acc.add_prev(lwp);
+            if (!PC && (it & 7u) == 0u)
+                spread_tally(v[0], v[1], true, ns, nt);
+        }
+        if (!PC)
+            publish_spread(a.sum, ns, nt);
     }
     // block reduction of the partial statistics
 #pragma unroll
@@ -346,18 +430,23 @@ cudaError_t launch_prepare_frame(ppf_ctx *c, const void *frame)
     const int64_t n = (int64_t)c->Wp * c->Hp;
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     const float bg = c->m.background;
+    // pcSIR and contexts without the binned path take the direct path
+    const int force = c->bin_key ? c->bin_force : 0;
     switch (c->m.frame_dtype) {
     case PPF_BF16:
         prepare_frame_kernel<__nv_bfloat16><<<grid, 256, 0, c->stream>>>(
-            (const __nv_bfloat16 *)frame, c->Zp, c->m.width, c->m.height, c->Wp, c->Hp, c->pad, bg);
+            (const __nv_bfloat16 *)frame, c->Zp, c->m.width, c->m.height, c->Wp, c->Hp, c->pad, bg, c->sum, force, c->bin_tot,
+            c->bin_nbins);
         break;
     case PPF_F16:
         prepare_frame_kernel<__half><<<grid, 256, 0, c->stream>>>(
-            (const __half *)frame, c->Zp, c->m.width, c->m.height, c->Wp, c->Hp, c->pad, bg);
+            (const __half *)frame, c->Zp, c->m.width, c->m.height, c->Wp, c->Hp, c->pad, bg, c->sum, force, c->bin_tot,
+            c->bin_nbins);
         break;
     default:
         prepare_frame_kernel<float><<<grid, 256, 0, c->stream>>>(
-            (const float *)frame, c->Zp, c->m.width, c->m.height, c->Wp, c->Hp, c->pad, bg);
+            (const float *)frame, c->Zp, c->m.width, c->m.height, c->Wp, c->Hp, c->pad, bg, c->sum, force, c->bin_tot,
+            c->bin_nbins);
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && c->lmap)
@@ -367,12 +456,27 @@ cudaError_t launch_prepare_frame(ppf_ctx *c, const void *frame)
 }
 
 template <int R>
-static void launch_step_r(const StepArgs &a, int grid, cudaStream_t s)
+static void launch_step_r(const StepArgs &a, int grid, int phase, cudaStream_t s)
 {
     if (a.lmap)
-        step_kernel<R, true><<<grid, 256, 0, s>>>(a);
+        step_kernel<R, true><<<grid, 256, 0, s>>>(a, phase);
     else
-        step_kernel<R, false><<<grid, 256, 0, s>>>(a);
+        step_kernel<R, false><<<grid, 256, 0, s>>>(a, phase);
+}
+
+static void launch_step_phase(const StepArgs &a, int R, int grid, int phase, cudaStream_t s)
+{
+    switch (R) {
+    case 0: launch_step_r<0>(a, grid, phase, s); break;
+    case 1: launch_step_r<1>(a, grid, phase, s); break;
+    case 2: launch_step_r<2>(a, grid, phase, s); break;
+    case 3: launch_step_r<3>(a, grid, phase, s); break;
+    case 4: launch_step_r<4>(a, grid, phase, s); break;
+    case 5: launch_step_r<5>(a, grid, phase, s); break;
+    case 6: launch_step_r<6>(a, grid, phase, s); break;
+    case 7: launch_step_r<7>(a, grid, phase, s); break;
+    default: launch_step_r<8>(a, grid, phase, s); break;
+    }
 }
 
 cudaError_t launch_step(ppf_ctx *c, int32_t k)
@@ -407,22 +511,27 @@ cudaError_t launch_step(ppf_ctx *c, int32_t k)
     a.part = c->part;
     a.done = &c->sum->blocks_done;
     a.sum = c->sum;
+    a.bin_key = c->bin_key;
+    a.bin_tot = c->bin_tot;
+    a.bin_l = c->bin_l;
+    a.bg = BinGeom{c->bin_T, c->bin_nx, c->bin_nbins};
     const int grid = step_grid(c);
     prof_mark(c, PH_STEP, 0);
-    switch (c->m.patch_radius) {
-    case 0: launch_step_r<0>(a, grid, c->stream); break;
-    case 1: launch_step_r<1>(a, grid, c->stream); break;
-    case 2: launch_step_r<2>(a, grid, c->stream); break;
-    case 3: launch_step_r<3>(a, grid, c->stream); break;
-    case 4: launch_step_r<4>(a, grid, c->stream); break;
-    case 5: launch_step_r<5>(a, grid, c->stream); break;
-    case 6: launch_step_r<6>(a, grid, c->stream); break;
-    case 7: launch_step_r<7>(a, grid, c->stream); break;
-    default: launch_step_r<8>(a, grid, c->stream); break;
+    launch_step_phase(a, c->m.patch_radius, grid, 0, c->stream);
+    c->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && c->bin_key) {
+        // the binned path's scan, scatter and likelihood, then its sums; all
+        // four return at once when this step takes the direct path
+        e = launch_binned(c);
+        if (e == cudaSuccess) {
+            launch_step_phase(a, c->m.patch_radius, grid, 1, c->stream);
+            c->launches += 1;
+            e = cudaGetLastError();
+        }
     }
     prof_mark(c, PH_STEP, 1);
-    c->launches += 1;
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace ppf

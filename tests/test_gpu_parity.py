@@ -411,3 +411,111 @@ def test_free_running_tracks_the_spot(ppf):
     err = est[5:, :2] - mv.truth[5:, :2]
     assert np.sqrt((err ** 2).sum(1).mean()) < 0.5
     pf.close()
+
+
+# ------------------------------------------------------------ likelihood paths
+def _path_run(ppf, gm, N, gs, frames, path, schemes, init=None):
+    """Frames through a context on one likelihood path; every output per frame."""
+    import torch
+    pf = ppf.ParticleFilter(gm, N, group_size=gs)
+    pf.set_likelihood_path(path)
+    if init is not None:
+        pf.set_particles(torch.from_numpy(init))
+    out = []
+    for k in range(1, frames.shape[0] + 1):
+        pf.step(frames[k - 1], k)
+        e = pf.estimate()
+        st, _, _ = pf.get_particles()
+        binned = pf.last_step_binned()
+        pf.resample(schemes[(k - 1) % len(schemes)], 0.25)
+        _, anc, lwp = pf.get_particles(state=False, anc=True, lw_prev=True)
+        out.append((st.cpu().numpy(), anc.cpu().numpy(), lwp.cpu().numpy(), e.mean, e.log_evidence, e.ess,
+                    e.max_log_weight, binned))
+    pf.close()
+    return out
+
+
+def _same(a, b):
+    for k, ((sa, aa, la, ma, le_a, ea, xa, ba), (sb, ab, lb, mb, le_b, eb, xb, bb)) in enumerate(zip(a, b)):
+        assert np.array_equal(sa, sb, equal_nan=True), k
+        assert np.array_equal(aa, ab) and np.array_equal(la, lb, equal_nan=True), k
+        assert np.array_equal(np.array([*ma, le_a, ea, xa]), np.array([*mb, le_b, eb, xb]), equal_nan=True), k
+
+
+@pytest.mark.parametrize("r", [0, 1, 4, 5, 8])
+def test_binned_path_equals_direct_path(ppf, movie, r):
+    """The binned likelihood path (particles binned by image tile, each tile's
+    window staged in shared memory by the tensor-memory accelerator) and the
+    direct path give the same bits for every output of the step: state,
+    log-weights, ancestors, posterior mean, log-evidence, N_eff.  Frame 1 is
+    the prior draw, spread over the whole frame."""
+    from gpu_common import paired_models
+    gm, _ = paired_models(ppf, seed=21, patch_radius=r)
+    fr = gpu_frames(movie)[:4]
+    schemes = [ppf.SYSTEMATIC, ppf.RPA_SGS, ppf.RNA, ppf.ARNA]
+    d = _path_run(ppf, gm, 20011, 2000, fr, ppf.PATH_DIRECT, schemes)
+    b = _path_run(ppf, gm, 20011, 2000, fr, ppf.PATH_BINNED, schemes)
+    assert not any(x[7] for x in d) and all(x[7] for x in b)
+    _same(d, b)
+
+
+def test_binned_path_odd_frames_borders_and_nonfinite(ppf):
+    """Both paths on a 97 x 61 frame with particles all around and outside
+    the borders, and non-finite and huge states (the bin of particles with no
+    patch sum)."""
+    import torch
+    from gpu_common import paired_models
+    W, H = 97, 61
+    mv = synth.make_movie(W=W, H=H, K=3, sigma=1.3, amplitude=40.0, background=10.0, seed=4)
+    gm, _ = paired_models(ppf, width=W, height=H, patch_radius=3, seed=12, psf_sigma=1.3, amplitude=40.0)
+    N = 7001
+    rng = np.random.default_rng(3)
+    st = np.zeros((6, N), dtype=np.float32)
+    st[0] = rng.uniform(-12, W + 12, N)
+    st[1] = rng.uniform(-12, H + 12, N)
+    st[2:4] = rng.normal(0.0, 0.5, (2, N))
+    st[4] = rng.uniform(10, 70, N)
+    st[0, :4] = [np.nan, np.inf, 1e30, -3.0]
+    st[4, 4] = np.nan
+    fr = torch.from_numpy(mv.frames).cuda()
+    schemes = [ppf.SYSTEMATIC, ppf.RPA_LGS]
+    d = _path_run(ppf, gm, N, 1000, fr, ppf.PATH_DIRECT, schemes, init=st)
+    b = _path_run(ppf, gm, N, 1000, fr, ppf.PATH_BINNED, schemes, init=st)
+    _same(d, b)
+
+
+@pytest.mark.parametrize("scheme", [orc.SYSTEMATIC, orc.RPA_SGS, orc.RNA])
+def test_binned_path_lockstep(ppf, movie, scheme):
+    """The binned path frame by frame against the oracle."""
+    from gpu_common import lockstep, paired_models
+    gm, om = paired_models(ppf, seed=3)
+    pf = ppf.ParticleFilter(gm, 16384, group_size=4096)
+    pf.set_likelihood_path(ppf.PATH_BINNED)
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), scheme, K=4, alpha=0.25)
+    pf.close()
+
+
+def test_automatic_path_choice(ppf):
+    """Chosen on the device: the prior draw (spread over the frame) is binned;
+    once the particles have collapsed onto the spot the direct path runs."""
+    from gpu_common import paired_models
+    mv = synth.make_movie(W=512, H=512, K=6, sigma=1.5, amplitude=50.0, background=10.0, seed=2)
+    gm, _ = paired_models(ppf, width=512, height=512, patch_radius=5, seed=2)
+    pf = ppf.ParticleFilter(gm, 200_000, group_size=4096)
+    fr = gpu_frames(mv)
+    seen = []
+    for k in range(1, 7):
+        pf.step(fr[k - 1], k)
+        seen.append(pf.last_step_binned())
+        pf.resample(ppf.SYSTEMATIC)
+    assert seen[0] and not seen[-1], seen
+    with pytest.raises(ppf.PPFError):
+        pf.set_likelihood_path(7)
+    pf.close()
+    pc, _ = paired_models(ppf, seed=2, likelihood=1)
+    p2 = ppf.ParticleFilter(pc, 1000, group_size=1000)
+    with pytest.raises(ppf.PPFError) as e:
+        p2.set_likelihood_path(ppf.PATH_BINNED)
+    assert e.value.status == ppf.EINVAL
+    p2.set_likelihood_path(ppf.PATH_DIRECT)
+    p2.close()
