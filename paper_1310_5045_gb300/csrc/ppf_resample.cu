@@ -417,33 +417,87 @@ __device__ void block_scan_i64(int64_t *a, int n, uint64_t *red, int64_t *total_
     __syncthreads();
 }
 
-// bitonic sort (ascending) of n <= MAX_SCHED_GROUPS u64 keys in shared memory
+// Sort (ascending) of n <= MAX_SCHED_GROUPS distinct u64 keys, one block of
+// 1024 threads.  sm: MAX_SCHED_GROUPS keys, then two index buffers of as many
+// u16 (SORT_SMEM_BYTES in all); g may be sm itself.  A merge sort on indices:
+// every thread sorts a run of 16 in registers, then ten levels of merges,
+// each thread writing 16 outputs after a merge-path search of its diagonal.
+constexpr int SORT_PER = 16;
+constexpr size_t SORT_SMEM_BYTES = (sizeof(uint64_t) + 2 * sizeof(uint16_t)) * MAX_SCHED_GROUPS;
+
 __device__ void block_sort_u64(uint64_t *g, int n, uint64_t *sm)
 {
-    int P = 1;
-    while (P < n)
-        P <<= 1;
-    for (int i = threadIdx.x; i < P; i += blockDim.x)
-        sm[i] = (i < n) ? g[i] : ~0ull;
+    uint16_t *ia = reinterpret_cast<uint16_t *>(sm + MAX_SCHED_GROUPS), *ib = ia + MAX_SCHED_GROUPS;
+    if (g != sm)
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            sm[i] = g[i];
     __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t a = sm[i], b = sm[ixj];
-                    const bool up = ((i & k) == 0);
-                    if ((a > b) == up) {
-                        sm[i] = b;
-                        sm[ixj] = a;
-                    }
-                }
-            }
-            __syncthreads();
+    const int t0 = threadIdx.x * SORT_PER;
+    {
+        uint64_t k[SORT_PER];
+        uint16_t id[SORT_PER];
+#pragma unroll
+        for (int e = 0; e < SORT_PER; ++e) {
+            k[e] = (t0 + e < n) ? sm[t0 + e] : ~0ull;  // past the end: sorts last
+            id[e] = (uint16_t)(t0 + e);
         }
+#pragma unroll
+        for (int e = 1; e < SORT_PER; ++e)
+#pragma unroll
+            for (int f = e; f > 0; --f)
+                if (k[f] < k[f - 1]) {
+                    const uint64_t tk = k[f];
+                    k[f] = k[f - 1];
+                    k[f - 1] = tk;
+                    const uint16_t ti = id[f];
+                    id[f] = id[f - 1];
+                    id[f - 1] = ti;
+                }
+#pragma unroll
+        for (int e = 0; e < SORT_PER; ++e)
+            if (t0 + e < n)
+                ia[t0 + e] = id[e];
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        g[i] = sm[i];
+    __syncthreads();
+    uint16_t *src = ia, *dst = ib;
+    for (int w = SORT_PER; w < n; w *= 2) {
+        if (t0 < n) {
+            const int base = (t0 / (2 * w)) * (2 * w);
+            const int an = (n - base < w) ? n - base : w;
+            const int b0 = base + w;
+            const int bn = (n - b0 <= 0) ? 0 : ((n - b0 < w) ? n - b0 : w);
+            const int d = t0 - base;
+            int lo = d - bn > 0 ? d - bn : 0, hi = d < an ? d : an;
+            while (lo < hi) {  // merge path: i taken from the first run, d - i from the second
+                const int mid = (lo + hi) >> 1;
+                if (sm[src[base + mid]] < sm[src[b0 + d - mid - 1]])
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            int i = lo, j = d - lo;
+            const int cnt = (an + bn - d < SORT_PER) ? an + bn - d : SORT_PER;
+            for (int e = 0; e < cnt; ++e) {
+                const bool take_a = i < an && (j >= bn || sm[src[base + i]] < sm[src[b0 + j]]);
+                dst[t0 + e] = take_a ? src[base + i] : src[b0 + j];
+                i += take_a ? 1 : 0;
+                j += take_a ? 0 : 1;
+            }
+        }
+        __syncthreads();
+        uint16_t *t = src;
+        src = dst;
+        dst = t;
+    }
+    uint64_t k[SORT_PER];
+#pragma unroll
+    for (int e = 0; e < SORT_PER; ++e)
+        k[e] = (t0 + e < n) ? sm[src[t0 + e]] : 0ull;
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < SORT_PER; ++e)
+        if (t0 + e < n)
+            g[t0 + e] = k[e];
     __syncthreads();
 }
 
@@ -732,7 +786,11 @@ __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
         A.seg_chunk[2 * G + 1] = nseg;  // remember the segment count
 }
 
-// routing copy: anc[dst + k] = anc_sys[tick + k] for every segment
+// routing copy: anc[dst + k] = anc_sys[tick + k] for every segment, in work
+// items of COPY_CHUNK slots; blocks loop over the items.  The first warp finds
+// an item's segment (the last with seg_chunk <= b) by a 32-way search: each
+// round probes 32 evenly spaced entries at once, so about three dependent
+// loads locate it among tens of thousands of segments.
 __global__ void __launch_bounds__(256) route_copy_kernel(const int32_t *__restrict__ anc_sys,
                                                          int32_t *__restrict__ anc, int32_t G,
                                                          const int32_t *__restrict__ seg_chunk,
@@ -742,34 +800,40 @@ __global__ void __launch_bounds__(256) route_copy_kernel(const int32_t *__restri
                                                          DevSummary *__restrict__ sum)
 {
     __shared__ int32_t sseg;
-    const int32_t b = blockIdx.x;
-    if (b >= sum->n_chunks)
-        return;
+    const int32_t nb = sum->n_chunks;
     const int32_t nseg = seg_chunk[2 * G + 1];
-    if (threadIdx.x == 0) {
-        int32_t a = 0, e = nseg - 1;  // last segment with seg_chunk <= b
-        while (a < e) {
-            const int32_t mid = (a + e + 1) >> 1;
-            if (seg_chunk[mid] <= b)
-                a = mid;
-            else
-                e = mid - 1;
+    const int lane = threadIdx.x & 31;
+    for (int32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        if (threadIdx.x < 32) {
+            int32_t lo = 0, hi = nseg;  // seg_chunk[lo] <= b < seg_chunk[hi] (hi may be nseg)
+            while (hi - lo > 1) {
+                const int32_t step = (hi - lo + 31) / 32;
+                const int32_t p = lo + lane * step;
+                const bool le = p < hi && __ldg(seg_chunk + p) <= b;
+                const unsigned m = __ballot_sync(0xffffffffu, le);  // a prefix of the lanes
+                const int32_t last = 31 - __clz(m);
+                lo = lo + last * step;
+                const int32_t nh = lo + step;
+                hi = nh < hi ? nh : hi;
+            }
+            if (lane == 0)
+                sseg = lo;
         }
-        sseg = a;
+        __syncthreads();
+        const int32_t s = sseg;
+        const int64_t k0 = (int64_t)(b - __ldg(seg_chunk + s)) * COPY_CHUNK;
+        const int64_t len = __ldg(seg_len + s);
+        const int64_t k1 = (k0 + COPY_CHUNK < len) ? k0 + COPY_CHUNK : len;
+        const int64_t src = __ldg(seg_tick + s), dst = __ldg(seg_dst + s);
+        if (src < 0 || dst < 0 || k0 < 0 || src + k1 > N || dst + k1 > N) {
+            if (threadIdx.x == 0)
+                atomicOr(&sum->flags, FLAG_INTERNAL);  // inconsistent schedule: never write out of bounds
+        } else {
+            for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x)
+                anc[dst + k] = __ldg(anc_sys + src + k);
+        }
+        __syncthreads();  // sseg is rewritten for the next item
     }
-    __syncthreads();
-    const int32_t s = sseg;
-    const int64_t k0 = (int64_t)(b - seg_chunk[s]) * COPY_CHUNK;
-    const int64_t len = seg_len[s];
-    const int64_t k1 = (k0 + COPY_CHUNK < len) ? k0 + COPY_CHUNK : len;
-    const int64_t src = seg_tick[s], dst = seg_dst[s];
-    if (src < 0 || dst < 0 || src + k1 > N || dst + k1 > N) {
-        if (threadIdx.x == 0)
-            atomicOr(&sum->flags, FLAG_INTERNAL);  // inconsistent schedule: never write out of bounds
-        return;
-    }
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x)
-        anc[dst + k] = anc_sys[src + k];
 }
 
 // ------------------------------------------------------------------- RNA
@@ -941,7 +1005,7 @@ __global__ void __launch_bounds__(1024) rna_prep_kernel(const int64_t *__restric
 // counts as lost): the groups in increasing order of the first Philox word of
 // (seed; g, frame, filter, RING), ties by index (a bitonic sort of
 // word << 32 | g).  Then every group's successor on the ring.
-// Dynamic shared memory: MAX_SCHED_GROUPS u64 (G <= MAX_SCHED_GROUPS).
+// Dynamic shared memory: SORT_SMEM_BYTES (G <= MAX_SCHED_GROUPS).
 __global__ void __launch_bounds__(1024) arna_prep_kernel(const int64_t *__restrict__ goff, int32_t G, float alpha,
                                                          DevSummary *sum, double ess_thr,
                                                          const int64_t *__restrict__ Tg, int32_t *__restrict__ ring,
@@ -1055,10 +1119,10 @@ cudaError_t resample_kernel_attributes()
                                  (int)FILL_SMEM_BYTES);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(schedule_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(uint64_t) * MAX_SCHED_GROUPS));
+                                 (int)SORT_SMEM_BYTES);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(arna_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(uint64_t) * MAX_SCHED_GROUPS));
+                                 (int)SORT_SMEM_BYTES);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(uint64_t) * (SCAN_SMEM_TILES + 1)));
@@ -1112,10 +1176,15 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     A.seg_dst = c->sc.seg_dst;
     A.seg_len = c->sc.seg_len;
     A.sum = c->sum;
-    const size_t smem = sizeof(uint64_t) * MAX_SCHED_GROUPS;
-    schedule_kernel<<<1, 1024, smem, c->stream>>>(A);
+    // Greedy needs no sort: shared memory only for its two prefix arrays (at
+    // most G words), which leaves the rest of the SM's L1 to the global reads
+    const size_t sched_smem = scheme == PPF_RPA_GS || scheme == PPF_RPA2_GS
+                                  ? sizeof(int64_t) * (size_t)(c->G > 0 ? c->G : 1)
+                                  : SORT_SMEM_BYTES;
+    schedule_kernel<<<1, 1024, sched_smem, c->stream>>>(A);
     const int max_chunks = 2 * c->G + 1 + (int)((c->N + COPY_CHUNK - 1) / COPY_CHUNK);
-    route_copy_kernel<<<max_chunks, 256, 0, c->stream>>>(c->anc_sys, c->anc, c->G, c->sc.seg_chunk,
+    const int gcopy = max_chunks < 8 * c->num_sms ? max_chunks : 8 * c->num_sms;
+    route_copy_kernel<<<gcopy, 256, 0, c->stream>>>(c->anc_sys, c->anc, c->G, c->sc.seg_chunk,
                                                          c->sc.seg_tick, c->sc.seg_dst, c->sc.seg_len, c->N,
                                                          c->sum);
     prof_mark(c, PH_RESAMPLE, 1);
@@ -1148,7 +1217,7 @@ cudaError_t launch_resample_arna(ppf_ctx *c, float alpha, double ess_thr)
     tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
         c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, nullptr, c->sum, ess_thr, c->m.seed, c->m.filter_id,
         (uint32_t)c->last_frame, c->goff, c->G, 1, c->sc.Cbl, c->sc.Tg, st_tiles, make_divisor((uint32_t)c->N));
-    arna_prep_kernel<<<1, 1024, sizeof(uint64_t) * MAX_SCHED_GROUPS, c->stream>>>(
+    arna_prep_kernel<<<1, 1024, SORT_SMEM_BYTES, c->stream>>>(
         c->goff, c->G, alpha, c->sum, ess_thr, c->sc.Tg, c->ring, c->succ, c->m.seed, c->m.filter_id,
         (uint32_t)c->last_frame);
     rna_kernel<<<c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(lw, c->N, c->G, c->goff, c->succ, c->sum, ess_thr,
