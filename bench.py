@@ -628,6 +628,56 @@ def run_ours(args):
     return 0
 
 
+PROFILE_CASES = ("step", "rpa_gs", "rpa_sgs", "rpa_lgs", "rpa2_lgs", "rna", "arna", "binned", "pcsir", "grad",
+                 "batch")
+
+
+def run_profile_case(args):
+    """A small run of one kernel family for an ncu capture (no JSON line): the
+    spot512 workload at --n particles, 6 frames (the first two with systematic
+    resampling to concentrate the cloud, then the case's scheme); "binned"
+    forces the binned likelihood on the prior draw of frame 1; "grad" runs
+    the gradient over 5 frames of 256^2 at --n; "batch" runs 512 filters."""
+    import torch
+    import paper_1310_5045_gb300 as ppf
+    import synth
+    case, n = args.profile, args.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if case == "grad":
+        gmv, _ = synth.preset("spot256_k50", seed=1, K=5)
+        gm = ppf.Model(width=256, height=256, patch_radius=4, psf_sigma=1.5, amplitude=50.0, background=10.0,
+                       sigma_xi=math.sqrt(10.0), sigma_m=0.5, sigma_v=0.1, sigma_I=0.0, seed=0)
+        pf = ppf.ParticleFilter(gm, n, group_size=GROUP)
+        fr = torch.from_numpy(gmv.frames).to(dev)
+        for _ in range(2):
+            pf.loglik_grad(fr)
+        pf.close()
+        return 0
+    if case == "batch":
+        mb = synth.make_movie_batch(F=512, W=64, H=64, K=6, n_range=(256, 65536), seed=0)
+        models = [ppf.Model(width=64, height=64, patch_radius=5, psf_sigma=float(mb.sigma[f]),
+                            amplitude=float(mb.amplitude[f]), background=10.0, sigma_xi=math.sqrt(10.0),
+                            sigma_m=0.5, sigma_v=0.1, sigma_I=1.0, seed=0, filter_id=f) for f in range(512)]
+        bf = ppf.BatchFilter(models, mb.n_particles)
+        bf.run(torch.from_numpy(mb.frames).to(dev), 1, use_graph=False, estimates=False)
+        torch.cuda.synchronize()
+        bf.close()
+        return 0
+    mv, params = make_workload(8, seed=0)
+    fr = torch.from_numpy(mv.frames).to(dev)
+    model = ppf.Model(**params, seed=0, likelihood=1 if case == "pcsir" else 0)
+    pf = ppf.ParticleFilter(model, n, group_size=GROUP)
+    pf.set_likelihood_path(ppf.PATH_BINNED if case == "binned" else
+                           (ppf.PATH_AUTO if case == "pcsir" else ppf.PATH_DIRECT))
+    scheme = ppf.SCHEMES["systematic" if case in ("step", "binned", "pcsir") else case]
+    for k in range(1, 7):
+        pf.step(fr[k - 1], k)
+        pf.resample(ppf.SYSTEMATIC if k <= 2 else scheme, 0.5)
+    torch.cuda.synchronize()
+    pf.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -658,7 +708,11 @@ def main():
     ap.add_argument("--precision-n", type=int, default=N_FULL)
     ap.add_argument("--precision-frames", type=int, default=5)
     ap.add_argument("--grad-evals", type=int, default=3)
+    ap.add_argument("--profile", choices=PROFILE_CASES, default=None,
+                    help="run a small case of one kernel family for an ncu capture (prints no JSON line)")
     args = ap.parse_args()
+    if args.profile:
+        return run_profile_case(args)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

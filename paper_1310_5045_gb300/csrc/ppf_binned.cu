@@ -6,18 +6,19 @@
 //   1. propagates every slot, writes its bin and counts the bin sizes (the
 //      step kernel's bin_propagate; a bin is an image tile of T x T patch
 //      anchors, plus one bin for particles that need no patch sum);
-//   2. turns the sizes into bin offsets and cuts the bins into work items;
-//   3. scatters each particle's record (x, y, I0) into its bin: each block
-//      takes a chunk of slots, ranks them by bin in shared memory and
-//      reserves one range per bin with one atomic, so a bin's records from
-//      one chunk are written contiguously; the slot keeps its record's place;
-//   4. runs the likelihood over work items of one bin: the tile's window
+//   2. scatters each particle's record (x, y, I0) into its bin: each block
+//      turns the bin sizes into bin starts, takes chunks of slots, ranks them
+//      by bin in shared memory and reserves one range per bin with one
+//      atomic, so a bin's records from one chunk are written contiguously;
+//      the slot keeps its record's place; the last block cuts the bins into
+//      work items;
+//   3. runs the likelihood over work items of one bin: the tile's window
 //      (the tile plus the patch halo) is copied into shared memory by the
 //      tensor-memory accelerator (cp.async.bulk.tensor, completion on an
 //      mbarrier), the next item's window copied while this one is summed,
 //      every patch read comes from shared memory, and l is written in bin
 //      order;
-//   5. sums in the direct path's slot order (the step kernel's phase 1),
+//   4. sums in the direct path's slot order (the step kernel's phase 1),
 //      fetching each slot's l from its record's place.
 // A particle's likelihood has the same bits on both paths (the same PSF
 // samples and the same patch_rows arithmetic), and the sums are taken in
@@ -86,88 +87,52 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-// ------------------------------------------------------------- the scan
-// One block: the bin sizes become their exclusive prefix (each bin's first
-// record; the scatter then advances it as a cursor), and every bin is cut into
-// work items of at most BIN_ITEM records.
-__global__ void __launch_bounds__(1024) bin_scan_kernel(int nbins, uint32_t *__restrict__ tot,
-                                                        int32_t *__restrict__ items, int items_max, DevSummary *sum)
-{
-    if (__ldcg(&sum->bin_this) == 0)
-        return;
-    __shared__ uint64_t red[33];
-    __shared__ uint32_t soff[BIN_MAX_BINS + 1], sio[BIN_MAX_BINS + 1];  // record and item prefix per bin
-    const int bp = (nbins + blockDim.x - 1) / blockDim.x;
-    const int t0 = threadIdx.x * bp, t1 = (t0 + bp < nbins) ? t0 + bp : nbins;
-    uint64_t ssz = 0, sit = 0;
-    for (int t = t0; t < t1; ++t) {
-        const uint32_t n = __ldcg(tot + t);
-        ssz += n;
-        sit += (n + BIN_ITEM - 1) / BIN_ITEM;
-    }
-    uint64_t nall, iall;
-    uint64_t off = block_excl_scan_u64(ssz, red, &nall);
-    uint64_t ioff = block_excl_scan_u64(sit, red, &iall);
-    for (int t = t0; t < t1; ++t) {
-        const uint32_t n = __ldcg(tot + t);
-        soff[t] = (uint32_t)off;
-        sio[t] = (uint32_t)ioff;
-        tot[t] = (uint32_t)off;
-        off += n;
-        ioff += (n + BIN_ITEM - 1) / BIN_ITEM;
-    }
-    if (threadIdx.x == 0) {
-        soff[nbins] = (uint32_t)nall;
-        sio[nbins] = (uint32_t)iall;
-        tot[nbins] = (uint32_t)nall;
-        sum->n_bin_items = (int32_t)iall;
-    }
-    __syncthreads();
-    // the work items, in parallel: item j lies in the bin t with sio[t] <= j < sio[t + 1]
-    for (uint32_t j = threadIdx.x; j < (uint32_t)iall; j += blockDim.x) {
-        int lo = 0, hi = nbins;  // last t with sio[t] <= j
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (sio[mid] <= j)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        const uint32_t s0 = (j - sio[lo]) * (uint32_t)BIN_ITEM;
-        const uint32_t n = soff[lo + 1] - soff[lo];
-        if (PPF_DCHECK(j < (uint32_t)items_max && s0 < n, &sum->flags, FLAG_INTERNAL)) {
-            items[j] = lo;
-            items[items_max + j] = (int32_t)(soff[lo] + s0);
-            items[2 * items_max + j] = (int32_t)((n - s0) < (uint32_t)BIN_ITEM ? (n - s0) : BIN_ITEM);
-        }
-    }
-}
-
 // ---------------------------------------------------------- the scatter
-// Each block takes chunks of BIN_CHUNK consecutive slots, each thread 16
-// consecutive slots read as 16-byte vectors.  The chunk is ranked by bin in
-// shared memory and staged there in bin order; one global atomic per nonempty
-// bin reserves the bin's range (its cursor), and the staged records are then
-// copied out so that consecutive threads write consecutive records of a run.
-// Each slot's key entry receives its record's place (read by the sums of
-// phase 1).
+// Each block first turns the bin sizes into their exclusive prefix (each
+// bin's first record).  It then takes chunks of BIN_CHUNK consecutive slots,
+// each thread 16 consecutive slots read as 16-byte vectors.  A chunk is
+// ranked by bin in shared memory and staged there in bin order; one global
+// atomic per nonempty bin reserves the chunk's range inside the bin (its
+// cursor), and the staged records are then copied out so that consecutive
+// threads write consecutive records of a run.  Each slot's key entry receives
+// its record's place (read by the sums of phase 1).  The last block to finish
+// cuts every bin into work items of at most BIN_ITEM records for the
+// likelihood.
 constexpr int BIN_PER_THREAD = 16;
 constexpr int BIN_CHUNK = 256 * BIN_PER_THREAD;
 
 __global__ void __launch_bounds__(256) bin_scatter_kernel(const float *__restrict__ st, int64_t N, int nbins,
-                                                          uint32_t *__restrict__ key, uint32_t *__restrict__ cursor,
-                                                          float4 *__restrict__ rec, const DevSummary *sum,
-                                                          int32_t *flags)
+                                                          uint32_t *__restrict__ key,
+                                                          const uint32_t *__restrict__ size,
+                                                          uint32_t *__restrict__ cursor, float4 *__restrict__ rec,
+                                                          int32_t *__restrict__ items, int items_max,
+                                                          DevSummary *sum)
 {
+    pdl_wait();  // launched as a dependent of the step kernel
+    pdl_trigger();
     if (__ldcg(&sum->bin_this) == 0)
         return;
+    int32_t *flags = &sum->flags;
     // [BIN_CHUNK] staged records, [BIN_CHUNK] their bins, then per bin: count,
-    // local start, global start
+    // local start, global start, bin start
     extern __shared__ float4 stage[];
     uint16_t *sbin = reinterpret_cast<uint16_t *>(stage + BIN_CHUNK);
     uint32_t *cnt = reinterpret_cast<uint32_t *>(sbin + BIN_CHUNK);
-    uint32_t *lstart = cnt + nbins, *gstart = lstart + nbins;
+    uint32_t *lstart = cnt + nbins, *gstart = lstart + nbins, *bstart = gstart + nbins;
     __shared__ uint64_t red[33];
+    {   // bin starts: exclusive prefix of the sizes
+        const int per = (nbins + blockDim.x - 1) / blockDim.x, t0 = threadIdx.x * per;
+        uint64_t sm = 0;
+        for (int t = t0; t < t0 + per && t < nbins; ++t)
+            sm += __ldcg(size + t);
+        uint64_t tot;
+        uint64_t run = block_excl_scan_u64(sm, red, &tot);
+        for (int t = t0; t < t0 + per && t < nbins; ++t) {
+            bstart[t] = (uint32_t)run;
+            run += __ldcg(size + t);
+        }
+        __syncthreads();
+    }
     const uint32_t n = (uint32_t)N;
     const bool vec_ok = (N & 3) == 0;  // 16-byte vectors need 16-byte aligned planes
     for (uint32_t lo = blockIdx.x * (uint32_t)BIN_CHUNK; lo < n; lo += gridDim.x * (uint32_t)BIN_CHUNK) {
@@ -202,7 +167,7 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(const float *__restric
             for (int t = t0; t < t0 + per && t < nbins; ++t) {
                 const uint32_t c = cnt[t];
                 lstart[t] = (uint32_t)run;
-                gstart[t] = c ? atomicAdd(cursor + t, c) : 0u;
+                gstart[t] = c ? bstart[t] + atomicAdd(cursor + t, c) : 0u;
                 run += c;
             }
         }
@@ -256,6 +221,53 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(const float *__restric
         }
         __syncthreads();
     }
+    // the last block: the likelihood's work items (no block waits for it)
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = (atomicAdd(&sum->bin_blocks_done, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last)
+        return;
+    __threadfence();
+    uint32_t *sio = reinterpret_cast<uint32_t *>(stage);  // [nbins + 1] item prefix (the stage is free now)
+    {
+        const int per = (nbins + blockDim.x - 1) / blockDim.x, t0 = threadIdx.x * per;
+        uint64_t sm = 0;
+        for (int t = t0; t < t0 + per && t < nbins; ++t)
+            sm += (__ldcg(size + t) + BIN_ITEM - 1) / BIN_ITEM;
+        uint64_t iall;
+        uint64_t run = block_excl_scan_u64(sm, red, &iall);
+        for (int t = t0; t < t0 + per && t < nbins; ++t) {
+            sio[t] = (uint32_t)run;
+            run += (__ldcg(size + t) + BIN_ITEM - 1) / BIN_ITEM;
+        }
+        if (threadIdx.x == 0) {
+            sio[nbins] = (uint32_t)iall;
+            sum->n_bin_items = (int32_t)iall;
+            sum->bin_blocks_done = 0u;
+        }
+    }
+    __syncthreads();
+    const uint32_t ni = sio[nbins];
+    for (uint32_t j = threadIdx.x; j < ni; j += blockDim.x) {
+        int lo = 0, hi = nbins;  // sio[lo] <= j < sio[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (sio[mid] <= j)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const uint32_t s0 = (j - sio[lo]) * (uint32_t)BIN_ITEM;
+        const uint32_t sz = __ldcg(size + lo);
+        if (PPF_DCHECK(j < (uint32_t)items_max && s0 < sz, flags, FLAG_INTERNAL)) {
+            items[j] = lo;
+            items[items_max + j] = (int32_t)(bstart[lo] + s0);
+            items[2 * items_max + j] = (int32_t)((sz - s0) < (uint32_t)BIN_ITEM ? (sz - s0) : BIN_ITEM);
+        }
+    }
 }
 
 // ------------------------------------------------------- the likelihood
@@ -275,6 +287,8 @@ struct BinLikArgs {
 template <int R>
 __global__ void __launch_bounds__(256) bin_loglik_kernel(const __grid_constant__ CUtensorMap tmap, BinLikArgs a)
 {
+    pdl_wait();  // launched as a dependent of the scatter
+    pdl_trigger();
     DevSummary *sum = a.sum;
     if (__ldcg(&sum->bin_this) == 0)
         return;
@@ -437,8 +451,8 @@ int win_stride_bytes(int box)
 
 size_t scatter_smem(int nbins)
 {
-    // staged records, their bins, and three words per bin
-    return sizeof(float4) * BIN_CHUNK + sizeof(uint16_t) * BIN_CHUNK + 3 * sizeof(uint32_t) * (size_t)nbins;
+    // staged records, their bins, and four words per bin
+    return sizeof(float4) * BIN_CHUNK + sizeof(uint16_t) * BIN_CHUNK + 4 * sizeof(uint32_t) * (size_t)nbins;
 }
 
 size_t loglik_smem(int box, int T)
@@ -533,7 +547,7 @@ cudaError_t bin_setup(ppf_ctx *c)
         return e;
     if ((e = dalloc(&c->bin_key, (size_t)c->N)) != cudaSuccess ||
         (e = dalloc(&c->bin_l, (size_t)c->N)) != cudaSuccess ||
-        (e = dalloc(&c->bin_tot, (size_t)c->bin_nbins + 1)) != cudaSuccess ||
+        (e = dalloc(&c->bin_tot, 2 * ((size_t)c->bin_nbins + 1))) != cudaSuccess ||
         (e = dalloc(&c->bin_item, 3 * (size_t)c->bin_items_max)) != cudaSuccess ||
         (e = dalloc(&c->bin_rec, (size_t)c->N)) != cudaSuccess)
         return e;
@@ -570,7 +584,7 @@ cudaError_t bin_set_next(ppf_ctx *c, int binned)
 template <int R>
 static void launch_loglik_r(const CUtensorMap &tm, const BinLikArgs &a, int grid, size_t smem, cudaStream_t s)
 {
-    bin_loglik_kernel<R><<<grid, 256, smem, s>>>(tm, a);
+    launch_pdl(bin_loglik_kernel<R>, grid, 256, smem, s, tm, a);
 }
 
 cudaError_t launch_binned(ppf_ctx *c)
@@ -578,11 +592,10 @@ cudaError_t launch_binned(ppf_ctx *c)
     const int R = c->m.patch_radius;
     const int nb = c->bin_nbins;
     float *dst = c->state[c->cur ^ 1];
-    bin_scan_kernel<<<1, 1024, 0, c->stream>>>(nb, c->bin_tot, c->bin_item, c->bin_items_max, c->sum);
     const int64_t chunks = (c->N + BIN_CHUNK - 1) / BIN_CHUNK;
     const int gscat = (int)(chunks < 4 * (int64_t)c->num_sms ? chunks : 4 * (int64_t)c->num_sms);
-    bin_scatter_kernel<<<gscat, 256, scatter_smem(nb), c->stream>>>(
-        dst, c->N, nb, c->bin_key, c->bin_tot, c->bin_rec, c->sum, &c->sum->flags);
+    launch_pdl(bin_scatter_kernel, gscat, 256, scatter_smem(nb), c->stream, (const float *)dst, c->N, nb, c->bin_key,
+               (const uint32_t *)c->bin_tot, c->bin_tot + nb + 1, c->bin_rec, c->bin_item, c->bin_items_max, c->sum);
     BinLikArgs a;
     memset(&a, 0, sizeof(a));
     a.N = c->N;
@@ -614,7 +627,7 @@ cudaError_t launch_binned(ppf_ctx *c)
     case 7: launch_loglik_r<7>(c->bin_tmap, a, c->bin_grid, smem, c->stream); break;
     default: launch_loglik_r<8>(c->bin_tmap, a, c->bin_grid, smem, c->stream); break;
     }
-    c->launches += 3;
+    c->launches += 2;
     return cudaGetLastError();
 }
 

@@ -38,6 +38,20 @@ __device__ __forceinline__ bool debug_check(bool ok, const int32_t *flags, int32
 #define PPF_DCHECK(cond, flags, bit) true
 #endif
 
+// Programmatic dependent launch: pdl_wait() blocks until the previous kernel
+// of the stream has completed and its writes are visible (a no-op for a
+// kernel launched without the attribute); pdl_trigger() lets the next kernel,
+// if launched with the attribute, be scheduled before this one completes.
+__device__ __forceinline__ void pdl_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 enum : uint32_t { PURPOSE_INIT = 0, PURPOSE_PROP = 1, PURPOSE_RESAMPLE = 2, PURPOSE_GROUP = 3, PURPOSE_RING = 4 };
 
 // One Philox4x32-10 block: ten rounds of two 32x32->64 multiplications of

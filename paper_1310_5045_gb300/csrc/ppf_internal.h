@@ -79,7 +79,7 @@ struct DevSummary {
     // decided by the step's finaliser from the warps it saw spread
     int32_t bin_this, bin_next;
     uint32_t spread_warps, total_warps;
-    uint32_t bin_blocks_done;  // binned path: scan blocks that finished
+    uint32_t bin_blocks_done;  // binned path: scatter blocks that finished
     int32_t n_bin_items;       // binned path: likelihood work items of this step
 };
 
@@ -139,7 +139,7 @@ struct ppf_ctx {
     int32_t bin_T, bin_nx, bin_nbins, bin_grid, bin_items_max;  // bin_grid: blocks of the binned likelihood
     int bin_force;                // -1: chosen per step on the device; 0: direct path; 1: binned path
     uint32_t *bin_key;            // [N] bin of every slot, then the place of its record in bin order
-    uint32_t *bin_tot;            // [nbins + 1] bin sizes, then their exclusive prefix (the scatter's cursors)
+    uint32_t *bin_tot;            // [2 (nbins + 1)] bin sizes, then the scatter's cursors (offsets inside each bin)
     int32_t *bin_item;            // [3 x items_max] work items: bin, first record, count
     float4 *bin_rec;              // [N] records in bin order: (x, y, I0, -)
     float *bin_l;                 // [N] l of every record, in bin order
@@ -159,6 +159,27 @@ struct ppf_ctx {
 
 namespace ppf {
 enum Phase { PH_PREPARE = 0, PH_STEP = 1, PH_FINALIZE = 2, PH_RESAMPLE = 3 };
+
+// A launch that the GPU may schedule while the previous kernel of the stream
+// is still running (programmatic dependent launch): the kernel must execute
+// pdl_wait() before it reads anything the previous kernel writes, and before
+// it returns, so that kernels launched after it still see every earlier one
+// complete.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
 // record the start / end event of a phase when profiling is on
 void prof_mark(ppf_ctx *c, int phase, int end);
 // launchers (each enqueues on ctx->stream; return cudaGetLastError())
@@ -178,6 +199,6 @@ cudaError_t launch_cell_map(ppf_ctx *c);
 int step_grid(ppf_ctx *c);
 // binned likelihood path (ppf_binned.cu)
 cudaError_t bin_setup(ppf_ctx *c);                      // tile geometry, buffers and tensor map (at create)
-cudaError_t launch_binned(ppf_ctx *c);                  // scan, scatter and likelihood (exit early when not chosen)
+cudaError_t launch_binned(ppf_ctx *c);                  // scatter and likelihood (exit early when not chosen)
 cudaError_t bin_set_next(ppf_ctx *c, int binned);       // the path of the next step in auto mode
 }  // namespace ppf

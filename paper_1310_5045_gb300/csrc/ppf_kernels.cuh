@@ -372,17 +372,19 @@ __device__ __forceinline__ uint32_t bin_of(const BinGeom &g, int W, int H, float
 // count as spread (their patch reads touch a separate cache line per lane)
 constexpr int BIN_SPREAD_PX = 64;
 
-// Per warp: the extent of the anchors of the active lanes; one count per
-// warp into the block's counters (its first active lane).  Called on a sample
-// of the iterations (every eighth): the decision needs a fraction, not a census.
+// Per warp: the extent of the anchors of the lanes' sampled particles (one
+// iteration of the step's loop per block; lanes without a sample pass
+// active = false); one count per warp into the counters (lane 0).  Called by
+// all 32 lanes after the loop: the decision needs a fraction, not a census.
 __device__ __forceinline__ void spread_tally(float x, float y, bool active, unsigned &n_spread, unsigned &n_total)
 {
     const bool fin = active && isfinite(x) && isfinite(y) && fabsf(x) < 1e9f && fabsf(y) < 1e9f;
     const int cx = fin ? (int)floorf(x + 0.5f) : 0, cy = fin ? (int)floorf(y + 0.5f) : 0;
-    const unsigned m = __activemask();
+    const unsigned m = 0xffffffffu;
     const int lox = __reduce_min_sync(m, fin ? cx : INT32_MAX), hix = __reduce_max_sync(m, fin ? cx : INT32_MIN);
     const int loy = __reduce_min_sync(m, fin ? cy : INT32_MAX), hiy = __reduce_max_sync(m, fin ? cy : INT32_MIN);
-    if ((threadIdx.x & 31) == (__ffs(m) - 1)) {
+    const bool any_fin = __any_sync(m, fin);
+    if ((threadIdx.x & 31) == 0 && any_fin) {
         n_total += 1u;
         if (lox <= hix && ((int64_t)hix - lox > BIN_SPREAD_PX || (int64_t)hiy - loy > BIN_SPREAD_PX))
             n_spread += 1u;

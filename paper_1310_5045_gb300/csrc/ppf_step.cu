@@ -52,8 +52,8 @@ __global__ void prepare_frame_kernel(const T *__restrict__ Z, float *__restrict_
     // previous step's finaliser decided; and the binned path's counts cleared
     if (blockIdx.x == 0 && threadIdx.x == 0 && sum)
         sum->bin_this = force >= 0 ? force : sum->bin_next;
-    if (bin_tot)
-        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= nbins; t += gridDim.x * blockDim.x)
+    if (bin_tot)  // the bin sizes and the scatter's cursors
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * (nbins + 1); t += gridDim.x * blockDim.x)
             bin_tot[t] = 0u;
     // pixel pairs: element (row, col) = (Zb(row, col), Zb(row, col + 1)) with
     // Zb = Z - bg inside the image and 0 in the border of `pad` (pitch Wp)
@@ -163,6 +163,9 @@ __device__ __forceinline__ void bin_propagate(const StepArgs &a, int mode)
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned ns = 0, nt = 0, it = 0;
+    const uint32_t ts = blockIdx.x % (((uint32_t)N / stride) > 0 ? ((uint32_t)N / stride) : 1u);
+    float tx = 0.0f, ty = 0.0f;
+    bool tok = false;
     uint32_t pn = (i0 < (uint32_t)N) ? ((mode == MODE_CARRY) ? i0 : (uint32_t)__ldg(a.anc + i0)) : 0u;
     for (uint32_t i = i0; i < (uint32_t)N; i += stride, ++it) {
         uint32_t p = pn;
@@ -179,9 +182,13 @@ __device__ __forceinline__ void bin_propagate(const StepArgs &a, int mode)
         const uint32_t key = bin_of<R>(a.bg, a.W, a.H, q.v[0], q.v[1], q.v[4]);
         a.bin_key[i] = key;
         atomicAdd(&shist[key], 1u);
-        if ((it & 7u) == 0u)
-            spread_tally(q.v[0], q.v[1], true, ns, nt);
+        if (it == ts) {
+            tx = q.v[0];
+            ty = q.v[1];
+            tok = true;
+        }
     }
+    spread_tally(tx, ty, tok, ns, nt);
     publish_spread(a.sum, ns, nt);
     __syncthreads();
     for (int t = threadIdx.x; t < nb; t += blockDim.x)
@@ -198,8 +205,12 @@ __device__ __forceinline__ void bin_propagate(const StepArgs &a, int mode)
 // accumulates exactly as the direct path does, so both paths give the same
 // bits for every result of the step.
 template <int R, bool PC>
-__global__ void __launch_bounds__(256) step_kernel(StepArgs a, int phase)
+__global__ void __launch_bounds__(256, 3) step_kernel(StepArgs a, int phase)
 {
+    if (phase == 1)
+        pdl_wait();  // the binned likelihood's l (launched as a dependent of it)
+    else
+        pdl_trigger();  // the binned path's kernels may be scheduled meanwhile
     int mode = a.mode;
     if (mode != MODE_CARRY && *a.degenerate)
         mode = MODE_CARRY;  // the last resample kept every particle
@@ -253,6 +264,11 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a, int phase)
         }
     } else {
         uint32_t pn = (i0 < (uint32_t)N) ? ((mode == MODE_CARRY) ? i0 : (uint32_t)__ldg(a.anc + i0)) : 0u;
+        // the spread statistic samples one iteration per block, blocks spread
+        // over the slots; its anchors are kept and tallied after the loop
+        const uint32_t ts = blockIdx.x % (((uint32_t)N / stride) > 0 ? ((uint32_t)N / stride) : 1u);
+        float tx = 0.0f, ty = 0.0f;
+        bool tok = false;
         unsigned it = 0;
         for (uint32_t i = i0; i < (uint32_t)N; i += stride, ++it) {
             uint32_t p = pn;
@@ -295,11 +311,16 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a, int phase)
                 acc.add_prev_zero();
             else
                 acc.add_prev(lwp);
-            if (!PC && (it & 7u) == 0u)
-                spread_tally(v[0], v[1], true, ns, nt);
+            if (it == ts) {
+                tx = v[0];
+                ty = v[1];
+                tok = true;
+            }
         }
-        if (!PC)
+        if (!PC) {
+            spread_tally(tx, ty, tok, ns, nt);
             publish_spread(a.sum, ns, nt);
+        }
     }
     // block reduction of the partial statistics
 #pragma unroll
@@ -458,7 +479,9 @@ cudaError_t launch_prepare_frame(ppf_ctx *c, const void *frame)
 template <int R>
 static void launch_step_r(const StepArgs &a, int grid, int phase, cudaStream_t s)
 {
-    if (a.lmap)
+    if (phase == 1)  // the binned path's sums: a dependent launch (it waits for the likelihood)
+        launch_pdl(step_kernel<R, false>, grid, 256, 0, s, a, phase);
+    else if (a.lmap)
         step_kernel<R, true><<<grid, 256, 0, s>>>(a, phase);
     else
         step_kernel<R, false><<<grid, 256, 0, s>>>(a, phase);
@@ -520,9 +543,9 @@ cudaError_t launch_step(ppf_ctx *c, int32_t k)
     launch_step_phase(a, c->m.patch_radius, grid, 0, c->stream);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && c->bin_key) {
-        // the binned path's scan, scatter and likelihood, then its sums; all
-        // four return at once when this step takes the direct path
+    if (e == cudaSuccess && c->bin_key && c->bin_force != 0) {  // (a forced direct path needs none of them)
+        // the binned path's scatter and likelihood, then its sums; all three
+        // return at once when this step takes the direct path
         e = launch_binned(c);
         if (e == cudaSuccess) {
             launch_step_phase(a, c->m.patch_radius, grid, 1, c->stream);

@@ -519,3 +519,27 @@ def test_automatic_path_choice(ppf):
     assert e.value.status == ppf.EINVAL
     p2.set_likelihood_path(ppf.PATH_DIRECT)
     p2.close()
+
+
+@pytest.mark.parametrize("path", ["direct", "binned"])
+def test_arna_unequal_groups_and_permuted_ring(ppf, movie, path):
+    """ARNA on an LGS-like layout of unequal groups installed with
+    ppf_set_groups and a permuted ring installed with ppf_set_ring, in
+    lockstep against the oracle: the involved test against each group's own
+    size, the migrant count from the smallest group, the exchange along the
+    permuted ring; ancestors, weights, ring and counts bit-exact."""
+    from gpu_common import lockstep, paired_models
+    gm, om = paired_models(ppf, seed=9)
+    sizes = np.array([2500, 600, 1900, 1300, 3700, 2000, 4384])
+    N = int(sizes.sum())
+    pf = ppf.ParticleFilter(gm, N, group_size=2400)  # ceil(16384 / 2400) = 7 groups
+    G = len(pf.groups()) - 1
+    assert G == len(sizes)
+    pf.set_groups(np.concatenate([[0], np.cumsum(sizes)]))
+    pf.set_ring(np.array([3, 0, 6, 4, 1, 5, 2], dtype=np.int32))
+    pf.set_likelihood_path(ppf.PATH_DIRECT if path == "direct" else ppf.PATH_BINNED)
+    log = []
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), orc.ARNA, K=4, alpha=0.5, log=log)
+    e = pf.estimate()
+    assert e.moved > 0 and e.min_group == 600 and e.max_group == 4384
+    pf.close()

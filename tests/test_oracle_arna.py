@@ -163,6 +163,7 @@ def test_unequal_groups(orc):
     assert rc == 0 and np.array_equal(gout, goff) and np.array_equal(ring_out, ring)
     inv = involved_groups(orc, m, N, frame, goff, lw)
     mig = int(math.floor(0.5 * (G - inv) * 120 / G))
+    assert mig > 0, "the case must move particles for the ring to be tested"
     assert st[4] == inv and st[2] == 740 and st[3] == 120 and st[1] == mig * G
     want_anc, want_lwr = expected_exchange(orc, m, N, frame, goff, lw, mig, ring)
     assert np.array_equal(anc, want_anc) and np.array_equal(lwr, want_lwr)
