@@ -37,9 +37,9 @@ R = 5
 # resample: ancestor 4 + gathered parent x, y, vx, vy, I0 20 + written state 24
 STEP_BYTES = 48
 # measured DRAM bytes per particle of the same kernel (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum, 10th launch at N = 16M, the step kernel's summary under profiles/),
-# scaled to a launch by N; set to None whenever step_kernel changes
-STEP_TRAFFIC_PER_PARTICLE = (351.25e6 + 340.96e6) / 16e6
+# dram__bytes_write.sum, the 5th launch at N = 16M, the step kernel's summary under
+# profiles/), scaled to a launch by N; set to None whenever step_kernel changes
+STEP_TRAFFIC_PER_PARTICLE = (347167744 + 338496768) / 16e6
 # algorithmic FP32 flops per particle of the likelihood + propagation (an FMA
 # counts 2), two counts:
 #  * the expanded form the kernel evaluates, l = I0 (B - I0 C / 2) / sigma_xi^2
@@ -381,7 +381,7 @@ def run_ours(args):
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
                 "bytes_per_particle": STEP_BYTES, "step_kernel_ms": step_ms,
                 "traffic": traffic,
-                "traffic_source": "ncu dram bytes at N=16M scaled by N (profiles/step_kernel_spot512_n16m.md)",
+                "traffic_source": "ncu dram bytes at N=16M scaled by N (profiles/step_kernel_direct_spot512_n8m.md)",
                 "phase_ms_per_step": {kk: prof[kk] / max(1, prof["timed_steps"]) for kk in
                                       ("prepare_ms", "step_ms", "finalize_ms", "resample_ms")}}
     # FP32 peak: FMA chains on every SM (scalar and packed two-lane), timed
