@@ -30,10 +30,11 @@ typedef enum {
     PPF_EINVAL = 1,      /* bad argument (size, radius, pointer, scheme)        */
     PPF_ENOMEM = 2,      /* device or host allocation failed                    */
     PPF_ECUDA = 3,       /* a CUDA runtime call failed (see ppf_last_error)      */
-    PPF_ETIMEOUT = 4,    /* reserved for a bounded device-side wait that gave up
-                            (no kernel of this library waits on another; the
-                            host fault injection PPF_FAULT=timeout makes
-                            ppf_estimate report it)                           */
+    PPF_ETIMEOUT = 4,    /* a bounded device-side wait gave up: the binned
+                            likelihood waits (about a second at most) for the
+                            tensor copies of its tile windows; no kernel waits
+                            on another.  The host fault injection
+                            PPF_FAULT=timeout makes ppf_estimate report it   */
     PPF_EDEGENERATE = 5, /* every weight was zero or NaN: nothing was resampled */
     PPF_ESTATE = 6       /* call out of order (e.g. resample before a step)     */
 } ppf_status;

@@ -68,6 +68,12 @@ void free_all(ppf_ctx *c)
             cudaFree(p);
     if (c->sum_host)
         cudaFreeHost(c->sum_host);
+    if (c->ev_scan)
+        cudaEventDestroy(c->ev_scan);
+    if (c->ev_sched)
+        cudaEventDestroy(c->ev_sched);
+    if (c->side_stream)
+        cudaStreamDestroy(c->side_stream);
     if (c->prof_ev) {
         for (int i = 0; i < 4 * 2 * c->prof_cap; ++i)
             cudaEventDestroy(c->prof_ev[i]);
@@ -233,6 +239,14 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
         chk(dalloc(&c->sc.seg_len, 2 * G + 1), "seg_len");
         chk(dalloc(&c->sc.seg_chunk, 2 * G + 2), "seg_chunk");
         chk(cudaMallocHost((void **)&c->sum_host, sizeof(DevSummary)), "sum_host");
+        {   // the side stream at the highest priority: its one-block schedule is
+            // dispatched before the fill's blocks fill the SMs
+            int lo = 0, hi = 0;
+            chk(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+            chk(cudaStreamCreateWithPriority(&c->side_stream, cudaStreamNonBlocking, hi), "side stream");
+        }
+        chk(cudaEventCreateWithFlags(&c->ev_scan, cudaEventDisableTiming), "event");
+        chk(cudaEventCreateWithFlags(&c->ev_sched, cudaEventDisableTiming), "event");
     }
     if (st == PPF_OK) {
         chk(cudaMemsetAsync(c->sum, 0, sizeof(DevSummary), c->stream), "memset summary");

@@ -108,6 +108,8 @@ struct ppf_ctx {
     int64_t N;
     int32_t group_size, G, T;     // groups, resampling tiles
     cudaStream_t stream;
+    cudaStream_t side_stream;     // the RPA schedule, concurrent with the fill
+    cudaEvent_t ev_scan, ev_sched;  // fork after the tile scan, join before the routing copy
     int device, num_sms;
     float *state[2];              // 6 x N SoA each
     int cur;                      // index of the current particles

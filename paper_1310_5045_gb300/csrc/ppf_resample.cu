@@ -1129,39 +1129,15 @@ cudaError_t resample_kernel_attributes()
     return e;
 }
 
-cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
+// The RPA schedule on the context's side stream, after the tile scan (an
+// event on the main stream), its completion recorded in ev_sched.
+static cudaError_t launch_schedule(ppf_ctx *c, int scheme, bool two_stage)
 {
-    const bool rpa = (scheme != PPF_SYSTEMATIC);
-    const float *lw = c->state[c->cur] + 5 * c->N;
-    const int T = c->T;
-    prof_mark(c, PH_RESAMPLE, 0);
-    c->launches += rpa ? 5 : 3;
-    if (rpa)
-        tile_group_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff,
-                                                                    c->G, c->sc.Cbl);
-    else
-        tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt);
-    const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
-    tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
-        c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sum, ess_thr, c->m.seed,
-        c->m.filter_id, (uint32_t)c->last_frame, c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg, st_tiles,
-        make_divisor((uint32_t)c->N));
-    int32_t *out = rpa ? c->anc_sys : c->anc;
-    const bool two_stage = (scheme >= PPF_RPA2_GS && scheme <= PPF_RPA2_LGS);
-    if (two_stage) {  // stage 2: every group draws its own offspring
-        group_fill_kernel<<<c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
-            lw, c->N, c->goff, c->sc.Tg, c->sum, ess_thr, c->m.seed, c->m.filter_id, (uint32_t)c->last_frame, out);
-    } else {
-        const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
-        fill_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
-            lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile,
-            out);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !rpa) {
-        prof_mark(c, PH_RESAMPLE, 1);
+    cudaError_t e = cudaEventRecord(c->ev_scan, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(c->side_stream, c->ev_scan, 0);
+    if (e != cudaSuccess)
         return e;
-    }
     SchedArgs A;
     A.N = c->N;
     A.G = c->G;
@@ -1181,7 +1157,57 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     const size_t sched_smem = scheme == PPF_RPA_GS || scheme == PPF_RPA2_GS
                                   ? sizeof(int64_t) * (size_t)(c->G > 0 ? c->G : 1)
                                   : SORT_SMEM_BYTES;
-    schedule_kernel<<<1, 1024, sched_smem, c->stream>>>(A);
+    schedule_kernel<<<1, 1024, sched_smem, c->side_stream>>>(A);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaEventRecord(c->ev_sched, c->side_stream);
+    return e;
+}
+
+cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
+{
+    const bool rpa = (scheme != PPF_SYSTEMATIC);
+    const float *lw = c->state[c->cur] + 5 * c->N;
+    const int T = c->T;
+    prof_mark(c, PH_RESAMPLE, 0);
+    c->launches += rpa ? 5 : 3;
+    if (rpa)
+        tile_group_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff,
+                                                                    c->G, c->sc.Cbl);
+    else
+        tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt);
+    const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
+    tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
+        c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sum, ess_thr, c->m.seed,
+        c->m.filter_id, (uint32_t)c->last_frame, c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg, st_tiles,
+        make_divisor((uint32_t)c->N));
+    int32_t *out = rpa ? c->anc_sys : c->anc;
+    const bool two_stage = (scheme >= PPF_RPA2_GS && scheme <= PPF_RPA2_LGS);
+    if (rpa) {
+        // The routing schedule needs only the tile scan (offspring counts per
+        // group), not the fill: it runs on a side stream, one block on one
+        // SM, while the fill runs on the others; the copy joins them.
+        cudaError_t e0 = launch_schedule(c, scheme, two_stage);
+        if (e0 != cudaSuccess)
+            return e0;
+    }
+    if (two_stage) {  // stage 2: every group draws its own offspring
+        group_fill_kernel<<<c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
+            lw, c->N, c->goff, c->sc.Tg, c->sum, ess_thr, c->m.seed, c->m.filter_id, (uint32_t)c->last_frame, out);
+    } else {
+        const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
+        fill_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
+            lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile,
+            out);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !rpa) {
+        prof_mark(c, PH_RESAMPLE, 1);
+        return e;
+    }
+    e = cudaStreamWaitEvent(c->stream, c->ev_sched, 0);  // join the schedule
+    if (e != cudaSuccess)
+        return e;
     const int max_chunks = 2 * c->G + 1 + (int)((c->N + COPY_CHUNK - 1) / COPY_CHUNK);
     const int gcopy = max_chunks < 8 * c->num_sms ? max_chunks : 8 * c->num_sms;
     route_copy_kernel<<<gcopy, 256, 0, c->stream>>>(c->anc_sys, c->anc, c->G, c->sc.seg_chunk,
