@@ -23,7 +23,7 @@ constexpr int TILE = 4096;          // particles per resampling tile (256 thread
 constexpr int TILE_THREADS = 256;
 constexpr int TILE_ITEMS = TILE / TILE_THREADS;
 constexpr int ITEM_TICKETS = 8192;  // tickets per fill work item
-constexpr int COPY_CHUNK = 2048;    // slots per routing-copy work item
+constexpr int COPY_CHUNK = 8192;    // slots per routing-copy work item
 constexpr int MAX_RADIUS = 8;
 constexpr int MAX_SCHED_GROUPS = 16384;
 constexpr int SCAN_SMEM_TILES = 16384;  // tile scan in shared memory up to this many tiles (N <= 67 M)

@@ -70,8 +70,14 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) tile_totals_kernel(const floa
         Qt[blockIdx.x] = total;
 }
 
-// Tile totals for RPA and ARNA: the tile's scan in shared memory gives, for
-// every group start inside the tile, the local prefix before it.
+// Tile totals for RPA and ARNA, and for every group start inside the tile the
+// local prefix before it.  A balanced layout puts one or two group starts in
+// a tile: their prefixes are masked sums of the weights the threads already
+// hold, reduced together with the total.  A tile with more starts (small
+// groups, or the unequal groups LGS leaves) scans its weights in shared
+// memory and reads the prefixes there.
+constexpr int GT_MASKED = 4;  // group starts per tile handled by masked sums
+
 __global__ void __launch_bounds__(TILE_THREADS) tile_group_totals_kernel(
     const float *__restrict__ lw, int64_t N, const DevSummary *__restrict__ sum, double ess_thr,
     uint64_t *__restrict__ Qt, const int64_t *__restrict__ goff, int32_t G, uint64_t *__restrict__ Cbl)
@@ -80,14 +86,12 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_group_totals_kernel(
         return;
     __shared__ uint64_t buf[TILE_SMEM_U64];
     __shared__ uint64_t red[33];
-    __shared__ int32_t gfirst;
+    __shared__ int32_t gfirst, nstart;
+    __shared__ int32_t spos[GT_MASKED];
+    __shared__ uint64_t wsum[TILE_THREADS / 32][GT_MASKED + 1];
     const int64_t lo = (int64_t)blockIdx.x * TILE;
     const int n = (int)(N - lo < TILE ? N - lo : TILE);
-    uint64_t q[TILE_ITEMS];
-    tile_weights(lw, lo, n, sum->M, scale_bits(N), buf, q);
-    const uint64_t total = tile_scan(q, buf, red);
     if (threadIdx.x == 0) {
-        Qt[blockIdx.x] = total;
         // first g with goff[g] >= lo.  For a balanced layout the guess
         // lo G / N or its successor is the answer (two loads); otherwise the
         // guess halves the bracket of the bisection.
@@ -110,7 +114,75 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_group_totals_kernel(
                 b = mid;
         }
         gfirst = a;
+        int ns = 0;  // starts inside the tile (GT_MASKED + 1 means more)
+        for (int32_t gg = a; gg <= G && ns <= GT_MASKED; ++gg) {
+            const int64_t pos = goff[gg];
+            if (pos >= lo + n)
+                break;
+            if (ns < GT_MASKED)
+                spos[ns] = (int)(pos - lo);
+            ++ns;
+        }
+        nstart = ns;
     }
+    __syncthreads();
+    const int ns = nstart;
+    const float M = sum->M;
+    const int s = scale_bits(N);
+    if (ns <= GT_MASKED && n == TILE && ((reinterpret_cast<uintptr_t>(lw + lo) & 15) == 0)) {
+        // thread t holds elements 4 (t + k TILE_THREADS) + j, j < 4
+        constexpr int V = TILE / 4 / TILE_THREADS;
+        const float4 *v4 = reinterpret_cast<const float4 *>(lw + lo) + threadIdx.x;
+        float4 v[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            v[k] = __ldg(v4 + k * TILE_THREADS);
+        uint64_t acc[GT_MASKED + 1] = {0, 0, 0, 0, 0};
+        int p[GT_MASKED];
+#pragma unroll
+        for (int j = 0; j < GT_MASKED; ++j)
+            p[j] = j < ns ? spos[j] : 0;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            uint64_t w[4];
+            quantise2(v[k].x, v[k].y, M, s, w[0], w[1]);
+            quantise2(v[k].z, v[k].w, M, s, w[2], w[3]);
+            const int e0 = 4 * (threadIdx.x + k * TILE_THREADS);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                acc[GT_MASKED] += w[c];
+#pragma unroll
+                for (int j = 0; j < GT_MASKED; ++j)
+                    acc[j] += (e0 + c < p[j]) ? w[c] : 0ull;
+            }
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int j = 0; j <= GT_MASKED; ++j) {
+            uint64_t x = acc[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0)
+                wsum[warp][j] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x <= GT_MASKED) {
+            uint64_t x = 0;
+            for (int w = 0; w < TILE_THREADS / 32; ++w)
+                x += wsum[w][threadIdx.x];
+            if (threadIdx.x == GT_MASKED)
+                Qt[blockIdx.x] = x;
+            else if (threadIdx.x < ns)
+                Cbl[gfirst + threadIdx.x] = x;
+        }
+        return;
+    }
+    uint64_t q[TILE_ITEMS];
+    tile_weights(lw, lo, n, M, s, buf, q);
+    const uint64_t total = tile_scan(q, buf, red);
+    if (threadIdx.x == 0)
+        Qt[blockIdx.x] = total;
     __syncthreads();
     for (int32_t g = gfirst + threadIdx.x; g <= G; g += blockDim.x) {
         const int64_t pos = goff[g];
@@ -829,8 +901,21 @@ __global__ void __launch_bounds__(256) route_copy_kernel(const int32_t *__restri
             if (threadIdx.x == 0)
                 atomicOr(&sum->flags, FLAG_INTERNAL);  // inconsistent schedule: never write out of bounds
         } else {
-            for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x)
-                anc[dst + k] = __ldg(anc_sys + src + k);
+            // four loads in flight per thread before the stores
+            for (int64_t k = k0 + threadIdx.x; k < k1; k += 4 * (int64_t)blockDim.x) {
+                int32_t v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t kk = k + q * (int64_t)blockDim.x;
+                    v[q] = kk < k1 ? __ldg(anc_sys + src + kk) : 0;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t kk = k + q * (int64_t)blockDim.x;
+                    if (kk < k1)
+                        anc[dst + kk] = v[q];
+                }
+            }
         }
         __syncthreads();  // sseg is rewritten for the next item
     }
