@@ -91,6 +91,7 @@ struct Scratch {
     int32_t *item_tile; // [T + ceil(N / ITEM_TICKETS)] tile of every fill work item
     uint64_t *Cbl;     // [G+1] local prefix at group starts (within their tile)
     int64_t *Tg;       // [G+1] tickets below each group start
+    int32_t *tile_g;   // [2T] per tile: first group starting at or after it, group starts inside (capped)
     // scheduler (RPA)
     uint64_t *skey;    // [2G] sort / merge buffers
     int64_t *sval;     // [5G]

@@ -30,6 +30,19 @@ __device__ __forceinline__ bool kept_by_ess(const DevSummary *sum, double ess_th
     return sum->ess >= ess_thr;
 }
 
+// Balanced layout: group g holds n_g = floor(N/G) + [g < N mod G] slots,
+// starting at off_g = g floor(N/G) + min(g, N mod G).
+__device__ __forceinline__ int64_t target_of(int64_t N, int32_t G, int32_t g)
+{
+    return N / G + ((int64_t)g < N % G ? 1 : 0);
+}
+
+__device__ __forceinline__ int64_t balanced_offset(int64_t N, int32_t G, int32_t g)
+{
+    const int64_t q = N / G, r = N % G;
+    return (int64_t)g * q + ((int64_t)g < r ? (int64_t)g : r);
+}
+
 // ---------------------------------------------------------------- R1 tiles
 // Tile totals Q_t: every thread loads its four float4 (coalesced, all in
 // flight together), then quantises them two at a time; one block sum.  No
@@ -75,12 +88,15 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) tile_totals_kernel(const floa
 // a tile: their prefixes are masked sums of the weights the threads already
 // hold, reduced together with the total.  A tile with more starts (small
 // groups, or the unequal groups LGS leaves) scans its weights in shared
-// memory and reads the prefixes there.
+// memory and reads the prefixes there.  Every tile also records the first
+// group starting at or after it and how many start inside it (GT_MASKED + 1
+// meaning more), for the fill's routing of kept tickets.
 constexpr int GT_MASKED = 4;  // group starts per tile handled by masked sums
 
 __global__ void __launch_bounds__(TILE_THREADS) tile_group_totals_kernel(
     const float *__restrict__ lw, int64_t N, const DevSummary *__restrict__ sum, double ess_thr,
-    uint64_t *__restrict__ Qt, const int64_t *__restrict__ goff, int32_t G, uint64_t *__restrict__ Cbl)
+    uint64_t *__restrict__ Qt, const int64_t *__restrict__ goff, int32_t G, uint64_t *__restrict__ Cbl,
+    int32_t *__restrict__ tile_g)
 {
     if (kept_by_ess(sum, ess_thr))
         return;
@@ -91,6 +107,18 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_group_totals_kernel(
     __shared__ uint64_t wsum[TILE_THREADS / 32][GT_MASKED + 1];
     const int64_t lo = (int64_t)blockIdx.x * TILE;
     const int n = (int)(N - lo < TILE ? N - lo : TILE);
+    // the weights first, so that their loads are in flight during the search
+    // thread 0 does for the tile's group starts.  Thread t holds elements
+    // 4 (t + k TILE_THREADS) + j, j < 4.
+    constexpr int V = TILE / 4 / TILE_THREADS;
+    const bool full = n == TILE && ((reinterpret_cast<uintptr_t>(lw + lo) & 15) == 0);
+    float4 v[V];
+    if (full) {
+        const float4 *v4 = reinterpret_cast<const float4 *>(lw + lo) + threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            v[k] = __ldg(v4 + k * TILE_THREADS);
+    }
     if (threadIdx.x == 0) {
         // first g with goff[g] >= lo.  For a balanced layout the guess
         // lo G / N or its successor is the answer (two loads); otherwise the
@@ -124,19 +152,14 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_group_totals_kernel(
             ++ns;
         }
         nstart = ns;
+        tile_g[2 * blockIdx.x] = a;
+        tile_g[2 * blockIdx.x + 1] = ns;
     }
     __syncthreads();
     const int ns = nstart;
     const float M = sum->M;
     const int s = scale_bits(N);
-    if (ns <= GT_MASKED && n == TILE && ((reinterpret_cast<uintptr_t>(lw + lo) & 15) == 0)) {
-        // thread t holds elements 4 (t + k TILE_THREADS) + j, j < 4
-        constexpr int V = TILE / 4 / TILE_THREADS;
-        const float4 *v4 = reinterpret_cast<const float4 *>(lw + lo) + threadIdx.x;
-        float4 v[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k)
-            v[k] = __ldg(v4 + k * TILE_THREADS);
+    if (ns <= GT_MASKED && full) {
         uint64_t acc[GT_MASKED + 1] = {0, 0, 0, 0, 0};
         int p[GT_MASKED];
 #pragma unroll
@@ -336,21 +359,111 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
     }
 }
 
+// ------------------------------------------------ kept tickets, GS and SGS
+// GS and SGS leave every group at its balanced size n_g: a sender keeps n_g
+// of its o_g tickets and sends the rest, a receiver keeps all o_g < n_g and
+// is filled up.  The first keep_g = min(o_g, n_g) tickets of group g (tickets
+// Tg[g] <= j < Tg[g+1], in ticket order) therefore land in slots off_g +
+// (j - Tg[g]) of the balanced layout whatever the schedule pairs; the fill
+// writes them there directly and only the sent tickets go to their ticket
+// slot of anc_sys, for the routing copy of the links.
+constexpr int KT_GROUPS = GT_MASKED + 1;  // groups holding one tile's particles, at most, for the table
+struct KeptTable {
+    int n;                         // groups in the table; -1: too many, look every ticket up
+    int64_t start[KT_GROUPS + 1];  // first ticket of each group, then the end of the last one
+    int64_t keep_end[KT_GROUPS];   // first ticket each group sends
+    int64_t shift[KT_GROUPS];      // a kept ticket j goes to slot j + shift
+};
+
+// ticket_parents_contig with the kept / sent split: per staged chunk, every
+// group's kept piece goes to anc (shifted to its balanced slot) and its sent
+// piece to anc_sys + sent_shift, each as one store_staged run.  With kt.n < 0
+// every ticket finds its group among Tg[0..G] by bisection (a tile crossed by
+// more than KT_GROUPS groups).
+__device__ __forceinline__ void ticket_parents_routed(const uint64_t *C, int n, uint64_t c0, const TicketGrid &tg,
+                                                      int64_t j_lo, int64_t j_hi, uint16_t *stage,
+                                                      const KeptTable &kt, int32_t *__restrict__ anc,
+                                                      int32_t *__restrict__ anc_sys, int64_t sent_shift,
+                                                      int32_t base, int64_t N, int32_t G,
+                                                      const int64_t *__restrict__ Tg, const int32_t *flags)
+{
+    for (int64_t c = j_lo; c < j_hi; c += STAGE_TICKETS) {
+        const int64_t ce = (j_hi - c < STAGE_TICKETS) ? j_hi : c + STAGE_TICKETS;
+        const int m = (int)(ce - c);
+        ticket_parents(C, n, c0, tg, c, m, [&](int64_t j, int i) { stage[j - c] = (uint16_t)i; });
+        __syncthreads();
+        if (kt.n >= 0) {
+            for (int e = 0; e < kt.n; ++e) {
+                const int64_t a0 = c > kt.start[e] ? c : kt.start[e];
+                const int64_t a1 = ce < kt.keep_end[e] ? ce : kt.keep_end[e];
+                if (a0 < a1) {
+                    if (a0 + kt.shift[e] >= 0 && a1 + kt.shift[e] <= N)
+                        store_staged(anc + (a0 + kt.shift[e]), stage + (a0 - c), (int)(a1 - a0), base, n, flags);
+                    else if (threadIdx.x == 0)
+                        atomicOr(const_cast<int32_t *>(flags), FLAG_INTERNAL);  // inconsistent counts: never write out of bounds
+                }
+                const int64_t b0 = c > kt.keep_end[e] ? c : kt.keep_end[e];
+                const int64_t b1 = ce < kt.start[e + 1] ? ce : kt.start[e + 1];
+                if (b0 < b1) {
+                    if (b0 + sent_shift >= 0 && b1 + sent_shift <= N)
+                        store_staged(anc_sys + (b0 + sent_shift), stage + (b0 - c), (int)(b1 - b0), base, n,
+                                     flags);
+                    else if (threadIdx.x == 0)
+                        atomicOr(const_cast<int32_t *>(flags), FLAG_INTERNAL);
+                }
+            }
+        } else {
+            for (int k = threadIdx.x; k < m; k += blockDim.x) {
+                const int64_t j = c + k;
+                int32_t a = 0, b = G - 1;  // the last g with Tg[g] <= j (Tg[0] = 0 <= j)
+                while (a < b) {
+                    const int32_t mid = (a + b + 1) >> 1;
+                    if (__ldg(Tg + mid) <= j)
+                        a = mid;
+                    else
+                        b = mid - 1;
+                }
+                const int64_t s0 = __ldg(Tg + a), o = __ldg(Tg + a + 1) - s0;
+                const int64_t nk = target_of(N, G, a);
+                const int64_t keep = o < nk ? o : nk;
+                const int64_t slot = (j - s0 < keep) ? balanced_offset(N, G, a) + (j - s0) : j + sent_shift;
+                int32_t *dst = (j - s0 < keep) ? anc : anc_sys;
+                if (slot >= 0 && slot < N && PPF_DCHECK(stage[k] < n, flags, FLAG_INTERNAL))
+                    dst[slot] = base + stage[k];
+                else if (slot < 0 || slot >= N)
+                    atomicOr(const_cast<int32_t *>(flags), FLAG_INTERNAL);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- R3 fill
 // Work item b covers tickets [i_lo, i_hi) of one tile (at most ITEM_TICKETS);
 // the tile's cumulative weights are built once in shared memory, the parents
-// of the item's tickets are staged there and written out coalesced.
-// Dynamic shared memory: FILL_SMEM_BYTES.
-__global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
-    const float *__restrict__ lw, int64_t N, int32_t T, Divisor ndiv, const DevSummary *__restrict__ sum,
-    const uint64_t *__restrict__ Ct, const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
-    const int32_t *__restrict__ item_tile, int32_t *__restrict__ out)
+// of the item's tickets are staged there and written out coalesced: to
+// out[j] (systematic, LGS), or split into kept and sent tickets (GS, SGS:
+// kr.anc set).  Dynamic shared memory: FILL_SMEM_BYTES.
+struct KeptRoute {
+    int32_t *anc;           // final ancestors; nullptr: every ticket to out[j]
+    const int64_t *Tg;      // [G+1] tickets below each group start
+    const int32_t *tile_g;  // [2T] per tile: first group starting at or after it, starts inside (capped)
+    int32_t G;
+};
+
+template <bool ROUTE>
+__device__ __forceinline__ void fill_item(const float *__restrict__ lw, int64_t N, int32_t T, Divisor ndiv,
+                                          const DevSummary *__restrict__ sum, const uint64_t *__restrict__ Ct,
+                                          const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
+                                          const int32_t *__restrict__ item_tile, int32_t *__restrict__ out,
+                                          const KeptRoute &kr)
 {
     extern __shared__ uint64_t fill_smem[];
     uint64_t *C = fill_smem;
     uint16_t *stage = reinterpret_cast<uint16_t *>(fill_smem + TILE_SMEM_U64);
     __shared__ uint64_t red[33];
     __shared__ int32_t st;
+    __shared__ KeptTable kt;
     const int32_t b = blockIdx.x;
     if (b >= sum->n_items)
         return;
@@ -365,30 +478,91 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
         }
         st = a;
     }
-    __syncthreads();
+    if (item_tile == nullptr)
+        __syncthreads();
     const int32_t t = item_tile ? item_tile[b] : st;
+    if (ROUTE && threadIdx.x >= blockDim.x - 32) {
+        // the last warp: the groups holding the tile's particles, one lane
+        // each (ga, the group of the tile's first particle, to gb, the last
+        // group starting inside it)
+        const int lane = threadIdx.x & 31;
+        const int32_t gf = __ldg(kr.tile_g + 2 * t), ns = __ldg(kr.tile_g + 2 * t + 1);
+        if (ns > GT_MASKED) {
+            if (lane == 0)
+                kt.n = -1;
+        } else {
+            const int32_t ga = gf > 0 ? gf - 1 : 0, gb = gf + ns - 1;  // gf = 0 only for tile 0, with ns >= 1
+            const int ng = gb - ga + 1;
+            if (lane <= ng) {
+                const int32_t g = ga + lane;
+                const int64_t s0 = __ldg(kr.Tg + g);
+                kt.start[lane] = s0;
+                if (lane < ng) {
+                    const int64_t o = __ldg(kr.Tg + g + 1) - s0, nk = target_of(N, kr.G, g);
+                    kt.keep_end[lane] = s0 + (o < nk ? o : nk);
+                    kt.shift[lane] = balanced_offset(N, kr.G, g) - s0;
+                }
+            }
+            if (lane == 0)
+                kt.n = ng;
+        }
+    }
     const int64_t lo = (int64_t)t * TILE;
     const int n = (int)(N - lo < TILE ? N - lo : TILE);
     uint64_t q[TILE_ITEMS];
-    tile_weights(lw, lo, n, sum->M, scale_bits(N), C, q);
+    tile_weights(lw, lo, n, sum->M, scale_bits(N), C, q);  // its barriers also publish the table
     tile_scan(q, C, red);
     const int64_t i_lo = Tt[t] + (int64_t)(b - item_off[t]) * ITEM_TICKETS;
     const int64_t i_hi = (Tt[t + 1] < i_lo + ITEM_TICKETS) ? Tt[t + 1] : i_lo + ITEM_TICKETS;
     const TicketGrid tg = ticket_grid(sum->Q, sum->u, sum->qN, sum->qR, ndiv);
-    ticket_parents_contig(C, n, Ct[t], tg, i_lo, i_hi, stage, out, (int32_t)lo, N, &sum->flags);
+    if (ROUTE)
+        ticket_parents_routed(C, n, Ct[t], tg, i_lo, i_hi, stage, kt, kr.anc, out, 0, (int32_t)lo, N, kr.G,
+                              kr.Tg, &sum->flags);
+    else
+        ticket_parents_contig(C, n, Ct[t], tg, i_lo, i_hi, stage, out, (int32_t)lo, N, &sum->flags);
+}
+
+__global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
+    const float *__restrict__ lw, int64_t N, int32_t T, Divisor ndiv, const DevSummary *__restrict__ sum,
+    const uint64_t *__restrict__ Ct, const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
+    const int32_t *__restrict__ item_tile, int32_t *__restrict__ out)
+{
+    const KeptRoute none{nullptr, nullptr, nullptr, 0};
+    fill_item<false>(lw, N, T, ndiv, sum, Ct, Tt, item_off, item_tile, out, none);
+}
+
+__global__ void __launch_bounds__(TILE_THREADS) fill_route_kernel(
+    const float *__restrict__ lw, int64_t N, int32_t T, Divisor ndiv, const DevSummary *__restrict__ sum,
+    const uint64_t *__restrict__ Ct, const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
+    const int32_t *__restrict__ item_tile, int32_t *__restrict__ anc_sys, KeptRoute kr)
+{
+    fill_item<true>(lw, N, T, ndiv, sum, Ct, Tt, item_off, item_tile, anc_sys, kr);
 }
 
 // ------------------------------------------------ two-stage RPA, stage 2
-// One block per group: the group's N_g = Tg[g+1] - Tg[g] offspring (stage 1:
-// the global tickets of its cumulative range) drawn again inside the group by
-// its own systematic draw over the same fixed-point weights, offset from
+// Every group g draws its N_g = Tg[g+1] - Tg[g] offspring (stage 1: the
+// global tickets of its cumulative range) again inside the group, by its own
+// systematic draw over the same fixed-point weights with the offset from
 // Philox(seed; g, frame, filter, GROUP).  They are written, in ticket order,
 // where the global draw would have put them (ticket slots Tg[g] ..), so the
-// RPA schedule and routing copy apply unchanged.
+// RPA schedule and routing copy apply unchanged; with kept_anc set (GS, SGS)
+// the group's first keep_g tickets go straight to its balanced slots in
+// kept_anc instead, as in the one-stage fill.
+//
+// The group's total and the cumulative weight below any tile start inside it
+// come from the global prefix of the tile pass (C(p) = Ct[p / TILE] + the
+// local prefix at p; integer sums, so exactly the group's own), which lets a
+// large group be split: blocks 0..G-1 take group g whole when it spans at
+// most two tiles, otherwise its head up to the first tile boundary; block
+// G + t takes tile t when the tile starts strictly inside such a large
+// group, so a group of any size costs about one tile's time.
+constexpr int64_t GROUP_SPLIT = 2 * TILE;
+
 __global__ void __launch_bounds__(TILE_THREADS) group_fill_kernel(
-    const float *__restrict__ lw, int64_t N, const int64_t *__restrict__ goff, const int64_t *__restrict__ Tg,
-    const DevSummary *__restrict__ sum, double ess_thr, uint64_t seed, uint32_t fid, uint32_t frame,
-    int32_t *__restrict__ out)
+    const float *__restrict__ lw, int64_t N, int32_t G, const int64_t *__restrict__ goff,
+    const int64_t *__restrict__ Tg, const uint64_t *__restrict__ Ct, const uint64_t *__restrict__ Cbl,
+    const int32_t *__restrict__ tile_g, const DevSummary *__restrict__ sum, double ess_thr, uint64_t seed,
+    uint32_t fid, uint32_t frame, int32_t *__restrict__ out, int32_t *__restrict__ kept_anc)
 {
     if (kept_by_ess(sum, ess_thr) || sum->degenerate)
         return;  // kept by the N_eff test, or no usable weight (the schedule keeps the layout)
@@ -396,44 +570,95 @@ __global__ void __launch_bounds__(TILE_THREADS) group_fill_kernel(
     uint64_t *C = fill_smem;
     uint16_t *stage = reinterpret_cast<uint16_t *>(fill_smem + TILE_SMEM_U64);
     __shared__ uint64_t red[33];
-    __shared__ uint64_t us, qNs;
+    __shared__ uint64_t us, qNs, Qgs, carry0s;
     __shared__ uint32_t qRs;
     __shared__ Divisor dvs;
-    const int32_t g = blockIdx.x;
-    const int64_t lo = goff[g], sz = goff[g + 1] - lo;
-    const int64_t nt = Tg[g + 1] - Tg[g];
-    if (sz <= 0 || nt <= 0)
-        return;
-    const float M = sum->M;
-    const int s = scale_bits(N);
-    // the group's total fixed-point weight
-    uint64_t qs = 0;
-    for (int64_t i = threadIdx.x; i < sz; i += blockDim.x)
-        qs += quantise(__ldg(lw + lo + i), M, s);
-    uint64_t Qg;
-    block_excl_scan_u64(qs, red, &Qg);
+    __shared__ int32_t gs;
+    __shared__ int64_t p0s, p1s;
     if (threadIdx.x == 0) {
-        us = ticket_offset(seed, fid, frame, PURPOSE_GROUP, (uint32_t)g, Qg);
-        dvs = make_divisor((uint32_t)nt);
-        qNs = Qg / (uint64_t)nt;
-        qRs = (uint32_t)(Qg % (uint64_t)nt);
+        int32_t g = -1;
+        int64_t p0 = 0, p1 = 0;
+        uint64_t carry0 = 0;
+        if ((int32_t)blockIdx.x < G) {
+            g = blockIdx.x;
+            p0 = goff[g];
+            p1 = goff[g + 1];
+            if (p1 - p0 > GROUP_SPLIT)
+                p1 = (p0 / TILE + 1) * TILE;  // the head; the tile blocks take the rest
+        } else {
+            const int32_t t = blockIdx.x - G;
+            const int64_t lo = (int64_t)t * TILE;
+            const int32_t gf = tile_g[2 * t];  // first group starting at or after lo
+            if (gf > 0 && goff[gf] > lo) {     // lo lies strictly inside group gf - 1
+                const int32_t gc = gf - 1;
+                const int64_t a = goff[gc], e = goff[gc + 1];
+                if (e - a > GROUP_SPLIT) {
+                    g = gc;
+                    p0 = lo;
+                    p1 = (lo + TILE < e) ? lo + TILE : e;
+                    carry0 = Ct[t] - (Ct[a / TILE] + Cbl[gc]);
+                }
+            }
+        }
+        gs = g;
+        if (g >= 0) {
+            const uint64_t Q = sum->Q;
+            const int64_t a = goff[g], e = goff[g + 1];
+            const uint64_t ca = (a >= N) ? Q : Ct[a / TILE] + Cbl[g];
+            const uint64_t ce = (e >= N) ? Q : Ct[e / TILE] + Cbl[g + 1];
+            const uint64_t Qg = ce - ca;
+            const int64_t nt = Tg[g + 1] - Tg[g];
+            Qgs = Qg;
+            p0s = p0;
+            p1s = p1;
+            carry0s = carry0;
+            if (nt > 0 && Qg > 0) {
+                us = ticket_offset(seed, fid, frame, PURPOSE_GROUP, (uint32_t)g, Qg);
+                dvs = make_divisor((uint32_t)nt);
+                qNs = Qg / (uint64_t)nt;
+                qRs = (uint32_t)(Qg % (uint64_t)nt);
+            } else {
+                gs = -1;  // no offspring, or no weight to draw them from
+            }
+        }
     }
     __syncthreads();
-    const uint64_t u = us;
+    const int32_t g = gs;
+    if (g < 0)
+        return;
+    const int64_t p0 = p0s, p1 = p1s;
+    const int64_t nt = Tg[g + 1] - Tg[g];
+    const uint64_t Qg = Qgs, u = us;
+    const float M = sum->M;
+    const int s = scale_bits(N);
     const TicketGrid tg = ticket_grid(Qg, u, qNs, qRs, dvs);
     int32_t *__restrict__ dst = out + Tg[g];
-    // chunks of TILE particles; the local tickets of chunk [c0, c0 + n) are
-    // [T(carry), T(carry + total)) with T the count below of the nt tickets
-    uint64_t carry = 0;
-    for (int64_t c0 = 0; c0 < sz; c0 += TILE) {
-        const int n = (int)(sz - c0 < TILE ? sz - c0 : TILE);
+    KeptTable kt;  // one group, in local ticket numbers
+    kt.n = 1;
+    kt.start[0] = 0;
+    kt.start[1] = nt;
+    {
+        const int64_t nk = target_of(N, G, g);
+        kt.keep_end[0] = nt < nk ? nt : nk;
+        kt.shift[0] = balanced_offset(N, G, g);
+    }
+    // chunks of at most TILE particles; the local tickets of a chunk with
+    // cumulative weight [carry, carry + total) inside the group are
+    // [T(carry), T(carry + total)), T the count below of the nt tickets
+    uint64_t carry = carry0s;
+    for (int64_t c0 = p0; c0 < p1; c0 += TILE) {
+        const int n = (int)(p1 - c0 < TILE ? p1 - c0 : TILE);
         uint64_t q[TILE_ITEMS];
-        tile_weights(lw, lo + c0, n, M, s, C, q);
+        tile_weights(lw, c0, n, M, s, C, q);
         const uint64_t tot = tile_scan(q, C, red);
         const int64_t t_lo = tickets_below(carry, nt, u, Qg);
         const int64_t t_hi = tickets_below(carry + tot, nt, u, Qg);
-        ticket_parents_contig(C, n, carry, tg, t_lo, t_hi, stage, dst, (int32_t)(lo + c0),
-                              (nt < N - Tg[g]) ? nt : N - Tg[g], &sum->flags);
+        if (kept_anc)
+            ticket_parents_routed(C, n, carry, tg, t_lo, t_hi, stage, kt, kept_anc, out, Tg[g], (int32_t)c0, N, G,
+                                  Tg, &sum->flags);
+        else
+            ticket_parents_contig(C, n, carry, tg, t_lo, t_hi, stage, dst, (int32_t)c0,
+                                  (nt < N - Tg[g]) ? nt : N - Tg[g], &sum->flags);
         carry += tot;
         __syncthreads();
     }
@@ -459,12 +684,8 @@ struct SchedArgs {
     int32_t *seg_chunk; // [2G + 2]
     int64_t *seg_tick, *seg_dst, *seg_len;  // [2G + 1]
     DevSummary *sum;
+    int links_only;  // the fill wrote the kept segments already: copy work items for the links only
 };
-
-__device__ __forceinline__ int64_t target_of(int64_t N, int32_t G, int32_t g)
-{
-    return N / G + ((int64_t)g < N % G ? 1 : 0);
-}
 
 // block-wide exclusive scan of an int64 array in place (single block)
 __device__ void block_scan_i64(int64_t *a, int n, uint64_t *red, int64_t *total_out)
@@ -831,7 +1052,8 @@ __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
         for (int k = 0; k < per; ++k) {
             const int i = i0 + k;
             if (i < nseg) {
-                c += (uint64_t)((seg_len[i] + COPY_CHUNK - 1) / COPY_CHUNK);
+                if (i >= G || !A.links_only)
+                    c += (uint64_t)((seg_len[i] + COPY_CHUNK - 1) / COPY_CHUNK);
                 if (i >= G)
                     mv += (uint64_t)seg_len[i];
             }
@@ -843,7 +1065,8 @@ __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
             const int i = i0 + k;
             if (i < nseg) {
                 A.seg_chunk[i] = (int32_t)run;
-                run += (uint64_t)((seg_len[i] + COPY_CHUNK - 1) / COPY_CHUNK);
+                if (i >= G || !A.links_only)
+                    run += (uint64_t)((seg_len[i] + COPY_CHUNK - 1) / COPY_CHUNK);
             }
         }
         if (threadIdx.x == 0) {
@@ -1198,6 +1421,9 @@ cudaError_t resample_kernel_attributes()
     cudaError_t e = cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)FILL_SMEM_BYTES);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fill_route_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FILL_SMEM_BYTES);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(rna_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILL_SMEM_BYTES);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(group_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1237,6 +1463,7 @@ static cudaError_t launch_schedule(ppf_ctx *c, int scheme, bool two_stage)
     A.seg_dst = c->sc.seg_dst;
     A.seg_len = c->sc.seg_len;
     A.sum = c->sum;
+    A.links_only = A.scheme != PPF_RPA_LGS;
     // Greedy needs no sort: shared memory only for its two prefix arrays (at
     // most G words), which leaves the rest of the SM's L1 to the global reads
     const size_t sched_smem = scheme == PPF_RPA_GS || scheme == PPF_RPA2_GS
@@ -1258,7 +1485,7 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     c->launches += rpa ? 5 : 3;
     if (rpa)
         tile_group_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff,
-                                                                    c->G, c->sc.Cbl);
+                                                                    c->G, c->sc.Cbl, c->sc.tile_g);
     else
         tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt);
     const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
@@ -1276,14 +1503,24 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
         if (e0 != cudaSuccess)
             return e0;
     }
+    // GS and SGS: the kept tickets go straight to their balanced slots
+    const bool kept_direct = rpa && scheme != PPF_RPA_LGS && scheme != PPF_RPA2_LGS;
     if (two_stage) {  // stage 2: every group draws its own offspring
-        group_fill_kernel<<<c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
-            lw, c->N, c->goff, c->sc.Tg, c->sum, ess_thr, c->m.seed, c->m.filter_id, (uint32_t)c->last_frame, out);
+        group_fill_kernel<<<c->G + T, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
+            lw, c->N, c->G, c->goff, c->sc.Tg, c->sc.Ct, c->sc.Cbl, c->sc.tile_g, c->sum, ess_thr, c->m.seed,
+            c->m.filter_id, (uint32_t)c->last_frame, out, kept_direct ? c->anc : nullptr);
     } else {
         const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
-        fill_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
-            lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile,
-            out);
+        if (kept_direct) {
+            const KeptRoute kr{c->anc, c->sc.Tg, c->sc.tile_g, c->G};
+            fill_route_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
+                lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, c->sc.item_off,
+                c->sc.item_tile, out, kr);
+        } else {
+            fill_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
+                lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, c->sc.item_off,
+                c->sc.item_tile, out);
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !rpa) {
@@ -1323,7 +1560,7 @@ cudaError_t launch_resample_arna(ppf_ctx *c, float alpha, double ess_thr)
     const int T = c->T;
     prof_mark(c, PH_RESAMPLE, 0);
     tile_group_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff, c->G,
-                                                                c->sc.Cbl);
+                                                                c->sc.Cbl, c->sc.tile_g);
     const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
     tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
         c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, nullptr, c->sum, ess_thr, c->m.seed, c->m.filter_id,

@@ -257,11 +257,34 @@ __device__ __forceinline__ void ticket_parents_staged(const uint64_t *C, int n, 
     }
 }
 
-// ticket_parents_staged for the common contiguous output out[j] = base + i:
-// the staged chunk is written as 16-byte int4 stores (after up to three
-// single stores that reach 16-byte alignment), four tickets per thread and
-// iteration.  The debug build checks every ticket's slot against [0, j_max)
-// and its parent against [0, n).
+// Writes o[k] = base + st[k] for k < m, called by every thread of the block:
+// up to three single stores reach a 16-byte boundary of o, then four tickets
+// per thread and iteration as int4.  The debug build checks every parent
+// against [0, n).
+__device__ __forceinline__ void store_staged(int32_t *__restrict__ o, const uint16_t *st, int m, int32_t base,
+                                             int n, const int32_t *flags)
+{
+    const int head = (int)((4u - ((uint32_t)(reinterpret_cast<uintptr_t>(o) >> 2) & 3u)) & 3u);
+    const int h = head < m ? head : m;
+    const int m4 = (m - h) >> 2;
+    const int t0 = h + 4 * m4;
+    const int k = threadIdx.x;
+    if (k < h && PPF_DCHECK(st[k] < n, flags, FLAG_INTERNAL))
+        o[k] = base + st[k];
+    int4 *o4 = reinterpret_cast<int4 *>(o + h);
+    for (int q = k; q < m4; q += blockDim.x) {
+        const int e = h + 4 * q;
+        const int32_t p0 = st[e], p1 = st[e + 1], p2 = st[e + 2], p3 = st[e + 3];
+        if (PPF_DCHECK(p0 < n && p1 < n && p2 < n && p3 < n, flags, FLAG_INTERNAL))
+            o4[q] = make_int4(base + p0, base + p1, base + p2, base + p3);
+    }
+    if (k < m - t0 && PPF_DCHECK(st[t0 + k] < n, flags, FLAG_INTERNAL))
+        o[t0 + k] = base + st[t0 + k];
+}
+
+// ticket_parents_staged for the common contiguous output out[j] = base + i,
+// each staged chunk written by store_staged.  The debug build checks every
+// ticket's slot against [0, j_max).
 __device__ __forceinline__ void ticket_parents_contig(const uint64_t *C, int n, uint64_t c0, const TicketGrid &tg,
                                                       int64_t j_lo, int64_t j_hi, uint16_t *stage,
                                                       int32_t *__restrict__ out, int32_t base, int64_t j_max,
@@ -272,27 +295,8 @@ __device__ __forceinline__ void ticket_parents_contig(const uint64_t *C, int n, 
         const int m = (int)(ce - c);
         ticket_parents(C, n, c0, tg, c, m, [&](int64_t j, int i) { stage[j - c] = (uint16_t)i; });
         __syncthreads();
-        if (!PPF_DCHECK(c >= 0 && ce <= j_max, flags, FLAG_INTERNAL)) {
-            __syncthreads();
-            continue;
-        }
-        int32_t *o = out + c;
-        const int head = (int)((4u - ((uint32_t)(reinterpret_cast<uintptr_t>(o) >> 2) & 3u)) & 3u);
-        const int h = head < m ? head : m;
-        const int m4 = (m - h) >> 2;
-        const int t0 = h + 4 * m4;
-        const int k = threadIdx.x;
-        if (k < h && PPF_DCHECK(stage[k] < n, flags, FLAG_INTERNAL))
-            o[k] = base + stage[k];
-        int4 *o4 = reinterpret_cast<int4 *>(o + h);
-        for (int q = k; q < m4; q += blockDim.x) {
-            const int e = h + 4 * q;
-            const int32_t p0 = stage[e], p1 = stage[e + 1], p2 = stage[e + 2], p3 = stage[e + 3];
-            if (PPF_DCHECK(p0 < n && p1 < n && p2 < n && p3 < n, flags, FLAG_INTERNAL))
-                o4[q] = make_int4(base + p0, base + p1, base + p2, base + p3);
-        }
-        if (k < m - t0 && PPF_DCHECK(stage[t0 + k] < n, flags, FLAG_INTERNAL))
-            o[t0 + k] = base + stage[t0 + k];
+        if (PPF_DCHECK(c >= 0 && ce <= j_max, flags, FLAG_INTERNAL))
+            store_staged(out + c, stage, m, base, n, flags);
         __syncthreads();
     }
 }

@@ -4,8 +4,8 @@ times.  Propagation and likelihood are checked on sampled slots that the
 oracle computes one by one; normalisation, estimate and log-evidence by the
 oracle's FP64 summary over all particles (same log-weight inputs, exact bound
 as in gpu_common); the ancestors and group offsets bit-exactly for systematic,
-RPA-LGS, RNA, two-stage RPA-GS and ARNA resampling (the oracle resamples all
-38 M weights)."""
+RPA-LGS, RPA-SGS, two-stage RPA-LGS, RNA, two-stage RPA-GS and ARNA
+resampling (the oracle resamples all 38 M weights)."""
 import math
 
 import numpy as np
@@ -29,7 +29,7 @@ def setup():
         pytest.skip("needs ~8 GB of free device memory")
     import paper_1310_5045_gb300 as ppf
     from gpu_common import paired_models
-    mv, p = synth.preset("spot512_k50", seed=0, K=5)
+    mv, p = synth.preset("spot512_k50", seed=0, K=7)
     gm, om = paired_models(ppf, width=512, height=512, patch_radius=5, psf_sigma=float(p["sigma"]),
                            amplitude=float(p["amplitude"]), seed=0)
     frames = torch.from_numpy(mv.frames).cuda()
@@ -102,11 +102,15 @@ def one_frame(ppf, pf, gm, om, mv, frames, k, scheme, alpha=0.1, n_sample=20000)
 
 def test_full_size_frames(setup):
     ppf, pf, gm, om, mv, frames = setup
+    # LGS leaves unequal groups: the one-stage SGS and two-stage GS frames
+    # after it route their kept tickets from tiles crossed by unequal groups
     one_frame(ppf, pf, gm, om, mv, frames, 1, orc.SYSTEMATIC)
     one_frame(ppf, pf, gm, om, mv, frames, 2, orc.RPA_LGS)
-    est = one_frame(ppf, pf, gm, om, mv, frames, 3, orc.RNA, alpha=0.1)
+    one_frame(ppf, pf, gm, om, mv, frames, 3, orc.RPA_SGS)
+    one_frame(ppf, pf, gm, om, mv, frames, 4, orc.RPA2_LGS)
+    est = one_frame(ppf, pf, gm, om, mv, frames, 5, orc.RNA, alpha=0.1)
     assert math.isfinite(est.log_evidence)
-    est = one_frame(ppf, pf, gm, om, mv, frames, 4, orc.RPA2_GS)
+    est = one_frame(ppf, pf, gm, om, mv, frames, 6, orc.RPA2_GS)
     assert math.isfinite(est.log_evidence)
-    est = one_frame(ppf, pf, gm, om, mv, frames, 5, orc.ARNA, alpha=0.5)
+    est = one_frame(ppf, pf, gm, om, mv, frames, 7, orc.ARNA, alpha=0.5)
     assert math.isfinite(est.log_evidence)

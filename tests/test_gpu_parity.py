@@ -58,6 +58,26 @@ def test_lockstep_frames(ppf, movie, scheme, N, gs):
     pf.close()
 
 
+@pytest.mark.parametrize("N,gs", [(16384, 4096), (20000, 1500), (10000, 777), (9001, 5000), (40000, 20000),
+                                  (50001, 12345)])
+def test_rpa_schemes_in_sequence(ppf, movie, N, gs):
+    """GS and SGS write every group's kept tickets straight to its balanced
+    slots and copy only the links; LGS leaves unequal groups, so the GS and
+    SGS frames after it start from tiles crossed by several groups of
+    different sizes (the per-tile table, and the per-ticket lookup where more
+    than five groups cross a tile).  Groups above two tiles (the last two
+    sizes, and those LGS grows) are drawn by the two-stage fill one tile per
+    block."""
+    from gpu_common import lockstep, paired_models
+    gm, om = paired_models(ppf, seed=5)
+    pf = ppf.ParticleFilter(gm, N, group_size=gs)
+    seq = [orc.RPA_LGS, orc.RPA_GS, orc.RPA_LGS, orc.RPA_LGS, orc.RPA_SGS, orc.RPA2_LGS]
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), seq, K=6)
+    seq = [orc.RPA_LGS, orc.RPA2_GS, orc.RPA2_LGS, orc.RPA2_SGS, orc.RPA_GS, orc.SYSTEMATIC]
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), seq, K=6)
+    pf.close()
+
+
 @pytest.mark.parametrize("scheme", [orc.SYSTEMATIC, orc.RPA_SGS, orc.RNA, orc.RPA2_GS, orc.ARNA])
 def test_ess_gated_resampling(ppf, scheme):
     """Alg. 1's N_eff test on the device: with sigma_xi^2 = 2000 and a
