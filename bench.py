@@ -632,7 +632,7 @@ def run_ours(args):
     return 0
 
 
-PROFILE_CASES = ("step", "rpa_gs", "rpa_sgs", "rpa_lgs", "rpa2_lgs", "rna", "arna", "binned", "pcsir", "grad",
+PROFILE_CASES = ("step", "rpa_gs", "rpa_sgs", "rpa_lgs", "rpa2_gs", "rpa2_lgs", "rna", "arna", "binned", "pcsir", "grad",
                  "batch")
 
 

@@ -61,7 +61,7 @@ void free_all(ppf_ctx *c)
     void *ptrs[] = {c->tang[0], c->tang[1], c->gpart,
                     c->state[0], c->state[1], c->anc, c->anc_sys, c->lwp, c->goff, c->goff_new, c->ring, c->succ, c->Zp,
                     c->frame_buf[0], c->frame_buf[1], c->lmap, c->part, c->sum, c->est_dev, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sc.Cbl,
-                    c->sc.Tg, c->sc.tile_g, c->sc.skey, c->sc.sval, c->sc.seg_tick, c->sc.seg_dst, c->sc.seg_len,
+                    c->sc.Tg, c->sc.tile_g, c->sc.ggrid, c->sc.split, c->sc.skey, c->sc.sval, c->sc.seg_tick, c->sc.seg_dst, c->sc.seg_len,
                     c->sc.seg_chunk, c->bin_key, c->bin_l, c->bin_tot, c->bin_item, c->bin_rec};
     for (void *p : ptrs)
         if (p)
@@ -233,6 +233,8 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
         chk(dalloc(&c->sc.Cbl, G + 1), "Cbl");
         chk(dalloc(&c->sc.Tg, G + 1), "Tg");
         chk(dalloc(&c->sc.tile_g, 2 * T), "tile groups");
+        chk(dalloc(&c->sc.ggrid, G), "group draws");
+        chk(dalloc(&c->sc.split, 2 * (T + N / ppf::ITEM_TICKETS + 1)), "split items");
         chk(dalloc(&c->sc.skey, 2 * G), "skey");
         chk(dalloc(&c->sc.sval, 5 * G), "sval");
         chk(dalloc(&c->sc.seg_tick, 2 * G + 1), "seg_tick");

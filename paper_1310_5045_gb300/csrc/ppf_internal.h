@@ -81,6 +81,18 @@ struct DevSummary {
     uint32_t spread_warps, total_warps;
     uint32_t bin_blocks_done;  // binned path: scatter blocks that finished
     int32_t n_bin_items;       // binned path: likelihood work items of this step
+    int32_t n_split;           // two-stage RPA: extra work items of large or heavy groups
+};
+
+// two-stage RPA: one group's own systematic draw (see group_grid_kernel)
+struct GroupGrid {
+    uint64_t Ca;   // cumulative fixed-point weight below the group
+    uint64_t Q;    // the group's total
+    uint64_t u;    // its ticket offset
+    uint64_t qN;   // Q = qN nt + qR
+    uint64_t dm;   // floor((2^64 - 1) / nt)
+    uint32_t qR;
+    uint32_t nt;   // its offspring count (0: nothing to draw)
 };
 
 struct Scratch {
@@ -92,6 +104,8 @@ struct Scratch {
     uint64_t *Cbl;     // [G+1] local prefix at group starts (within their tile)
     int64_t *Tg;       // [G+1] tickets below each group start
     int32_t *tile_g;   // [2T] per tile: first group starting at or after it, group starts inside (capped)
+    GroupGrid *ggrid;  // [G]  two-stage RPA: every group's draw
+    int32_t *split;    // [2 (T + N / ITEM_TICKETS + 1)] two-stage RPA: extra work items (interior tile or -run, group)
     // scheduler (RPA)
     uint64_t *skey;    // [2G] sort / merge buffers
     int64_t *sval;     // [5G]

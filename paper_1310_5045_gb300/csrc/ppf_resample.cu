@@ -30,17 +30,26 @@ __device__ __forceinline__ bool kept_by_ess(const DevSummary *sum, double ess_th
     return sum->ess >= ess_thr;
 }
 
-// Balanced layout: group g holds n_g = floor(N/G) + [g < N mod G] slots,
-// starting at off_g = g floor(N/G) + min(g, N mod G).
-__device__ __forceinline__ int64_t target_of(int64_t N, int32_t G, int32_t g)
+// Balanced layout: group g holds n_g = q + [g < r] slots, q = floor(N/G) and
+// r = N mod G (divided once on the host: 64-bit division is a long software
+// sequence on the device), starting at off_g = g q + min(g, r).
+struct Balanced {
+    int64_t q, r;
+};
+
+inline Balanced balanced_layout(int64_t N, int32_t G)
 {
-    return N / G + ((int64_t)g < N % G ? 1 : 0);
+    return Balanced{N / G, N % G};
 }
 
-__device__ __forceinline__ int64_t balanced_offset(int64_t N, int32_t G, int32_t g)
+__device__ __forceinline__ int64_t target_of(const Balanced &b, int32_t g)
 {
-    const int64_t q = N / G, r = N % G;
-    return (int64_t)g * q + ((int64_t)g < r ? (int64_t)g : r);
+    return b.q + ((int64_t)g < b.r ? 1 : 0);
+}
+
+__device__ __forceinline__ int64_t balanced_offset(const Balanced &b, int32_t g)
+{
+    return (int64_t)g * b.q + ((int64_t)g < b.r ? (int64_t)g : b.r);
 }
 
 // ---------------------------------------------------------------- R1 tiles
@@ -93,7 +102,41 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) tile_totals_kernel(const floa
 // meaning more), for the fill's routing of kept tickets.
 constexpr int GT_MASKED = 4;  // group starts per tile handled by masked sums
 
-__global__ void __launch_bounds__(TILE_THREADS) tile_group_totals_kernel(
+// The thread's part of the tile total (acc[GT_MASKED]) and of the prefix
+// before each of the NS group starts at local positions spos[j] (acc[j]).
+// Thread t holds the quads 4 (t + k TILE_THREADS) .. + 3: a quad lies wholly
+// below or above a start except the one quad that holds it, so each start
+// costs a select of the quad's sum, and the partial quad a few more.
+template <int NS>
+__device__ __forceinline__ void masked_sums(const float4 (&v)[TILE / 4 / TILE_THREADS], const int32_t *spos, float M,
+                                            int s, uint64_t (&acc)[GT_MASKED + 1])
+{
+    constexpr int V = TILE / 4 / TILE_THREADS;
+    int p[NS > 0 ? NS : 1];
+#pragma unroll
+    for (int j = 0; j < NS; ++j)
+        p[j] = spos[j];
+#pragma unroll
+    for (int j = 0; j <= GT_MASKED; ++j)
+        acc[j] = 0;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        uint64_t w0, w1, w2, w3;
+        quantise2(v[k].x, v[k].y, M, s, w0, w1);
+        quantise2(v[k].z, v[k].w, M, s, w2, w3);
+        const uint64_t w01 = w0 + w1, qs = w01 + w2 + w3;
+        acc[GT_MASKED] += qs;
+        const int e0 = 4 * ((int)threadIdx.x + k * TILE_THREADS);
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            const int d = p[j] - e0;  // elements of the quad below start j
+            const uint64_t part = d >= 4 ? qs : (d == 3 ? w01 + w2 : (d == 2 ? w01 : (d == 1 ? w0 : 0ull)));
+            acc[j] += d > 0 ? part : 0ull;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TILE_THREADS, 5) tile_group_totals_kernel(
     const float *__restrict__ lw, int64_t N, const DevSummary *__restrict__ sum, double ess_thr,
     uint64_t *__restrict__ Qt, const int64_t *__restrict__ goff, int32_t G, uint64_t *__restrict__ Cbl,
     int32_t *__restrict__ tile_g)
@@ -160,40 +203,32 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_group_totals_kernel(
     const float M = sum->M;
     const int s = scale_bits(N);
     if (ns <= GT_MASKED && full) {
-        uint64_t acc[GT_MASKED + 1] = {0, 0, 0, 0, 0};
-        int p[GT_MASKED];
-#pragma unroll
-        for (int j = 0; j < GT_MASKED; ++j)
-            p[j] = j < ns ? spos[j] : 0;
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            uint64_t w[4];
-            quantise2(v[k].x, v[k].y, M, s, w[0], w[1]);
-            quantise2(v[k].z, v[k].w, M, s, w[2], w[3]);
-            const int e0 = 4 * (threadIdx.x + k * TILE_THREADS);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                acc[GT_MASKED] += w[c];
-#pragma unroll
-                for (int j = 0; j < GT_MASKED; ++j)
-                    acc[j] += (e0 + c < p[j]) ? w[c] : 0ull;
-            }
+        uint64_t acc[GT_MASKED + 1];
+        switch (ns) {  // uniform over the block: only the starts the tile has
+        case 0: masked_sums<0>(v, spos, M, s, acc); break;
+        case 1: masked_sums<1>(v, spos, M, s, acc); break;
+        case 2: masked_sums<2>(v, spos, M, s, acc); break;
+        case 3: masked_sums<3>(v, spos, M, s, acc); break;
+        default: masked_sums<4>(v, spos, M, s, acc); break;
         }
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
         for (int j = 0; j <= GT_MASKED; ++j) {
-            uint64_t x = acc[j];
+            if (j < ns || j == GT_MASKED) {
+                uint64_t x = acc[j];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0)
-                wsum[warp][j] = x;
+                for (int o = 16; o > 0; o >>= 1)
+                    x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 0)
+                    wsum[warp][j] = x;
+            }
         }
         __syncthreads();
         if (threadIdx.x <= GT_MASKED) {
             uint64_t x = 0;
-            for (int w = 0; w < TILE_THREADS / 32; ++w)
-                x += wsum[w][threadIdx.x];
+            if (threadIdx.x < ns || threadIdx.x == GT_MASKED)
+                for (int w = 0; w < TILE_THREADS / 32; ++w)
+                    x += wsum[w][threadIdx.x];
             if (threadIdx.x == GT_MASKED)
                 Qt[blockIdx.x] = x;
             else if (threadIdx.x < ns)
@@ -235,6 +270,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
     __shared__ uint64_t red[33];
     __shared__ uint64_t su, s_qN;
     __shared__ uint32_t s_qR;
+    if (threadIdx.x == 0)
+        sum->n_split = 0;  // the two-stage draw's split list is rebuilt after the scan
     if (kept_by_ess(sum, ess_thr)) {  // N_eff test: keep the particles and the layout
         if (threadIdx.x == 0) {
             sum->degenerate = 1;
@@ -384,7 +421,7 @@ __device__ __forceinline__ void ticket_parents_routed(const uint64_t *C, int n, 
                                                       int64_t j_lo, int64_t j_hi, uint16_t *stage,
                                                       const KeptTable &kt, int32_t *__restrict__ anc,
                                                       int32_t *__restrict__ anc_sys, int64_t sent_shift,
-                                                      int32_t base, int64_t N, int32_t G,
+                                                      int32_t base, int64_t N, int32_t G, const Balanced &bl,
                                                       const int64_t *__restrict__ Tg, const int32_t *flags)
 {
     for (int64_t c = j_lo; c < j_hi; c += STAGE_TICKETS) {
@@ -424,9 +461,9 @@ __device__ __forceinline__ void ticket_parents_routed(const uint64_t *C, int n, 
                         b = mid - 1;
                 }
                 const int64_t s0 = __ldg(Tg + a), o = __ldg(Tg + a + 1) - s0;
-                const int64_t nk = target_of(N, G, a);
+                const int64_t nk = target_of(bl, a);
                 const int64_t keep = o < nk ? o : nk;
-                const int64_t slot = (j - s0 < keep) ? balanced_offset(N, G, a) + (j - s0) : j + sent_shift;
+                const int64_t slot = (j - s0 < keep) ? balanced_offset(bl, a) + (j - s0) : j + sent_shift;
                 int32_t *dst = (j - s0 < keep) ? anc : anc_sys;
                 if (slot >= 0 && slot < N && PPF_DCHECK(stage[k] < n, flags, FLAG_INTERNAL))
                     dst[slot] = base + stage[k];
@@ -449,6 +486,7 @@ struct KeptRoute {
     const int64_t *Tg;      // [G+1] tickets below each group start
     const int32_t *tile_g;  // [2T] per tile: first group starting at or after it, starts inside (capped)
     int32_t G;
+    Balanced bl;            // the balanced layout GS and SGS leave
 };
 
 template <bool ROUTE>
@@ -465,6 +503,9 @@ __device__ __forceinline__ void fill_item(const float *__restrict__ lw, int64_t 
     __shared__ int32_t st;
     __shared__ KeptTable kt;
     const int32_t b = blockIdx.x;
+    // item_tile has an entry for every block of the launch: read it together
+    // with the item count
+    const int32_t t_pre = item_tile ? item_tile[b] : 0;
     if (b >= sum->n_items)
         return;
     if (item_tile == nullptr && threadIdx.x == 0) {
@@ -480,7 +521,14 @@ __device__ __forceinline__ void fill_item(const float *__restrict__ lw, int64_t 
     }
     if (item_tile == nullptr)
         __syncthreads();
-    const int32_t t = item_tile ? item_tile[b] : st;
+    const int32_t t = item_tile ? t_pre : st;
+    // the tile's ticket range and prefix, and the draw, loaded before the
+    // tile pass so that their latency overlaps it
+    const int64_t tt0 = Tt[t], tt1 = Tt[t + 1];
+    const int32_t io = item_off[t];
+    const uint64_t ct = Ct[t];
+    const uint64_t sQ = sum->Q, su = sum->u, sqN = sum->qN;
+    const uint32_t sqR = sum->qR;
     if (ROUTE && threadIdx.x >= blockDim.x - 32) {
         // the last warp: the groups holding the tile's particles, one lane
         // each (ga, the group of the tile's first particle, to gb, the last
@@ -498,9 +546,9 @@ __device__ __forceinline__ void fill_item(const float *__restrict__ lw, int64_t 
                 const int64_t s0 = __ldg(kr.Tg + g);
                 kt.start[lane] = s0;
                 if (lane < ng) {
-                    const int64_t o = __ldg(kr.Tg + g + 1) - s0, nk = target_of(N, kr.G, g);
+                    const int64_t o = __ldg(kr.Tg + g + 1) - s0, nk = target_of(kr.bl, g);
                     kt.keep_end[lane] = s0 + (o < nk ? o : nk);
-                    kt.shift[lane] = balanced_offset(N, kr.G, g) - s0;
+                    kt.shift[lane] = balanced_offset(kr.bl, g) - s0;
                 }
             }
             if (lane == 0)
@@ -512,14 +560,14 @@ __device__ __forceinline__ void fill_item(const float *__restrict__ lw, int64_t 
     uint64_t q[TILE_ITEMS];
     tile_weights(lw, lo, n, sum->M, scale_bits(N), C, q);  // its barriers also publish the table
     tile_scan(q, C, red);
-    const int64_t i_lo = Tt[t] + (int64_t)(b - item_off[t]) * ITEM_TICKETS;
-    const int64_t i_hi = (Tt[t + 1] < i_lo + ITEM_TICKETS) ? Tt[t + 1] : i_lo + ITEM_TICKETS;
-    const TicketGrid tg = ticket_grid(sum->Q, sum->u, sum->qN, sum->qR, ndiv);
+    const int64_t i_lo = tt0 + (int64_t)(b - io) * ITEM_TICKETS;
+    const int64_t i_hi = (tt1 < i_lo + ITEM_TICKETS) ? tt1 : i_lo + ITEM_TICKETS;
+    const TicketGrid tg = ticket_grid(sQ, su, sqN, sqR, ndiv);
     if (ROUTE)
-        ticket_parents_routed(C, n, Ct[t], tg, i_lo, i_hi, stage, kt, kr.anc, out, 0, (int32_t)lo, N, kr.G,
+        ticket_parents_routed(C, n, ct, tg, i_lo, i_hi, stage, kt, kr.anc, out, 0, (int32_t)lo, N, kr.G, kr.bl,
                               kr.Tg, &sum->flags);
     else
-        ticket_parents_contig(C, n, Ct[t], tg, i_lo, i_hi, stage, out, (int32_t)lo, N, &sum->flags);
+        ticket_parents_contig(C, n, ct, tg, i_lo, i_hi, stage, out, (int32_t)lo, N, &sum->flags);
 }
 
 __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
@@ -527,7 +575,7 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     const uint64_t *__restrict__ Ct, const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
     const int32_t *__restrict__ item_tile, int32_t *__restrict__ out)
 {
-    const KeptRoute none{nullptr, nullptr, nullptr, 0};
+    const KeptRoute none{nullptr, nullptr, nullptr, 0, Balanced{0, 0}};
     fill_item<false>(lw, N, T, ndiv, sum, Ct, Tt, item_off, item_tile, out, none);
 }
 
@@ -551,116 +599,164 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_route_kernel(
 //
 // The group's total and the cumulative weight below any tile start inside it
 // come from the global prefix of the tile pass (C(p) = Ct[p / TILE] + the
-// local prefix at p; integer sums, so exactly the group's own), which lets a
-// large group be split: blocks 0..G-1 take group g whole when it spans at
-// most two tiles, otherwise its head up to the first tile boundary; block
-// G + t takes tile t when the tile starts strictly inside such a large
-// group, so a group of any size costs about one tile's time.
+// local prefix at p; integer sums, so exactly the group's own sums), which
+// lets a large group be split at tile boundaries: a group spanning more
+// than GROUP_SPLIT particles is drawn by one block for its head (up to the
+// first tile boundary) and one block per interior tile.  A smaller group
+// with more than ITEM_TICKETS offspring is split by tickets instead: its
+// block draws the first ITEM_TICKETS, and one more block each further run
+// of ITEM_TICKETS, so that no block carries a heavy group alone.
 constexpr int64_t GROUP_SPLIT = 2 * TILE;
 
-__global__ void __launch_bounds__(TILE_THREADS) group_fill_kernel(
-    const float *__restrict__ lw, int64_t N, int32_t G, const int64_t *__restrict__ goff,
-    const int64_t *__restrict__ Tg, const uint64_t *__restrict__ Ct, const uint64_t *__restrict__ Cbl,
-    const int32_t *__restrict__ tile_g, const DevSummary *__restrict__ sum, double ess_thr, uint64_t seed,
-    uint32_t fid, uint32_t frame, int32_t *__restrict__ out, int32_t *__restrict__ kept_anc)
+// One thread per group: the group's draw, and the extra work items of a
+// large or heavy group appended to the split list as (tile, g) for an
+// interior tile or (-run, g) for a further run of tickets (the order of the
+// list does not matter: every entry writes its own tickets).
+__global__ void __launch_bounds__(256) group_grid_kernel(
+    int64_t N, int32_t G, const int64_t *__restrict__ goff, const int64_t *__restrict__ Tg,
+    const uint64_t *__restrict__ Ct, const uint64_t *__restrict__ Cbl, DevSummary *__restrict__ sum, double ess_thr,
+    uint64_t seed, uint32_t fid, uint32_t frame, GroupGrid *__restrict__ grid, int32_t *__restrict__ split)
 {
-    if (kept_by_ess(sum, ess_thr) || sum->degenerate)
-        return;  // kept by the N_eff test, or no usable weight (the schedule keeps the layout)
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G || kept_by_ess(sum, ess_thr) || sum->degenerate)
+        return;
+    const uint64_t Q = sum->Q;
+    const int64_t a = goff[g], e = goff[g + 1];
+    const uint64_t ca = (a >= N) ? Q : Ct[a / TILE] + Cbl[g];
+    const uint64_t ce = (e >= N) ? Q : Ct[e / TILE] + Cbl[g + 1];
+    const int64_t nt = Tg[g + 1] - Tg[g];
+    GroupGrid gg;
+    gg.Ca = ca;
+    gg.Q = ce - ca;
+    gg.nt = (nt > 0 && gg.Q > 0) ? (uint32_t)nt : 0u;
+    gg.u = gg.qN = gg.dm = 0;
+    gg.qR = 0;
+    if (gg.nt > 0) {
+        gg.u = ticket_offset(seed, fid, frame, PURPOSE_GROUP, (uint32_t)g, gg.Q);
+        gg.dm = make_divisor(gg.nt).m;
+        gg.qN = gg.Q / gg.nt;
+        gg.qR = (uint32_t)(gg.Q % gg.nt);
+    }
+    grid[g] = gg;
+    if (gg.nt == 0)
+        return;
+    if (e - a > GROUP_SPLIT) {
+        const int64_t t1 = a / TILE + 1, t2 = (e - 1) / TILE;  // tiles starting strictly inside (a, e)
+        if (t2 >= t1) {
+            const int32_t pos = atomicAdd(&sum->n_split, (int32_t)(t2 - t1 + 1));
+            for (int64_t t = t1; t <= t2; ++t) {
+                split[2 * (pos + (t - t1))] = (int32_t)t;
+                split[2 * (pos + (t - t1)) + 1] = g;
+            }
+        }
+    } else if (nt > ITEM_TICKETS) {
+        const int32_t runs = (int32_t)((nt + ITEM_TICKETS - 1) / ITEM_TICKETS);
+        const int32_t pos = atomicAdd(&sum->n_split, runs - 1);
+        for (int32_t r = 1; r < runs; ++r) {
+            split[2 * (pos + r - 1)] = -r;
+            split[2 * (pos + r - 1) + 1] = g;
+        }
+    }
+}
+
+// Blocks [0, n_workers) take the split list's entries in turn; block
+// n_workers + g takes group g: whole, its head when the group is large, or
+// its first ITEM_TICKETS tickets when it is heavy.
+__global__ void __launch_bounds__(TILE_THREADS, 4) group_fill_kernel(
+    const float *__restrict__ lw, int64_t N, int32_t G, const int64_t *__restrict__ goff,
+    const int64_t *__restrict__ Tg, const uint64_t *__restrict__ Ct, const GroupGrid *__restrict__ grid,
+    const int32_t *__restrict__ split, int32_t n_workers, const DevSummary *__restrict__ sum, double ess_thr,
+    int32_t *__restrict__ out, int32_t *__restrict__ kept_anc, Balanced bl)
+{
     extern __shared__ uint64_t fill_smem[];  // FILL_SMEM_BYTES
     uint64_t *C = fill_smem;
     uint16_t *stage = reinterpret_cast<uint16_t *>(fill_smem + TILE_SMEM_U64);
     __shared__ uint64_t red[33];
-    __shared__ uint64_t us, qNs, Qgs, carry0s;
-    __shared__ uint32_t qRs;
-    __shared__ Divisor dvs;
-    __shared__ int32_t gs;
-    __shared__ int64_t p0s, p1s;
-    if (threadIdx.x == 0) {
-        int32_t g = -1;
-        int64_t p0 = 0, p1 = 0;
-        uint64_t carry0 = 0;
-        if ((int32_t)blockIdx.x < G) {
-            g = blockIdx.x;
-            p0 = goff[g];
-            p1 = goff[g + 1];
-            if (p1 - p0 > GROUP_SPLIT)
-                p1 = (p0 / TILE + 1) * TILE;  // the head; the tile blocks take the rest
-        } else {
-            const int32_t t = blockIdx.x - G;
-            const int64_t lo = (int64_t)t * TILE;
-            const int32_t gf = tile_g[2 * t];  // first group starting at or after lo
-            if (gf > 0 && goff[gf] > lo) {     // lo lies strictly inside group gf - 1
-                const int32_t gc = gf - 1;
-                const int64_t a = goff[gc], e = goff[gc + 1];
-                if (e - a > GROUP_SPLIT) {
-                    g = gc;
-                    p0 = lo;
-                    p1 = (lo + TILE < e) ? lo + TILE : e;
-                    carry0 = Ct[t] - (Ct[a / TILE] + Cbl[gc]);
-                }
-            }
-        }
-        gs = g;
-        if (g >= 0) {
-            const uint64_t Q = sum->Q;
-            const int64_t a = goff[g], e = goff[g + 1];
-            const uint64_t ca = (a >= N) ? Q : Ct[a / TILE] + Cbl[g];
-            const uint64_t ce = (e >= N) ? Q : Ct[e / TILE] + Cbl[g + 1];
-            const uint64_t Qg = ce - ca;
-            const int64_t nt = Tg[g + 1] - Tg[g];
-            Qgs = Qg;
-            p0s = p0;
-            p1s = p1;
-            carry0s = carry0;
-            if (nt > 0 && Qg > 0) {
-                us = ticket_offset(seed, fid, frame, PURPOSE_GROUP, (uint32_t)g, Qg);
-                dvs = make_divisor((uint32_t)nt);
-                qNs = Qg / (uint64_t)nt;
-                qRs = (uint32_t)(Qg % (uint64_t)nt);
-            } else {
-                gs = -1;  // no offspring, or no weight to draw them from
-            }
-        }
-    }
-    __syncthreads();
-    const int32_t g = gs;
-    if (g < 0)
-        return;
-    const int64_t p0 = p0s, p1 = p1s;
-    const int64_t nt = Tg[g + 1] - Tg[g];
-    const uint64_t Qg = Qgs, u = us;
+    const bool worker = (int32_t)blockIdx.x < n_workers;
+    // the loads a group block needs, issued together before any test on them
+    const int32_t gb = worker ? 0 : (int32_t)blockIdx.x - n_workers;
+    const double ess = sum->ess;
+    const int32_t deg = sum->degenerate;
     const float M = sum->M;
+    const int32_t n_items = worker ? sum->n_split : 1;
+    const int64_t gb_lo = goff[gb], gb_hi = goff[gb + 1];
+    const GroupGrid gb_grid = grid[gb];
+    if (ess >= ess_thr || deg)
+        return;  // kept by the N_eff test, or no usable weight (the schedule keeps the layout)
     const int s = scale_bits(N);
-    const TicketGrid tg = ticket_grid(Qg, u, qNs, qRs, dvs);
-    int32_t *__restrict__ dst = out + Tg[g];
-    KeptTable kt;  // one group, in local ticket numbers
-    kt.n = 1;
-    kt.start[0] = 0;
-    kt.start[1] = nt;
-    {
-        const int64_t nk = target_of(N, G, g);
-        kt.keep_end[0] = nt < nk ? nt : nk;
-        kt.shift[0] = balanced_offset(N, G, g);
-    }
-    // chunks of at most TILE particles; the local tickets of a chunk with
-    // cumulative weight [carry, carry + total) inside the group are
-    // [T(carry), T(carry + total)), T the count below of the nt tickets
-    uint64_t carry = carry0s;
-    for (int64_t c0 = p0; c0 < p1; c0 += TILE) {
-        const int n = (int)(p1 - c0 < TILE ? p1 - c0 : TILE);
-        uint64_t q[TILE_ITEMS];
-        tile_weights(lw, c0, n, M, s, C, q);
-        const uint64_t tot = tile_scan(q, C, red);
-        const int64_t t_lo = tickets_below(carry, nt, u, Qg);
-        const int64_t t_hi = tickets_below(carry + tot, nt, u, Qg);
-        if (kept_anc)
-            ticket_parents_routed(C, n, carry, tg, t_lo, t_hi, stage, kt, kept_anc, out, Tg[g], (int32_t)c0, N, G,
-                                  Tg, &sum->flags);
-        else
-            ticket_parents_contig(C, n, carry, tg, t_lo, t_hi, stage, dst, (int32_t)c0,
-                                  (nt < N - Tg[g]) ? nt : N - Tg[g], &sum->flags);
-        carry += tot;
-        __syncthreads();
+    for (int32_t it = worker ? (int32_t)blockIdx.x : 0; it < n_items; it += worker ? n_workers : 1) {
+        int32_t g, run = 0;  // run >= 0: this item draws tickets [run, run + 1) ITEM_TICKETS of a heavy group
+        int64_t p0, p1;
+        bool inner = false;  // an interior tile of a large group
+        if (worker) {
+            const int32_t code = split[2 * it];
+            g = split[2 * it + 1];
+            if (code >= 0) {
+                p0 = (int64_t)code * TILE;
+                const int64_t e = goff[g + 1];
+                p1 = (p0 + TILE < e) ? p0 + TILE : e;
+                inner = true;
+                run = -1;
+            } else {
+                p0 = goff[g];
+                p1 = goff[g + 1];
+                run = -code;
+            }
+        } else {
+            g = gb;
+            p0 = gb_lo;
+            p1 = gb_hi;
+            if (p1 - p0 > GROUP_SPLIT) {
+                p1 = (p0 / TILE + 1) * TILE;  // the head; the split list has the rest
+                run = -1;
+            }
+        }
+        const GroupGrid gg = worker ? grid[g] : gb_grid;
+        if (gg.nt == 0)
+            continue;
+        const int64_t g_end = worker ? goff[g + 1] : gb_hi;
+        const int64_t nt = gg.nt;
+        Divisor dv;
+        dv.m = gg.dm;
+        dv.d = gg.nt;
+        const TicketGrid tg = ticket_grid(gg.Q, gg.u, gg.qN, gg.qR, dv);
+        const int64_t tg0 = Tg[g];
+        KeptTable kt;  // one group, in local ticket numbers
+        kt.n = 1;
+        kt.start[0] = 0;
+        kt.start[1] = nt;
+        {
+            const int64_t nk = target_of(bl, g);
+            kt.keep_end[0] = nt < nk ? nt : nk;
+            kt.shift[0] = balanced_offset(bl, g);
+        }
+        // the item's window of the group's tickets: all of them for a whole
+        // group, a head or an interior tile; one run of a heavy group
+        const int64_t j0 = run > 0 ? (int64_t)run * ITEM_TICKETS : 0;
+        const int64_t j1 = (run < 0 || nt <= ITEM_TICKETS) ? nt
+                           : ((j0 + ITEM_TICKETS < nt) ? j0 + ITEM_TICKETS : nt);
+        // chunks of at most TILE particles; the local tickets of a chunk with
+        // cumulative weight [carry, carry + total) inside the group are
+        // [T(carry), T(carry + total)), T the count below of the nt tickets
+        uint64_t carry = inner ? Ct[p0 / TILE] - gg.Ca : 0ull;
+        for (int64_t c0 = p0; c0 < p1; c0 += TILE) {
+            const int n = (int)(p1 - c0 < TILE ? p1 - c0 : TILE);
+            uint64_t q[TILE_ITEMS];
+            tile_weights(lw, c0, n, M, s, C, q);
+            const uint64_t tot = tile_scan(q, C, red);
+            // no ticket lies below the group's start, all of them below its end
+            const int64_t c_lo = carry == 0 ? 0 : tickets_below(carry, nt, gg.u, gg.Q);
+            const int64_t c_hi = c0 + n == g_end ? nt : tickets_below(carry + tot, nt, gg.u, gg.Q);
+            const int64_t t_lo = c_lo > j0 ? c_lo : j0, t_hi = c_hi < j1 ? c_hi : j1;
+            if (kept_anc)
+                ticket_parents_routed(C, n, carry, tg, t_lo, t_hi, stage, kt, kept_anc, out, tg0, (int32_t)c0, N, G,
+                                      bl, Tg, &sum->flags);
+            else
+                ticket_parents_contig(C, n, carry, tg, t_lo, t_hi, stage, out + tg0, (int32_t)c0,
+                                      (nt < N - tg0) ? nt : N - tg0, &sum->flags);
+            carry += tot;
+            __syncthreads();
+        }
     }
 }
 
@@ -685,6 +781,7 @@ struct SchedArgs {
     int64_t *seg_tick, *seg_dst, *seg_len;  // [2G + 1]
     DevSummary *sum;
     int links_only;  // the fill wrote the kept segments already: copy work items for the links only
+    Balanced bl;     // the balanced targets n_g
 };
 
 // block-wide exclusive scan of an int64 array in place (single block)
@@ -710,17 +807,24 @@ __device__ void block_scan_i64(int64_t *a, int n, uint64_t *red, int64_t *total_
     __syncthreads();
 }
 
-// Sort (ascending) of n <= MAX_SCHED_GROUPS distinct u64 keys, one block of
-// 1024 threads.  sm: MAX_SCHED_GROUPS keys, then two index buffers of as many
-// u16 (SORT_SMEM_BYTES in all); g may be sm itself.  A merge sort on indices:
-// every thread sorts a run of 16 in registers, then ten levels of merges,
-// each thread writing 16 outputs after a merge-path search of its diagonal.
+// Sort (ascending) of n <= cap distinct u64 keys, one block of 1024 threads.
+// sm: cap keys, then two index buffers of cap u16 (sort_smem_bytes(cap) in
+// all, cap <= MAX_SCHED_GROUPS); g may be sm itself.  A merge sort on
+// indices: every thread sorts a run of 16 in registers, then the merge
+// levels, each thread writing 16 outputs after a merge-path search of its
+// diagonal.  Launches size the buffer by their G, not by the largest G, so
+// that the rest of the SM's 256 KB stays L1 cache for the kernel's global
+// reads.
 constexpr int SORT_PER = 16;
 constexpr size_t SORT_SMEM_BYTES = (sizeof(uint64_t) + 2 * sizeof(uint16_t)) * MAX_SCHED_GROUPS;
-
-__device__ void block_sort_u64(uint64_t *g, int n, uint64_t *sm)
+__host__ __device__ inline size_t sort_smem_bytes(int cap)
 {
-    uint16_t *ia = reinterpret_cast<uint16_t *>(sm + MAX_SCHED_GROUPS), *ib = ia + MAX_SCHED_GROUPS;
+    return (sizeof(uint64_t) + 2 * sizeof(uint16_t)) * (size_t)(cap > 0 ? cap : 1);
+}
+
+__device__ void block_sort_u64(uint64_t *g, int n, uint64_t *sm, int cap)
+{
+    uint16_t *ia = reinterpret_cast<uint16_t *>(sm + cap), *ib = ia + cap;
     if (g != sm)
         for (int i = threadIdx.x; i < n; i += blockDim.x)
             sm[i] = g[i];
@@ -823,7 +927,7 @@ __device__ __forceinline__ int lower_bound_i64(const int64_t *a, int n, int64_t 
 
 __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
 {
-    extern __shared__ uint64_t sm[];   // MAX_SCHED_GROUPS keys
+    extern __shared__ uint64_t sm[];   // sort_smem_bytes(G) (GS: G words)
     __shared__ uint64_t red[33];
     __shared__ int nS_s, nR_s, L_s;
     const int32_t G = A.G;
@@ -857,7 +961,7 @@ __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
         for (int k = 0; k < per; ++k) {
             const int g = g0 + k;
             if (g < G) {
-                const int64_t o = A.Tg[g + 1] - A.Tg[g], t = target_of(N, G, g);
+                const int64_t o = A.Tg[g + 1] - A.Tg[g], t = target_of(A.bl, g);
                 cs += (o > t);
                 cr += (o < t);
             }
@@ -869,7 +973,7 @@ __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
         for (int k = 0; k < per; ++k) {
             const int g = g0 + k;
             if (g < G) {
-                const int64_t o = A.Tg[g + 1] - A.Tg[g], t = target_of(N, G, g);
+                const int64_t o = A.Tg[g + 1] - A.Tg[g], t = target_of(A.bl, g);
                 if (o > t) {
                     const uint64_t amt = (uint64_t)(o - t);
                     Skey[ps++] = sorted ? (((0xFFFFFFFFFFull - amt) << 24) | (uint64_t)g) : ((amt << 24) | (uint64_t)g);
@@ -889,8 +993,8 @@ __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
     const int nS = nS_s, nR = nR_s;
     const bool sorted = (A.scheme != PPF_RPA_GS);
     if (sorted) {
-        block_sort_u64(Skey, nS, sm);
-        block_sort_u64(Rkey, nR, sm);
+        block_sort_u64(Skey, nS, sm, G);
+        block_sort_u64(Rkey, nR, sm, G);
     }
     auto amount = [&](uint64_t k) -> int64_t {
         return sorted ? (int64_t)(0xFFFFFFFFFFull - (k >> 24)) : (int64_t)(k >> 24);
@@ -1313,7 +1417,7 @@ __global__ void __launch_bounds__(1024) rna_prep_kernel(const int64_t *__restric
 // counts as lost): the groups in increasing order of the first Philox word of
 // (seed; g, frame, filter, RING), ties by index (a bitonic sort of
 // word << 32 | g).  Then every group's successor on the ring.
-// Dynamic shared memory: SORT_SMEM_BYTES (G <= MAX_SCHED_GROUPS).
+// Dynamic shared memory: sort_smem_bytes(G) (G <= MAX_SCHED_GROUPS).
 __global__ void __launch_bounds__(1024) arna_prep_kernel(const int64_t *__restrict__ goff, int32_t G, float alpha,
                                                          DevSummary *sum, double ess_thr,
                                                          const int64_t *__restrict__ Tg, int32_t *__restrict__ ring,
@@ -1356,7 +1460,7 @@ __global__ void __launch_bounds__(1024) arna_prep_kernel(const int64_t *__restri
             sm[g] = ((uint64_t)r.x << 32) | (uint32_t)g;
         }
         __syncthreads();
-        block_sort_u64(sm, G, sm);
+        block_sort_u64(sm, G, sm, G);
         for (int p = threadIdx.x; p < G; p += blockDim.x)
             ring[p] = (int32_t)(uint32_t)sm[p];
         __syncthreads();
@@ -1464,11 +1568,12 @@ static cudaError_t launch_schedule(ppf_ctx *c, int scheme, bool two_stage)
     A.seg_len = c->sc.seg_len;
     A.sum = c->sum;
     A.links_only = A.scheme != PPF_RPA_LGS;
+    A.bl = balanced_layout(c->N, c->G);
     // Greedy needs no sort: shared memory only for its two prefix arrays (at
     // most G words), which leaves the rest of the SM's L1 to the global reads
     const size_t sched_smem = scheme == PPF_RPA_GS || scheme == PPF_RPA2_GS
                                   ? sizeof(int64_t) * (size_t)(c->G > 0 ? c->G : 1)
-                                  : SORT_SMEM_BYTES;
+                                  : sort_smem_bytes(c->G);
     schedule_kernel<<<1, 1024, sched_smem, c->side_stream>>>(A);
     e = cudaGetLastError();
     if (e == cudaSuccess)
@@ -1506,13 +1611,18 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     // GS and SGS: the kept tickets go straight to their balanced slots
     const bool kept_direct = rpa && scheme != PPF_RPA_LGS && scheme != PPF_RPA2_LGS;
     if (two_stage) {  // stage 2: every group draws its own offspring
-        group_fill_kernel<<<c->G + T, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
-            lw, c->N, c->G, c->goff, c->sc.Tg, c->sc.Ct, c->sc.Cbl, c->sc.tile_g, c->sum, ess_thr, c->m.seed,
-            c->m.filter_id, (uint32_t)c->last_frame, out, kept_direct ? c->anc : nullptr);
+        group_grid_kernel<<<(c->G + 255) / 256, 256, 0, c->stream>>>(
+            c->N, c->G, c->goff, c->sc.Tg, c->sc.Ct, c->sc.Cbl, c->sum, ess_thr, c->m.seed, c->m.filter_id,
+            (uint32_t)c->last_frame, c->sc.ggrid, c->sc.split);
+        const int n_workers = 2 * c->num_sms < T ? 2 * c->num_sms : T;
+        group_fill_kernel<<<n_workers + c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
+            lw, c->N, c->G, c->goff, c->sc.Tg, c->sc.Ct, c->sc.ggrid, c->sc.split, n_workers, c->sum, ess_thr, out,
+            kept_direct ? c->anc : nullptr, balanced_layout(c->N, c->G));
+        c->launches += 1;
     } else {
         const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
         if (kept_direct) {
-            const KeptRoute kr{c->anc, c->sc.Tg, c->sc.tile_g, c->G};
+            const KeptRoute kr{c->anc, c->sc.Tg, c->sc.tile_g, c->G, balanced_layout(c->N, c->G)};
             fill_route_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
                 lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, c->sc.item_off,
                 c->sc.item_tile, out, kr);
@@ -1565,7 +1675,7 @@ cudaError_t launch_resample_arna(ppf_ctx *c, float alpha, double ess_thr)
     tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
         c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, nullptr, c->sum, ess_thr, c->m.seed, c->m.filter_id,
         (uint32_t)c->last_frame, c->goff, c->G, 1, c->sc.Cbl, c->sc.Tg, st_tiles, make_divisor((uint32_t)c->N));
-    arna_prep_kernel<<<1, 1024, SORT_SMEM_BYTES, c->stream>>>(
+    arna_prep_kernel<<<1, 1024, sort_smem_bytes(c->G), c->stream>>>(
         c->goff, c->G, alpha, c->sum, ess_thr, c->sc.Tg, c->ring, c->succ, c->m.seed, c->m.filter_id,
         (uint32_t)c->last_frame);
     rna_kernel<<<c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(lw, c->N, c->G, c->goff, c->succ, c->sum, ess_thr,

@@ -178,6 +178,9 @@ def lockstep(pf, gm, om, frames_np, frames_gpu, scheme, K, alpha=0.1, check_resa
         assert rc == 0
         a1 = anc1.cpu().numpy()
         assert np.array_equal(a1, anc_ref), f"frame {k}: {np.sum(a1 != anc_ref)} ancestors differ"
+        if log is not None:  # the most offspring any group's particles had
+            per_group = np.bincount(np.searchsorted(goff0, a1, side="right") - 1, minlength=len(goff0) - 1)
+            log.append(("offspring", k, int(per_group.max())))
         assert np.array_equal(goff1, goff_ref)
         l1 = lwp1.cpu().double().numpy()
         tol = 1e-5 * np.maximum(1.0, np.abs(lwr_ref))

@@ -59,22 +59,26 @@ def test_lockstep_frames(ppf, movie, scheme, N, gs):
 
 
 @pytest.mark.parametrize("N,gs", [(16384, 4096), (20000, 1500), (10000, 777), (9001, 5000), (40000, 20000),
-                                  (50001, 12345)])
+                                  (50001, 12345), (200000, 4000)])
 def test_rpa_schemes_in_sequence(ppf, movie, N, gs):
     """GS and SGS write every group's kept tickets straight to its balanced
     slots and copy only the links; LGS leaves unequal groups, so the GS and
     SGS frames after it start from tiles crossed by several groups of
     different sizes (the per-tile table, and the per-ticket lookup where more
-    than five groups cross a tile).  Groups above two tiles (the last two
-    sizes, and those LGS grows) are drawn by the two-stage fill one tile per
-    block."""
+    than five groups cross a tile).  Groups above two tiles (40000 / 20000,
+    50001 / 12345, and those LGS grows) are drawn by the two-stage fill one
+    tile per block, and groups with more than 8192 offspring (the
+    concentrated clouds at N = 200000) one run of 8192 tickets per block."""
     from gpu_common import lockstep, paired_models
     gm, om = paired_models(ppf, seed=5)
     pf = ppf.ParticleFilter(gm, N, group_size=gs)
     seq = [orc.RPA_LGS, orc.RPA_GS, orc.RPA_LGS, orc.RPA_LGS, orc.RPA_SGS, orc.RPA2_LGS]
     lockstep(pf, gm, om, movie.frames, gpu_frames(movie), seq, K=6)
     seq = [orc.RPA_LGS, orc.RPA2_GS, orc.RPA2_LGS, orc.RPA2_SGS, orc.RPA_GS, orc.SYSTEMATIC]
-    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), seq, K=6)
+    log = []
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), seq, K=6, log=log)
+    if N == 200000:  # the run split is exercised: some frame gives one group > 8192 offspring
+        assert max(e[2] for e in log if e[0] == "offspring") > 8192
     pf.close()
 
 
