@@ -20,13 +20,24 @@ __device__ __forceinline__ int padc(int i) { return i + (i >> 4); }
 constexpr int TILE_SMEM_U64 = TILE + TILE / 16;  // >= (TILE + TILE/32) / 2 floats
 
 // Quantised weights of particles [lo, lo + n): coalesced loads into smem, then
-// thread t takes items [16t, 16t + 16).  q = 0 beyond n.
+// thread t takes items [16t, 16t + 16).  q = 0 beyond n.  Every caller runs
+// TILE_THREADS threads: each thread issues all of its TILE / TILE_THREADS
+// loads before its first shared store, so that they are in flight together
+// (a load-store loop waits one memory latency per element).
 __device__ __forceinline__ void tile_weights(const float *__restrict__ lw, int64_t lo, int n, float M, int s,
                                              uint64_t *buf, uint64_t q[TILE_ITEMS])
 {
     float *f = reinterpret_cast<float *>(buf);
-    for (int e = threadIdx.x; e < TILE; e += blockDim.x)
-        f[padf(e)] = (e < n) ? __ldg(lw + lo + e) : -INFINITY;
+    constexpr int TW = TILE / TILE_THREADS;
+    float v[TW];
+#pragma unroll
+    for (int k = 0; k < TW; ++k) {
+        const int e = (int)threadIdx.x + k * TILE_THREADS;
+        v[k] = (e < n) ? __ldg(lw + lo + e) : -INFINITY;
+    }
+#pragma unroll
+    for (int k = 0; k < TW; ++k)
+        f[padf((int)threadIdx.x + k * TILE_THREADS)] = v[k];
     __syncthreads();
     const int base = threadIdx.x * TILE_ITEMS;
 #pragma unroll
