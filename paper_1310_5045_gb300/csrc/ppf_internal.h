@@ -84,15 +84,20 @@ struct DevSummary {
     int32_t n_split;           // two-stage RPA: extra work items of large or heavy groups
 };
 
-// two-stage RPA: one group's own systematic draw (see group_grid_kernel)
-struct GroupGrid {
-    uint64_t Ca;   // cumulative fixed-point weight below the group
-    uint64_t Q;    // the group's total
-    uint64_t u;    // its ticket offset
-    uint64_t qN;   // Q = qN nt + qR
-    uint64_t dm;   // floor((2^64 - 1) / nt)
+// two-stage RPA: one group's own systematic draw and where its offspring go
+// (see group_grid_kernel), read by the group's block as six 16-byte loads
+struct alignas(16) GroupGrid {
+    uint64_t Ca;     // cumulative fixed-point weight below the group
+    uint64_t Q;      // the group's total
+    uint64_t u;      // its ticket offset
+    uint64_t qN;     // Q = qN nt + qR
+    uint64_t dm;     // floor((2^64 - 1) / nt)
+    int64_t p0, p1;  // its particles [p0, p1)
+    int64_t tg0;     // its first ticket slot in the global ticket order
+    int64_t keep;    // its offspring that stay (GS, SGS: min(nt, n_g))
+    int64_t shift;   // the slot of its first kept offspring (the balanced offset)
     uint32_t qR;
-    uint32_t nt;   // its offspring count (0: nothing to draw)
+    uint32_t nt;     // its offspring count (0: nothing to draw)
 };
 
 struct Scratch {

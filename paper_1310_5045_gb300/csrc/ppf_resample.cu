@@ -615,7 +615,8 @@ constexpr int64_t GROUP_SPLIT = 2 * TILE;
 __global__ void __launch_bounds__(256) group_grid_kernel(
     int64_t N, int32_t G, const int64_t *__restrict__ goff, const int64_t *__restrict__ Tg,
     const uint64_t *__restrict__ Ct, const uint64_t *__restrict__ Cbl, DevSummary *__restrict__ sum, double ess_thr,
-    uint64_t seed, uint32_t fid, uint32_t frame, GroupGrid *__restrict__ grid, int32_t *__restrict__ split)
+    uint64_t seed, uint32_t fid, uint32_t frame, GroupGrid *__restrict__ grid, int32_t *__restrict__ split,
+    Balanced bl)
 {
     const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G || kept_by_ess(sum, ess_thr) || sum->degenerate)
@@ -631,6 +632,14 @@ __global__ void __launch_bounds__(256) group_grid_kernel(
     gg.nt = (nt > 0 && gg.Q > 0) ? (uint32_t)nt : 0u;
     gg.u = gg.qN = gg.dm = 0;
     gg.qR = 0;
+    gg.p0 = a;
+    gg.p1 = e;
+    gg.tg0 = Tg[g];
+    {
+        const int64_t nk = target_of(bl, g);
+        gg.keep = nt < nk ? nt : nk;
+        gg.shift = balanced_offset(bl, g);
+    }
     if (gg.nt > 0) {
         gg.u = ticket_offset(seed, fid, frame, PURPOSE_GROUP, (uint32_t)g, gg.Q);
         gg.dm = make_divisor(gg.nt).m;
@@ -659,103 +668,95 @@ __global__ void __launch_bounds__(256) group_grid_kernel(
     }
 }
 
+// One work item of the two-stage draw: particles [p0, p1) of group gg, the
+// group's tickets [j0, j1) among them; carry is the group's cumulative weight
+// below p0.
+__device__ __forceinline__ void group_fill_item(const float *__restrict__ lw, int64_t N, int32_t G,
+                                                const int64_t *__restrict__ Tg, const GroupGrid &gg, int64_t p0,
+                                                int64_t p1, int64_t j0, int64_t j1, uint64_t carry, float M, int s,
+                                                const DevSummary *__restrict__ sum, int32_t *__restrict__ out,
+                                                int32_t *__restrict__ kept_anc, const Balanced &bl, uint64_t *C,
+                                                uint16_t *stage, uint64_t *red)
+{
+    const int64_t nt = gg.nt;
+    Divisor dv;
+    dv.m = gg.dm;
+    dv.d = gg.nt;
+    const TicketGrid tg = ticket_grid(gg.Q, gg.u, gg.qN, gg.qR, dv);
+    KeptTable kt;  // one group, in local ticket numbers
+    kt.n = 1;
+    kt.start[0] = 0;
+    kt.start[1] = nt;
+    kt.keep_end[0] = gg.keep;
+    kt.shift[0] = gg.shift;
+    // chunks of at most TILE particles; the local tickets of a chunk with
+    // cumulative weight [carry, carry + total) inside the group are
+    // [T(carry), T(carry + total)), T the count below of the nt tickets
+    for (int64_t c0 = p0; c0 < p1; c0 += TILE) {
+        const int n = (int)(p1 - c0 < TILE ? p1 - c0 : TILE);
+        uint64_t q[TILE_ITEMS];
+        tile_weights(lw, c0, n, M, s, C, q);
+        const uint64_t tot = tile_scan(q, C, red);
+        // no ticket lies below the group's start, all of them below its end
+        const int64_t c_lo = carry == 0 ? 0 : tickets_below(carry, nt, gg.u, gg.Q);
+        const int64_t c_hi = c0 + n == gg.p1 ? nt : tickets_below(carry + tot, nt, gg.u, gg.Q);
+        const int64_t t_lo = c_lo > j0 ? c_lo : j0, t_hi = c_hi < j1 ? c_hi : j1;
+        if (kept_anc)
+            ticket_parents_routed(C, n, carry, tg, t_lo, t_hi, stage, kt, kept_anc, out, gg.tg0, (int32_t)c0, N, G,
+                                  bl, Tg, &sum->flags);
+        else
+            ticket_parents_contig(C, n, carry, tg, t_lo, t_hi, stage, out + gg.tg0, (int32_t)c0,
+                                  (nt < N - gg.tg0) ? nt : N - gg.tg0, &sum->flags);
+        carry += tot;
+        __syncthreads();
+    }
+}
+
 // Blocks [0, n_workers) take the split list's entries in turn; block
 // n_workers + g takes group g: whole, its head when the group is large, or
-// its first ITEM_TICKETS tickets when it is heavy.
+// its first ITEM_TICKETS tickets when it is heavy.  s: scale_bits(N).
 __global__ void __launch_bounds__(TILE_THREADS, 4) group_fill_kernel(
-    const float *__restrict__ lw, int64_t N, int32_t G, const int64_t *__restrict__ goff,
-    const int64_t *__restrict__ Tg, const uint64_t *__restrict__ Ct, const GroupGrid *__restrict__ grid,
-    const int32_t *__restrict__ split, int32_t n_workers, const DevSummary *__restrict__ sum, double ess_thr,
-    int32_t *__restrict__ out, int32_t *__restrict__ kept_anc, Balanced bl)
+    const float *__restrict__ lw, int64_t N, int32_t G, const int64_t *__restrict__ Tg,
+    const uint64_t *__restrict__ Ct, const GroupGrid *__restrict__ grid, const int32_t *__restrict__ split,
+    int32_t n_workers, const DevSummary *__restrict__ sum, double ess_thr, int32_t *__restrict__ out,
+    int32_t *__restrict__ kept_anc, Balanced bl, int s)
 {
     extern __shared__ uint64_t fill_smem[];  // FILL_SMEM_BYTES
     uint64_t *C = fill_smem;
     uint16_t *stage = reinterpret_cast<uint16_t *>(fill_smem + TILE_SMEM_U64);
     __shared__ uint64_t red[33];
-    const bool worker = (int32_t)blockIdx.x < n_workers;
-    // the loads a group block needs, issued together before any test on them
-    const int32_t gb = worker ? 0 : (int32_t)blockIdx.x - n_workers;
-    const double ess = sum->ess;
-    const int32_t deg = sum->degenerate;
+    if ((int32_t)blockIdx.x >= n_workers) {  // a group block: one item, no loop
+        const GroupGrid gg = grid[blockIdx.x - n_workers];
+        const double ess = sum->ess;
+        const int32_t deg = sum->degenerate;
+        const float M = sum->M;
+        if (ess >= ess_thr || deg || gg.nt == 0)
+            return;  // kept by the N_eff test, no usable weight, or no offspring
+        int64_t p1 = gg.p1, j1 = gg.nt;
+        if (p1 - gg.p0 > GROUP_SPLIT)
+            p1 = (gg.p0 / TILE + 1) * TILE;  // the head; the split list has the rest
+        else if (j1 > ITEM_TICKETS)
+            j1 = ITEM_TICKETS;  // the first run; the split list has the rest
+        group_fill_item(lw, N, G, Tg, gg, gg.p0, p1, 0, j1, 0, M, s, sum, out, kept_anc, bl, C, stage, red);
+        return;
+    }
+    if (sum->ess >= ess_thr || sum->degenerate)
+        return;
     const float M = sum->M;
-    const int32_t n_items = worker ? sum->n_split : 1;
-    const int64_t gb_lo = goff[gb], gb_hi = goff[gb + 1];
-    const GroupGrid gb_grid = grid[gb];
-    if (ess >= ess_thr || deg)
-        return;  // kept by the N_eff test, or no usable weight (the schedule keeps the layout)
-    const int s = scale_bits(N);
-    for (int32_t it = worker ? (int32_t)blockIdx.x : 0; it < n_items; it += worker ? n_workers : 1) {
-        int32_t g, run = 0;  // run >= 0: this item draws tickets [run, run + 1) ITEM_TICKETS of a heavy group
-        int64_t p0, p1;
-        bool inner = false;  // an interior tile of a large group
-        if (worker) {
-            const int32_t code = split[2 * it];
-            g = split[2 * it + 1];
-            if (code >= 0) {
-                p0 = (int64_t)code * TILE;
-                const int64_t e = goff[g + 1];
-                p1 = (p0 + TILE < e) ? p0 + TILE : e;
-                inner = true;
-                run = -1;
-            } else {
-                p0 = goff[g];
-                p1 = goff[g + 1];
-                run = -code;
-            }
-        } else {
-            g = gb;
-            p0 = gb_lo;
-            p1 = gb_hi;
-            if (p1 - p0 > GROUP_SPLIT) {
-                p1 = (p0 / TILE + 1) * TILE;  // the head; the split list has the rest
-                run = -1;
-            }
-        }
-        const GroupGrid gg = worker ? grid[g] : gb_grid;
-        if (gg.nt == 0)
-            continue;
-        const int64_t g_end = worker ? goff[g + 1] : gb_hi;
-        const int64_t nt = gg.nt;
-        Divisor dv;
-        dv.m = gg.dm;
-        dv.d = gg.nt;
-        const TicketGrid tg = ticket_grid(gg.Q, gg.u, gg.qN, gg.qR, dv);
-        const int64_t tg0 = Tg[g];
-        KeptTable kt;  // one group, in local ticket numbers
-        kt.n = 1;
-        kt.start[0] = 0;
-        kt.start[1] = nt;
-        {
-            const int64_t nk = target_of(bl, g);
-            kt.keep_end[0] = nt < nk ? nt : nk;
-            kt.shift[0] = balanced_offset(bl, g);
-        }
-        // the item's window of the group's tickets: all of them for a whole
-        // group, a head or an interior tile; one run of a heavy group
-        const int64_t j0 = run > 0 ? (int64_t)run * ITEM_TICKETS : 0;
-        const int64_t j1 = (run < 0 || nt <= ITEM_TICKETS) ? nt
-                           : ((j0 + ITEM_TICKETS < nt) ? j0 + ITEM_TICKETS : nt);
-        // chunks of at most TILE particles; the local tickets of a chunk with
-        // cumulative weight [carry, carry + total) inside the group are
-        // [T(carry), T(carry + total)), T the count below of the nt tickets
-        uint64_t carry = inner ? Ct[p0 / TILE] - gg.Ca : 0ull;
-        for (int64_t c0 = p0; c0 < p1; c0 += TILE) {
-            const int n = (int)(p1 - c0 < TILE ? p1 - c0 : TILE);
-            uint64_t q[TILE_ITEMS];
-            tile_weights(lw, c0, n, M, s, C, q);
-            const uint64_t tot = tile_scan(q, C, red);
-            // no ticket lies below the group's start, all of them below its end
-            const int64_t c_lo = carry == 0 ? 0 : tickets_below(carry, nt, gg.u, gg.Q);
-            const int64_t c_hi = c0 + n == g_end ? nt : tickets_below(carry + tot, nt, gg.u, gg.Q);
-            const int64_t t_lo = c_lo > j0 ? c_lo : j0, t_hi = c_hi < j1 ? c_hi : j1;
-            if (kept_anc)
-                ticket_parents_routed(C, n, carry, tg, t_lo, t_hi, stage, kt, kept_anc, out, tg0, (int32_t)c0, N, G,
-                                      bl, Tg, &sum->flags);
-            else
-                ticket_parents_contig(C, n, carry, tg, t_lo, t_hi, stage, out + tg0, (int32_t)c0,
-                                      (nt < N - tg0) ? nt : N - tg0, &sum->flags);
-            carry += tot;
-            __syncthreads();
+    const int32_t n_items = sum->n_split;
+    for (int32_t it = (int32_t)blockIdx.x; it < n_items; it += n_workers) {
+        const int32_t code = split[2 * it], g = split[2 * it + 1];
+        const GroupGrid gg = grid[g];
+        if (code >= 0) {  // an interior tile of a large group: all its tickets
+            const int64_t p0 = (int64_t)code * TILE;
+            const int64_t p1 = (p0 + TILE < gg.p1) ? p0 + TILE : gg.p1;
+            group_fill_item(lw, N, G, Tg, gg, p0, p1, 0, gg.nt, Ct[code] - gg.Ca, M, s, sum, out, kept_anc, bl,
+                            C, stage, red);
+        } else {  // run -code of a heavy group
+            const int64_t j0 = (int64_t)(-code) * ITEM_TICKETS;
+            const int64_t j1 = (j0 + ITEM_TICKETS < (int64_t)gg.nt) ? j0 + ITEM_TICKETS : (int64_t)gg.nt;
+            group_fill_item(lw, N, G, Tg, gg, gg.p0, gg.p1, j0, j1, 0, M, s, sum, out, kept_anc, bl, C, stage,
+                            red);
         }
     }
 }
@@ -931,7 +932,6 @@ __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
     __shared__ uint64_t red[33];
     __shared__ int nS_s, nR_s, L_s;
     const int32_t G = A.G;
-    const int64_t N = A.N;
     DevSummary *sum = A.sum;
     if (sum->degenerate) {
         for (int g = threadIdx.x; g <= G; g += blockDim.x)
@@ -1613,11 +1613,11 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     if (two_stage) {  // stage 2: every group draws its own offspring
         group_grid_kernel<<<(c->G + 255) / 256, 256, 0, c->stream>>>(
             c->N, c->G, c->goff, c->sc.Tg, c->sc.Ct, c->sc.Cbl, c->sum, ess_thr, c->m.seed, c->m.filter_id,
-            (uint32_t)c->last_frame, c->sc.ggrid, c->sc.split);
+            (uint32_t)c->last_frame, c->sc.ggrid, c->sc.split, balanced_layout(c->N, c->G));
         const int n_workers = 2 * c->num_sms < T ? 2 * c->num_sms : T;
         group_fill_kernel<<<n_workers + c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
-            lw, c->N, c->G, c->goff, c->sc.Tg, c->sc.Ct, c->sc.ggrid, c->sc.split, n_workers, c->sum, ess_thr, out,
-            kept_direct ? c->anc : nullptr, balanced_layout(c->N, c->G));
+            lw, c->N, c->G, c->sc.Tg, c->sc.Ct, c->sc.ggrid, c->sc.split, n_workers, c->sum, ess_thr, out,
+            kept_direct ? c->anc : nullptr, balanced_layout(c->N, c->G), scale_bits(c->N));
         c->launches += 1;
     } else {
         const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
