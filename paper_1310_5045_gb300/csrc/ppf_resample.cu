@@ -1278,6 +1278,77 @@ __global__ void __launch_bounds__(TILE_THREADS, 4) rna_kernel(
     const int32_t gn = succ ? succ[g] : (g + 1) % G;
     const int64_t gn_lo = goff[gn], gn_sz = goff[gn + 1] - gn_lo;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto dest = [&](int64_t s2) -> int64_t {
+        return (s2 < sz - mig) ? lo + s2 : gn_lo + gn_sz - mig + (s2 - (sz - mig));
+    };
+    if (sz <= TILE) {
+        // the whole group in one tile: its weights are loaded once and kept
+        // in registers for the maximum, the sum of e^(lw - Mg), and the
+        // quantised scan (whose total is the group's Q)
+        const int n = (int)sz;
+        float v[TILE_LOADS];
+        tile_load(lw, lo, n, v);
+        float m = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < TILE_LOADS; ++k)
+            m = fmaxf(m, v[k]);
+        m = warp_max(m);
+        if (lane == 0)
+            smf[warp] = m;
+        __syncthreads();
+        float Mg = -INFINITY;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            Mg = fmaxf(Mg, smf[w]);
+        float es = 0.0f;
+#pragma unroll
+        for (int k = 0; k < TILE_LOADS; ++k)
+            if (v[k] > -INFINITY)
+                es += __expf(v[k] - Mg);
+        es = warp_sum(es);
+        __syncthreads();  // every thread has read smf
+        if (lane == 0)
+            smf[warp] = es;
+        const int s = scale_bits(sz);
+        uint64_t q[TILE_ITEMS];
+        tile_quantise(v, Mg, s, C, q);  // its barriers also publish smf
+        const uint64_t Qg = tile_scan(q, C, red);
+        if (threadIdx.x == 0) {
+            float e = 0.0f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                e += smf[w];
+            dvs = make_divisor((uint32_t)sz);
+            qNs = Qg / (uint64_t)sz;
+            qRs = (uint32_t)(Qg % (uint64_t)sz);
+            if (Qg == 0ull) {
+                lwg_s = -INFINITY;
+                us = 0ull;
+            } else {
+                lwg_s = ((double)Mg + log((double)e)) - sum->log_total - log((double)sz);
+                us = ticket_offset(seed, fid, frame, PURPOSE_GROUP, (uint32_t)g, Qg);
+            }
+        }
+        __syncthreads();
+        const float lwg = (float)lwg_s;
+        if (Qg == 0ull) {  // no usable weight in the group: it keeps its slots
+            for (int64_t s2 = threadIdx.x; s2 < sz; s2 += blockDim.x) {
+                const int64_t d = dest(s2);
+                if (!PPF_DCHECK(d >= 0 && d < N, &sum->flags, FLAG_INTERNAL))
+                    continue;
+                anc[d] = (int32_t)(lo + s2);
+                lwp[d] = lwg;
+            }
+            return;
+        }
+        const TicketGrid tg = ticket_grid(Qg, us, qNs, qRs, dvs);
+        ticket_parents_staged(C, n, 0, tg, 0, sz, stage, [&](int64_t j, int i) {
+            const int64_t d = dest(j);
+            if (!PPF_DCHECK(d >= 0 && d < N && i >= 0 && i < n, &sum->flags, FLAG_INTERNAL))
+                return;
+            anc[d] = (int32_t)(lo + i);
+            lwp[d] = lwg;
+        });
+        return;
+    }
     // pass 1: group maximum
     float m = -INFINITY;
     for (int64_t i = threadIdx.x; i < sz; i += blockDim.x)
@@ -1332,9 +1403,6 @@ __global__ void __launch_bounds__(TILE_THREADS, 4) rna_kernel(
     __syncthreads();
     const uint64_t Q = Qs, u = us;
     const float lwg = (float)lwg_s;
-    auto dest = [&](int64_t s2) -> int64_t {
-        return (s2 < sz - mig) ? lo + s2 : gn_lo + gn_sz - mig + (s2 - (sz - mig));
-    };
     if (Q == 0ull) {  // no usable weight in the group: it keeps its slots
         for (int64_t s2 = threadIdx.x; s2 < sz; s2 += blockDim.x) {
             const int64_t d = dest(s2);

@@ -24,19 +24,44 @@ constexpr int TILE_SMEM_U64 = TILE + TILE / 16;  // >= (TILE + TILE/32) / 2 floa
 // TILE_THREADS threads: each thread issues all of its TILE / TILE_THREADS
 // loads before its first shared store, so that they are in flight together
 // (a load-store loop waits one memory latency per element).
+constexpr int TILE_LOADS = TILE / TILE_THREADS;  // weights a thread loads per tile
+
+// The loads of tile_weights on their own: thread t gets elements
+// t + k TILE_THREADS of [lo, lo + n) (-inf beyond n), all in flight together.
+__device__ __forceinline__ void tile_load(const float *__restrict__ lw, int64_t lo, int n, float (&v)[TILE_LOADS])
+{
+#pragma unroll
+    for (int k = 0; k < TILE_LOADS; ++k) {
+        const int e = (int)threadIdx.x + k * TILE_THREADS;
+        v[k] = (e < n) ? __ldg(lw + lo + e) : -INFINITY;
+    }
+}
+
+// The rest of tile_weights: the loaded weights through shared memory to the
+// per-thread layout, quantised against M.
+__device__ __forceinline__ void tile_quantise(const float (&v)[TILE_LOADS], float M, int s, uint64_t *buf,
+                                              uint64_t q[TILE_ITEMS])
+{
+    float *f = reinterpret_cast<float *>(buf);
+#pragma unroll
+    for (int k = 0; k < TILE_LOADS; ++k)
+        f[padf((int)threadIdx.x + k * TILE_THREADS)] = v[k];
+    __syncthreads();
+    const int base = threadIdx.x * TILE_ITEMS;
+#pragma unroll
+    for (int k = 0; k < TILE_ITEMS; k += 2)
+        quantise2(f[padf(base + k)], f[padf(base + k + 1)], M, s, q[k], q[k + 1]);
+    __syncthreads();
+}
+
 __device__ __forceinline__ void tile_weights(const float *__restrict__ lw, int64_t lo, int n, float M, int s,
                                              uint64_t *buf, uint64_t q[TILE_ITEMS])
 {
     float *f = reinterpret_cast<float *>(buf);
-    constexpr int TW = TILE / TILE_THREADS;
-    float v[TW];
+    float v[TILE_LOADS];
+    tile_load(lw, lo, n, v);
 #pragma unroll
-    for (int k = 0; k < TW; ++k) {
-        const int e = (int)threadIdx.x + k * TILE_THREADS;
-        v[k] = (e < n) ? __ldg(lw + lo + e) : -INFINITY;
-    }
-#pragma unroll
-    for (int k = 0; k < TW; ++k)
+    for (int k = 0; k < TILE_LOADS; ++k)
         f[padf((int)threadIdx.x + k * TILE_THREADS)] = v[k];
     __syncthreads();
     const int base = threadIdx.x * TILE_ITEMS;
