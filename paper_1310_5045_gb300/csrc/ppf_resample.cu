@@ -817,6 +817,8 @@ __device__ void block_scan_i64(int64_t *a, int n, uint64_t *red, int64_t *total_
 // that the rest of the SM's 256 KB stays L1 cache for the kernel's global
 // reads.
 constexpr int SORT_PER = 16;
+// every key needs a thread: the 1024 threads' runs cover the largest group count
+static_assert(SORT_PER * 1024 >= MAX_SCHED_GROUPS, "block_sort_u64 covers at most SORT_PER x 1024 keys");
 constexpr size_t SORT_SMEM_BYTES = (sizeof(uint64_t) + 2 * sizeof(uint16_t)) * MAX_SCHED_GROUPS;
 __host__ __device__ inline size_t sort_smem_bytes(int cap)
 {
