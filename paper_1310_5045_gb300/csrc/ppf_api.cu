@@ -234,7 +234,7 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
         chk(dalloc(&c->sc.Tg, G + 1), "Tg");
         chk(dalloc(&c->sc.tile_g, 2 * T), "tile groups");
         chk(dalloc(&c->sc.ggrid, G), "group draws");
-        chk(dalloc(&c->sc.split, 2 * (T + N / ppf::ITEM_TICKETS + 1)), "split items");
+        chk(dalloc(&c->sc.split, 4 * (T + G + 2 * (N / ppf::ITEM_TICKETS) + 2)), "split items");
         chk(dalloc(&c->sc.skey, 2 * G), "skey");
         chk(dalloc(&c->sc.sval, 5 * G), "sval");
         chk(dalloc(&c->sc.seg_tick, 2 * G + 1), "seg_tick");

@@ -81,7 +81,8 @@ struct DevSummary {
     uint32_t spread_warps, total_warps;
     uint32_t bin_blocks_done;  // binned path: scatter blocks that finished
     int32_t n_bin_items;       // binned path: likelihood work items of this step
-    int32_t n_split;           // two-stage RPA: extra work items of large or heavy groups
+    int32_t n_split;           // two-stage RPA: extra work items of large or heavy groups (group_grid_kernel)
+    int32_t n_runs;            // and the further runs of heavy tile parts, listed after them (split_runs_kernel)
 };
 
 // two-stage RPA: one group's own systematic draw and where its offspring go
@@ -110,7 +111,7 @@ struct Scratch {
     int64_t *Tg;       // [G+1] tickets below each group start
     int32_t *tile_g;   // [2T] per tile: first group starting at or after it, group starts inside (capped)
     GroupGrid *ggrid;  // [G]  two-stage RPA: every group's draw
-    int32_t *split;    // [2 (T + N / ITEM_TICKETS + 1)] two-stage RPA: extra work items (interior tile or -run, group)
+    int32_t *split;    // [4 (T + G + 2 N / ITEM_TICKETS + 2)] two-stage RPA: extra work items (tile or -1, group, run, 0)
     // scheduler (RPA)
     uint64_t *skey;    // [2G] sort / merge buffers
     int64_t *sval;     // [5G]

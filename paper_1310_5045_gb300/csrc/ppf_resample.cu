@@ -270,8 +270,10 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
     __shared__ uint64_t red[33];
     __shared__ uint64_t su, s_qN;
     __shared__ uint32_t s_qR;
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         sum->n_split = 0;  // the two-stage draw's split list is rebuilt after the scan
+        sum->n_runs = 0;
+    }
     if (kept_by_ess(sum, ess_thr)) {  // N_eff test: keep the particles and the layout
         if (threadIdx.x == 0) {
             sum->degenerate = 1;
@@ -608,14 +610,14 @@ __global__ void __launch_bounds__(TILE_THREADS) fill_route_kernel(
 // of ITEM_TICKETS, so that no block carries a heavy group alone.
 constexpr int64_t GROUP_SPLIT = 2 * TILE;
 
-// One thread per group: the group's draw, and the extra work items of a
-// large or heavy group appended to the split list as (tile, g) for an
-// interior tile or (-run, g) for a further run of tickets (the order of the
-// list does not matter: every entry writes its own tickets).
+// One thread per group: the group's draw; a large group lists all its tile
+// parts (tile, g, run 0), a heavy small group its further runs (-1, g, r),
+// r >= 1, in the split list (four ints an entry; the order of the list does
+// not matter: every entry writes its own tickets).
 __global__ void __launch_bounds__(256) group_grid_kernel(
     int64_t N, int32_t G, const int64_t *__restrict__ goff, const int64_t *__restrict__ Tg,
     const uint64_t *__restrict__ Ct, const uint64_t *__restrict__ Cbl, DevSummary *__restrict__ sum, double ess_thr,
-    uint64_t seed, uint32_t fid, uint32_t frame, GroupGrid *__restrict__ grid, int32_t *__restrict__ split,
+    uint64_t seed, uint32_t fid, uint32_t frame, GroupGrid *__restrict__ grid, int4 *__restrict__ split,
     Balanced bl)
 {
     const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -650,33 +652,70 @@ __global__ void __launch_bounds__(256) group_grid_kernel(
     if (gg.nt == 0)
         return;
     if (e - a > GROUP_SPLIT) {
-        const int64_t t1 = a / TILE + 1, t2 = (e - 1) / TILE;  // tiles starting strictly inside (a, e)
-        if (t2 >= t1) {
-            const int32_t pos = atomicAdd(&sum->n_split, (int32_t)(t2 - t1 + 1));
-            for (int64_t t = t1; t <= t2; ++t) {
-                split[2 * (pos + (t - t1))] = (int32_t)t;
-                split[2 * (pos + (t - t1)) + 1] = g;
-            }
-        }
+        const int64_t t1 = a / TILE, t2 = (e - 1) / TILE;  // every tile the group reaches
+        const int32_t pos = atomicAdd(&sum->n_split, (int32_t)(t2 - t1 + 1));
+        for (int64_t t = t1; t <= t2; ++t)
+            split[pos + (t - t1)] = make_int4((int32_t)t, g, 0, 0);
     } else if (nt > ITEM_TICKETS) {
         const int32_t runs = (int32_t)((nt + ITEM_TICKETS - 1) / ITEM_TICKETS);
         const int32_t pos = atomicAdd(&sum->n_split, runs - 1);
-        for (int32_t r = 1; r < runs; ++r) {
-            split[2 * (pos + r - 1)] = -r;
-            split[2 * (pos + r - 1) + 1] = g;
+        for (int32_t r = 1; r < runs; ++r)
+            split[pos + r - 1] = make_int4(-1, g, r, 0);
+    }
+}
+
+// The part of a large group in one tile: its particles and the group's
+// cumulative weight below them.
+__device__ __forceinline__ void tile_part(const GroupGrid &gg, int32_t t, const uint64_t *__restrict__ Ct,
+                                          int64_t &p0, int64_t &p1, uint64_t &carry)
+{
+    const int64_t lo = (int64_t)t * TILE;
+    p0 = lo > gg.p0 ? lo : gg.p0;
+    p1 = lo + TILE < gg.p1 ? lo + TILE : gg.p1;
+    carry = p0 == gg.p0 ? 0ull : Ct[t] - gg.Ca;
+}
+
+// One thread per tile part listed by group_grid_kernel: a part with more than
+// ITEM_TICKETS offspring appends its further runs (tile, g, r), r >= 1, so
+// that a heavy tile of a large group is drawn by several blocks too.
+__global__ void __launch_bounds__(256) split_runs_kernel(const uint64_t *__restrict__ Ct,
+                                                         const GroupGrid *__restrict__ grid, int4 *__restrict__ split,
+                                                         DevSummary *__restrict__ sum, double ess_thr)
+{
+    if (kept_by_ess(sum, ess_thr) || sum->degenerate)
+        return;
+    const int32_t n0 = sum->n_split;  // the entries group_grid_kernel listed; the runs go after them
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x) {
+        const int4 en = split[i];
+        if (en.x < 0 || en.z != 0)
+            continue;
+        const GroupGrid gg = grid[en.y];
+        int64_t p0, p1;
+        uint64_t c_lo;
+        tile_part(gg, en.x, Ct, p0, p1, c_lo);
+        const uint64_t c_hi = p1 == gg.p1 ? gg.Q : Ct[en.x + 1] - gg.Ca;
+        const int64_t nt = gg.nt;
+        const int64_t j_lo = c_lo == 0 ? 0 : tickets_below(c_lo, nt, gg.u, gg.Q);
+        const int64_t j_hi = c_hi == gg.Q ? nt : tickets_below(c_hi, nt, gg.u, gg.Q);
+        if (j_hi - j_lo > ITEM_TICKETS) {
+            const int32_t runs = (int32_t)((j_hi - j_lo + ITEM_TICKETS - 1) / ITEM_TICKETS);
+            const int32_t pos = n0 + atomicAdd(&sum->n_runs, runs - 1);
+            for (int32_t r = 1; r < runs; ++r)
+                split[pos + r - 1] = make_int4(en.x, en.y, r, 0);
         }
     }
 }
 
-// One work item of the two-stage draw: particles [p0, p1) of group gg, the
-// group's tickets [j0, j1) among them; carry is the group's cumulative weight
-// below p0.
+// One work item of the two-stage draw: particles [p0, p1) of group gg, carry
+// the group's cumulative weight below p0.  Its tickets: the group's [j0, j1)
+// among them (run < 0), or run `run` of ITEM_TICKETS among the tickets of a
+// one-tile part (run >= 0).
 __device__ __forceinline__ void group_fill_item(const float *__restrict__ lw, int64_t N, int32_t G,
                                                 const int64_t *__restrict__ Tg, const GroupGrid &gg, int64_t p0,
-                                                int64_t p1, int64_t j0, int64_t j1, uint64_t carry, float M, int s,
-                                                const DevSummary *__restrict__ sum, int32_t *__restrict__ out,
-                                                int32_t *__restrict__ kept_anc, const Balanced &bl, uint64_t *C,
-                                                uint16_t *stage, uint64_t *red)
+                                                int64_t p1, int64_t j0, int64_t j1, int32_t run, uint64_t carry,
+                                                float M, int s, const DevSummary *__restrict__ sum,
+                                                int32_t *__restrict__ out, int32_t *__restrict__ kept_anc,
+                                                const Balanced &bl, uint64_t *C, uint16_t *stage, uint64_t *red)
 {
     const int64_t nt = gg.nt;
     Divisor dv;
@@ -700,7 +739,14 @@ __device__ __forceinline__ void group_fill_item(const float *__restrict__ lw, in
         // no ticket lies below the group's start, all of them below its end
         const int64_t c_lo = carry == 0 ? 0 : tickets_below(carry, nt, gg.u, gg.Q);
         const int64_t c_hi = c0 + n == gg.p1 ? nt : tickets_below(carry + tot, nt, gg.u, gg.Q);
-        const int64_t t_lo = c_lo > j0 ? c_lo : j0, t_hi = c_hi < j1 ? c_hi : j1;
+        int64_t t_lo, t_hi;
+        if (run >= 0) {
+            t_lo = c_lo + (int64_t)run * ITEM_TICKETS;
+            t_hi = (t_lo + ITEM_TICKETS < c_hi) ? t_lo + ITEM_TICKETS : c_hi;
+        } else {
+            t_lo = c_lo > j0 ? c_lo : j0;
+            t_hi = c_hi < j1 ? c_hi : j1;
+        }
         if (kept_anc)
             ticket_parents_routed(C, n, carry, tg, t_lo, t_hi, stage, kt, kept_anc, out, gg.tg0, (int32_t)c0, N, G,
                                   bl, Tg, &sum->flags);
@@ -713,11 +759,12 @@ __device__ __forceinline__ void group_fill_item(const float *__restrict__ lw, in
 }
 
 // Blocks [0, n_workers) take the split list's entries in turn; block
-// n_workers + g takes group g: whole, its head when the group is large, or
-// its first ITEM_TICKETS tickets when it is heavy.  s: scale_bits(N).
+// n_workers + g takes a small group g whole, or its first ITEM_TICKETS
+// tickets when it is heavy (a large group is all in the split list).
+// s: scale_bits(N).
 __global__ void __launch_bounds__(TILE_THREADS, 4) group_fill_kernel(
     const float *__restrict__ lw, int64_t N, int32_t G, const int64_t *__restrict__ Tg,
-    const uint64_t *__restrict__ Ct, const GroupGrid *__restrict__ grid, const int32_t *__restrict__ split,
+    const uint64_t *__restrict__ Ct, const GroupGrid *__restrict__ grid, const int4 *__restrict__ split,
     int32_t n_workers, const DevSummary *__restrict__ sum, double ess_thr, int32_t *__restrict__ out,
     int32_t *__restrict__ kept_anc, Balanced bl, int s)
 {
@@ -730,32 +777,30 @@ __global__ void __launch_bounds__(TILE_THREADS, 4) group_fill_kernel(
         const double ess = sum->ess;
         const int32_t deg = sum->degenerate;
         const float M = sum->M;
-        if (ess >= ess_thr || deg || gg.nt == 0)
-            return;  // kept by the N_eff test, no usable weight, or no offspring
-        int64_t p1 = gg.p1, j1 = gg.nt;
-        if (p1 - gg.p0 > GROUP_SPLIT)
-            p1 = (gg.p0 / TILE + 1) * TILE;  // the head; the split list has the rest
-        else if (j1 > ITEM_TICKETS)
-            j1 = ITEM_TICKETS;  // the first run; the split list has the rest
-        group_fill_item(lw, N, G, Tg, gg, gg.p0, p1, 0, j1, 0, M, s, sum, out, kept_anc, bl, C, stage, red);
+        if (ess >= ess_thr || deg || gg.nt == 0 || gg.p1 - gg.p0 > GROUP_SPLIT)
+            return;  // kept by the N_eff test, no usable weight, no offspring, or a large group
+        const int64_t j1 = gg.nt > ITEM_TICKETS ? ITEM_TICKETS : gg.nt;  // a heavy group's first run
+        group_fill_item(lw, N, G, Tg, gg, gg.p0, gg.p1, 0, j1, -1, 0, M, s, sum, out, kept_anc, bl, C, stage,
+                        red);
         return;
     }
     if (sum->ess >= ess_thr || sum->degenerate)
         return;
     const float M = sum->M;
-    const int32_t n_items = sum->n_split;
+    const int32_t n_items = sum->n_split + sum->n_runs;
     for (int32_t it = (int32_t)blockIdx.x; it < n_items; it += n_workers) {
-        const int32_t code = split[2 * it], g = split[2 * it + 1];
-        const GroupGrid gg = grid[g];
-        if (code >= 0) {  // an interior tile of a large group: all its tickets
-            const int64_t p0 = (int64_t)code * TILE;
-            const int64_t p1 = (p0 + TILE < gg.p1) ? p0 + TILE : gg.p1;
-            group_fill_item(lw, N, G, Tg, gg, p0, p1, 0, gg.nt, Ct[code] - gg.Ca, M, s, sum, out, kept_anc, bl,
-                            C, stage, red);
-        } else {  // run -code of a heavy group
-            const int64_t j0 = (int64_t)(-code) * ITEM_TICKETS;
+        const int4 en = split[it];
+        const GroupGrid gg = grid[en.y];
+        if (en.x >= 0) {  // run en.z of a large group's part in tile en.x
+            int64_t p0, p1;
+            uint64_t carry;
+            tile_part(gg, en.x, Ct, p0, p1, carry);
+            group_fill_item(lw, N, G, Tg, gg, p0, p1, 0, 0, en.z, carry, M, s, sum, out, kept_anc, bl, C, stage,
+                            red);
+        } else {  // run en.z of a heavy small group
+            const int64_t j0 = (int64_t)en.z * ITEM_TICKETS;
             const int64_t j1 = (j0 + ITEM_TICKETS < (int64_t)gg.nt) ? j0 + ITEM_TICKETS : (int64_t)gg.nt;
-            group_fill_item(lw, N, G, Tg, gg, gg.p0, gg.p1, j0, j1, 0, M, s, sum, out, kept_anc, bl, C, stage,
+            group_fill_item(lw, N, G, Tg, gg, gg.p0, gg.p1, j0, j1, -1, 0, M, s, sum, out, kept_anc, bl, C, stage,
                             red);
         }
     }
@@ -1681,14 +1726,16 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     // GS and SGS: the kept tickets go straight to their balanced slots
     const bool kept_direct = rpa && scheme != PPF_RPA_LGS && scheme != PPF_RPA2_LGS;
     if (two_stage) {  // stage 2: every group draws its own offspring
+        int4 *split = reinterpret_cast<int4 *>(c->sc.split);
         group_grid_kernel<<<(c->G + 255) / 256, 256, 0, c->stream>>>(
             c->N, c->G, c->goff, c->sc.Tg, c->sc.Ct, c->sc.Cbl, c->sum, ess_thr, c->m.seed, c->m.filter_id,
-            (uint32_t)c->last_frame, c->sc.ggrid, c->sc.split, balanced_layout(c->N, c->G));
-        const int n_workers = 2 * c->num_sms < T ? 2 * c->num_sms : T;
+            (uint32_t)c->last_frame, c->sc.ggrid, split, balanced_layout(c->N, c->G));
+        split_runs_kernel<<<c->num_sms, 256, 0, c->stream>>>(c->sc.Ct, c->sc.ggrid, split, c->sum, ess_thr);
+        const int n_workers = 4 * c->num_sms;
         group_fill_kernel<<<n_workers + c->G, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
-            lw, c->N, c->G, c->sc.Tg, c->sc.Ct, c->sc.ggrid, c->sc.split, n_workers, c->sum, ess_thr, out,
+            lw, c->N, c->G, c->sc.Tg, c->sc.Ct, c->sc.ggrid, split, n_workers, c->sum, ess_thr, out,
             kept_direct ? c->anc : nullptr, balanced_layout(c->N, c->G), scale_bits(c->N));
-        c->launches += 1;
+        c->launches += 2;
     } else {
         const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
         if (kept_direct) {

@@ -181,6 +181,7 @@ def lockstep(pf, gm, om, frames_np, frames_gpu, scheme, K, alpha=0.1, check_resa
         if log is not None:  # the most offspring any group's particles had
             per_group = np.bincount(np.searchsorted(goff0, a1, side="right") - 1, minlength=len(goff0) - 1)
             log.append(("offspring", k, int(per_group.max())))
+            log.append(("tile offspring", k, int(np.bincount(a1 // 4096).max())))
         assert np.array_equal(goff1, goff_ref)
         l1 = lwp1.cpu().double().numpy()
         tol = 1e-5 * np.maximum(1.0, np.abs(lwr_ref))

@@ -82,6 +82,21 @@ def test_rpa_schemes_in_sequence(ppf, movie, N, gs):
     pf.close()
 
 
+@pytest.mark.parametrize("scheme", [orc.RPA2_GS, orc.RPA2_SGS, orc.RPA2_LGS])
+def test_two_stage_large_groups_with_heavy_tiles(ppf, movie, scheme):
+    """Groups of 50000 particles (above two tiles) are drawn one tile part per
+    block, and a tile part with more than 8192 offspring (the concentrated
+    clouds of this movie put several times that in one tile) one run of 8192
+    tickets per block."""
+    from gpu_common import lockstep, paired_models
+    gm, om = paired_models(ppf, seed=7)
+    pf = ppf.ParticleFilter(gm, 200000, group_size=50000)
+    log = []
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), scheme, K=5, log=log)
+    assert max(e[2] for e in log if e[0] == "tile offspring") > 8192
+    pf.close()
+
+
 @pytest.mark.parametrize("scheme", [orc.SYSTEMATIC, orc.RPA_SGS, orc.RNA, orc.RPA2_GS, orc.ARNA])
 def test_ess_gated_resampling(ppf, scheme):
     """Alg. 1's N_eff test on the device: with sigma_xi^2 = 2000 and a
