@@ -973,6 +973,165 @@ __device__ __forceinline__ int lower_bound_i64(const int64_t *a, int n, int64_t 
     return lo;
 }
 
+// first index in sorted a[0..n) with a[i] > v (int32 values in shared memory)
+__device__ __forceinline__ int upper_bound_i32(const int32_t *a, int n, int32_t v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] > v)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// exclusive prefix of a[0..n) in place, a[n] = the total (one block; every
+// thread takes one contiguous segment)
+__device__ void block_scan_smem_i32(int32_t *a, int n, uint64_t *red)
+{
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int i0 = threadIdx.x * per;
+    uint64_t loc = 0;
+    for (int k = 0; k < per; ++k)
+        if (i0 + k < n)
+            loc += (uint32_t)a[i0 + k];
+    uint64_t total;
+    uint64_t run = block_excl_scan_u64(loc, red, &total);
+    for (int k = 0; k < per; ++k)
+        if (i0 + k < n) {
+            const int32_t v = a[i0 + k];
+            a[i0 + k] = (int32_t)run;
+            run += (uint32_t)v;
+        }
+    if (threadIdx.x == 0)
+        a[n] = (int32_t)total;
+    __syncthreads();
+}
+
+// Shared memory of schedule_kernel: the sort's buffer, and at least what
+// schedule_links_balanced lays out (two u16 id lists, three int32 arrays).
+__host__ __device__ inline size_t sched_smem_bytes(int G)
+{
+    const size_t need = 10 * (size_t)(G > 0 ? G : 1) + 64;
+    const size_t sort = sort_smem_bytes(G);
+    return sort > need ? sort : need;
+}
+
+// GS and SGS: every group ends at its balanced size, so the new offsets are
+// the balanced ones and every sender keeps exactly n_g of its tickets (the
+// fill already wrote those).  What remains are the links: the pieces of
+// [0, D) cut at every sender and receiver prefix boundary, in the senders'
+// and receivers' list order (group order for GS, sorted for SGS), and the
+// copy work items of the links.  Everything but Tg stays in shared memory:
+// the list order's group ids (u16), the prefix sums of the amounts (int32,
+// with the total D as a sentinel), and the merge of the two prefix lists.
+__device__ void schedule_links_balanced(const SchedArgs &A, int nS, int nR, bool sorted, uint64_t *sm,
+                                        uint64_t *red)
+{
+    const int32_t G = A.G;
+    const Balanced &bl = A.bl;
+    DevSummary *sum = A.sum;
+    const uint64_t *Skey = A.key, *Rkey = A.key + G;
+    uint16_t *gS = reinterpret_cast<uint16_t *>(sm);
+    uint16_t *gR = gS + nS;
+    int32_t *PS = reinterpret_cast<int32_t *>(sm) + ((nS + nR + 1) / 2 + 1);  // after the ids, 4-byte aligned
+    int32_t *PR = PS + nS + 1;
+    int32_t *MG = PR + nR + 1;
+    auto amount = [&](uint64_t k) -> int32_t {
+        return sorted ? (int32_t)(0xFFFFFFFFFFull - (k >> 24)) : (int32_t)(k >> 24);
+    };
+    // 1. ids and amounts in list order; the balanced offsets and extent
+    for (int i = threadIdx.x; i < nS; i += blockDim.x) {
+        const uint64_t k = Skey[i];
+        gS[i] = (uint16_t)(k & 0xFFFFFFull);
+        PS[i] = amount(k);
+    }
+    for (int j = threadIdx.x; j < nR; j += blockDim.x) {
+        const uint64_t k = Rkey[j];
+        gR[j] = (uint16_t)(k & 0xFFFFFFull);
+        PR[j] = amount(k);
+    }
+    for (int g = threadIdx.x; g <= G; g += blockDim.x)
+        A.goff_new[g] = balanced_offset(bl, g);
+    if (threadIdx.x == 0) {
+        sum->max_group = bl.q + (bl.r > 0 ? 1 : 0);
+        sum->min_group = bl.q;
+    }
+    __syncthreads();
+    // 2. exclusive prefix sums (PS[nS] = PR[nR] = D)
+    block_scan_smem_i32(PS, nS, red);
+    block_scan_smem_i32(PR, nR, red);
+    // 3. the merge of the two start lists (senders first on ties)
+    for (int i = threadIdx.x; i < nS; i += blockDim.x)
+        MG[i + lower_bound_i32(PR, nR, PS[i])] = PS[i];
+    for (int j = threadIdx.x; j < nR; j += blockDim.x)
+        MG[j + upper_bound_i32(PS, nS, PR[j])] = PR[j];
+    __syncthreads();
+    // 4. one link per distinct start, in order; each thread takes one
+    //    contiguous range of the merge and knows its links' places
+    const int nm = nS + nR;
+    const int per = (nm + blockDim.x - 1) / blockDim.x;
+    const int i0 = threadIdx.x * per;
+    uint64_t c = 0;
+    for (int k = 0; k < per; ++k) {
+        const int i = i0 + k;
+        if (i < nm && (i == 0 || MG[i] != MG[i - 1]))
+            ++c;
+    }
+    uint64_t L;
+    const uint64_t pos0 = block_excl_scan_u64(c, red, &L);
+    uint64_t pos = pos0, chunks = 0;
+    for (int k = 0; k < per; ++k) {
+        const int i = i0 + k;
+        if (i < nm && (i == 0 || MG[i] != MG[i - 1])) {
+            const int32_t a = MG[i];
+            const int si = upper_bound_i32(PS, nS, a) - 1;  // the sender piece holding a
+            const int rj = upper_bound_i32(PR, nR, a) - 1;
+            const int32_t e = PS[si + 1] < PR[rj + 1] ? PS[si + 1] : PR[rj + 1];
+            const int32_t gs = gS[si], gr = gR[rj];
+            const int64_t ts = A.Tg[gs], tr0 = A.Tg[gr], tr1 = A.Tg[gr + 1];
+            // a sender keeps n_s; a receiver keeps its o_r and is filled after them
+            A.seg_tick[G + pos] = ts + target_of(bl, gs) + (a - PS[si]);
+            A.seg_dst[G + pos] = balanced_offset(bl, gr) + (tr1 - tr0) + (a - PR[rj]);
+            A.seg_len[G + pos] = e - a;
+            chunks += (uint64_t)((e - a + COPY_CHUNK - 1) / COPY_CHUNK);
+            ++pos;
+        }
+    }
+    // 5. copy work items: none for the kept segments [0, G), then the links
+    uint64_t total_chunks;
+    uint64_t run = block_excl_scan_u64(chunks, red, &total_chunks);
+    for (int g = threadIdx.x; g < G; g += blockDim.x)
+        A.seg_chunk[g] = 0;
+    for (uint64_t p = pos0; p < pos; ++p) {
+        A.seg_chunk[G + p] = (int32_t)run;
+        run += (uint64_t)((A.seg_len[G + p] + COPY_CHUNK - 1) / COPY_CHUNK);
+    }
+    if (threadIdx.x == 0) {
+        const int32_t nseg = G + (int32_t)L;
+        A.seg_chunk[nseg] = (int32_t)total_chunks;
+        A.seg_chunk[2 * G + 1] = nseg;  // the segment count
+        sum->n_chunks = (int32_t)total_chunks;
+        sum->links = (int64_t)L;
+        sum->moved = PS[nS];
+    }
+}
+
 __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
 {
     extern __shared__ uint64_t sm[];   // sort_smem_bytes(G) (GS: G words)
@@ -1042,6 +1201,10 @@ __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs A)
     if (sorted) {
         block_sort_u64(Skey, nS, sm, G);
         block_sort_u64(Rkey, nR, sm, G);
+    }
+    if (A.links_only) {
+        schedule_links_balanced(A, nS, nR, sorted, sm, red);
+        return;
     }
     auto amount = [&](uint64_t k) -> int64_t {
         return sorted ? (int64_t)(0xFFFFFFFFFFull - (k >> 24)) : (int64_t)(k >> 24);
@@ -1684,11 +1847,7 @@ static cudaError_t launch_schedule(ppf_ctx *c, int scheme, bool two_stage)
     A.sum = c->sum;
     A.links_only = A.scheme != PPF_RPA_LGS;
     A.bl = balanced_layout(c->N, c->G);
-    // Greedy needs no sort: shared memory only for its two prefix arrays (at
-    // most G words), which leaves the rest of the SM's L1 to the global reads
-    const size_t sched_smem = scheme == PPF_RPA_GS || scheme == PPF_RPA2_GS
-                                  ? sizeof(int64_t) * (size_t)(c->G > 0 ? c->G : 1)
-                                  : sort_smem_bytes(c->G);
+    const size_t sched_smem = sched_smem_bytes(c->G);
     schedule_kernel<<<1, 1024, sched_smem, c->side_stream>>>(A);
     e = cudaGetLastError();
     if (e == cudaSuccess)
