@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 5) tile_group_totals_kernel(
     const int64_t lo = (int64_t)blockIdx.x * TILE;
     const int n = (int)(N - lo < TILE ? N - lo : TILE);
     // the weights first, so that their loads are in flight during the search
-    // thread 0 does for the tile's group starts.  Thread t holds elements
+    // warp 0 does for the tile's group starts.  Thread t holds elements
     // 4 (t + k TILE_THREADS) + j, j < 4.
     constexpr int V = TILE / 4 / TILE_THREADS;
     const bool full = n == TILE && ((reinterpret_cast<uintptr_t>(lw + lo) & 15) == 0);
@@ -162,41 +162,58 @@ __global__ void __launch_bounds__(TILE_THREADS, 5) tile_group_totals_kernel(
         for (int k = 0; k < V; ++k)
             v[k] = __ldg(v4 + k * TILE_THREADS);
     }
-    if (threadIdx.x == 0) {
-        // first g with goff[g] >= lo.  For a balanced layout the guess
-        // lo G / N or its successor is the answer (two loads); otherwise the
-        // guess halves the bracket of the bisection.
-        const int32_t g = (int32_t)(lo * (int64_t)G / N);
-        int32_t a = 0, b = G + 1;
-        if (goff[g] >= lo) {
-            b = g;
-            if (g == 0 || goff[g - 1] < lo)
-                a = g;
-        } else {
-            a = g + 1;
-            if (goff[g + 1] >= lo)
-                b = g + 1;
+    if (threadIdx.x < 32) {
+        // warp 0: the first g with goff[g] >= lo (goff[G] = N >= lo, so it
+        // exists).  The first round probes the 32 groups around the balanced
+        // layout's guess lo G / N, which holds the answer for a balanced
+        // layout; otherwise 32-way rounds narrow [a, b] (invariant: the
+        // answer lies in it) by a factor 32 each.
+        const int lane = threadIdx.x;
+        const int32_t guess = (int32_t)(lo * (int64_t)G / N);
+        int32_t a = guess > 0 ? guess - 1 : 0, b = a + 31 < G ? a + 31 : G;
+        {
+            const int32_t p = a + lane;
+            const unsigned m = __ballot_sync(0xffffffffu, p <= b && goff[p] >= lo);
+            if (m & 1u) {          // goff[a] >= lo: the answer is at or before a
+                b = a;
+                a = 0;
+            } else if (m != 0u) {  // the first lane at or past lo
+                a = b = a + __ffs(m) - 1;
+            } else {               // every probe below lo
+                a = b + 1;
+                b = G;
+            }
         }
         while (a < b) {
-            const int32_t mid = (a + b) >> 1;
-            if (goff[mid] < lo)
-                a = mid + 1;
-            else
-                b = mid;
+            const int32_t step = (b - a + 30) / 31;  // 31 steps reach b
+            const int32_t p = a + lane * step;
+            const unsigned m = __ballot_sync(0xffffffffu, p <= b && goff[p] >= lo);
+            if (m & 1u) {
+                b = a;
+            } else if (m != 0u) {
+                const int f = __ffs(m) - 1;  // probes f - 1 below lo, f at or past it
+                b = a + f * step;
+                a = a + (f - 1) * step + 1;
+            } else {
+                const int last = (b - a) / step;  // the last probe (at or below b)
+                a = a + last * step + 1;
+            }
         }
-        gfirst = a;
-        int ns = 0;  // starts inside the tile (GT_MASKED + 1 means more)
-        for (int32_t gg = a; gg <= G && ns <= GT_MASKED; ++gg) {
-            const int64_t pos = goff[gg];
-            if (pos >= lo + n)
-                break;
-            if (ns < GT_MASKED)
-                spos[ns] = (int)(pos - lo);
-            ++ns;
+        // the group starts inside the tile: lanes 0 .. GT_MASKED look at
+        // goff[a + lane] (a prefix of them lie inside; lane GT_MASKED tells
+        // whether there are more than GT_MASKED)
+        const int32_t gg = a + lane;
+        const bool inside = lane <= GT_MASKED && gg <= G && goff[gg] < lo + n;
+        const unsigned mi = __ballot_sync(0xffffffffu, inside);
+        const int ns = __popc(mi);
+        if (inside && lane < GT_MASKED)
+            spos[lane] = (int)(goff[gg] - lo);
+        if (lane == 0) {
+            gfirst = a;
+            nstart = ns;
+            tile_g[2 * blockIdx.x] = a;
+            tile_g[2 * blockIdx.x + 1] = ns;
         }
-        nstart = ns;
-        tile_g[2 * blockIdx.x] = a;
-        tile_g[2 * blockIdx.x + 1] = ns;
     }
     __syncthreads();
     const int ns = nstart;
