@@ -267,12 +267,13 @@ def timed_frames(pf, frames, k0, K, scheme, alpha, stream):
 
 def spread_ab(ppf, params, rank, n, stream, args):
     """Frame 1 (the prior draw, spread over the whole frame) on each
-    likelihood path, and an ARNA run through a movie whose spot vanishes for
-    ten frames (direct path forced against the automatic choice)."""
+    likelihood path; the first four frames with systematic resampling; and an
+    ARNA run through a movie whose spot vanishes for ten frames (direct path
+    forced against the automatic choice)."""
     import torch
     import synth
-    out = {"workload": f"spot512 at N={n:,}: frame 1 from the prior; and 5 frames, the spot gone for 10, 5 more "
-                       "(ARNA, maximum alpha 0.5)"}
+    out = {"workload": f"spot512 at N={n:,}: frame 1 from the prior; frames 1-4 with systematic resampling; and "
+                       "5 frames, the spot gone for 10, 5 more (ARNA, maximum alpha 0.5)"}
     mv, _ = make_workload(20, seed=0)
     blank = synth.make_movie(W=W, H=H, K=20, sigma=1.5, amplitude=0.0, background=10.0, seed=99)
     frames = torch.from_numpy(mv.frames).cuda()
@@ -295,6 +296,25 @@ def spread_ab(ppf, params, rank, n, stream, args):
         first[name] = {"ms": e0.elapsed_time(e1), "step_ms": pr["step_ms"], "binned": pf.last_step_binned()}
         pf.close()
     out["frame1"] = first
+    # the first frames with systematic resampling: the draw after the spread
+    # frame concentrates the cloud, so the automatic choice goes direct at once
+    sysrun = {}
+    for name, path in (("direct", ppf.PATH_DIRECT), ("auto", ppf.PATH_AUTO)):
+        pf = ppf.ParticleFilter(model, n, group_size=GROUP, stream=stream)
+        pf.set_likelihood_path(path)
+        ms, binned = [], []
+        for k in range(1, 5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pf.step(frames[k - 1], k)
+            e1.record(stream)
+            pf.resample(ppf.SYSTEMATIC)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            binned.append(pf.last_step_binned())
+        sysrun[name] = {"step_ms_per_frame": ms, "binned": binned}
+        pf.close()
+    out["first_frames_systematic"] = sysrun
     lostrun = {}
     for name, path in (("direct", ppf.PATH_DIRECT), ("auto", ppf.PATH_AUTO)):
         pf = ppf.ParticleFilter(model, n, group_size=GROUP, stream=stream)

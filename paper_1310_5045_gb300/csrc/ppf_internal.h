@@ -26,6 +26,11 @@ constexpr int ITEM_TICKETS = 8192;  // tickets per fill work item
 constexpr int COPY_CHUNK = 8192;    // slots per routing-copy work item
 constexpr int MAX_RADIUS = 8;
 constexpr int MAX_SCHED_GROUPS = 16384;
+// A proportional draw (systematic, RPA) with N_eff below N / BIN_CONCENTRATE
+// fills every warp of 32 consecutive slots with the children of one or two
+// parents, so the next step reads coherent patches whatever the spread
+// before the draw: the resampling then sets the next step to the direct path.
+constexpr double BIN_CONCENTRATE = 64.0;
 constexpr int SCAN_SMEM_TILES = 16384;  // tile scan in shared memory up to this many tiles (N <= 67 M)
 constexpr int BIN_MAX_BINS = 3073;      // binned likelihood: at most this many bins (tiles + 1)
 

@@ -271,7 +271,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 5) tile_group_totals_kernel(
 // ---------------------------------------------------------------- R2 scan
 // One block: exclusive tile prefix, total Q, ticket offset u, tickets below
 // each tile start, fill work items (and the tile of each item when item_tile
-// is given); for RPA the tickets below each group start.
+// is given); for RPA (rpa = 1) and ARNA (rpa = 2) the tickets below each
+// group start.  A proportional draw (rpa != 2) at a low N_eff also sets the
+// next step to the direct likelihood path.
 // When the T + 1 tile values fit the dynamic shared memory (T <= smem_tiles),
 // they are loaded there with coalesced reads, and each of the two prefix sums
 // gives every thread one contiguous segment: a local sum, one block scan,
@@ -354,6 +356,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
             sum->n_items = 0;
         return;
     }
+    if (threadIdx.x == 0 && rpa != 2 && sum->ess < (double)N / BIN_CONCENTRATE)
+        sum->bin_next = 0;  // a concentrating proportional draw: the next step is direct
     for (int t = threadIdx.x; t <= T; t += blockDim.x) {
         const int64_t v = (t == T) ? N : tickets_below_grid(in_smem ? sT[t] : Ct[t], tg);
         Tt[t] = v;
@@ -1967,7 +1971,7 @@ cudaError_t launch_resample_arna(ppf_ctx *c, float alpha, double ess_thr)
     const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
     tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
         c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, nullptr, c->sum, ess_thr, c->m.seed, c->m.filter_id,
-        (uint32_t)c->last_frame, c->goff, c->G, 1, c->sc.Cbl, c->sc.Tg, st_tiles, make_divisor((uint32_t)c->N));
+        (uint32_t)c->last_frame, c->goff, c->G, 2, c->sc.Cbl, c->sc.Tg, st_tiles, make_divisor((uint32_t)c->N));
     arna_prep_kernel<<<1, 1024, sort_smem_bytes(c->G), c->stream>>>(
         c->goff, c->G, alpha, c->sum, ess_thr, c->sc.Tg, c->ring, c->succ, c->m.seed, c->m.filter_id,
         (uint32_t)c->last_frame);

@@ -536,18 +536,28 @@ def test_binned_path_lockstep(ppf, movie, scheme):
 
 def test_automatic_path_choice(ppf):
     """Chosen on the device: the prior draw (spread over the frame) is binned;
-    once the particles have collapsed onto the spot the direct path runs."""
+    the systematic draw after it (N_eff far below N / 64) collapses the cloud
+    onto the spot, so the next step is direct already.  Without resampling
+    (SIS) or with RNA's local draws the cloud stays spread, and so does the
+    binned path."""
     from gpu_common import paired_models
     mv = synth.make_movie(W=512, H=512, K=6, sigma=1.5, amplitude=50.0, background=10.0, seed=2)
     gm, _ = paired_models(ppf, width=512, height=512, patch_radius=5, seed=2)
-    pf = ppf.ParticleFilter(gm, 200_000, group_size=4096)
     fr = gpu_frames(mv)
-    seen = []
-    for k in range(1, 7):
-        pf.step(fr[k - 1], k)
-        seen.append(pf.last_step_binned())
-        pf.resample(ppf.SYSTEMATIC)
-    assert seen[0] and not seen[-1], seen
+    for scheme, want in [(ppf.SYSTEMATIC, [True, False]), (ppf.RPA_SGS, [True, False]), (None, [True, True]),
+                         (ppf.RNA, [True, True])]:
+        pf = ppf.ParticleFilter(gm, 200_000, group_size=4096)
+        seen = []
+        for k in range(1, 7 if scheme == ppf.SYSTEMATIC else 3):
+            pf.step(fr[k - 1], k)
+            seen.append(pf.last_step_binned())
+            if scheme is not None:
+                pf.resample(scheme, 0.1)
+        assert seen[:2] == want, (scheme, seen)
+        if scheme == ppf.SYSTEMATIC:
+            assert not any(seen[1:]), seen
+        pf.close()
+    pf = ppf.ParticleFilter(gm, 200_000, group_size=4096)
     with pytest.raises(ppf.PPFError):
         pf.set_likelihood_path(7)
     pf.close()
