@@ -60,7 +60,7 @@ void free_all(ppf_ctx *c)
 {
     void *ptrs[] = {c->tang[0], c->tang[1], c->gpart,
                     c->state[0], c->state[1], c->anc, c->anc_sys, c->lwp, c->goff, c->goff_new, c->ring, c->succ, c->Zp,
-                    c->frame_buf[0], c->frame_buf[1], c->lmap, c->part, c->sum, c->est_dev, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sc.Cbl,
+                    c->frame_buf[0], c->frame_buf[1], c->lmap, c->part, c->sum, c->est_dev, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.extra, c->sc.Cbl,
                     c->sc.Tg, c->sc.tile_g, c->sc.ggrid, c->sc.split, c->sc.skey, c->sc.sval, c->sc.seg_tick, c->sc.seg_dst, c->sc.seg_len,
                     c->sc.seg_chunk, c->bin_key, c->bin_l, c->bin_tot, c->bin_item, c->bin_rec};
     for (void *p : ptrs)
@@ -229,7 +229,7 @@ ppf_status ppf_create(const ppf_model *m, int64_t n, int32_t group_size, void *s
         chk(dalloc(&c->sc.Ct, T + 1), "Ct");
         chk(dalloc(&c->sc.Tt, T + 1), "Tt");
         chk(dalloc(&c->sc.item_off, T + 1), "item_off");
-        chk(dalloc(&c->sc.item_tile, T + (N + ppf::ITEM_TICKETS - 1) / ppf::ITEM_TICKETS), "item_tile");
+        chk(dalloc(&c->sc.extra, 2 * (N / ppf::ITEM_TICKETS + 1)), "further runs");
         chk(dalloc(&c->sc.Cbl, G + 1), "Cbl");
         chk(dalloc(&c->sc.Tg, G + 1), "Tg");
         chk(dalloc(&c->sc.tile_g, 2 * T), "tile groups");

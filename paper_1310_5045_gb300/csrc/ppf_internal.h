@@ -88,6 +88,7 @@ struct DevSummary {
     int32_t n_bin_items;       // binned path: likelihood work items of this step
     int32_t n_split;           // two-stage RPA: extra work items of large or heavy groups (group_grid_kernel)
     int32_t n_runs;            // and the further runs of heavy tile parts, listed after them (split_runs_kernel)
+    int32_t n_extra;           // the fill's further runs of ticket-heavy tiles (tile_tickets_kernel)
 };
 
 // two-stage RPA: one group's own systematic draw and where its offspring go
@@ -111,7 +112,7 @@ struct Scratch {
     uint64_t *Ct;      // [T+1] exclusive tile prefix
     int64_t *Tt;       // [T+1] tickets below each tile start
     int32_t *item_off; // [T+1] fill work-item prefix per tile
-    int32_t *item_tile; // [T + ceil(N / ITEM_TICKETS)] tile of every fill work item
+    int32_t *extra;    // [2 (N / ITEM_TICKETS + 1)] the fill's further runs (tile, run) of ticket-heavy tiles
     uint64_t *Cbl;     // [G+1] local prefix at group starts (within their tile)
     int64_t *Tg;       // [G+1] tickets below each group start
     int32_t *tile_g;   // [2T] per tile: first group starting at or after it, group starts inside (capped)

@@ -273,7 +273,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 5) tile_group_totals_kernel(
 // each tile start, fill work items (and the tile of each item when item_tile
 // is given); for RPA (rpa = 1) and ARNA (rpa = 2) the tickets below each
 // group start.  A proportional draw (rpa != 2) at a low N_eff also sets the
-// next step to the direct likelihood path.
+// next step to the direct likelihood path.  With prefix_only the kernel stops
+// after the prefix and the draw (tile_tickets_kernel does the rest in
+// parallel).
 // When the T + 1 tile values fit the dynamic shared memory (T <= smem_tiles),
 // they are loaded there with coalesced reads, and each of the two prefix sums
 // gives every thread one contiguous segment: a local sum, one block scan,
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
     int64_t N, int32_t T, const uint64_t *__restrict__ Qt, uint64_t *__restrict__ Ct, int64_t *__restrict__ Tt,
     int32_t *__restrict__ item_off, int32_t *__restrict__ item_tile, DevSummary *sum, double ess_thr, uint64_t seed,
     uint32_t fid, uint32_t frame, const int64_t *__restrict__ goff, int32_t G, int rpa,
-    const uint64_t *__restrict__ Cbl, int64_t *__restrict__ Tg, int32_t smem_tiles, Divisor ndiv)
+    const uint64_t *__restrict__ Cbl, int64_t *__restrict__ Tg, int32_t smem_tiles, Divisor ndiv, int prefix_only)
 {
     extern __shared__ uint64_t sT[];  // (smem_tiles + 1) tile values
     __shared__ uint64_t red[33];
@@ -292,6 +294,7 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
     if (threadIdx.x == 0) {
         sum->n_split = 0;  // the two-stage draw's split list is rebuilt after the scan
         sum->n_runs = 0;
+        sum->n_extra = 0;  // and the fill's list of further ticket runs
     }
     if (kept_by_ess(sum, ess_thr)) {  // N_eff test: keep the particles and the layout
         if (threadIdx.x == 0) {
@@ -358,6 +361,16 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
     }
     if (threadIdx.x == 0 && rpa != 2 && sum->ess < (double)N / BIN_CONCENTRATE)
         sum->bin_next = 0;  // a concentrating proportional draw: the next step is direct
+    if (prefix_only) {  // tile_tickets_kernel takes it from here, one thread per tile and group
+        if (threadIdx.x == 0) {
+            sum->n_items = 0;
+            if (!rpa) {
+                sum->links = 0;
+                sum->moved = 0;
+            }
+        }
+        return;
+    }
     for (int t = threadIdx.x; t <= T; t += blockDim.x) {
         const int64_t v = (t == T) ? N : tickets_below_grid(in_smem ? sT[t] : Ct[t], tg);
         Tt[t] = v;
@@ -416,6 +429,40 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
             sum->links = 0;
             sum->moved = 0;
         }
+    }
+}
+
+// The tickets below every tile start and, for RPA and ARNA, every group
+// start: one thread each, after tile_scan_kernel's prefix (the same counts
+// tile_scan_kernel forms one block wide).  A tile with more than
+// ITEM_TICKETS tickets lists its further runs (t, k), k >= 1, for the fill's
+// extra blocks; the order of the list does not matter.
+__global__ void __launch_bounds__(256) tile_tickets_kernel(
+    int64_t N, int32_t T, const uint64_t *__restrict__ Ct, int64_t *__restrict__ Tt, DevSummary *__restrict__ sum,
+    Divisor ndiv, const int64_t *__restrict__ goff, int32_t G, int rpa, const uint64_t *__restrict__ Cbl,
+    int64_t *__restrict__ Tg, int2 *__restrict__ extra)
+{
+    if (sum->degenerate)
+        return;  // kept by the N_eff test, or no usable weight
+    const TicketGrid tg = ticket_grid(sum->Q, sum->u, sum->qN, sum->qR, ndiv);
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= T) {
+        const int64_t a = (i == T) ? N : tickets_below_grid(Ct[i], tg);
+        Tt[i] = a;
+        if (i < T) {
+            const int64_t b = (i + 1 == T) ? N : tickets_below_grid(Ct[i + 1], tg);
+            const int64_t runs = (b - a + ITEM_TICKETS - 1) / ITEM_TICKETS;
+            if (runs > 1) {
+                const int32_t pos = atomicAdd(&sum->n_extra, (int32_t)(runs - 1));
+                for (int64_t k = 1; k < runs; ++k)
+                    extra[pos + k - 1] = make_int2(i, (int32_t)k);
+            }
+        }
+    }
+    if (rpa && i <= G) {
+        const int64_t pos = goff[i];
+        const uint64_t c = (pos >= N) ? sum->Q : Ct[pos / TILE] + Cbl[i];
+        Tg[i] = (pos >= N) ? N : tickets_below_grid(c, tg);
     }
 }
 
@@ -512,44 +559,21 @@ struct KeptRoute {
     Balanced bl;            // the balanced layout GS and SGS leave
 };
 
+// The parents of tickets [i_lo, i_hi) of tile t: the tile's cumulative
+// weights are built once in shared memory, the parents of the tickets are
+// staged there and written out coalesced: to out[j] (systematic, LGS), or
+// split into kept and sent tickets (GS, SGS: kr.anc set).
 template <bool ROUTE>
-__device__ __forceinline__ void fill_item(const float *__restrict__ lw, int64_t N, int32_t T, Divisor ndiv,
-                                          const DevSummary *__restrict__ sum, const uint64_t *__restrict__ Ct,
-                                          const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
-                                          const int32_t *__restrict__ item_tile, int32_t *__restrict__ out,
-                                          const KeptRoute &kr)
+__device__ __forceinline__ void fill_tile_tickets(const float *__restrict__ lw, int64_t N, Divisor ndiv,
+                                                  const DevSummary *__restrict__ sum, uint64_t ct, int32_t t,
+                                                  int64_t i_lo, int64_t i_hi, int32_t *__restrict__ out,
+                                                  const KeptRoute &kr)
 {
     extern __shared__ uint64_t fill_smem[];
     uint64_t *C = fill_smem;
     uint16_t *stage = reinterpret_cast<uint16_t *>(fill_smem + TILE_SMEM_U64);
     __shared__ uint64_t red[33];
-    __shared__ int32_t st;
     __shared__ KeptTable kt;
-    const int32_t b = blockIdx.x;
-    // item_tile has an entry for every block of the launch: read it together
-    // with the item count
-    const int32_t t_pre = item_tile ? item_tile[b] : 0;
-    if (b >= sum->n_items)
-        return;
-    if (item_tile == nullptr && threadIdx.x == 0) {
-        int32_t a = 0, e = T;  // last t with item_off[t] <= b
-        while (a < e) {
-            const int32_t mid = (a + e + 1) >> 1;
-            if (item_off[mid] <= b)
-                a = mid;
-            else
-                e = mid - 1;
-        }
-        st = a;
-    }
-    if (item_tile == nullptr)
-        __syncthreads();
-    const int32_t t = item_tile ? t_pre : st;
-    // the tile's ticket range and prefix, and the draw, loaded before the
-    // tile pass so that their latency overlaps it
-    const int64_t tt0 = Tt[t], tt1 = Tt[t + 1];
-    const int32_t io = item_off[t];
-    const uint64_t ct = Ct[t];
     const uint64_t sQ = sum->Q, su = sum->u, sqN = sum->qN;
     const uint32_t sqR = sum->qR;
     if (ROUTE && threadIdx.x >= blockDim.x - 32) {
@@ -583,8 +607,6 @@ __device__ __forceinline__ void fill_item(const float *__restrict__ lw, int64_t 
     uint64_t q[TILE_ITEMS];
     tile_weights(lw, lo, n, sum->M, scale_bits(N), C, q);  // its barriers also publish the table
     tile_scan(q, C, red);
-    const int64_t i_lo = tt0 + (int64_t)(b - io) * ITEM_TICKETS;
-    const int64_t i_hi = (tt1 < i_lo + ITEM_TICKETS) ? tt1 : i_lo + ITEM_TICKETS;
     const TicketGrid tg = ticket_grid(sQ, su, sqN, sqR, ndiv);
     if (ROUTE)
         ticket_parents_routed(C, n, ct, tg, i_lo, i_hi, stage, kt, kr.anc, out, 0, (int32_t)lo, N, kr.G, kr.bl,
@@ -593,21 +615,72 @@ __device__ __forceinline__ void fill_item(const float *__restrict__ lw, int64_t 
         ticket_parents_contig(C, n, ct, tg, i_lo, i_hi, stage, out, (int32_t)lo, N, &sum->flags);
 }
 
+// The fill of the one-block tile scan (the allocation-free entry point): work
+// item b covers tickets [i_lo, i_hi) of one tile (at most ITEM_TICKETS), the
+// tile found from the item map, or by bisection over item_off without it.
+// Dynamic shared memory: FILL_SMEM_BYTES.
 __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(
     const float *__restrict__ lw, int64_t N, int32_t T, Divisor ndiv, const DevSummary *__restrict__ sum,
     const uint64_t *__restrict__ Ct, const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
     const int32_t *__restrict__ item_tile, int32_t *__restrict__ out)
 {
+    __shared__ int32_t st;
+    const int32_t b = blockIdx.x;
+    // item_tile has an entry for every block of the launch: read it together
+    // with the item count
+    const int32_t t_pre = item_tile ? item_tile[b] : 0;
+    if (b >= sum->n_items)
+        return;
+    if (item_tile == nullptr && threadIdx.x == 0) {
+        int32_t a = 0, e = T;  // last t with item_off[t] <= b
+        while (a < e) {
+            const int32_t mid = (a + e + 1) >> 1;
+            if (item_off[mid] <= b)
+                a = mid;
+            else
+                e = mid - 1;
+        }
+        st = a;
+    }
+    if (item_tile == nullptr)
+        __syncthreads();
+    const int32_t t = item_tile ? t_pre : st;
+    const int64_t tt0 = Tt[t], tt1 = Tt[t + 1];
+    const int64_t i_lo = tt0 + (int64_t)(b - item_off[t]) * ITEM_TICKETS;
+    const int64_t i_hi = (tt1 < i_lo + ITEM_TICKETS) ? tt1 : i_lo + ITEM_TICKETS;
     const KeptRoute none{nullptr, nullptr, nullptr, 0, Balanced{0, 0}};
-    fill_item<false>(lw, N, T, ndiv, sum, Ct, Tt, item_off, item_tile, out, none);
+    fill_tile_tickets<false>(lw, N, ndiv, sum, Ct[t], t, i_lo, i_hi, out, none);
 }
 
-__global__ void __launch_bounds__(TILE_THREADS) fill_route_kernel(
+// The fill after tile_tickets_kernel: block t < T takes tile t's first
+// ITEM_TICKETS tickets, block T + e the e-th entry (t, k) of the list of
+// further runs.  A tile without tickets returns at once.
+template <bool ROUTE>
+__global__ void __launch_bounds__(TILE_THREADS) fill_tiles_kernel(
     const float *__restrict__ lw, int64_t N, int32_t T, Divisor ndiv, const DevSummary *__restrict__ sum,
-    const uint64_t *__restrict__ Ct, const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
-    const int32_t *__restrict__ item_tile, int32_t *__restrict__ anc_sys, KeptRoute kr)
+    const uint64_t *__restrict__ Ct, const int64_t *__restrict__ Tt, const int2 *__restrict__ extra,
+    int32_t *__restrict__ out, KeptRoute kr)
 {
-    fill_item<true>(lw, N, T, ndiv, sum, Ct, Tt, item_off, item_tile, anc_sys, kr);
+    const int32_t b = blockIdx.x;
+    if (sum->degenerate)
+        return;  // kept by the N_eff test, or no usable weight
+    int32_t t, k;
+    if (b < T) {
+        t = b;
+        k = 0;
+    } else {
+        if (b - T >= sum->n_extra)
+            return;
+        const int2 e = extra[b - T];
+        t = e.x;
+        k = e.y;
+    }
+    const int64_t tt0 = Tt[t], tt1 = Tt[t + 1];
+    const int64_t i_lo = tt0 + (int64_t)k * ITEM_TICKETS;
+    const int64_t i_hi = (tt1 < i_lo + ITEM_TICKETS) ? tt1 : i_lo + ITEM_TICKETS;
+    if (i_lo >= i_hi)
+        return;  // a tile without tickets
+    fill_tile_tickets<ROUTE>(lw, N, ndiv, sum, Ct[t], t, i_lo, i_hi, out, kr);
 }
 
 // ------------------------------------------------ two-stage RPA, stage 2
@@ -1824,7 +1897,10 @@ cudaError_t resample_kernel_attributes()
     cudaError_t e = cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)FILL_SMEM_BYTES);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fill_route_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(fill_tiles_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FILL_SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fill_tiles_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)FILL_SMEM_BYTES);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(rna_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILL_SMEM_BYTES);
@@ -1841,6 +1917,23 @@ cudaError_t resample_kernel_attributes()
         e = cudaFuncSetAttribute(tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(uint64_t) * (SCAN_SMEM_TILES + 1)));
     return e;
+}
+
+// The tile prefix and the draw (one block), then the tickets below every
+// tile and group start and the fill's list of further runs (one thread each).
+// rpa: 0 systematic, 1 RPA, 2 ARNA.
+static void launch_tile_tickets(ppf_ctx *c, double ess_thr, int rpa)
+{
+    const int T = c->T;
+    const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
+    const Divisor nd = make_divisor((uint32_t)c->N);
+    tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
+        c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, nullptr, c->sum, ess_thr, c->m.seed, c->m.filter_id,
+        (uint32_t)c->last_frame, c->goff, c->G, rpa, c->sc.Cbl, c->sc.Tg, st_tiles, nd, 1);
+    const int n = (rpa && c->G > T ? c->G : T) + 1;
+    tile_tickets_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(c->N, T, c->sc.Ct, c->sc.Tt, c->sum, nd, c->goff,
+                                                                c->G, rpa, c->sc.Cbl, c->sc.Tg,
+                                                                reinterpret_cast<int2 *>(c->sc.extra));
 }
 
 // The RPA schedule on the context's side stream, after the tile scan (an
@@ -1882,17 +1975,13 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     const float *lw = c->state[c->cur] + 5 * c->N;
     const int T = c->T;
     prof_mark(c, PH_RESAMPLE, 0);
-    c->launches += rpa ? 5 : 3;
+    c->launches += rpa ? 6 : 4;
     if (rpa)
         tile_group_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff,
                                                                     c->G, c->sc.Cbl, c->sc.tile_g);
     else
         tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt);
-    const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
-    tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
-        c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, c->sc.item_tile, c->sum, ess_thr, c->m.seed,
-        c->m.filter_id, (uint32_t)c->last_frame, c->goff, c->G, rpa ? 1 : 0, c->sc.Cbl, c->sc.Tg, st_tiles,
-        make_divisor((uint32_t)c->N));
+    launch_tile_tickets(c, ess_thr, rpa ? 1 : 0);
     int32_t *out = rpa ? c->anc_sys : c->anc;
     const bool two_stage = (scheme >= PPF_RPA2_GS && scheme <= PPF_RPA2_LGS);
     if (rpa) {
@@ -1917,16 +2006,17 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
             kept_direct ? c->anc : nullptr, balanced_layout(c->N, c->G), scale_bits(c->N));
         c->launches += 2;
     } else {
-        const int max_items = T + (int)((c->N + ITEM_TICKETS - 1) / ITEM_TICKETS);
+        // block t < T: tile t's first run of tickets; the rest: the listed further runs
+        const int max_items = T + (int)(c->N / ITEM_TICKETS) + 1;
+        const int2 *extra = reinterpret_cast<const int2 *>(c->sc.extra);
         if (kept_direct) {
             const KeptRoute kr{c->anc, c->sc.Tg, c->sc.tile_g, c->G, balanced_layout(c->N, c->G)};
-            fill_route_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
-                lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, c->sc.item_off,
-                c->sc.item_tile, out, kr);
+            fill_tiles_kernel<true><<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
+                lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, extra, out, kr);
         } else {
-            fill_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
-                lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, c->sc.item_off,
-                c->sc.item_tile, out);
+            const KeptRoute none{nullptr, nullptr, nullptr, 0, Balanced{0, 0}};
+            fill_tiles_kernel<false><<<max_items, TILE_THREADS, FILL_SMEM_BYTES, c->stream>>>(
+                lw, c->N, T, make_divisor((uint32_t)c->N), c->sum, c->sc.Ct, c->sc.Tt, extra, out, none);
         }
     }
     cudaError_t e = cudaGetLastError();
@@ -1968,10 +2058,8 @@ cudaError_t launch_resample_arna(ppf_ctx *c, float alpha, double ess_thr)
     prof_mark(c, PH_RESAMPLE, 0);
     tile_group_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff, c->G,
                                                                 c->sc.Cbl, c->sc.tile_g);
-    const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
-    tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
-        c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, nullptr, c->sum, ess_thr, c->m.seed, c->m.filter_id,
-        (uint32_t)c->last_frame, c->goff, c->G, 2, c->sc.Cbl, c->sc.Tg, st_tiles, make_divisor((uint32_t)c->N));
+    launch_tile_tickets(c, ess_thr, 2);
+    c->launches += 1;
     arna_prep_kernel<<<1, 1024, sort_smem_bytes(c->G), c->stream>>>(
         c->goff, c->G, alpha, c->sum, ess_thr, c->sc.Tg, c->ring, c->succ, c->m.seed, c->m.filter_id,
         (uint32_t)c->last_frame);
