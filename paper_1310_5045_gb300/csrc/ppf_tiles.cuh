@@ -216,10 +216,11 @@ __device__ __forceinline__ void ticket_parents(const uint64_t *C, int n, uint64_
     const float frem0 = (float)rem0, fqR = (float)qR, rnt = 1.0f / (float)nt;
     // thr_{j_lo + b} - c0 and rem_{j_lo + b}: with v = rem0 + b qR the step
     // past lt0 is b qN + floor(v / nt); the quotient is at most b + 1 <= 2^14,
-    // so its float estimate is off by at most one
+    // so its float estimate is off by at most one (and converts as a 32-bit
+    // integer: a 64-bit conversion runs on the FP64 pipe)
     auto lt_at = [&](int b, uint32_t *rem) -> uint64_t {
         const int64_t v = (int64_t)rem0 + (int64_t)b * qR;
-        int64_t q = (int64_t)(fmaf((float)b, fqR, frem0) * rnt);
+        int64_t q = (int32_t)(fmaf((float)b, fqR, frem0) * rnt);
         int64_t r = v - q * (int64_t)nt;
         while (r < 0) {
             --q;
