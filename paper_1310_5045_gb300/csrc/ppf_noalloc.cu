@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int64_t N, int32_t T, c
                                  int32_t *__restrict__ item_tile, DevSummary *sum, double ess_thr, uint64_t seed,
                                  uint32_t fid, uint32_t frame, const int64_t *__restrict__ goff, int32_t G, int rpa,
                                  const uint64_t *__restrict__ Cbl, int64_t *__restrict__ Tg, int32_t smem_tiles,
-                                 Divisor ndiv, int prefix_only);
+                                 Divisor ndiv, int prefix_only, int2 *__restrict__ extra);
 __global__ void __launch_bounds__(TILE_THREADS) fill_kernel(const float *__restrict__ lw, int64_t N, int32_t T, Divisor ndiv,
                             const DevSummary *__restrict__ sum, const uint64_t *__restrict__ Ct,
                             const int64_t *__restrict__ Tt, const int32_t *__restrict__ item_off,
@@ -214,7 +214,8 @@ extern "C" ppf_status ppf_systematic_resample_noalloc(const float *lw_dev, int64
     // (T <= 4096 tiles: the scan's tile values, 32 KB, fit the default shared memory)
     tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (T + 1), st>>>(n, T, Qt, Ct, Tt, item_off, nullptr, sum, INFINITY,
                                                                   seed, filter_id, (uint32_t)frame, nullptr, 0, 0,
-                                                                  nullptr, nullptr, T, make_divisor((uint32_t)n), 0);
+                                                                  nullptr, nullptr, T, make_divisor((uint32_t)n), 0,
+                                                                  nullptr);
     const int max_items = T + (int)((n + ITEM_TICKETS - 1) / ITEM_TICKETS);
     fill_kernel<<<max_items, TILE_THREADS, FILL_SMEM_BYTES, st>>>(lw_dev, n, T, make_divisor((uint32_t)n), sum, Ct,
                                                                   Tt, item_off, nullptr, anc_dev);

@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
     int64_t N, int32_t T, const uint64_t *__restrict__ Qt, uint64_t *__restrict__ Ct, int64_t *__restrict__ Tt,
     int32_t *__restrict__ item_off, int32_t *__restrict__ item_tile, DevSummary *sum, double ess_thr, uint64_t seed,
     uint32_t fid, uint32_t frame, const int64_t *__restrict__ goff, int32_t G, int rpa,
-    const uint64_t *__restrict__ Cbl, int64_t *__restrict__ Tg, int32_t smem_tiles, Divisor ndiv, int prefix_only)
+    const uint64_t *__restrict__ Cbl, int64_t *__restrict__ Tg, int32_t smem_tiles, Divisor ndiv, int prefix_only,
+    int2 *__restrict__ extra)
 {
     extern __shared__ uint64_t sT[];  // (smem_tiles + 1) tile values
     __shared__ uint64_t red[33];
@@ -378,6 +379,17 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(
             sT[t] = (uint64_t)v;  // each thread rewrites only the entries it read
     }
     __syncthreads();
+    if (extra) {  // the tile-major fill's further runs of ticket-heavy tiles, as tile_tickets_kernel lists them
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            const int64_t a = in_smem ? (int64_t)sT[t] : Tt[t], b = in_smem ? (int64_t)sT[t + 1] : Tt[t + 1];
+            const int64_t runs = (b - a + ITEM_TICKETS - 1) / ITEM_TICKETS;
+            if (runs > 1) {
+                const int32_t pos = atomicAdd(&sum->n_extra, (int32_t)(runs - 1));
+                for (int64_t k = 1; k < runs; ++k)
+                    extra[pos + k - 1] = make_int2(t, (int32_t)k);
+            }
+        }
+    }
     // fill work items: ceil(tickets / ITEM_TICKETS) per tile
     uint64_t items_total = 0;
     if (in_smem) {
@@ -1927,13 +1939,19 @@ static void launch_tile_tickets(ppf_ctx *c, double ess_thr, int rpa)
     const int T = c->T;
     const int32_t st_tiles = T <= SCAN_SMEM_TILES ? T : 0;
     const Divisor nd = make_divisor((uint32_t)c->N);
+    int2 *extra = reinterpret_cast<int2 *>(c->sc.extra);
+    // up to a tile or a group per thread, the block counts the tickets itself
+    // (one launch less); beyond, one thread per tile and group does
+    const bool one_block = T <= 1024 && (!rpa || c->G <= 1024);
     tile_scan_kernel<<<1, 1024, sizeof(uint64_t) * (st_tiles + 1), c->stream>>>(
         c->N, T, c->sc.Qt, c->sc.Ct, c->sc.Tt, c->sc.item_off, nullptr, c->sum, ess_thr, c->m.seed, c->m.filter_id,
-        (uint32_t)c->last_frame, c->goff, c->G, rpa, c->sc.Cbl, c->sc.Tg, st_tiles, nd, 1);
+        (uint32_t)c->last_frame, c->goff, c->G, rpa, c->sc.Cbl, c->sc.Tg, st_tiles, nd, one_block ? 0 : 1, extra);
+    if (one_block)
+        return;
     const int n = (rpa && c->G > T ? c->G : T) + 1;
     tile_tickets_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(c->N, T, c->sc.Ct, c->sc.Tt, c->sum, nd, c->goff,
-                                                                c->G, rpa, c->sc.Cbl, c->sc.Tg,
-                                                                reinterpret_cast<int2 *>(c->sc.extra));
+                                                                c->G, rpa, c->sc.Cbl, c->sc.Tg, extra);
+    c->launches += 1;
 }
 
 // The RPA schedule on the context's side stream, after the tile scan (an
@@ -1975,7 +1993,7 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     const float *lw = c->state[c->cur] + 5 * c->N;
     const int T = c->T;
     prof_mark(c, PH_RESAMPLE, 0);
-    c->launches += rpa ? 6 : 4;
+    c->launches += rpa ? 5 : 3;
     if (rpa)
         tile_group_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff,
                                                                     c->G, c->sc.Cbl, c->sc.tile_g);
@@ -2059,7 +2077,6 @@ cudaError_t launch_resample_arna(ppf_ctx *c, float alpha, double ess_thr)
     tile_group_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff, c->G,
                                                                 c->sc.Cbl, c->sc.tile_g);
     launch_tile_tickets(c, ess_thr, 2);
-    c->launches += 1;
     arna_prep_kernel<<<1, 1024, sort_smem_bytes(c->G), c->stream>>>(
         c->goff, c->G, alpha, c->sum, ess_thr, c->sc.Tg, c->ring, c->succ, c->m.seed, c->m.filter_id,
         (uint32_t)c->last_frame);
