@@ -27,7 +27,7 @@
 namespace ppf {
 
 // kernels of ppf_resample.cu used unchanged
-__global__ void __launch_bounds__(TILE_THREADS, 8) tile_totals_kernel(const float *__restrict__ lw, int64_t N,
+__global__ void __launch_bounds__(TILE_THREADS, 5) tile_totals_kernel(const float *__restrict__ lw, int64_t N,
                                                                       const DevSummary *__restrict__ sum,
                                                                       double ess_thr, uint64_t *__restrict__ Qt);
 __global__ void __launch_bounds__(1024) tile_scan_kernel(int64_t N, int32_t T, const uint64_t *__restrict__ Qt, uint64_t *__restrict__ Ct,

@@ -56,40 +56,73 @@ __device__ __forceinline__ int64_t balanced_offset(const Balanced &b, int32_t g)
 // Tile totals Q_t: every thread loads its four float4 (coalesced, all in
 // flight together), then quantises them two at a time; one block sum.  No
 // shared buffer, so more blocks fit an SM.
-__global__ void __launch_bounds__(TILE_THREADS, 8) tile_totals_kernel(const float *__restrict__ lw, int64_t N,
+__global__ void __launch_bounds__(TILE_THREADS, 5) tile_totals_kernel(const float *__restrict__ lw, int64_t N,
                                                                       const DevSummary *__restrict__ sum,
                                                                       double ess_thr, uint64_t *__restrict__ Qt)
 {
+    // Blocks take tiles blockIdx.x, + gridDim.x, ... (one each when the grid
+    // has a block per tile).  A full, aligned tile's loads go out one tile
+    // ahead, so that they are in flight while the block quantises the tile
+    // before and waits at its reduction.
     if (kept_by_ess(sum, ess_thr))
         return;
-    __shared__ uint64_t red[33];
-    const int64_t lo = (int64_t)blockIdx.x * TILE;
-    const int n = (int)(N - lo < TILE ? N - lo : TILE);
+    constexpr int V = TILE / 4 / TILE_THREADS;
+    __shared__ uint64_t wsum[TILE_THREADS / 32];
+    const int64_t T = (N + TILE - 1) / TILE;
     const float M = sum->M;
     const int s = scale_bits(N);
-    uint64_t acc = 0;
-    if (n == TILE && ((reinterpret_cast<uintptr_t>(lw + lo) & 15) == 0) && blockDim.x == TILE_THREADS) {
-        constexpr int V = TILE / 4 / TILE_THREADS;
-        const float4 *v4 = reinterpret_cast<const float4 *>(lw + lo) + threadIdx.x;
-        float4 v[V];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto full_tile = [&](int64_t t) {
+        const int64_t lo = t * TILE;
+        return N - lo >= TILE && ((reinterpret_cast<uintptr_t>(lw + lo) & 15) == 0);
+    };
+    auto load = [&](int64_t t, float4 (&v)[V]) {
+        const float4 *v4 = reinterpret_cast<const float4 *>(lw + t * TILE) + threadIdx.x;
 #pragma unroll
         for (int k = 0; k < V; ++k)
             v[k] = __ldg(v4 + k * TILE_THREADS);
+    };
+    int64_t t = blockIdx.x;
+    float4 v[V];
+    if (t < T && full_tile(t))
+        load(t, v);
+    for (; t < T; t += gridDim.x) {
+        const int64_t tn = t + gridDim.x;
+        float4 vn[V];
+        if (tn < T && full_tile(tn))
+            load(tn, vn);
+        uint64_t acc = 0;
+        if (full_tile(t)) {
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
-            uint64_t a, b, c, d;
-            quantise2(v[k].x, v[k].y, M, s, a, b);
-            quantise2(v[k].z, v[k].w, M, s, c, d);
-            acc += a + b + c + d;
+            for (int k = 0; k < V; ++k) {
+                uint64_t a, b, c, d;
+                quantise2(v[k].x, v[k].y, M, s, a, b);
+                quantise2(v[k].z, v[k].w, M, s, c, d);
+                acc += a + b + c + d;
+            }
+        } else {
+            const int64_t lo = t * TILE;
+            const int n = (int)(N - lo < TILE ? N - lo : TILE);
+            for (int e = threadIdx.x; e < n; e += blockDim.x)
+                acc += quantise(__ldg(lw + lo + e), M, s);
         }
-    } else {
-        for (int e = threadIdx.x; e < n; e += blockDim.x)
-            acc += quantise(__ldg(lw + lo + e), M, s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0)
+            wsum[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t total = 0;
+            for (int w = 0; w < TILE_THREADS / 32; ++w)
+                total += wsum[w];
+            Qt[t] = total;
+        }
+        __syncthreads();  // wsum is rewritten for the next tile
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            v[k] = vn[k];
     }
-    uint64_t total;
-    block_excl_scan_u64(acc, red, &total);
-    if (threadIdx.x == 0)
-        Qt[blockIdx.x] = total;
 }
 
 // Tile totals for RPA and ARNA, and for every group start inside the tile the
@@ -1997,8 +2030,9 @@ cudaError_t launch_resample_global(ppf_ctx *c, int scheme, double ess_thr)
     if (rpa)
         tile_group_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt, c->goff,
                                                                     c->G, c->sc.Cbl, c->sc.tile_g);
-    else
-        tile_totals_kernel<<<T, TILE_THREADS, 0, c->stream>>>(lw, c->N, c->sum, ess_thr, c->sc.Qt);
+    else  // five blocks per SM (47 registers), each tile's loads one tile ahead
+        tile_totals_kernel<<<T < 5 * c->num_sms ? T : 5 * c->num_sms, TILE_THREADS, 0, c->stream>>>(
+            lw, c->N, c->sum, ess_thr, c->sc.Qt);
     launch_tile_tickets(c, ess_thr, rpa ? 1 : 0);
     int32_t *out = rpa ? c->anc_sys : c->anc;
     const bool two_stage = (scheme >= PPF_RPA2_GS && scheme <= PPF_RPA2_LGS);
