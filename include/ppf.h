@@ -359,7 +359,7 @@ ppf_status ppf_profile_read(ppf_ctx *ctx, ppf_profile_t *out);
  *                    particles of neighbouring slots lie close together (after
  *                    resampling from a concentrated posterior).
  *   PPF_PATH_BINNED  the particles are binned by image tile (T x T patch
- *                    anchors, T = 16 up to 512 x 512 frames), each tile's
+ *                    anchors, T = 32 up to 512 x 512 frames), each tile's
  *                    window (tile plus patch halo) is copied once into shared
  *                    memory by the tensor-memory accelerator, and every patch
  *                    is read from there.  Fastest when the particles are
@@ -367,8 +367,11 @@ ppf_status ppf_profile_read(ppf_ctx *ctx, ppf_profile_t *out);
  *   PPF_PATH_AUTO    (the default) each step's path is chosen on the device
  *                    from the previous step: binned when more than a quarter
  *                    of its warps held particles whose patch anchors spanned
- *                    more than 64 pixels.  The first step after ppf_create or
- *                    ppf_set_particles is binned.
+ *                    more than 64 pixels, unless a systematic or RPA
+ *                    resampling after it had N_eff below N / 64 (its
+ *                    offspring then fill every warp with the children of a
+ *                    few parents: direct).  The first step after ppf_create
+ *                    or ppf_set_particles is binned.
  * Errors: PPF_EINVAL (path out of range; PPF_PATH_BINNED for a pcSIR context
  * or a frame whose tiles would exceed 3072). */
 enum { PPF_PATH_AUTO = 0, PPF_PATH_DIRECT = 1, PPF_PATH_BINNED = 2 };
