@@ -25,8 +25,9 @@ def test_parity_under_the_debug_build():
     r = subprocess.run([sys.executable, "-c", "import paper_1310_5045_gb300 as p; p.load(); print(p.lib_path())"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0 and r.stdout.strip().endswith("libppf_debug.so"), r.stdout + r.stderr
-    sel = ("lockstep_frames or schemes_in_sequence or two_stage or arna or piecewise_constant_likelihood or odd_frame "
-           "or single_particle or outside_image or equals_single or batch_lockstep")
+    sel = ("lockstep_frames or schemes_in_sequence or two_stage or tiny_and_ragged or arna "
+           "or piecewise_constant_likelihood or odd_frame or single_particle or outside_image or equals_single "
+           "or batch_lockstep")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "-m", "gpu",
                         os.path.join("tests", "test_gpu_parity.py"), os.path.join("tests", "test_gpu_batch.py"),
                         "-k", sel], cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)

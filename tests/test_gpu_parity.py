@@ -177,6 +177,22 @@ def test_single_particle(ppf, movie):
     pf.close()
 
 
+@pytest.mark.parametrize("N,gs", [(1, 1), (2, 1), (3, 2), (5, 5), (33, 4), (4097, 4097), (4097, 1)])
+def test_tiny_and_ragged_layouts_every_scheme(ppf, movie, N, gs):
+    """Degenerate layouts for every scheme: one particle, one particle per
+    group, one group, a ragged last group, a group one past a tile, and 4097
+    groups of one particle (more group starts in a tile than the routing
+    table holds)."""
+    from gpu_common import lockstep, paired_models
+    gm, om = paired_models(ppf, seed=11)
+    seq = [orc.SYSTEMATIC, orc.RPA_GS, orc.RPA_SGS, orc.RPA_LGS, orc.RNA, orc.RPA2_GS, orc.RPA2_SGS,
+           orc.RPA2_LGS, orc.ARNA]
+    pf = ppf.ParticleFilter(gm, N, group_size=gs)
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), seq[:6], K=6)
+    lockstep(pf, gm, om, movie.frames, gpu_frames(movie), (seq[6:] + seq)[:6], K=6)
+    pf.close()
+
+
 @pytest.mark.parametrize("dtype_name", ["bfloat16", "float16"])
 def test_reduced_precision_frames(ppf, movie, dtype_name):
     """Frames stored in BF16 / FP16; the oracle sees the same stored values."""
