@@ -948,11 +948,12 @@ __global__ void __launch_bounds__(TILE_THREADS, 4) group_fill_kernel(
 // ------------------------------------------------------------ RPA schedule
 // One block.  Senders / receivers from the offspring counts o_g = T_{g+1} -
 // T_g and the balanced targets n_g; SGS and LGS sort both lists by amount,
-// descending, ties by group index (bitonic sort in shared memory).  GS/SGS
+// descending, ties by group index (a merge sort in shared memory).  GS/SGS
 // links are the pieces of [0, D) cut at every sender and receiver prefix
 // boundary (D = total surplus = total deficit); LGS pairs the i-th sender
 // with the i-th receiver.  Output: new group offsets and the routing
-// segments (ticket start, slot start, length) with their copy work items.
+// segments (ticket start, slot start, length) with their copy work items
+// (GS and SGS: the links only, from schedule_links_balanced).
 struct SchedArgs {
     int64_t N;
     int32_t G;
@@ -1832,7 +1833,7 @@ __global__ void __launch_bounds__(1024) rna_prep_kernel(const int64_t *__restric
 // mig = floor(alpha (G - |I|) min_g n_g / G) (FP64, in that order), and the
 // ring -- redrawn when the step's log-evidence is negative (the object
 // counts as lost): the groups in increasing order of the first Philox word of
-// (seed; g, frame, filter, RING), ties by index (a bitonic sort of
+// (seed; g, frame, filter, RING), ties by index (the merge sort of
 // word << 32 | g).  Then every group's successor on the ring.
 // Dynamic shared memory: sort_smem_bytes(G) (G <= MAX_SCHED_GROUPS).
 __global__ void __launch_bounds__(1024) arna_prep_kernel(const int64_t *__restrict__ goff, int32_t G, float alpha,
