@@ -591,11 +591,11 @@ __device__ __forceinline__ void ticket_parents_routed(const uint64_t *C, int n, 
 }
 
 // ---------------------------------------------------------------- R3 fill
-// Work item b covers tickets [i_lo, i_hi) of one tile (at most ITEM_TICKETS);
-// the tile's cumulative weights are built once in shared memory, the parents
-// of the item's tickets are staged there and written out coalesced: to
-// out[j] (systematic, LGS), or split into kept and sent tickets (GS, SGS:
-// kr.anc set).  Dynamic shared memory: FILL_SMEM_BYTES.
+// A fill block covers tickets [i_lo, i_hi) of one tile (at most
+// ITEM_TICKETS); the tile's cumulative weights are built once in shared
+// memory, the parents of the tickets are staged there and written out
+// coalesced: to out[j] (systematic, LGS), or split into kept and sent
+// tickets (GS, SGS: kr.anc set).  Dynamic shared memory: FILL_SMEM_BYTES.
 struct KeptRoute {
     int32_t *anc;           // final ancestors; nullptr: every ticket to out[j]
     const int64_t *Tg;      // [G+1] tickets below each group start
