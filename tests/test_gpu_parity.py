@@ -573,6 +573,17 @@ def test_automatic_path_choice(ppf):
         if scheme == ppf.SYSTEMATIC:
             assert not any(seen[1:]), seen
         pf.close()
+    # a fixed path ignores both the tally and the concentrating draw
+    for path, want in [(ppf.PATH_BINNED, True), (ppf.PATH_DIRECT, False)]:
+        pf = ppf.ParticleFilter(gm, 200_000, group_size=4096)
+        pf.set_likelihood_path(path)
+        seen = []
+        for k in range(1, 4):
+            pf.step(fr[k - 1], k)
+            seen.append(pf.last_step_binned())
+            pf.resample(ppf.SYSTEMATIC)
+        assert seen == [want] * 3, (path, seen)
+        pf.close()
     pf = ppf.ParticleFilter(gm, 200_000, group_size=4096)
     with pytest.raises(ppf.PPFError):
         pf.set_likelihood_path(7)
