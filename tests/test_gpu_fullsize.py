@@ -5,7 +5,10 @@ oracle computes one by one; normalisation, estimate and log-evidence by the
 oracle's FP64 summary over all particles (same log-weight inputs, exact bound
 as in gpu_common); the ancestors and group offsets bit-exactly for systematic,
 RPA-LGS, RPA-SGS, two-stage RPA-LGS, RNA, two-stage RPA-GS and ARNA
-resampling (the oracle resamples all 38 M weights)."""
+resampling (the oracle resamples all 38 M weights).  Above 16384 tiles
+(N > 67,108,864) the one-block tile scan walks the tile sums in rounds
+instead of shared memory; a filter of 67,112,961 particles checks that path
+the same way."""
 import math
 
 import numpy as np
@@ -40,6 +43,7 @@ def setup():
 
 def one_frame(ppf, pf, gm, om, mv, frames, k, scheme, alpha=0.1, n_sample=20000):
     import torch
+    N_FULL = pf.n
     rng = np.random.default_rng(k)
     st0, anc0, lwp0 = pf.get_particles(state=True, anc=True, lw_prev=True)
     goff0 = pf.groups()
@@ -114,3 +118,35 @@ def test_full_size_frames(setup):
     assert math.isfinite(est.log_evidence)
     est = one_frame(ppf, pf, gm, om, mv, frames, 7, orc.ARNA, alpha=0.5)
     assert math.isfinite(est.log_evidence)
+
+
+# 16384 tiles of 4096 and a ragged tile of 4097 more: the tile scan walks the
+# 16386 tile sums in rounds (more than its shared memory holds)
+N_ROUNDS = 16384 * 4096 + 4097
+
+
+def test_tile_scan_in_rounds_above_16384_tiles():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    free, _ = torch.cuda.mem_get_info()
+    if free < 16 * 2**30:
+        pytest.skip("needs ~16 GB of free device memory")
+    import paper_1310_5045_gb300 as ppf
+    from gpu_common import paired_models
+    mv, p = synth.preset("spot512_k50", seed=1, K=3)
+    gm, om = paired_models(ppf, width=512, height=512, patch_radius=5, psf_sigma=float(p["sigma"]),
+                           amplitude=float(p["amplitude"]), seed=1)
+    frames = torch.from_numpy(mv.frames).cuda()
+    # groups of 8192: 8193 groups, within the RPA schedule's 16384
+    pf = ppf.ParticleFilter(gm, N_ROUNDS, group_size=8192)
+    try:
+        # frame 1 from the prior (the spread cloud takes the binned path),
+        # then a routed RPA draw and an RNA draw over the concentrated cloud
+        one_frame(ppf, pf, gm, om, mv, frames, 1, orc.SYSTEMATIC)
+        assert pf.last_step_binned()
+        one_frame(ppf, pf, gm, om, mv, frames, 2, orc.RPA_SGS)
+        est = one_frame(ppf, pf, gm, om, mv, frames, 3, orc.RNA, alpha=0.1)
+        assert math.isfinite(est.log_evidence)
+    finally:
+        pf.close()
