@@ -39,6 +39,21 @@ def test_quantiser_properties(orc):
     assert orc.quantise([-200.0], 0.0, s)[0] == 0
 
 
+def test_balanced_offsets_reading_r14(orc):
+    """R14's targets n_g = floor(N/G) + [g < N mod G]: hand cases, then sizes
+    that differ by at most one with the larger groups first, for every G <= N."""
+    assert list(orc.balanced_offsets(10, 4)) == [0, 3, 6, 8, 10]
+    assert list(orc.balanced_offsets(7, 7)) == list(range(8))
+    assert list(orc.balanced_offsets(9, 1)) == [0, 9]
+    for N in range(1, 60):
+        for G in range(1, N + 1):
+            off = orc.balanced_offsets(N, G)
+            sz = np.diff(off)
+            assert off[0] == 0 and off[-1] == N
+            assert sz.max() - sz.min() <= 1 and sz.min() == N // G
+            assert np.all(np.diff(sz) <= 0)  # the N mod G larger groups come first
+
+
 def test_tickets_below_brute_force(orc):
     rng = np.random.default_rng(2)
     for _ in range(300):
